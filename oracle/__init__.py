@@ -1,0 +1,262 @@
+"""CPU oracle of the parallel multicanonical method (arXiv:1312.2213).
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` may import this package.  It shares no code
+with the CUDA library; the C source (``muca_oracle.c``) is a plain, slow,
+one-walker-at-a-time restatement of the method, and ``exact.py`` holds exact
+reference results (transfer matrices, Kaufman's closed form) used to pin it.
+"""
+from __future__ import annotations
+
+import ctypes
+import functools
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "muca_oracle.c")
+_LIB = os.path.join(_HERE, "libmuca_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+ISING, POTTS, MUMA, POLYMER = 0, 1, 2, 3
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with -O2 -ffp-contract=off (no FMA contraction, no fast-math)."""
+    srcs = [_SRC, os.path.join(_HERE, "polymer_oracle.c")]
+    srcs = [s for s in srcs if os.path.exists(s)]
+    newest = max(os.path.getmtime(s) for s in srcs + [os.path.join(_HERE, "muca_oracle.h")])
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < newest:
+        tmp = _LIB + ".tmp%d" % os.getpid()
+        cmd = ["gcc", "-std=c11", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
+               "-pthread", "-D_DEFAULT_SOURCE", "-o", tmp] + srcs + ["-lm"]
+        subprocess.check_call(cmd)
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            L = ctypes.CDLL(_LIB)
+            u32p = ctypes.POINTER(ctypes.c_uint32)
+            L.orc_philox4x32_10.argtypes = [u32p, u32p, u32p]
+            L.orc_det_exp.argtypes = [ctypes.c_double]
+            L.orc_det_exp.restype = ctypes.c_double
+            L.orc_det_log.argtypes = [ctypes.c_double]
+            L.orc_det_log.restype = ctypes.c_double
+            L.orc_create.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                     ctypes.c_uint64, ctypes.c_double, ctypes.c_int]
+            L.orc_create.restype = ctypes.c_void_p
+            for name in ("orc_free", "orc_init", "orc_update"):
+                getattr(L, name).argtypes = [ctypes.c_void_p]
+            for name in ("orc_num_bins", "orc_num_cols", "orc_num_sites"):
+                getattr(L, name).argtypes = [ctypes.c_void_p]
+                getattr(L, name).restype = ctypes.c_int
+            L.orc_iterate.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int]
+            L.orc_iterate_range.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_int,
+                                            ctypes.c_int]
+            L.orc_advance.argtypes = [ctypes.c_void_p, ctypes.c_int64]
+            L.orc_is_flat.argtypes = [ctypes.c_void_p, ctypes.c_double, ctypes.c_void_p]
+            L.orc_is_flat.restype = ctypes.c_int
+            L.orc_reweight.argtypes = [ctypes.c_void_p, ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p]
+            for name in ("orc_reachable", "orc_get_lnW", "orc_get_lnW_sampled", "orc_get_histogram",
+                         "orc_get_thresholds", "orc_get_spins", "orc_get_bins", "orc_set_open_histogram"):
+                getattr(L, name).argtypes = [ctypes.c_void_p, ctypes.c_void_p]
+            L.orc_get_sweep_counter.argtypes = [ctypes.c_void_p]
+            L.orc_get_sweep_counter.restype = ctypes.c_int64
+            L.orc_bruteforce_ising.argtypes = [ctypes.c_int, ctypes.c_void_p]
+            L.orc_bruteforce_ising_EM.argtypes = [ctypes.c_int, ctypes.c_void_p]
+            L.orc_bruteforce_potts.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_void_p]
+            for name in ("orc_bruteforce_ising", "orc_bruteforce_ising_EM", "orc_bruteforce_potts"):
+                getattr(L, name).restype = ctypes.c_int
+            L.orc_tm_ising.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_void_p]
+            L.orc_tm_ising.restype = ctypes.c_int
+            L.orc_tm_potts.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_void_p]
+            L.orc_tm_potts.restype = ctypes.c_int
+            if hasattr(L, "orc_poly_create"):
+                _bind_polymer(L)
+            _lib = L
+    return _lib
+
+
+def _bind_polymer(L):
+    c = ctypes
+    L.orc_poly_create.argtypes = [c.c_int, c.c_int, c.c_uint64, c.c_double, c.c_double, c.c_double,
+                                  c.c_double, c.c_int]
+    L.orc_poly_create.restype = c.c_void_p
+    L.orc_poly_free.argtypes = [c.c_void_p]
+    L.orc_poly_init.argtypes = [c.c_void_p]
+    L.orc_poly_num_bins.argtypes = [c.c_void_p]
+    L.orc_poly_num_bins.restype = c.c_int
+    L.orc_poly_iterate.argtypes = [c.c_void_p, c.c_int64, c.c_int]
+    L.orc_poly_iterate_range.argtypes = [c.c_void_p, c.c_int64, c.c_int, c.c_int, c.c_int]
+    L.orc_poly_advance.argtypes = [c.c_void_p, c.c_int64]
+    L.orc_poly_update.argtypes = [c.c_void_p]
+    for name in ("orc_poly_get_lnW", "orc_poly_get_histogram", "orc_poly_get_coords",
+                 "orc_poly_get_energy", "orc_poly_get_bins", "orc_poly_get_counters"):
+        getattr(L, name).argtypes = [c.c_void_p, c.c_void_p]
+    L.orc_poly_energy.argtypes = [c.c_int, c.c_void_p, c.c_int]
+    L.orc_poly_energy.restype = c.c_double
+    L.orc_poly_pair.argtypes = [c.c_double, c.c_int, c.c_int]
+    L.orc_poly_pair.restype = c.c_double
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def philox(ctr, key) -> np.ndarray:
+    """One Philox4x32-10 block."""
+    c = np.ascontiguousarray(np.asarray(ctr, dtype=np.uint32))
+    k = np.ascontiguousarray(np.asarray(key, dtype=np.uint32))
+    out = np.zeros(4, dtype=np.uint32)
+    u32p = ctypes.POINTER(ctypes.c_uint32)
+    lib().orc_philox4x32_10(c.ctypes.data_as(u32p), k.ctypes.data_as(u32p), out.ctypes.data_as(u32p))
+    return out
+
+
+def det_exp(x: float) -> float:
+    return lib().orc_det_exp(float(x))
+
+
+def det_log(x: float) -> float:
+    return lib().orc_det_log(float(x))
+
+
+class Run:
+    """One oracle MUCA/MUMA run: p walkers sharing one ln W (Fig. 1 scheme)."""
+
+    def __init__(self, system: int, L: int, q: int, p: int, seed: int, beta: float = 0.0, record: int = 0):
+        self._lib = lib()
+        self.h = self._lib.orc_create(system, L, q, p, seed, beta, record)
+        if not self.h:
+            raise ValueError("oracle: unsupported configuration")
+        self.system, self.L, self.q, self.p, self.seed = system, L, q, p, seed
+        self.B = self._lib.orc_num_bins(self.h)
+        self.K = self._lib.orc_num_cols(self.h)
+        self.N = self._lib.orc_num_sites(self.h)
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            self._lib.orc_free(self.h)
+            self.h = None
+
+    def init(self):
+        self._lib.orc_init(self.h)
+
+    def iterate(self, sweeps: int, nthreads: int = 1):
+        self._lib.orc_iterate(self.h, sweeps, nthreads)
+
+    def iterate_range(self, sweeps: int, w0: int, w1: int, nthreads: int = 1):
+        self._lib.orc_iterate_range(self.h, sweeps, w0, w1, nthreads)
+
+    def advance(self, sweeps: int):
+        self._lib.orc_advance(self.h, sweeps)
+
+    def update(self):
+        self._lib.orc_update(self.h)
+
+    def set_open_histogram(self, H):
+        H = np.ascontiguousarray(np.asarray(H, dtype=np.uint64))
+        assert H.shape == (self.B,)
+        self._lib.orc_set_open_histogram(self.h, _ptr(H))
+
+    def is_flat(self, ratio: float = 0.5):
+        st = np.zeros(3)
+        f = self._lib.orc_is_flat(self.h, ratio, _ptr(st))
+        return bool(f), st
+
+    def reweight(self, beta: float):
+        out = np.zeros(4)
+        lnP = np.zeros(self.B)
+        self._lib.orc_reweight(self.h, beta, _ptr(out), _ptr(lnP))
+        return out, lnP
+
+    def _get(self, name, n, dtype):
+        a = np.zeros(n, dtype=dtype)
+        getattr(self._lib, name)(self.h, _ptr(a))
+        return a
+
+    def reachable(self):
+        return self._get("orc_reachable", self.B, np.uint8).astype(bool)
+
+    def lnW(self):
+        return self._get("orc_get_lnW", self.B, np.float64)
+
+    def lnW_sampled(self):
+        return self._get("orc_get_lnW_sampled", self.B, np.float64)
+
+    def histogram(self):
+        return self._get("orc_get_histogram", self.B, np.uint64)
+
+    def thresholds(self):
+        return self._get("orc_get_thresholds", self.B * self.K, np.uint32).reshape(self.B, self.K)
+
+    def spins(self):
+        return self._get("orc_get_spins", self.p * self.N, np.int8).reshape(self.p, self.L, self.L)
+
+    def bins(self):
+        return self._get("orc_get_bins", self.p, np.int32)
+
+    def sweep_counter(self) -> int:
+        return int(self._lib.orc_get_sweep_counter(self.h))
+
+
+def bruteforce_ising(L: int) -> np.ndarray:
+    N = L * L
+    out = np.zeros(N + 1, dtype=np.uint64)
+    assert lib().orc_bruteforce_ising(L, _ptr(out)) == 0
+    return out
+
+
+def bruteforce_ising_EM(L: int) -> np.ndarray:
+    N = L * L
+    out = np.zeros((N + 1) * (N + 1), dtype=np.uint64)
+    assert lib().orc_bruteforce_ising_EM(L, _ptr(out)) == 0
+    return out.reshape(N + 1, N + 1)
+
+
+def bruteforce_potts(L: int, q: int) -> np.ndarray:
+    N = L * L
+    out = np.zeros(2 * N + 1, dtype=np.uint64)
+    assert lib().orc_bruteforce_potts(L, q, _ptr(out)) == 0
+    return out
+
+
+def _u128(a: np.ndarray) -> list:
+    return [int(a[2 * i]) + (int(a[2 * i + 1]) << 64) for i in range(a.size // 2)]
+
+
+@functools.lru_cache(maxsize=None)
+def tm_ising(L: int) -> list:
+    """Exact Omega(E) of the periodic L x L Ising model (Python ints), index (E+2N)/4."""
+    N = L * L
+    out = np.zeros(2 * (N + 1), dtype=np.uint64)
+    assert lib().orc_tm_ising(L, 0, _ptr(out)) == 0
+    return _u128(out)
+
+
+@functools.lru_cache(maxsize=None)
+def tm_ising_EM(L: int) -> list:
+    """Exact Omega(E, M), as a list of rows [(E+2N)/4][(M+N)/2] of Python ints."""
+    N = L * L
+    out = np.zeros(2 * (N + 1) * (N + 1), dtype=np.uint64)
+    assert lib().orc_tm_ising(L, 1, _ptr(out)) == 0
+    flat = _u128(out)
+    return [flat[i * (N + 1):(i + 1) * (N + 1)] for i in range(N + 1)]
+
+
+@functools.lru_cache(maxsize=None)
+def tm_potts(L: int, q: int) -> list:
+    """Exact Omega(E) of the periodic L x L q-state Potts model, index E+2N."""
+    N = L * L
+    out = np.zeros(2 * (2 * N + 1), dtype=np.uint64)
+    assert lib().orc_tm_potts(L, q, _ptr(out)) == 0
+    return _u128(out)

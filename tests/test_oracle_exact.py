@@ -1,0 +1,87 @@
+"""Pins for the exact tools: brute force == transfer matrix == Kaufman's closed form,
+plus the textbook invariants of Omega(E).  These tools in turn pin the MUCA oracle."""
+import mpmath
+import numpy as np
+import pytest
+
+import oracle.exact as ex
+
+
+def test_ising_bruteforce_equals_tm(orc):
+    bf = [int(x) for x in orc.bruteforce_ising(4)]
+    assert bf == orc.tm_ising(4)
+
+
+@pytest.mark.parametrize("L", [4, 6, 8])
+def test_ising_tm_equals_kaufman(orc, L):
+    om = orc.tm_ising(L)
+    N = L * L
+    Es = [4 * j - 2 * N for j in range(N + 1)]
+    for beta in (0.05, 0.3, float(mpmath.log(1 + mpmath.sqrt(2)) / 2), 0.6, 1.0):
+        a = ex.lnZ_from_omega(om, Es, beta)
+        b = ex.kaufman_lnZ(L, L, beta)
+        assert abs(a - b) < mpmath.mpf(10) ** -40 * abs(b)
+
+
+@pytest.fixture(scope="module")
+def omega8(orc):
+    return orc.tm_ising(8)
+
+
+def test_ising_L8_invariants(omega8):
+    N = 64
+    om = omega8
+    assert sum(om) == 2 ** N
+    assert om == om[::-1]                     # Omega(E) = Omega(-E) for even L
+    assert om[0] == 2 and om[1] == 0          # ground state doubly degenerate, no 2-bond state
+    assert om[2] == 2 * N and om[3] == 4 * N  # one flipped spin; two neighbouring flipped spins
+
+
+def test_ising_L8_golden_file(omega8):
+    """tests/golden/ising_L8_omega.txt was written by tests/golden/make_golden.py (oracle only)."""
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "ising_L8_omega.txt")
+    vals = [int(l.split()[1]) for l in open(path) if l.strip() and not l.startswith("#")]
+    assert vals == omega8
+
+
+@pytest.mark.parametrize("L", [4, 6, 8])
+def test_ising_reachable_rule(orc, L, omega8):
+    om = omega8 if L == 8 else orc.tm_ising(L)
+    r = orc.Run(orc.ISING, L, 2, 1, 1)
+    np.testing.assert_array_equal(r.reachable(), np.array(om) > 0)
+
+
+def test_potts_bruteforce_equals_tm(orc):
+    bf = [int(x) for x in orc.bruteforce_potts(4, 3)]
+    assert bf == orc.tm_potts(4, 3)
+
+
+@pytest.mark.parametrize("q,L", [(2, 4), (3, 4), (4, 4), (5, 4), (3, 6)])
+def test_potts_invariants_and_reachable(orc, q, L):
+    om = orc.tm_potts(L, q)
+    N = L * L
+    assert sum(om) == q ** N
+    assert om[0] == q                          # E = -2N: all spins equal
+    assert om[4] == (q * (q - 1) * N if q > 2 else 2 * N)  # one site differs from its 4 neighbours
+    r = orc.Run(orc.POTTS, L, q, 1, 1)
+    np.testing.assert_array_equal(r.reachable(), np.array(om) > 0)
+
+
+def test_potts_q2_is_ising(orc):
+    """q = 2 Potts: E_P = -2N + n_b and E_I = -2N + 2 n_b, so Omega_P(n_b) = Omega_I(n_b / 2)."""
+    L, N = 4, 16
+    p = orc.tm_potts(L, 2)
+    i = orc.tm_ising(L)
+    for nb in range(2 * N + 1):
+        assert p[nb] == (i[nb // 2] if nb % 2 == 0 else 0)
+
+
+def test_ising_EM_bruteforce_equals_tm_and_marginals(orc):
+    bf = orc.bruteforce_ising_EM(4)
+    tm = orc.tm_ising_EM(4)
+    assert [[int(x) for x in row] for row in bf] == tm
+    tm6 = orc.tm_ising_EM(6)
+    assert [sum(row) for row in tm6] == orc.tm_ising(6)
+    for row in tm6:
+        assert row == row[::-1]                # Omega(E, M) = Omega(E, -M)

@@ -1,0 +1,281 @@
+"""Pins for the oracle's MUCA / multimagnetic chains, merge, recursion, thresholds and
+reweighting (Eq. 1-3, Fig. 1 scheme), against exact results and invariants."""
+import math
+
+import mpmath
+import numpy as np
+import pytest
+
+import oracle.exact as ex
+
+NT = 8  # oracle threads
+
+
+def energy_from_spins(spins, system):
+    """From-scratch energy of each lattice, E = -sum over right and down bonds."""
+    s = spins.astype(np.int64)
+    rt = np.roll(s, -1, axis=2)
+    dn = np.roll(s, -1, axis=1)
+    if system == 1:
+        return -((s == rt).sum(axis=(1, 2)) + (s == dn).sum(axis=(1, 2)))
+    return -((s * rt).sum(axis=(1, 2)) + (s * dn).sum(axis=(1, 2)))
+
+
+def bins_from_spins(spins, system):
+    N = spins.shape[1] * spins.shape[2]
+    if system == 0:
+        return (energy_from_spins(spins, 0) + 2 * N) // 4
+    if system == 1:
+        return energy_from_spins(spins, 1) + 2 * N
+    return (spins.astype(np.int64).sum(axis=(1, 2)) + N) // 2
+
+
+@pytest.mark.parametrize("system,q", [(0, 2), (1, 3), (1, 8), (2, 2)])
+def test_bins_track_lattices(orc, system, q):
+    r = orc.Run(system, 8, q, 16, 99, beta=0.44)
+    r.init()
+    np.testing.assert_array_equal(r.bins(), bins_from_spins(r.spins(), system))
+    for _ in range(3):
+        r.iterate(50, NT)
+        r.update()
+        np.testing.assert_array_equal(r.bins(), bins_from_spins(r.spins(), system))
+    assert r.sweep_counter() == 150
+
+
+def test_init_spins_are_uniform(orc):
+    r = orc.Run(1, 32, 8, 64, 5)
+    r.init()
+    counts = np.bincount(r.spins().ravel(), minlength=8)
+    exp = counts.sum() / 8
+    assert ((counts - exp) ** 2 / exp).sum() < 30  # 7 dof
+
+
+def test_first_sweep_accepts_everything(orc):
+    """ln W = 0 gives T = always on every reachable move, so one sequential sweep
+    flips every spin once: the lattice becomes its negative (Ising)."""
+    r = orc.Run(0, 8, 2, 8, 3)
+    r.init()
+    s0 = r.spins().copy()
+    T = r.thresholds()
+    reach = r.reachable()
+    for b in range(r.B):
+        for k in range(5):
+            b2 = b + k - 2
+            ok = reach[b] and 0 <= b2 < r.B and reach[b2]
+            assert T[b, k] == (0xFFFFFFFF if ok else 0)
+    r.iterate(1, 1)
+    np.testing.assert_array_equal(r.spins(), -s0)
+
+
+@pytest.mark.parametrize("record", [0, 1])
+def test_histogram_totals(orc, record):
+    r = orc.Run(0, 8, 2, 32, 4, record=record)
+    r.init()
+    r.iterate(30, NT)
+    r.iterate(20, NT)
+    r.update()
+    per = 64 if record == 0 else 1
+    assert int(r.histogram().sum()) == 32 * 50 * per
+
+
+def test_merge_is_partition_independent(orc):
+    """Any split of the walkers into groups gives the same merged histogram (a4)."""
+    a = orc.Run(1, 8, 5, 24, 17)
+    b = orc.Run(1, 8, 5, 24, 17)
+    a.init(); b.init()
+    a.iterate(40, 1); a.update()
+    for w0, w1 in ((0, 5), (5, 6), (6, 24)):
+        b.iterate_range(40, w0, w1, 3)
+    b.advance(40); b.update()
+    np.testing.assert_array_equal(a.histogram(), b.histogram())
+    np.testing.assert_array_equal(a.lnW(), b.lnW())
+    np.testing.assert_array_equal(a.spins(), b.spins())
+
+
+def test_recursion_ideal_histogram_gives_minus_ln_omega(orc):
+    """Feeding H = Omega (sampled with W = 1) returns ln W = -ln Omega + const; a second
+    histogram proportional to Omega*W is flat and leaves ln W unchanged."""
+    om = np.array([float(x) for x in orc.tm_ising(8)])
+    r = orc.Run(0, 8, 2, 1, 1)
+    r.init()
+    reach = r.reachable()
+    r.set_open_histogram(np.array(orc.tm_ising(8), dtype=np.uint64))
+    r.update()
+    lnW = r.lnW()
+    target = -np.log(om[reach])
+    d = lnW[reach] - target
+    assert np.max(np.abs(d - d[0])) < 1e-12 * np.max(np.abs(target))
+    assert np.all(np.isneginf(lnW[~reach]))
+    H2 = np.zeros(r.B, dtype=np.uint64)
+    H2[reach] = np.round(1e12 * np.exp(np.log(om[reach]) + lnW[reach] - (np.log(om[reach]) + lnW[reach]).max()))
+    r.set_open_histogram(H2)
+    r.update()
+    assert np.max(np.abs(r.lnW()[reach] - lnW[reach])) < 1e-9
+
+
+def test_first_update_is_plain_w_over_h(orc):
+    """kappa = 1 on the first update: W^(1)(E) = W^(0)(E)/H^(0)(E) (the simple recursion)."""
+    rng = np.random.default_rng(0)
+    r = orc.Run(1, 4, 3, 1, 1)
+    r.init()
+    reach = r.reachable()
+    H = np.zeros(r.B, dtype=np.uint64)
+    H[reach] = rng.integers(1, 10**9, reach.sum())
+    r.set_open_histogram(H)
+    r.update()
+    d = r.lnW()[reach] + np.log(H[reach].astype(float))
+    assert np.ptp(d) < 1e-12 * 30
+
+
+def test_recursion_is_a_weighted_mean_of_naive_estimates(orc):
+    """After two updates each neighbour ratio lnR is the g-weighted mean of the two naive
+    estimates R^(n) + ln h0 - ln h1, with g = h0 h1/(h0+h1) (accumulated statistics)."""
+    rng = np.random.default_rng(1)
+    r = orc.Run(0, 4, 2, 1, 1)
+    r.init()
+    reach = np.nonzero(r.reachable())[0]
+    H1 = np.zeros(r.B, dtype=np.uint64); H1[reach] = rng.integers(1, 1000, reach.size)
+    H2 = np.zeros(r.B, dtype=np.uint64); H2[reach] = rng.integers(1, 1000, reach.size)
+    H2[reach[3]] = 0  # pairs touching an empty bin keep their ratio
+    r.set_open_histogram(H1); r.update(); w1 = r.lnW()[reach]
+    r.set_open_histogram(H2); r.update(); w2 = r.lnW()[reach]
+    R1, R2 = np.diff(w1), np.diff(w2)
+    for k in range(reach.size - 1):
+        a1, c1 = float(H1[reach[k]]), float(H1[reach[k + 1]])
+        a2, c2 = float(H2[reach[k]]), float(H2[reach[k + 1]])
+        est1 = math.log(a1) - math.log(c1)       # naive estimate from W^(0) = 1
+        if a2 == 0 or c2 == 0:
+            assert R2[k] == pytest.approx(R1[k], abs=1e-12)
+            continue
+        est2 = R1[k] + math.log(a2) - math.log(c2)
+        g1, g2 = a1 * c1 / (a1 + c1), a2 * c2 / (a2 + c2)
+        assert R2[k] == pytest.approx((g1 * est1 + g2 * est2) / (g1 + g2), abs=1e-11)
+
+
+def test_thresholds_match_exact_exponential(orc):
+    rng = np.random.default_rng(2)
+    r = orc.Run(1, 4, 3, 1, 1)
+    r.init()
+    reach = r.reachable()
+    H = np.zeros(r.B, dtype=np.uint64)
+    H[reach] = rng.integers(1, 10**6, reach.sum())
+    r.set_open_histogram(H)
+    r.update()
+    lnW, T = r.lnW(), r.thresholds()
+    n_exact = n = 0
+    for b in np.nonzero(reach)[0]:
+        for k in range(9):
+            b2 = b + k - 4
+            if not (0 <= b2 < r.B and reach[b2]):
+                assert T[b, k] == 0
+                continue
+            d = lnW[b2] - lnW[b]
+            if d >= 0:
+                assert T[b, k] == 0xFFFFFFFF
+                continue
+            ref = int(mpmath.floor(mpmath.ldexp(mpmath.exp(mpmath.mpf(d)), 32)))
+            assert abs(int(T[b, k]) - ref) <= 1
+            n += 1
+            n_exact += int(T[b, k]) == ref
+    assert n > 50 and n_exact >= n - 1
+
+
+def test_multimagnetic_thresholds_include_beta(orc):
+    """MUMA (Eq. 3): d = ln W(M') - ln W(M) - beta dE; with ln W = 0 only beta dE remains."""
+    beta = 0.4407
+    r = orc.Run(2, 4, 2, 1, 1, beta=beta)
+    r.init()
+    T = r.thresholds()
+    for b in range(1, r.B - 1):
+        for sidx in range(2):
+            for k in range(5):
+                dE = 4 * (k - 2)
+                t = T[b, sidx * 5 + k]
+                if dE <= 0:
+                    assert t == 0xFFFFFFFF
+                else:
+                    ref = int(mpmath.floor(mpmath.ldexp(mpmath.exp(-beta * dE), 32)))
+                    assert abs(int(t) - ref) <= 1
+
+
+def test_reweight_exact_omega(orc):
+    """Eq. (2) on an exact histogram (H = Omega, W = 1) reproduces <E>, C_V and ln Z of
+    direct summation and of Kaufman's formula."""
+    om = orc.tm_ising(8)
+    r = orc.Run(0, 8, 2, 1, 1)
+    r.init()
+    r.set_open_histogram(np.array(om, dtype=np.uint64))
+    r.update()
+    N = 64
+    Es = [4 * j - 2 * N for j in range(N + 1)]
+    for beta in (0.2, 0.4406868, 0.7):
+        out, lnP = r.reweight(beta)
+        with mpmath.workdps(50):
+            b = mpmath.mpf(beta)
+            w = [mpmath.mpf(o) * mpmath.exp(-b * E) for o, E in zip(om, Es)]
+            Z = mpmath.fsum(w)
+            e1 = mpmath.fsum(wi * E for wi, E in zip(w, Es)) / Z
+            e2 = mpmath.fsum(wi * E * E for wi, E in zip(w, Es)) / Z
+        assert out[0] == pytest.approx(float(e1), rel=1e-12, abs=1e-10)
+        assert out[1] == pytest.approx(float(e2), rel=1e-12)
+        assert out[2] == pytest.approx(float(b * b * (e2 - e1 * e1) / N), rel=1e-9)
+        assert out[3] == pytest.approx(float(ex.kaufman_lnZ(8, 8, beta)), rel=1e-12)
+        assert np.exp(lnP[np.isfinite(lnP)]).sum() == pytest.approx(1.0, rel=1e-12)
+
+
+def test_muca_converges_to_exact_ising_L8(orc):
+    """The config-1 workload (L = 8, p = 64, 10 iterations of 1e4 sweeps): flat histogram and
+    ln Omega_hat = ln H - ln W within 0.15 of Beale's exact Omega in every reachable bin."""
+    om = np.array([float(x) for x in orc.tm_ising(8)])
+    r = orc.Run(0, 8, 2, 64, 1)
+    r.init()
+    for _ in range(10):
+        r.iterate(10000, NT)
+        r.update()
+    flat, st = r.is_flat(0.5)
+    assert flat
+    reach = r.reachable()
+    lo = np.log(r.histogram()[reach].astype(float)) - r.lnW_sampled()[reach]
+    le = np.log(om[reach])
+    lo += le[0] - lo[0]   # normalise at the ground state, Omega(-2N) = 2
+    assert np.max(np.abs(lo - le)) < 0.15
+
+
+def test_muca_potts_q3_L6_converges(orc):
+    om = np.array([float(x) for x in orc.tm_potts(6, 3)])
+    r = orc.Run(1, 6, 3, 64, 2)
+    r.init()
+    for _ in range(12):
+        r.iterate(4000, NT)
+        r.update()
+    reach = r.reachable()
+    lo = np.log(r.histogram()[reach].astype(float)) - r.lnW_sampled()[reach]
+    le = np.log(om[reach])
+    lo += le[0] - lo[0]
+    assert np.max(np.abs(lo - le)) < 0.25
+
+
+def test_multimagnetic_converges_to_exact_P_of_M(orc):
+    """MUMA at beta = 0.4407, L = 6: ln W(M) -> -ln P_beta(M) + const, with
+    P_beta(M) = sum_E Omega(E, M) exp(-beta E) from the exact transfer matrix."""
+    beta, L, N = 0.4407, 6, 36
+    em = orc.tm_ising_EM(L)
+    with mpmath.workdps(40):
+        lnPM = []
+        for m in range(N + 1):
+            s = mpmath.fsum(mpmath.mpf(em[j][m]) * mpmath.exp(-beta * (4 * j - 2 * N)) for j in range(N + 1))
+            lnPM.append(float(mpmath.log(s)))
+    lnPM = np.array(lnPM)
+    r = orc.Run(2, L, 2, 64, 3, beta=beta)
+    r.init()
+    for _ in range(10):
+        r.iterate(3000, NT)
+        r.update()
+    lo = np.log(r.histogram().astype(float)) - r.lnW_sampled()
+    lo += lnPM[0] - lo[0]
+    assert np.max(np.abs(lo - lnPM)) < 0.15
+    out, _ = r.reweight(beta)
+    with mpmath.workdps(30):
+        P = np.exp(lnPM - lnPM.max()); P /= P.sum()
+    absM = np.abs(2 * np.arange(N + 1) - N)
+    assert out[0] == pytest.approx((P * absM).sum() / N, rel=0.02)
