@@ -1,0 +1,287 @@
+#!/usr/bin/env python
+"""Benchmark of the parallel multicanonical hot path on GB300.
+
+Workload (one "step" = one multicanonical iteration of the Fig. 1 loop for each system):
+  * 2D Ising L = 32, periodic, p = 8192 walkers, multicanonical in E (bins E = -2048..2048 step 4);
+  * 2D Ising L = 32, p = 8192, multimagnetic in M at beta = 0.4407 (Eq. 3);
+each with 1e4 sweeps of every walker, then the histogram merge, the accumulated-statistics
+recursion of ln W and the threshold rebuild.  Metric: move attempts per second (an attempt is one
+proposed single-spin update, accepted or not), whole job.
+
+  value      device-timed (CUDA events on the launching stream), state resident in HBM;
+  e2e        the same step through the C ABI with the state copied in from pinned host memory
+             (muca_set_state) and back out (muca_get_state) every step;
+  roofline   the sweep kernel against the integer issue peak (SMs x 4 schedulers x 32 lanes x f_SM);
+  cpu_baseline  the CPU oracle (all host cores) on a bounded sample of the same workload.
+
+`--impl reference` times the CPU oracle itself as the reference arm.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+L, P, SWEEPS, BETA_MUMA = 32, 8192, 10000, 0.4407
+N = L * L
+# Algorithmic integer instructions per attempt of the spin sweep (per walker-thread); the
+# breakdown is stated with the kernel: Philox4x32-10 amortised over the 4 words of one call
+# (10 rounds x 4 ops / 4 = 10), neighbour bits and count 8, table column and address 2,
+# threshold load 1, integer compare 2, flip/select 3, bin update 2, histogram atomic 1, loop 1.
+INSTR_PER_ATTEMPT = 30
+METRIC = "MUCA move attempts/s (Ising L=32 p=8192: MUCA in E + MUMA in M)"
+UNIT = "attempts/s"
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--sweeps", type=int, default=SWEEPS)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sweeps", type=int, default=100, help="sweeps per system in the CPU sample")
+    return ap.parse_args()
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_sample(sweeps: int, seed0: int):
+    """The oracle, as it stands, over the same workload with fewer sweeps (all host cores)."""
+    import oracle
+
+    nth = os.cpu_count() or 1
+    attempts = 0
+    t0 = time.perf_counter()
+    for system, beta, seed in ((oracle.ISING, 0.0, seed0), (oracle.MUMA, BETA_MUMA, seed0 + 1000)):
+        r = oracle.Run(system, L, 2, P, seed, beta=beta)
+        r.init()
+        r.iterate(sweeps, nth)
+        r.update()
+        attempts += P * sweeps * N
+    dt = time.perf_counter() - t0
+    return {"value": attempts / dt, "unit": UNIT, "cores": nth, "kind": "oracle",
+            "sample": "Ising L=32 p=8192 MUCA + MUMA, 1 iteration of %d sweeps each (%.3g attempts, %.1f s)"
+                      % (sweeps, attempts, dt)}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle  # noqa: F401  (the reference arm is the CPU oracle)
+
+    for _ in range(args.warmup):
+        cpu_sample(max(1, args.cpu_sweeps // 10), 7)
+    vals, tot_t = [], 0.0
+    for k in range(args.steps):
+        s = cpu_sample(args.cpu_sweeps, 7 + k)
+        vals.append(s["value"])
+    val = statistics.median(vals)
+    step_attempts = 2 * P * args.cpu_sweeps * N
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * step_attempts / val,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+            "data": "synthetic",
+            "config": {"workload": "ising2d_L32_p8192_muca+muma", "L": L, "p": P, "systems": 2,
+                       "sweeps_per_step": args.cpu_sweeps, "note": "bounded sample of the 1e4-sweep step"},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": "%d sweeps per system per step" % args.cpu_sweeps},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import paper_1312_2213_gb300 as m
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    m.load()
+    stream = torch.cuda.Stream()
+    seed = 1 + 7919 * rank
+    systems = [m.Muca(m.ISING2D, L, 2, P, seed, stream=stream),
+               m.Muca(m.ISING2D_MUMA, L, 2, P, seed + 1000, beta=BETA_MUMA, stream=stream)]
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    sweeps = args.sweeps
+    step_attempts = len(systems) * P * sweeps * N
+    launches_per_step = len(systems) * 5  # sweep, counter advance, merge, recursion, thresholds
+
+    def step(kevents=None):
+        for s in systems:
+            if kevents is not None:
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                s.iterate(sweeps)
+                b.record(stream)
+                kevents.append((a, b))
+            else:
+                s.iterate(sweeps)
+            s.merge_and_update()
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            flush.zero_()
+            step()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    kev = []
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        t0.record(stream)
+        for _ in range(args.steps):
+            flush.zero_()  # L2 flush between timed steps (written on the same stream)
+            step(kev)
+        t1.record(stream)
+    torch.cuda.synchronize()
+    ck = clocks.stop()
+    ms = t0.elapsed_time(t1)
+    ms_t = torch.tensor([ms], device="cuda")
+    if world > 1:
+        torch.distributed.all_reduce(ms_t, op=torch.distributed.ReduceOp.MAX)
+        torch.distributed.barrier()
+    ms = float(ms_t.item())
+    value = world * step_attempts * args.steps / (ms / 1e3)
+    sweep_ms = statistics.mean(a.elapsed_time(b) for a, b in kev)
+
+    # end to end through the C ABI: state in from pinned host memory, state out, every step
+    bufs = []
+    for s in systems:
+        n = m.muca_get_state(s.h, None)
+        t = torch.empty(n, dtype=torch.uint8, pin_memory=True)
+        buf = t.numpy()
+        m.muca_get_state(s.h, buf)
+        bufs.append((t, buf))
+    e2e_steps = max(1, min(args.steps, 3))
+    torch.cuda.synchronize()
+    h0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        for s, (_, buf) in zip(systems, bufs):
+            m.muca_set_state(s.h, buf)
+            s.iterate(sweeps)
+            s.merge_and_update()
+            m.muca_get_state(s.h, buf)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - h0
+    state_bytes = sum(b.nbytes for _, b in bufs)
+    e2e = {"value": world * step_attempts * e2e_steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": state_bytes,
+           "d2h_bytes_per_step": state_bytes, "steps": e2e_steps}
+    if world > 1:
+        v = torch.tensor([e2e_s], device="cuda")
+        torch.distributed.all_reduce(v, op=torch.distributed.ReduceOp.MAX)
+        e2e["value"] = world * step_attempts * e2e_steps / float(v.item())
+
+    if rank != 0:
+        torch.distributed.destroy_process_group()
+        return
+    props = torch.cuda.get_device_properties(local)
+    sms = props.multi_processor_count
+    f_mhz = ck["sm_mhz"] if ck else 2070.0
+    peak_tinst = sms * 4 * 32 * f_mhz * 1e6 / 1e12
+    achieved_tinst = P * sweeps * N * INSTR_PER_ATTEMPT / (sweep_ms / 1e3) / 1e12
+    roofline = {"bound": "alu", "achieved": achieved_tinst, "peak": peak_tinst, "unit": "Tinst/s",
+                "frac": achieved_tinst / peak_tinst, "traffic": None,
+                "kernel": "k_sweep_spin (Ising L=32 MUCA/MUMA)", "kernel_ms": sweep_ms,
+                "peak_basis": "%d SMs x 4 schedulers x 32 lanes x %.0f MHz (median sampled SM clock)" % (sms, f_mhz),
+                "instr_per_attempt": INSTR_PER_ATTEMPT}
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": "ising2d_L32_p8192_muca+muma", "L": L, "p": P, "systems": 2,
+                       "sweeps_per_step": sweeps, "beta_muma": BETA_MUMA,
+                       "l2": "flushed between steps (256 MiB write on the stream)",
+                       "parallelism": "walkers (one chain per thread)" if world == 1 else
+                       "independent replicas, one per GPU"},
+            "e2e": e2e, "gpu_launches": launches_per_step * args.steps, "roofline": roofline,
+            "clocks": ck}
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_sample(args.cpu_sweeps, 5)
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,166 @@
+/*
+ * muca.h -- C ABI of a GB300 (sm_103a) implementation of the parallel
+ * multicanonical (MUCA) method of Zierenberg, Marenz and Janke,
+ * "Scaling Properties of Parallelized Multicanonical Simulations"
+ * (arXiv:1312.2213).
+ *
+ * The method (paper, Fig. 1 and the paragraph before it): p independent
+ * Markov chains ("walkers") share one weight function W; each iteration they
+ * sweep and fill histograms, the histograms are merged, a new W is computed
+ * from the merged histogram and handed back to all walkers; this repeats until
+ * the histogram is flat.  Here all p walkers of a system live on one GPU, the
+ * merge is an integer reduction on the device and the weight recursion runs on
+ * the device, so nothing crosses the host inside the loop.
+ *
+ * Conventions for every function:
+ *   - Return value: MUCA_OK (0) or a negative MUCA_ERR_* code.  No function
+ *     aborts or exits; on error muca_last_error() returns a message (storage
+ *     owned by the library, valid until the next call on the same host thread).
+ *   - Pointers named host_* are caller-owned HOST memory of the stated length;
+ *     the call copies synchronously and returns when the data is there.
+ *   - Device work is enqueued on the context's stream (muca_set_stream) and is
+ *     asynchronous unless the call returns data to the host.
+ *   - A context is used by one host thread at a time.
+ *   - Lengths that do not match the context (nbins, p, ...) give MUCA_ERR_ARG.
+ */
+#ifndef MUCA_H
+#define MUCA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MUCA_OK 0
+#define MUCA_ERR_ARG (-1)         /* bad argument or unsupported combination */
+#define MUCA_ERR_CUDA (-2)        /* a CUDA runtime call or kernel launch failed */
+#define MUCA_ERR_OOM (-3)         /* device allocation failed / arena too small */
+#define MUCA_ERR_TIMEOUT (-4)     /* a bounded device wait gave up */
+#define MUCA_ERR_STATE (-5)       /* call not allowed in the context's current state */
+#define MUCA_ERR_RANGE (-6)       /* value outside the supported range */
+
+/* Systems (paper: Ising paragraph, Potts paragraph, multimagnetic ensemble
+ * Eq. 3, bead-spring polymer Eq. 7). */
+enum {
+    MUCA_ISING2D = 0,      /* H = -J sum_<ij> s_i s_j, L x L periodic, MUCA in E   */
+    MUCA_POTTS2D = 1,      /* H = -J sum_<ij> delta(s_i,s_j), q states, MUCA in E  */
+    MUCA_ISING2D_MUMA = 2, /* Ising at fixed beta, weight exp(-beta E) W(M), Eq. 3 */
+    MUCA_POLYMER3D = 3     /* FENE + Lennard-Jones chain, Eq. 7 (see muca_set_param) */
+};
+
+typedef struct muca_ctx muca_ctx;     /* opaque, library-owned */
+typedef struct muca_batch muca_batch; /* opaque, library-owned */
+
+/* Message of the last failed call on this host thread ("" if none). */
+const char *muca_last_error(void);
+
+/* Create a simulation of p walkers of one system sharing one ln W table
+ * (Fig. 1: "initialized in p independent realizations with the same weight
+ * function").  L_or_N is the lattice side L (spins) or the bead count N
+ * (polymer); q is the number of Potts states (ignored otherwise).
+ * Spins: L even, 4 <= L <= 64 and L % 4 == 0; Potts 2 <= q <= 16, L <= 48.
+ * The walkers' initial states are drawn from the counter-based generator
+ * keyed by `seed` (ln W = 0 everywhere, so the first iteration samples
+ * beta = 0, where a random state is already in equilibrium: the paper
+ * thermalises only at the start).  The library allocates its device memory
+ * with cudaMalloc on the current device; the context uses the legacy default
+ * stream until muca_set_stream.  *out receives the context. */
+int muca_init(muca_ctx **out, int system, int L_or_N, int q, int p, uint64_t seed);
+
+/* Same, but every device buffer is carved from a caller-provided device arena
+ * (e.g. a torch uint8 tensor) of at least muca_workspace_size() bytes, 256-byte
+ * aligned.  The caller keeps the arena alive until muca_free. */
+int muca_workspace_size(int system, int L_or_N, int q, int p, size_t *bytes);
+int muca_init_ex(muca_ctx **out, int system, int L_or_N, int q, int p, uint64_t seed,
+                 void *device_arena, size_t arena_bytes);
+
+/* Set a parameter.  Keys:
+ *   "beta"        MUMA inverse temperature (Eq. 3); before the first iterate.
+ *   "record"      0 = count the current bin after every attempt (default),
+ *                 1 = once per sweep; before the first iterate.
+ *   "flat_ratio"  flatness criterion min H / mean H (default 0.5); any time.
+ *   "block"       walkers per thread block of the sweep kernel (32..512,
+ *                 multiple of 32); before the first iterate.
+ *   "walker_offset" global id of this context's walker 0 when one system's
+ *                 walkers are split over several contexts (e.g. one per GPU):
+ *                 walker w draws from the stream of walker w + offset, so the
+ *                 union of the shards equals one context of all walkers;
+ *                 re-draws the initial states; before the first iterate.
+ *   Polymer only (before the first iterate): "e_lo", "e_hi", "bin_width",
+ *   "step" (side of the displacement cube), "fene_K", "fene_R",
+ *   "lj_cutoff".
+ * Unknown key or bad value: MUCA_ERR_ARG; too late: MUCA_ERR_STATE. */
+int muca_set_param(muca_ctx *ctx, const char *key, double value);
+
+/* Use `cuda_stream` (a cudaStream_t, e.g. torch.cuda.current_stream().cuda_stream)
+ * for all later device work of this context. */
+int muca_set_stream(muca_ctx *ctx, void *cuda_stream);
+
+/* Run `sweeps` sweeps of every walker under the current weights (one
+ * iteration's worth of independent equilibrium simulation, Fig. 1), filling
+ * the histogram of the open iteration.  Asynchronous. sweeps >= 1. */
+int muca_iterate(muca_ctx *ctx, int64_t sweeps);
+
+/* Merge the walkers' histograms into H^(n), compute W^(n+1) with the
+ * accumulated-statistics recursion in log form (paper: "use the full
+ * statistics of previous iterations ... implemented with logarithmic
+ * weights") and rebuild the acceptance thresholds ("distributed to all p
+ * cores").  If is_flat is non-NULL the call synchronises and stores 1 when
+ * every reachable bin of H^(n) is non-zero and min/mean >= flat_ratio. */
+int muca_merge_and_update(muca_ctx *ctx, int *is_flat);
+
+/* Number of histogram bins B of the context. */
+int muca_num_bins(const muca_ctx *ctx, int *nbins);
+
+/* ln W^(n) (the current weights), B doubles; unreachable bins hold -inf. */
+int muca_get_lnW(muca_ctx *ctx, double *host_out, int nbins);
+/* The weights the last merged histogram was sampled with (ln W^(n-1)). */
+int muca_get_lnW_sampled(muca_ctx *ctx, double *host_out, int nbins);
+/* Last merged histogram H^(n), B counts. */
+int muca_get_histogram(muca_ctx *ctx, uint64_t *host_out, int nbins);
+/* {min, mean, max} of the last merged histogram over reachable bins. */
+int muca_get_flatness(muca_ctx *ctx, double host_stats[3]);
+
+/* Reweighting, Eq. (2), of the last merged histogram with the weights it was
+ * sampled with: ln Omega(b) = ln H(b) - ln W(b).
+ * Ising / Potts: host_out = {<E>, <E^2>, C_V per site, ln Z} at beta, with
+ *   ln Z normalised by the ground-state degeneracy (2, resp. q); NaN if the
+ *   ground state was never visited.
+ * MUMA (at its own beta; `beta` is ignored): {<|M|>/N, <M^2>/N^2,
+ *   susceptibility per site, ln P(M=0) - ln P(M=N)}.
+ * host_lnP (nullable, B doubles) receives ln P(b). */
+int muca_get_reweight(muca_ctx *ctx, double beta, double host_out[4], double *host_lnP);
+
+/* Checkpoint: the complete state (walkers, weights, recursion state, counters).
+ * Call with host_buf == NULL to get the size in *bytes.  muca_set_state
+ * restores a buffer produced by a context of the same configuration; resuming
+ * is bit-exact because the random numbers are keyed by (seed, walker, sweep). */
+int muca_get_state(muca_ctx *ctx, void *host_buf, size_t *bytes);
+int muca_set_state(muca_ctx *ctx, const void *host_buf, size_t bytes);
+
+/* Inspection (parity checks).  Spins unpacked to one int8 per site, walker-major
+ * (Ising/MUMA: +1/-1, Potts: 0..q-1), n = p*L*L; current bin of each walker;
+ * threshold table T[b][c] (B*C uint32, C = 5 Ising, 9 Potts, 10 MUMA);
+ * the global sweep counter. */
+int muca_get_spins(muca_ctx *ctx, int8_t *host_out, int64_t n);
+int muca_get_walker_bins(muca_ctx *ctx, int32_t *host_out, int p);
+int muca_get_thresholds(muca_ctx *ctx, uint32_t *host_out, int64_t n);
+int muca_get_sweep_counter(muca_ctx *ctx, int64_t *host_out);
+
+/* Diagnostics: evaluate the library's deterministic binary64 exp (fn = 0) or
+ * log (fn = 1) -- the functions the weight recursion and the threshold build
+ * use -- on n host values, on the current device.  Synchronous. */
+int muca_det_math(int fn, const double *host_in, double *host_out, int64_t n);
+
+/* Wait for the context's stream. */
+int muca_synchronize(muca_ctx *ctx);
+
+/* Release the context and (unless it came from muca_init_ex) its device memory. */
+int muca_free(muca_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MUCA_H */

@@ -1,0 +1,261 @@
+"""GB300 (sm_103a) parallel multicanonical simulations (arXiv:1312.2213).
+
+A thin Python layer over the C ABI in ``include/muca.h``: the functions below
+carry the same names and only marshal arguments; every step of the method runs
+in the CUDA library ``libmuca.so``.  PyTorch is used only to hand over CUDA
+streams (``muca_set_stream``) and, optionally, a device arena (``Muca(...,
+arena="torch")``).
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from ._native import MucaError, check, library_path, load
+
+ISING2D, POTTS2D, ISING2D_MUMA, POLYMER3D = 0, 1, 2, 3
+SYSTEM_NAMES = {ISING2D: "ising2d", POTTS2D: "potts2d", ISING2D_MUMA: "ising2d_muma", POLYMER3D: "polymer3d"}
+
+__all__ = ["Muca", "MucaError", "ISING2D", "POTTS2D", "ISING2D_MUMA", "POLYMER3D", "library_path", "load",
+           "muca_init", "muca_init_ex", "muca_workspace_size", "muca_set_param", "muca_set_stream",
+           "muca_iterate", "muca_merge_and_update", "muca_num_bins", "muca_get_lnW", "muca_get_lnW_sampled",
+           "muca_get_histogram", "muca_get_flatness", "muca_get_reweight", "muca_get_state", "muca_set_state",
+           "muca_get_spins", "muca_get_walker_bins", "muca_get_thresholds", "muca_get_sweep_counter",
+           "muca_synchronize", "muca_free", "muca_last_error", "muca_det_math"]
+
+
+def _p(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+# ---- one-to-one wrappers of the C ABI --------------------------------------------------------
+def muca_last_error() -> str:
+    return (load().muca_last_error() or b"").decode(errors="replace")
+
+
+def muca_init(system: int, L_or_N: int, q: int, p: int, seed: int):
+    h = ctypes.c_void_p()
+    check(load().muca_init(ctypes.byref(h), system, L_or_N, q, p, seed), "muca_init")
+    return h
+
+
+def muca_workspace_size(system: int, L_or_N: int, q: int, p: int) -> int:
+    n = ctypes.c_size_t()
+    check(load().muca_workspace_size(system, L_or_N, q, p, ctypes.byref(n)), "muca_workspace_size")
+    return n.value
+
+
+def muca_init_ex(system: int, L_or_N: int, q: int, p: int, seed: int, device_arena: int, arena_bytes: int):
+    h = ctypes.c_void_p()
+    check(load().muca_init_ex(ctypes.byref(h), system, L_or_N, q, p, seed, ctypes.c_void_p(device_arena),
+                              arena_bytes), "muca_init_ex")
+    return h
+
+
+def muca_set_param(h, key: str, value: float):
+    check(load().muca_set_param(h, key.encode(), float(value)), "muca_set_param(%s)" % key)
+
+
+def muca_set_stream(h, stream: int):
+    check(load().muca_set_stream(h, ctypes.c_void_p(stream)), "muca_set_stream")
+
+
+def muca_iterate(h, sweeps: int):
+    check(load().muca_iterate(h, sweeps), "muca_iterate")
+
+
+def muca_merge_and_update(h, want_flat: bool = False):
+    if want_flat:
+        f = ctypes.c_int()
+        check(load().muca_merge_and_update(h, ctypes.byref(f)), "muca_merge_and_update")
+        return bool(f.value)
+    check(load().muca_merge_and_update(h, None), "muca_merge_and_update")
+    return None
+
+
+def muca_num_bins(h) -> int:
+    n = ctypes.c_int()
+    check(load().muca_num_bins(h, ctypes.byref(n)), "muca_num_bins")
+    return n.value
+
+
+def muca_get_lnW(h, out: np.ndarray):
+    check(load().muca_get_lnW(h, _p(out), out.size), "muca_get_lnW")
+
+
+def muca_get_lnW_sampled(h, out: np.ndarray):
+    check(load().muca_get_lnW_sampled(h, _p(out), out.size), "muca_get_lnW_sampled")
+
+
+def muca_get_histogram(h, out: np.ndarray):
+    check(load().muca_get_histogram(h, _p(out), out.size), "muca_get_histogram")
+
+
+def muca_get_flatness(h, out: np.ndarray):
+    check(load().muca_get_flatness(h, _p(out)), "muca_get_flatness")
+
+
+def muca_get_reweight(h, beta: float, out: np.ndarray, lnP: np.ndarray | None = None):
+    check(load().muca_get_reweight(h, float(beta), _p(out), None if lnP is None else _p(lnP)), "muca_get_reweight")
+
+
+def muca_get_state(h, buf: np.ndarray | None = None) -> int:
+    n = ctypes.c_size_t(0 if buf is None else buf.nbytes)
+    check(load().muca_get_state(h, None if buf is None else _p(buf), ctypes.byref(n)), "muca_get_state")
+    return n.value
+
+
+def muca_set_state(h, buf: np.ndarray):
+    check(load().muca_set_state(h, _p(buf), buf.nbytes), "muca_set_state")
+
+
+def muca_get_spins(h, out: np.ndarray):
+    check(load().muca_get_spins(h, _p(out), out.size), "muca_get_spins")
+
+
+def muca_get_walker_bins(h, out: np.ndarray):
+    check(load().muca_get_walker_bins(h, _p(out), out.size), "muca_get_walker_bins")
+
+
+def muca_get_thresholds(h, out: np.ndarray):
+    check(load().muca_get_thresholds(h, _p(out), out.size), "muca_get_thresholds")
+
+
+def muca_get_sweep_counter(h) -> int:
+    v = ctypes.c_int64()
+    check(load().muca_get_sweep_counter(h, ctypes.byref(v)), "muca_get_sweep_counter")
+    return v.value
+
+
+def muca_det_math(fn: int, x: np.ndarray) -> np.ndarray:
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    out = np.zeros_like(x)
+    check(load().muca_det_math(fn, _p(x), _p(out), x.size), "muca_det_math")
+    return out
+
+
+def muca_synchronize(h):
+    check(load().muca_synchronize(h), "muca_synchronize")
+
+
+def muca_free(h):
+    check(load().muca_free(h), "muca_free")
+
+
+# ---- convenience object -----------------------------------------------------------------------
+class Muca:
+    """One system of p walkers on the current CUDA device (owns a muca_ctx)."""
+
+    def __init__(self, system: int, L: int, q: int = 2, p: int = 64, seed: int = 1, *, beta: float | None = None,
+                 record: int = 0, block: int | None = None, walker_offset: int = 0, stream=None,
+                 arena: str | None = None):
+        self.system, self.L, self.q, self.p, self.seed = system, L, q, p, seed
+        self._arena = None
+        if arena == "torch":
+            import torch
+
+            nbytes = muca_workspace_size(system, L, q, p)
+            self._arena = torch.empty(nbytes + 256, dtype=torch.uint8, device="cuda")
+            ptr = (self._arena.data_ptr() + 255) // 256 * 256
+            self.h = muca_init_ex(system, L, q, p, seed, ptr, nbytes)
+        else:
+            self.h = muca_init(system, L, q, p, seed)
+        self.B = muca_num_bins(self.h)
+        self.N = L * L
+        self.C = {ISING2D: 5, POTTS2D: 9, ISING2D_MUMA: 10}.get(system, 0)
+        if stream is not None:
+            muca_set_stream(self.h, int(getattr(stream, "cuda_stream", stream)))
+        if beta is not None:
+            muca_set_param(self.h, "beta", beta)
+        if record:
+            muca_set_param(self.h, "record", record)
+        if block is not None:
+            muca_set_param(self.h, "block", block)
+        if walker_offset:
+            muca_set_param(self.h, "walker_offset", walker_offset)
+
+    def close(self):
+        if getattr(self, "h", None) is not None:
+            muca_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def set_param(self, key: str, value: float):
+        muca_set_param(self.h, key, value)
+
+    def set_stream(self, stream):
+        muca_set_stream(self.h, int(getattr(stream, "cuda_stream", stream)))
+
+    def iterate(self, sweeps: int):
+        muca_iterate(self.h, sweeps)
+
+    def merge_and_update(self, want_flat: bool = False):
+        return muca_merge_and_update(self.h, want_flat)
+
+    def lnW(self) -> np.ndarray:
+        a = np.zeros(self.B, dtype=np.float64)
+        muca_get_lnW(self.h, a)
+        return a
+
+    def lnW_sampled(self) -> np.ndarray:
+        a = np.zeros(self.B, dtype=np.float64)
+        muca_get_lnW_sampled(self.h, a)
+        return a
+
+    def histogram(self) -> np.ndarray:
+        a = np.zeros(self.B, dtype=np.uint64)
+        muca_get_histogram(self.h, a)
+        return a
+
+    def flatness(self) -> np.ndarray:
+        a = np.zeros(3, dtype=np.float64)
+        muca_get_flatness(self.h, a)
+        return a
+
+    def reweight(self, beta: float):
+        out = np.zeros(4, dtype=np.float64)
+        lnP = np.zeros(self.B, dtype=np.float64)
+        muca_get_reweight(self.h, beta, out, lnP)
+        return out, lnP
+
+    def spins(self) -> np.ndarray:
+        a = np.zeros(self.p * self.N, dtype=np.int8)
+        muca_get_spins(self.h, a)
+        return a.reshape(self.p, self.L, self.L)
+
+    def bins(self) -> np.ndarray:
+        a = np.zeros(self.p, dtype=np.int32)
+        muca_get_walker_bins(self.h, a)
+        return a
+
+    def thresholds(self) -> np.ndarray:
+        a = np.zeros(self.B * self.C, dtype=np.uint32)
+        muca_get_thresholds(self.h, a)
+        return a.reshape(self.B, self.C)
+
+    def sweep_counter(self) -> int:
+        return muca_get_sweep_counter(self.h)
+
+    def get_state(self) -> np.ndarray:
+        n = muca_get_state(self.h, None)
+        buf = np.zeros(n, dtype=np.uint8)
+        muca_get_state(self.h, buf)
+        return buf
+
+    def set_state(self, buf: np.ndarray):
+        muca_set_state(self.h, np.ascontiguousarray(buf, dtype=np.uint8))
+
+    def synchronize(self):
+        muca_synchronize(self.h)

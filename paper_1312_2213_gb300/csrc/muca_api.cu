@@ -1,0 +1,644 @@
+// muca_api.cu -- host runtime behind include/muca.h.  It owns the context,
+// lays out the device arena, turns every C call into kernel launches on the
+// context's stream, and maps CUDA errors onto MUCA_ERR_* codes with a
+// thread-local message.  No compute happens on the host.
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "muca.h"
+#include "muca_internal.h"
+
+using namespace muca;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+#define MUCA_CUDA(expr)                                                                         \
+    do {                                                                                        \
+        cudaError_t e_ = (expr);                                                                \
+        if (e_ != cudaSuccess) return fail(MUCA_ERR_CUDA, "%s: %s", #expr, cudaGetErrorString(e_)); \
+    } while (0)
+
+constexpr size_t kAlign = 256;
+size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+struct Layout {
+    size_t lat, bin, T, lnW, lnW_sampled, G, lnR, H, Hpart, rlist, reach, state, out, total;
+};
+
+}  // namespace
+
+struct muca_ctx {
+    int system = 0, L = 0, q = 2, p = 0, N = 0, B = 0, C = 0, nreach = 0;
+    uint64_t seed = 0;
+    double beta = 0.0, flat_ratio = 0.5;
+    int record = 0, block = 64, walker_offset = 0;
+    int pstride = 0, wpw = 0, nblk_max = 0;
+    cudaStream_t stream = nullptr;
+    bool owns_arena = false, started = false;
+    void *arena = nullptr;
+    size_t arena_bytes = 0;
+    uint32_t *lat = nullptr;
+    int32_t *bin = nullptr;
+    uint32_t *T = nullptr;
+    double *lnW = nullptr, *lnW_sampled = nullptr, *G = nullptr, *lnR = nullptr;
+    unsigned long long *H = nullptr, *Hpart = nullptr;
+    int32_t *rlist = nullptr;
+    uint8_t *reach = nullptr;
+    DevState *state = nullptr;
+    double *out = nullptr;  // reweight outputs: 4 + B doubles
+    std::vector<uint8_t> h_reach;
+    std::vector<int32_t> h_rlist;
+};
+
+namespace {
+
+bool valid_config(int system, int L, int q, int p, std::string &why)
+{
+    if (p < 1) { why = "p must be >= 1"; return false; }
+    if (system == kPolymer) { why = "the polymer system is not available in this build"; return false; }
+    if (system != kIsing && system != kPotts && system != kMuma) { why = "unknown system"; return false; }
+    if (system == kPotts && (q < 2 || q > 16)) { why = "Potts q must be in [2, 16]"; return false; }
+    if (!spin_sweep_supported(system, L)) {
+        why = "lattice size not supported (L in {4,8,12,16,24,32,48,64}; Potts L <= 48)";
+        return false;
+    }
+    return true;
+}
+
+void fill_shape(muca_ctx *c, int system, int L, int q, int p)
+{
+    c->system = system;
+    c->L = L;
+    c->q = (system == kPotts) ? q : 2;
+    c->p = p;
+    c->N = L * L;
+    c->B = (system == kPotts) ? 2 * c->N + 1 : c->N + 1;
+    c->C = num_cols(system);
+    c->pstride = (p + 31) / 32 * 32;
+    c->wpw = words_per_walker(system, L);
+    c->nblk_max = (p + 31) / 32;  // smallest allowed block is one warp
+}
+
+// Reachable bins of the periodic L x L lattice (L even): the Ising model has
+// no state with exactly 2 or 2N-2 broken bonds; the q >= 3 Potts model none
+// with 1, 2, 3 or 5; the q = 2 Potts model follows Ising (even counts only);
+// every magnetisation is reachable.
+void reachable_bins(muca_ctx *c)
+{
+    const int N = c->N, B = c->B;
+    c->h_reach.assign(B, 1);
+    if (c->system == kIsing) {
+        c->h_reach[1] = 0;
+        c->h_reach[N - 1] = 0;
+    } else if (c->system == kPotts) {
+        if (c->q == 2) {
+            for (int b = 0; b < B; ++b)
+                if ((b & 1) || b == 2 || b == 2 * N - 2) c->h_reach[b] = 0;
+        } else {
+            for (int b : {1, 2, 3, 5}) c->h_reach[b] = 0;
+        }
+    }
+    c->h_rlist.clear();
+    for (int b = 0; b < B; ++b)
+        if (c->h_reach[b]) c->h_rlist.push_back(b);
+    c->nreach = (int)c->h_rlist.size();
+}
+
+Layout plan(const muca_ctx *c)
+{
+    Layout l{};
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        size_t o = off;
+        off += align_up(bytes);
+        return o;
+    };
+    l.lat = take(sizeof(uint32_t) * (size_t)c->wpw * c->pstride);
+    l.bin = take(sizeof(int32_t) * (size_t)c->pstride);
+    l.T = take(sizeof(uint32_t) * (size_t)c->B * c->C);
+    l.lnW = take(sizeof(double) * c->B);
+    l.lnW_sampled = take(sizeof(double) * c->B);
+    l.G = take(sizeof(double) * c->B);
+    l.lnR = take(sizeof(double) * c->B);
+    l.H = take(sizeof(unsigned long long) * c->B);
+    l.Hpart = take(sizeof(unsigned long long) * (size_t)c->nblk_max * c->B);
+    l.rlist = take(sizeof(int32_t) * c->B);
+    l.reach = take((size_t)c->B);
+    l.state = take(sizeof(DevState));
+    l.out = take(sizeof(double) * (4 + (size_t)c->B));
+    l.total = off;
+    return l;
+}
+
+UpdateArgs update_args(const muca_ctx *c)
+{
+    UpdateArgs a{};
+    a.system = c->system;
+    a.B = c->B;
+    a.nreach = c->nreach;
+    a.nblocks = (c->p + c->block - 1) / c->block;
+    a.N = c->N;
+    a.q = c->q;
+    a.p = c->p;
+    a.pstride = c->pstride;
+    a.L = c->L;
+    a.beta = c->beta;
+    a.flat_ratio = c->flat_ratio;
+    a.reach = c->reach;
+    a.rlist = c->rlist;
+    a.Hpart = c->Hpart;
+    a.H = c->H;
+    a.lnW = c->lnW;
+    a.lnW_sampled = c->lnW_sampled;
+    a.G = c->G;
+    a.lnR = c->lnR;
+    a.T = c->T;
+    a.state = c->state;
+    return a;
+}
+
+int init_walkers(muca_ctx *c)
+{
+    MUCA_CUDA(launch_init_spins(c->system, c->L, c->q, c->p, c->pstride, (uint32_t)(c->seed & 0xffffffffu),
+                                (uint32_t)(c->seed >> 32), c->walker_offset, c->lat, c->bin, c->stream));
+    return MUCA_OK;
+}
+
+int setup(muca_ctx *c)
+{
+    Layout l = plan(c);
+    char *base = (char *)c->arena;
+    c->lat = (uint32_t *)(base + l.lat);
+    c->bin = (int32_t *)(base + l.bin);
+    c->T = (uint32_t *)(base + l.T);
+    c->lnW = (double *)(base + l.lnW);
+    c->lnW_sampled = (double *)(base + l.lnW_sampled);
+    c->G = (double *)(base + l.G);
+    c->lnR = (double *)(base + l.lnR);
+    c->H = (unsigned long long *)(base + l.H);
+    c->Hpart = (unsigned long long *)(base + l.Hpart);
+    c->rlist = (int32_t *)(base + l.rlist);
+    c->reach = (uint8_t *)(base + l.reach);
+    c->state = (DevState *)(base + l.state);
+    c->out = (double *)(base + l.out);
+    reachable_bins(c);
+    MUCA_CUDA(cudaMemsetAsync(c->arena, 0, l.total, c->stream));
+    MUCA_CUDA(cudaMemcpyAsync(c->reach, c->h_reach.data(), c->B, cudaMemcpyHostToDevice, c->stream));
+    MUCA_CUDA(cudaMemcpyAsync(c->rlist, c->h_rlist.data(), sizeof(int32_t) * c->nreach, cudaMemcpyHostToDevice,
+                              c->stream));
+    UpdateArgs a = update_args(c);
+    MUCA_CUDA(launch_init_lnW(a, c->stream));
+    int rc = init_walkers(c);
+    if (rc) return rc;
+    MUCA_CUDA(launch_thresholds(a, c->stream));
+    MUCA_CUDA(cudaStreamSynchronize(c->stream));
+    return MUCA_OK;
+}
+
+int create(muca_ctx **out, int system, int L, int q, int p, uint64_t seed, void *arena, size_t arena_bytes)
+{
+    if (!out) return fail(MUCA_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    std::string why;
+    if (!valid_config(system, L, q, p, why)) return fail(MUCA_ERR_ARG, "muca_init: %s", why.c_str());
+    muca_ctx *c = new (std::nothrow) muca_ctx();
+    if (!c) return fail(MUCA_ERR_OOM, "host allocation failed");
+    fill_shape(c, system, L, q, p);
+    c->seed = seed;
+    const size_t need = plan(c).total;
+    if (arena) {
+        if (arena_bytes < need || ((uintptr_t)arena % kAlign) != 0) {
+            delete c;
+            return fail(MUCA_ERR_OOM, "arena too small or misaligned: need %zu bytes, 256-byte aligned", need);
+        }
+        c->arena = arena;
+        c->arena_bytes = arena_bytes;
+        c->owns_arena = false;
+    } else {
+        cudaError_t e = cudaMalloc(&c->arena, need);
+        if (e != cudaSuccess) {
+            delete c;
+            return fail(MUCA_ERR_OOM, "cudaMalloc(%zu): %s", need, cudaGetErrorString(e));
+        }
+        c->arena_bytes = need;
+        c->owns_arena = true;
+    }
+    int rc = setup(c);
+    if (rc) {
+        if (c->owns_arena) cudaFree(c->arena);
+        delete c;
+        return rc;
+    }
+    *out = c;
+    return MUCA_OK;
+}
+
+int check_ctx(const muca_ctx *c)
+{
+    if (!c) return fail(MUCA_ERR_ARG, "context is NULL");
+    return MUCA_OK;
+}
+
+int d2h(muca_ctx *c, void *host, const void *dev, size_t bytes)
+{
+    MUCA_CUDA(cudaMemcpyAsync(host, dev, bytes, cudaMemcpyDeviceToHost, c->stream));
+    MUCA_CUDA(cudaStreamSynchronize(c->stream));
+    return MUCA_OK;
+}
+
+// Checkpoint blob: fixed header, then the device sections in this order.
+struct StateHeader {
+    char magic[8];
+    int32_t version, system, L, q, p, B, C, wpw, pstride, record, walker_offset;
+    uint64_t seed;
+    double beta;
+    DevState dev;
+};
+
+size_t state_bytes(const muca_ctx *c)
+{
+    return sizeof(StateHeader) + sizeof(uint32_t) * (size_t)c->wpw * c->pstride + sizeof(int32_t) * (size_t)c->p +
+           sizeof(double) * 4 * (size_t)c->B + sizeof(unsigned long long) * 2 * (size_t)c->B +
+           sizeof(uint32_t) * (size_t)c->B * c->C;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *muca_last_error(void) { return g_err.c_str(); }
+
+int muca_workspace_size(int system, int L_or_N, int q, int p, size_t *bytes)
+{
+    if (!bytes) return fail(MUCA_ERR_ARG, "bytes is NULL");
+    std::string why;
+    if (!valid_config(system, L_or_N, q, p, why)) return fail(MUCA_ERR_ARG, "muca_workspace_size: %s", why.c_str());
+    muca_ctx c;
+    fill_shape(&c, system, L_or_N, q, p);
+    *bytes = plan(&c).total;
+    return MUCA_OK;
+}
+
+int muca_init(muca_ctx **out, int system, int L_or_N, int q, int p, uint64_t seed)
+{
+    return create(out, system, L_or_N, q, p, seed, nullptr, 0);
+}
+
+int muca_init_ex(muca_ctx **out, int system, int L_or_N, int q, int p, uint64_t seed, void *device_arena,
+                 size_t arena_bytes)
+{
+    if (!device_arena) return fail(MUCA_ERR_ARG, "device_arena is NULL");
+    return create(out, system, L_or_N, q, p, seed, device_arena, arena_bytes);
+}
+
+int muca_set_param(muca_ctx *c, const char *key, double v)
+{
+    if (int rc = check_ctx(c)) return rc;
+    if (!key) return fail(MUCA_ERR_ARG, "key is NULL");
+    const std::string k(key);
+    if (k == "flat_ratio") {
+        if (!(v > 0.0 && v <= 1.0)) return fail(MUCA_ERR_ARG, "flat_ratio must be in (0, 1]");
+        c->flat_ratio = v;
+        return MUCA_OK;
+    }
+    const bool locked = c->started;
+    if (k == "beta") {
+        if (locked) return fail(MUCA_ERR_STATE, "beta must be set before the first iterate");
+        if (!(v == v) || v < 0.0) return fail(MUCA_ERR_ARG, "beta must be >= 0");
+        c->beta = v;
+        UpdateArgs a = update_args(c);
+        MUCA_CUDA(launch_thresholds(a, c->stream));
+        return MUCA_OK;
+    }
+    if (k == "record") {
+        if (locked) return fail(MUCA_ERR_STATE, "record must be set before the first iterate");
+        if (v != 0.0 && v != 1.0) return fail(MUCA_ERR_ARG, "record must be 0 or 1");
+        c->record = (int)v;
+        return MUCA_OK;
+    }
+    if (k == "block") {
+        if (locked) return fail(MUCA_ERR_STATE, "block must be set before the first iterate");
+        const int b = (int)v;
+        if ((double)b != v || b < 32 || b > kMaxSweepBlock || (b % 32) != 0)
+            return fail(MUCA_ERR_ARG, "block must be a multiple of 32 in [32, %d]", kMaxSweepBlock);
+        c->block = b;
+        return MUCA_OK;
+    }
+    if (k == "walker_offset") {
+        if (locked) return fail(MUCA_ERR_STATE, "walker_offset must be set before the first iterate");
+        const long long o = (long long)v;
+        if ((double)o != v || o < 0 || o + c->p > 0x7fffffffLL) return fail(MUCA_ERR_ARG, "bad walker_offset");
+        c->walker_offset = (int)o;
+        return init_walkers(c);
+    }
+    return fail(MUCA_ERR_ARG, "unknown parameter '%s'", key);
+}
+
+int muca_set_stream(muca_ctx *c, void *stream)
+{
+    if (int rc = check_ctx(c)) return rc;
+    MUCA_CUDA(cudaStreamSynchronize(c->stream));
+    c->stream = (cudaStream_t)stream;
+    return MUCA_OK;
+}
+
+int muca_iterate(muca_ctx *c, int64_t sweeps)
+{
+    if (int rc = check_ctx(c)) return rc;
+    if (sweeps < 1) return fail(MUCA_ERR_ARG, "sweeps must be >= 1");
+    SpinSweepArgs a{};
+    a.T = c->T;
+    a.lattice = c->lat;
+    a.bin = c->bin;
+    a.Hpart = c->Hpart;
+    a.state = c->state;
+    a.p = c->p;
+    a.pstride = c->pstride;
+    a.B = c->B;
+    a.q = c->q;
+    a.sweeps = sweeps;
+    const unsigned long long per_sweep = (unsigned long long)c->block * (c->record == 0 ? (unsigned)c->N : 1u);
+    unsigned long long fe = 0xFFFFFFFFull / per_sweep;
+    if (fe < 1) fe = 1;
+    if (fe > (unsigned long long)sweeps) fe = (unsigned long long)sweeps;
+    a.flush_every = (int)(fe > 0x7fffffffull ? 0x7fffffffull : fe);
+    a.key0 = (uint32_t)(c->seed & 0xffffffffu);
+    a.key1 = (uint32_t)(c->seed >> 32);
+    a.record = c->record;
+    a.walker_offset = c->walker_offset;
+    MUCA_CUDA(launch_spin_sweep(c->system, c->L, a, c->block, c->stream));
+    MUCA_CUDA(launch_advance(c->state, sweeps, c->stream));
+    c->started = true;
+    return MUCA_OK;
+}
+
+int muca_merge_and_update(muca_ctx *c, int *is_flat)
+{
+    if (int rc = check_ctx(c)) return rc;
+    UpdateArgs a = update_args(c);
+    MUCA_CUDA(launch_merge(a, c->stream));
+    MUCA_CUDA(launch_recursion(a, c->stream));
+    MUCA_CUDA(launch_thresholds(a, c->stream));
+    c->started = true;
+    if (is_flat) {
+        int f = 0;
+        if (int rc = d2h(c, &f, &c->state->flat, sizeof(int))) return rc;
+        *is_flat = f;
+    }
+    return MUCA_OK;
+}
+
+int muca_num_bins(const muca_ctx *c, int *nbins)
+{
+    if (int rc = check_ctx(c)) return rc;
+    if (!nbins) return fail(MUCA_ERR_ARG, "nbins is NULL");
+    *nbins = c->B;
+    return MUCA_OK;
+}
+
+int muca_get_lnW(muca_ctx *c, double *host_out, int nbins)
+{
+    if (int rc = check_ctx(c)) return rc;
+    if (!host_out || nbins != c->B) return fail(MUCA_ERR_ARG, "need a host buffer of %d doubles", c->B);
+    return d2h(c, host_out, c->lnW, sizeof(double) * c->B);
+}
+
+int muca_get_lnW_sampled(muca_ctx *c, double *host_out, int nbins)
+{
+    if (int rc = check_ctx(c)) return rc;
+    if (!host_out || nbins != c->B) return fail(MUCA_ERR_ARG, "need a host buffer of %d doubles", c->B);
+    return d2h(c, host_out, c->lnW_sampled, sizeof(double) * c->B);
+}
+
+int muca_get_histogram(muca_ctx *c, uint64_t *host_out, int nbins)
+{
+    if (int rc = check_ctx(c)) return rc;
+    if (!host_out || nbins != c->B) return fail(MUCA_ERR_ARG, "need a host buffer of %d uint64", c->B);
+    return d2h(c, host_out, c->H, sizeof(uint64_t) * c->B);
+}
+
+int muca_get_flatness(muca_ctx *c, double host_stats[3])
+{
+    if (int rc = check_ctx(c)) return rc;
+    if (!host_stats) return fail(MUCA_ERR_ARG, "stats is NULL");
+    DevState st;
+    if (int rc = d2h(c, &st, c->state, sizeof st)) return rc;
+    host_stats[0] = st.flat_min;
+    host_stats[1] = st.flat_mean;
+    host_stats[2] = st.flat_max;
+    return MUCA_OK;
+}
+
+int muca_get_reweight(muca_ctx *c, double beta, double host_out[4], double *host_lnP)
+{
+    if (int rc = check_ctx(c)) return rc;
+    if (!host_out) return fail(MUCA_ERR_ARG, "out is NULL");
+    if (!(beta == beta)) return fail(MUCA_ERR_ARG, "beta is NaN");
+    UpdateArgs a = update_args(c);
+    MUCA_CUDA(launch_reweight(a, beta, c->out, c->out + 4, c->stream));
+    if (int rc = d2h(c, host_out, c->out, sizeof(double) * 4)) return rc;
+    if (host_lnP) return d2h(c, host_lnP, c->out + 4, sizeof(double) * c->B);
+    return MUCA_OK;
+}
+
+int muca_get_spins(muca_ctx *c, int8_t *host_out, int64_t n)
+{
+    if (int rc = check_ctx(c)) return rc;
+    if (!host_out || n != (int64_t)c->p * c->N) return fail(MUCA_ERR_ARG, "need p*L*L = %lld bytes",
+                                                              (long long)c->p * c->N);
+    int8_t *tmp = nullptr;
+    MUCA_CUDA(cudaMalloc(&tmp, (size_t)n));
+    cudaError_t e = launch_unpack_spins(c->system, c->L, c->p, c->pstride, c->lat, tmp, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(host_out, tmp, (size_t)n, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    cudaFree(tmp);
+    if (e != cudaSuccess) return fail(MUCA_ERR_CUDA, "muca_get_spins: %s", cudaGetErrorString(e));
+    return MUCA_OK;
+}
+
+int muca_get_walker_bins(muca_ctx *c, int32_t *host_out, int p)
+{
+    if (int rc = check_ctx(c)) return rc;
+    if (!host_out || p != c->p) return fail(MUCA_ERR_ARG, "need a host buffer of p = %d int32", c->p);
+    return d2h(c, host_out, c->bin, sizeof(int32_t) * c->p);
+}
+
+int muca_get_thresholds(muca_ctx *c, uint32_t *host_out, int64_t n)
+{
+    if (int rc = check_ctx(c)) return rc;
+    if (!host_out || n != (int64_t)c->B * c->C) return fail(MUCA_ERR_ARG, "need B*C = %lld uint32",
+                                                              (long long)c->B * c->C);
+    return d2h(c, host_out, c->T, sizeof(uint32_t) * (size_t)n);
+}
+
+int muca_get_sweep_counter(muca_ctx *c, int64_t *host_out)
+{
+    if (int rc = check_ctx(c)) return rc;
+    if (!host_out) return fail(MUCA_ERR_ARG, "out is NULL");
+    unsigned long long v = 0;
+    if (int rc = d2h(c, &v, &c->state->sweep_counter, sizeof v)) return rc;
+    *host_out = (int64_t)v;
+    return MUCA_OK;
+}
+
+int muca_get_state(muca_ctx *c, void *host_buf, size_t *bytes)
+{
+    if (int rc = check_ctx(c)) return rc;
+    if (!bytes) return fail(MUCA_ERR_ARG, "bytes is NULL");
+    const size_t need = state_bytes(c);
+    if (!host_buf) {
+        *bytes = need;
+        return MUCA_OK;
+    }
+    if (*bytes < need) return fail(MUCA_ERR_ARG, "state buffer too small: need %zu bytes", need);
+    char *p = (char *)host_buf;
+    StateHeader h{};
+    memcpy(h.magic, "MUCAST1", 8);
+    h.version = 1;
+    h.system = c->system;
+    h.L = c->L;
+    h.q = c->q;
+    h.p = c->p;
+    h.B = c->B;
+    h.C = c->C;
+    h.wpw = c->wpw;
+    h.pstride = c->pstride;
+    h.record = c->record;
+    h.walker_offset = c->walker_offset;
+    h.seed = c->seed;
+    h.beta = c->beta;
+    if (int rc = d2h(c, &h.dev, c->state, sizeof h.dev)) return rc;
+    memcpy(p, &h, sizeof h);
+    p += sizeof h;
+    auto pull = [&](const void *dev, size_t n) -> int {
+        cudaError_t e = cudaMemcpyAsync(p, dev, n, cudaMemcpyDeviceToHost, c->stream);
+        if (e != cudaSuccess) return fail(MUCA_ERR_CUDA, "muca_get_state: %s", cudaGetErrorString(e));
+        p += n;
+        return MUCA_OK;
+    };
+    int rc = 0;
+    if ((rc = pull(c->lat, sizeof(uint32_t) * (size_t)c->wpw * c->pstride))) return rc;
+    if ((rc = pull(c->bin, sizeof(int32_t) * (size_t)c->p))) return rc;
+    if ((rc = pull(c->lnW, sizeof(double) * c->B))) return rc;
+    if ((rc = pull(c->lnW_sampled, sizeof(double) * c->B))) return rc;
+    if ((rc = pull(c->G, sizeof(double) * c->B))) return rc;
+    if ((rc = pull(c->lnR, sizeof(double) * c->B))) return rc;
+    if ((rc = pull(c->H, sizeof(unsigned long long) * c->B))) return rc;
+    // open histogram: sum of the block slots (integer, exact)
+    std::vector<unsigned long long> part((size_t)c->nblk_max * c->B), open(c->B, 0ull);
+    {
+        cudaError_t e = cudaMemcpyAsync(part.data(), c->Hpart, sizeof(unsigned long long) * part.size(),
+                                        cudaMemcpyDeviceToHost, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) return fail(MUCA_ERR_CUDA, "muca_get_state: %s", cudaGetErrorString(e));
+        for (int k = 0; k < c->nblk_max; ++k)
+            for (int b = 0; b < c->B; ++b) open[b] += part[(size_t)k * c->B + b];
+    }
+    memcpy(p, open.data(), sizeof(unsigned long long) * c->B);
+    p += sizeof(unsigned long long) * c->B;
+    if ((rc = pull(c->T, sizeof(uint32_t) * (size_t)c->B * c->C))) return rc;
+    MUCA_CUDA(cudaStreamSynchronize(c->stream));
+    *bytes = need;
+    return MUCA_OK;
+}
+
+int muca_set_state(muca_ctx *c, const void *host_buf, size_t bytes)
+{
+    if (int rc = check_ctx(c)) return rc;
+    if (!host_buf) return fail(MUCA_ERR_ARG, "buffer is NULL");
+    const size_t need = state_bytes(c);
+    if (bytes != need) return fail(MUCA_ERR_ARG, "state size %zu does not match this context (%zu)", bytes, need);
+    StateHeader h;
+    memcpy(&h, host_buf, sizeof h);
+    if (memcmp(h.magic, "MUCAST1", 8) != 0 || h.version != 1) return fail(MUCA_ERR_ARG, "not a muca state buffer");
+    if (h.system != c->system || h.L != c->L || h.q != c->q || h.p != c->p || h.B != c->B || h.C != c->C ||
+        h.wpw != c->wpw || h.pstride != c->pstride || h.seed != c->seed)
+        return fail(MUCA_ERR_ARG, "state buffer was written by a different configuration");
+    if (h.record != 0 && h.record != 1) return fail(MUCA_ERR_ARG, "state buffer: bad record mode");
+    {
+        // every walker's bin indexes the shared-memory tables of the sweep kernel: check them here
+        const int32_t *bins = (const int32_t *)((const char *)host_buf + sizeof h +
+                                                sizeof(uint32_t) * (size_t)c->wpw * c->pstride);
+        for (int w = 0; w < c->p; ++w) {
+            int32_t b;
+            memcpy(&b, bins + w, sizeof b);
+            if (b < 0 || b >= c->B || !c->h_reach[b]) return fail(MUCA_ERR_ARG, "state buffer: walker %d has bin %d", w, b);
+        }
+    }
+    c->record = h.record;
+    c->walker_offset = h.walker_offset;
+    c->beta = h.beta;
+    const char *p = (const char *)host_buf + sizeof h;
+    auto push = [&](void *dev, size_t n) -> int {
+        cudaError_t e = cudaMemcpyAsync(dev, p, n, cudaMemcpyHostToDevice, c->stream);
+        if (e != cudaSuccess) return fail(MUCA_ERR_CUDA, "muca_set_state: %s", cudaGetErrorString(e));
+        p += n;
+        return MUCA_OK;
+    };
+    int rc = 0;
+    if ((rc = push(c->lat, sizeof(uint32_t) * (size_t)c->wpw * c->pstride))) return rc;
+    if ((rc = push(c->bin, sizeof(int32_t) * (size_t)c->p))) return rc;
+    if ((rc = push(c->lnW, sizeof(double) * c->B))) return rc;
+    if ((rc = push(c->lnW_sampled, sizeof(double) * c->B))) return rc;
+    if ((rc = push(c->G, sizeof(double) * c->B))) return rc;
+    if ((rc = push(c->lnR, sizeof(double) * c->B))) return rc;
+    if ((rc = push(c->H, sizeof(unsigned long long) * c->B))) return rc;
+    MUCA_CUDA(cudaMemsetAsync(c->Hpart, 0, sizeof(unsigned long long) * (size_t)c->nblk_max * c->B, c->stream));
+    if ((rc = push(c->Hpart, sizeof(unsigned long long) * c->B))) return rc;  // open histogram -> slot 0
+    if ((rc = push(c->T, sizeof(uint32_t) * (size_t)c->B * c->C))) return rc;
+    MUCA_CUDA(cudaMemcpyAsync(c->state, &h.dev, sizeof h.dev, cudaMemcpyHostToDevice, c->stream));
+    MUCA_CUDA(cudaStreamSynchronize(c->stream));
+    c->started = true;
+    return MUCA_OK;
+}
+
+int muca_det_math(int fn, const double *host_in, double *host_out, int64_t n)
+{
+    if (fn != 0 && fn != 1) return fail(MUCA_ERR_ARG, "fn must be 0 (exp) or 1 (log)");
+    if (n < 0 || (n > 0 && (!host_in || !host_out))) return fail(MUCA_ERR_ARG, "bad buffers");
+    if (n == 0) return MUCA_OK;
+    double *d = nullptr;
+    MUCA_CUDA(cudaMalloc(&d, sizeof(double) * 2 * (size_t)n));
+    cudaError_t e = cudaMemcpy(d, host_in, sizeof(double) * (size_t)n, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = launch_det_math(fn, d, d + n, (long long)n, 0);
+    if (e == cudaSuccess) e = cudaMemcpy(host_out, d + n, sizeof(double) * (size_t)n, cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    if (e != cudaSuccess) return fail(MUCA_ERR_CUDA, "muca_det_math: %s", cudaGetErrorString(e));
+    return MUCA_OK;
+}
+
+int muca_synchronize(muca_ctx *c)
+{
+    if (int rc = check_ctx(c)) return rc;
+    MUCA_CUDA(cudaStreamSynchronize(c->stream));
+    return MUCA_OK;
+}
+
+int muca_free(muca_ctx *c)
+{
+    if (!c) return MUCA_OK;
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (c->owns_arena && c->arena) cudaFree(c->arena);
+    delete c;
+    if (e != cudaSuccess) return fail(MUCA_ERR_CUDA, "muca_free: %s", cudaGetErrorString(e));
+    return MUCA_OK;
+}
+
+}  // extern "C"

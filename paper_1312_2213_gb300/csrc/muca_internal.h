@@ -1,0 +1,80 @@
+// muca_internal.h -- host-side context and the launch interfaces between the
+// C ABI (muca_api.cu) and the kernels (sweep_spin.cu, update.cu).
+#pragma once
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace muca {
+
+enum System { kIsing = 0, kPotts = 1, kMuma = 2, kPolymer = 3 };
+
+// Largest thread block of the sweep kernels (keeps up to 128 registers a thread).
+constexpr int kMaxSweepBlock = 512;
+
+// Threshold meaning "always accept"; any other value t accepts iff u < t.
+constexpr uint32_t kAlways = 0xFFFFFFFFu;
+
+// Device-resident loop state: the sweep counter lives on the device so that a
+// captured iterate -> merge -> update sequence can be replayed unchanged.
+struct DevState {
+    unsigned long long sweep_counter;  // global sweep index of the next sweep
+    unsigned long long iteration;      // completed merge+update steps
+    double flat_min, flat_mean, flat_max;
+    int flat;
+    int pad;
+};
+
+// Everything one spin sweep launch needs.  All pointers are device pointers.
+struct SpinSweepArgs {
+    const uint32_t *T;       // [B][C] thresholds
+    uint32_t *lattice;       // packed rows, word j of walker w at lattice[j * pstride + w]
+    int32_t *bin;            // [p] current bin
+    unsigned long long *Hpart;  // [nblocks][B] per-block histograms (uint64)
+    const DevState *state;   // sweep counter
+    int p, pstride, B, q;
+    int64_t sweeps;
+    int flush_every;         // sweeps between smem -> global histogram flushes
+    uint32_t key0, key1;
+    int record;
+    int walker_offset;       // global id of walker 0 (for sharding)
+};
+
+// Layout helpers shared by host and kernels.
+__host__ __device__ constexpr int ising_words_per_row(int L) { return (L + 31) / 32; }
+__host__ __device__ constexpr int potts_words_per_row(int L) { return (4 * L + 31) / 32; }
+__host__ __device__ constexpr int words_per_walker(int system, int L)
+{
+    return L * (system == kPotts ? potts_words_per_row(L) : ising_words_per_row(L));
+}
+__host__ __device__ constexpr int num_cols(int system) { return system == kPotts ? 9 : (system == kMuma ? 10 : 5); }
+
+// Launchers (return cudaSuccess or the launch error; cudaErrorInvalidValue for
+// an unsupported lattice size).
+bool spin_sweep_supported(int system, int L);
+size_t spin_sweep_smem_bytes(int system, int B);
+cudaError_t launch_spin_sweep(int system, int L, const SpinSweepArgs &a, int block, cudaStream_t s);
+
+struct UpdateArgs {
+    int system, B, nreach, nblocks, N, q, p, pstride, L;
+    double beta, flat_ratio;
+    const uint8_t *reach;
+    const int32_t *rlist;
+    unsigned long long *Hpart, *H;
+    double *lnW, *lnW_sampled, *G, *lnR;
+    uint32_t *T;
+    DevState *state;
+};
+cudaError_t launch_merge(const UpdateArgs &a, cudaStream_t s);
+cudaError_t launch_recursion(const UpdateArgs &a, cudaStream_t s);
+cudaError_t launch_thresholds(const UpdateArgs &a, cudaStream_t s);
+cudaError_t launch_advance(DevState *st, int64_t sweeps, cudaStream_t s);
+cudaError_t launch_init_lnW(const UpdateArgs &a, cudaStream_t s);
+cudaError_t launch_init_spins(int system, int L, int q, int p, int pstride, uint32_t key0, uint32_t key1,
+                              int walker_offset, uint32_t *lattice, int32_t *bin, cudaStream_t s);
+cudaError_t launch_unpack_spins(int system, int L, int p, int pstride, const uint32_t *lattice, int8_t *out,
+                                cudaStream_t s);
+cudaError_t launch_det_math(int fn, const double *in, double *out, long long n, cudaStream_t s);
+cudaError_t launch_reweight(const UpdateArgs &a, double beta, double *out4, double *lnP, cudaStream_t s);
+
+}  // namespace muca

@@ -1,0 +1,195 @@
+"""GPU parity of the spin hot path (sweep -> histogram -> merge -> recursion -> thresholds)
+against the oracle, through the C ABI.  Ising / Potts / multimagnetic histograms, lattices,
+walker bins, ln W and thresholds must agree bit for bit (the integer-threshold acceptance
+and the deterministic binary64 recursion make the two paths identical)."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_1312_2213_gb300 as m
+from gpu_util import compare_state, run_pair
+
+pytestmark = pytest.mark.gpu
+
+NT = 16
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    m.load()
+
+
+def test_det_math_bitwise_equals_oracle():
+    rng = np.random.default_rng(0)
+    x = np.concatenate([rng.uniform(-23, 0, 200000), rng.uniform(-745, 709, 50000), [0.0, -1e-300, -800.0]])
+    ge = m.muca_det_math(0, x)
+    oe = np.array([oracle.det_exp(v) for v in x])
+    np.testing.assert_array_equal(ge.view(np.uint64), oe.view(np.uint64))
+    y = np.concatenate([rng.integers(1, 2**53, 200000).astype(np.float64), 10.0 ** rng.uniform(-300, 300, 50000),
+                        [1.0, 2.0, 5e-324, np.inf]])
+    gl = m.muca_det_math(1, y)
+    ol = np.array([oracle.det_log(v) for v in y])
+    np.testing.assert_array_equal(gl.view(np.uint64), ol.view(np.uint64))
+
+
+@pytest.mark.parametrize("system,L,q,p", [
+    (m.ISING2D, 4, 2, 37), (m.ISING2D, 8, 2, 64), (m.ISING2D, 12, 2, 33), (m.ISING2D, 16, 2, 100),
+    (m.ISING2D, 24, 2, 70), (m.ISING2D, 32, 2, 130), (m.ISING2D, 48, 2, 40), (m.ISING2D, 64, 2, 35),
+    (m.POTTS2D, 4, 3, 37), (m.POTTS2D, 8, 8, 64), (m.POTTS2D, 16, 10, 65), (m.POTTS2D, 32, 8, 96),
+    (m.POTTS2D, 48, 10, 33), (m.POTTS2D, 16, 2, 40), (m.POTTS2D, 12, 16, 40),
+    (m.ISING2D_MUMA, 8, 2, 50), (m.ISING2D_MUMA, 32, 2, 100), (m.ISING2D_MUMA, 64, 2, 33),
+])
+def test_iterations_bit_exact(system, L, q, p):
+    """Several tiles and a ragged last block; every iteration compared."""
+    sweeps = max(2, 4000 // (L * L))
+    run_pair(system, L, q, p, seed=1000 + L + q, iters=4, sweeps=sweeps, beta=0.4407, nthreads=NT)
+
+
+def test_config_ising_L8_p64_full_length():
+    """Ising L = 8, p = 64, 10 iterations of 1e4 sweeps: bit-exact at every iteration."""
+    g, o = run_pair(m.ISING2D, 8, 2, 64, seed=1, iters=10, sweeps=10000, nthreads=NT)
+    flat, _ = o.is_flat(0.5)
+    assert flat and g.merge_and_update is not None
+
+
+@pytest.mark.parametrize("record", [1])
+def test_record_per_sweep(record):
+    run_pair(m.ISING2D, 16, 2, 64, seed=5, iters=3, sweeps=50, record=record, nthreads=NT)
+    run_pair(m.POTTS2D, 16, 5, 64, seed=6, iters=3, sweeps=50, record=record, nthreads=NT)
+
+
+@pytest.mark.parametrize("block", [32, 96, 256, 512])
+def test_block_size_does_not_change_results(block):
+    run_pair(m.POTTS2D, 16, 8, 300, seed=7, iters=2, sweeps=20, block=block, nthreads=NT)
+
+
+def test_full_size_first_iteration_sampled_walkers():
+    """Config sizes (Ising L=32, Potts q=8 L=32, MUMA L=32; p = 8192): one full iteration of
+    1e4 sweeps in the benchmark's launch configuration; sampled walkers recomputed one by one
+    by the oracle must match bit for bit, and the merged histogram must hold p*sweeps*N counts."""
+    sweeps = 10000
+    for system, q in ((m.ISING2D, 2), (m.POTTS2D, 8), (m.ISING2D_MUMA, 2)):
+        p, L = 8192, 32
+        g = m.Muca(system, L, q, p, 11, beta=0.4407 if system == m.ISING2D_MUMA else None)
+        g.iterate(sweeps)
+        g.merge_and_update()
+        assert int(g.histogram().sum()) == p * sweeps * L * L
+        gs, gb = g.spins(), g.bins()
+        o = oracle.Run(system, L, q, p, 11, beta=0.4407)
+        o.init()
+        sample = [0, 1, 31, 32, 4095, 8191]
+        for w in sample:
+            o.iterate_range(sweeps, w, w + 1, 1)
+        os_, ob = o.spins(), o.bins()
+        for w in sample:
+            np.testing.assert_array_equal(gs[w], os_[w])
+            assert gb[w] == ob[w]
+
+
+def test_full_size_bookkeeping_after_several_iterations():
+    """At full size the walkers' bins always equal the bins recomputed from their lattices."""
+    from test_oracle_muca import bins_from_spins
+
+    for system, q in ((m.ISING2D, 2), (m.POTTS2D, 8), (m.ISING2D_MUMA, 2)):
+        g = m.Muca(system, 32, q, 8192, 12, beta=0.4407 if system == m.ISING2D_MUMA else None)
+        for _ in range(3):
+            g.iterate(300)
+            g.merge_and_update()
+        np.testing.assert_array_equal(g.bins(), bins_from_spins(g.spins(), system))
+        assert int(g.histogram().sum()) == 8192 * 300 * 1024
+        assert g.sweep_counter() == 900
+
+
+def test_reweight_matches_oracle():
+    g, o = run_pair(m.ISING2D, 8, 2, 64, seed=3, iters=6, sweeps=3000, nthreads=NT, check_each=False)
+    for beta in (0.2, 0.44, 0.8):
+        go, glp = g.reweight(beta)
+        oo, olp = o.reweight(beta)
+        np.testing.assert_allclose(go, oo, rtol=1e-12, atol=1e-12)
+        fin = np.isfinite(olp)
+        np.testing.assert_array_equal(np.isfinite(glp), fin)
+        np.testing.assert_allclose(glp[fin], olp[fin], rtol=1e-12, atol=1e-11)
+    gm, om_ = run_pair(m.ISING2D_MUMA, 8, 2, 64, seed=4, iters=5, sweeps=2000, beta=0.4407, nthreads=NT,
+                       check_each=False)
+    go, _ = gm.reweight(0.0)
+    oo, _ = om_.reweight(0.0)
+    np.testing.assert_allclose(go, oo, rtol=1e-12, atol=1e-12)
+
+
+def test_checkpoint_resume_is_bit_exact():
+    a = m.Muca(m.POTTS2D, 16, 8, 200, 21)
+    for _ in range(4):
+        a.iterate(100)
+        a.merge_and_update()
+    b = m.Muca(m.POTTS2D, 16, 8, 200, 21)
+    for _ in range(2):
+        b.iterate(100)
+        b.merge_and_update()
+    b.iterate(30)                 # an open (unmerged) iteration is part of the state
+    st = b.get_state()
+    c = m.Muca(m.POTTS2D, 16, 8, 200, 21)
+    c.set_state(st)
+    c.iterate(70)
+    c.merge_and_update()
+    for _ in range(1):
+        c.iterate(100)
+        c.merge_and_update()
+    for f in ("lnW", "histogram", "spins", "bins", "thresholds"):
+        np.testing.assert_array_equal(getattr(a, f)(), getattr(c, f)())
+    assert a.sweep_counter() == c.sweep_counter()
+
+
+def test_walker_shards_reproduce_one_context():
+    """Two contexts holding walkers [0, 60) and [60, 128) (walker_offset) draw the same streams
+    as one context of 128 walkers: lattices agree and the histograms add up (the merge is an
+    integer sum)."""
+    full = m.Muca(m.ISING2D, 16, 2, 128, 9)
+    s0 = m.Muca(m.ISING2D, 16, 2, 60, 9)
+    s1 = m.Muca(m.ISING2D, 16, 2, 68, 9, walker_offset=60)
+    for c in (full, s0, s1):
+        c.iterate(40)
+        c.merge_and_update()
+    np.testing.assert_array_equal(full.spins()[:60], s0.spins())
+    np.testing.assert_array_equal(full.spins()[60:], s1.spins())
+    np.testing.assert_array_equal(full.histogram(), s0.histogram() + s1.histogram())
+
+
+def test_torch_arena_and_stream():
+    import torch
+
+    s = torch.cuda.Stream()
+    a = m.Muca(m.ISING2D, 16, 2, 64, 5, arena="torch", stream=s)
+    b = m.Muca(m.ISING2D, 16, 2, 64, 5)
+    for c in (a, b):
+        c.iterate(25)
+        c.merge_and_update()
+    np.testing.assert_array_equal(a.histogram(), b.histogram())
+    np.testing.assert_array_equal(a.lnW(), b.lnW())
+
+
+def test_errors_are_reported_not_raised_in_c():
+    with pytest.raises(m.MucaError):
+        m.Muca(m.ISING2D, 30, 2, 64, 1)
+    g = m.Muca(m.ISING2D, 8, 2, 8, 1)
+    with pytest.raises(m.MucaError):
+        m.muca_get_lnW(g.h, np.zeros(3))
+    g.iterate(1)
+    with pytest.raises(m.MucaError) as e:
+        g.set_param("record", 1)
+    assert e.value.code == -5
+    with pytest.raises(m.MucaError):
+        g.set_param("nonsense", 1)
+    with pytest.raises(m.MucaError):
+        g.iterate(0)
+    bad = np.zeros(10, dtype=np.uint8)
+    with pytest.raises(m.MucaError):
+        g.set_state(bad)
+
+
+def test_p_equals_one_and_tiny_lattice():
+    run_pair(m.ISING2D, 4, 2, 1, seed=8, iters=3, sweeps=200, nthreads=1)
+    run_pair(m.POTTS2D, 4, 16, 1, seed=8, iters=3, sweeps=200, nthreads=1)
