@@ -154,6 +154,27 @@ int muca_get_sweep_counter(muca_ctx *ctx, int64_t *host_out);
  * use -- on n host values, on the current device.  Synchronous. */
 int muca_det_math(int fn, const double *host_in, double *host_out, int64_t n);
 
+/* No-allocation variant of one iteration's sweeps and histogram merge.
+ * The paper has no counterpart: this serves callers that cannot call cudaMalloc
+ * when they run an iteration (code that must not allocate during CUDA graph
+ * capture, hosts whose memory pools forbid raw driver allocations, processes at
+ * their device-memory limit).  It runs `sweeps` sweeps of every walker of `ctx`
+ * (like muca_iterate) and writes the merged histogram of exactly these sweeps to
+ * the caller's DEVICE buffer dev_H_out (B uint64, overwritten; the context's own
+ * open histogram and H are not touched, the weights are not updated).  Walkers,
+ * bins and the sweep counter advance as with muca_iterate.
+ * Scratch: the per-block partial histograms live in one static device array of
+ * 2^19 uint64 slots (4 MiB) that every GPU loading the library holds until the
+ * process exits; a call needs ceil(p/block) * B slots and returns MUCA_ERR_RANGE
+ * beyond that.  The call allocates nothing: no cudaMalloc, no cudaFree.
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) for the device that is current; make that first call
+ * before any stream capture.  Every call uses the same array (it clears the
+ * slots it needs first), so calls whose GPU work overlaps -- on two streams, or
+ * two contexts on the same device from two threads -- race and give wrong
+ * histograms; serialise them. */
+int muca_iterate_noalloc(muca_ctx *ctx, int64_t sweeps, uint64_t *dev_H_out);
+
 /* Wait for the context's stream. */
 int muca_synchronize(muca_ctx *ctx);
 

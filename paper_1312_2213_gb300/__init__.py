@@ -22,7 +22,8 @@ __all__ = ["Muca", "MucaError", "ISING2D", "POTTS2D", "ISING2D_MUMA", "POLYMER3D
            "muca_iterate", "muca_merge_and_update", "muca_num_bins", "muca_get_lnW", "muca_get_lnW_sampled",
            "muca_get_histogram", "muca_get_flatness", "muca_get_reweight", "muca_get_state", "muca_set_state",
            "muca_get_spins", "muca_get_walker_bins", "muca_get_thresholds", "muca_get_sweep_counter",
-           "muca_synchronize", "muca_free", "muca_last_error", "muca_det_math"]
+           "muca_synchronize", "muca_free", "muca_last_error", "muca_det_math",
+           "muca_iterate_noalloc"]
 
 
 def _p(a: np.ndarray):
@@ -133,6 +134,12 @@ def muca_det_math(fn: int, x: np.ndarray) -> np.ndarray:
     out = np.zeros_like(x)
     check(load().muca_det_math(fn, _p(x), _p(out), x.size), "muca_det_math")
     return out
+
+
+def muca_iterate_noalloc(h, sweeps: int, dev_H_out: int):
+    """Sweeps + merge into a caller-provided device buffer, with no device allocation
+    (partial histograms in the library's static device array; see include/muca.h)."""
+    check(load().muca_iterate_noalloc(h, sweeps, ctypes.c_void_p(dev_H_out)), "muca_iterate_noalloc")
 
 
 def muca_synchronize(h):

@@ -39,6 +39,7 @@ PROTOTYPES = {
     "muca_get_thresholds": (c_int, [c_vp, c_vp, c_i64]),
     "muca_get_sweep_counter": (c_int, [c_vp, P(c_i64)]),
     "muca_det_math": (c_int, [c_int, c_vp, c_vp, c_i64]),
+    "muca_iterate_noalloc": (c_int, [c_vp, c_i64, c_vp]),
     "muca_synchronize": (c_int, [c_vp]),
     "muca_free": (c_int, [c_vp]),
 }

@@ -5,6 +5,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -642,3 +643,91 @@ int muca_free(muca_ctx *c)
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// No-allocation variant of one iteration's sweeps + histogram merge.
+//
+// Some callers cannot call cudaMalloc at the point where they run an iteration:
+// code that must not allocate while a CUDA graph is being captured, hosts whose
+// memory pools forbid raw driver allocations, or processes that run the GPU at
+// its memory limit and cannot risk an allocation failure mid-run.  For them this
+// entry point keeps the per-block partial histograms of the sweep kernel in a
+// fixed array that is part of the library image instead of in memory allocated
+// at run time.  The array is a file-scope __device__ array: every GPU that loads
+// the library holds it (4 MiB) until the process exits.
+namespace {
+
+constexpr size_t kStaticHistSlots = size_t(1) << 19;  // 524288 uint64 bins = 4 MiB
+static __device__ __align__(256) unsigned long long g_static_hist[kStaticHistSlots];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_static_mu;
+unsigned long long *g_static_ptr[kMaxDevices] = {};
+
+// Device address of g_static_hist on the current device, looked up once per
+// device (host code cannot use the symbol itself: in host code its name is a
+// host-side stand-in, not a device address).
+int static_hist_ptr(unsigned long long **out)
+{
+    int dev = 0;
+    MUCA_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxDevices) return fail(MUCA_ERR_RANGE, "device %d beyond the supported %d", dev, kMaxDevices);
+    std::lock_guard<std::mutex> lock(g_static_mu);
+    if (!g_static_ptr[dev]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_static_hist);
+        if (e != cudaSuccess)
+            return fail(MUCA_ERR_CUDA, "cudaGetSymbolAddress(g_static_hist): %s", cudaGetErrorString(e));
+        g_static_ptr[dev] = (unsigned long long *)p;
+    }
+    *out = g_static_ptr[dev];
+    return MUCA_OK;
+}
+
+}  // namespace
+
+extern "C" int muca_iterate_noalloc(muca_ctx *c, int64_t sweeps, uint64_t *dev_H_out)
+{
+    if (int rc = check_ctx(c)) return rc;
+    if (sweeps < 1) return fail(MUCA_ERR_ARG, "sweeps must be >= 1");
+    if (!dev_H_out) return fail(MUCA_ERR_ARG, "dev_H_out is NULL");
+    const size_t nblocks = (size_t)((c->p + c->block - 1) / c->block);
+    const size_t need = nblocks * (size_t)c->B;
+    if (need > kStaticHistSlots)
+        return fail(MUCA_ERR_RANGE,
+                    "muca_iterate_noalloc: %zu thread blocks x %d bins = %zu partial-histogram slots exceed the "
+                    "static maximum of %zu (use fewer walkers, a larger block, or muca_iterate)",
+                    nblocks, c->B, need, kStaticHistSlots);
+    unsigned long long *scratch = nullptr;
+    if (int rc = static_hist_ptr(&scratch)) return rc;
+    // The array keeps whatever the previous call left in it: clear the slots used here.
+    MUCA_CUDA(cudaMemsetAsync(scratch, 0, need * sizeof(unsigned long long), c->stream));
+    SpinSweepArgs a{};
+    a.T = c->T;
+    a.lattice = c->lat;
+    a.bin = c->bin;
+    a.Hpart = scratch;
+    a.state = c->state;
+    a.p = c->p;
+    a.pstride = c->pstride;
+    a.B = c->B;
+    a.q = c->q;
+    a.sweeps = sweeps;
+    const unsigned long long per_sweep = (unsigned long long)c->block * (c->record == 0 ? (unsigned)c->N : 1u);
+    unsigned long long fe = 0xFFFFFFFFull / per_sweep;
+    if (fe < 1) fe = 1;
+    if (fe > (unsigned long long)sweeps) fe = (unsigned long long)sweeps;
+    a.flush_every = (int)(fe > 0x7fffffffull ? 0x7fffffffull : fe);
+    a.key0 = (uint32_t)(c->seed & 0xffffffffu);
+    a.key1 = (uint32_t)(c->seed >> 32);
+    a.record = c->record;
+    a.walker_offset = c->walker_offset;
+    MUCA_CUDA(launch_spin_sweep(c->system, c->L, a, c->block, c->stream));
+    MUCA_CUDA(launch_advance(c->state, sweeps, c->stream));
+    UpdateArgs u = update_args(c);
+    u.Hpart = scratch;
+    u.H = (unsigned long long *)dev_H_out;
+    MUCA_CUDA(launch_merge(u, c->stream));
+    c->started = true;
+    return MUCA_OK;
+}
