@@ -380,8 +380,7 @@ int muca_iterate(muca_ctx *c, int64_t sweeps)
     if (fe < 1) fe = 1;
     if (fe > (unsigned long long)sweeps) fe = (unsigned long long)sweeps;
     a.flush_every = (int)(fe > 0x7fffffffull ? 0x7fffffffull : fe);
-    a.key0 = (uint32_t)(c->seed & 0xffffffffu);
-    a.key1 = (uint32_t)(c->seed >> 32);
+    fill_round_keys(a, c->seed);
     a.record = c->record;
     a.walker_offset = c->walker_offset;
     MUCA_CUDA(launch_spin_sweep(c->system, c->L, a, c->block, c->stream));
@@ -718,8 +717,7 @@ extern "C" int muca_iterate_noalloc(muca_ctx *c, int64_t sweeps, uint64_t *dev_H
     if (fe < 1) fe = 1;
     if (fe > (unsigned long long)sweeps) fe = (unsigned long long)sweeps;
     a.flush_every = (int)(fe > 0x7fffffffull ? 0x7fffffffull : fe);
-    a.key0 = (uint32_t)(c->seed & 0xffffffffu);
-    a.key1 = (uint32_t)(c->seed >> 32);
+    fill_round_keys(a, c->seed);
     a.record = c->record;
     a.walker_offset = c->walker_offset;
     MUCA_CUDA(launch_spin_sweep(c->system, c->L, a, c->block, c->stream));

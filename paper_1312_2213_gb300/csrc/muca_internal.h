@@ -38,7 +38,22 @@ struct SpinSweepArgs {
     uint32_t key0, key1;
     int record;
     int walker_offset;       // global id of walker 0 (for sharding)
+    uint32_t rk[20];         // Philox round keys (k0 + r*W0, k1 + r*W1), r = 0..9
 };
+
+// Philox round keys for a seed: round r uses (lo + r*W0, hi + r*W1).
+inline void fill_round_keys(SpinSweepArgs &a, uint64_t seed)
+{
+    uint32_t k0 = (uint32_t)(seed & 0xffffffffu), k1 = (uint32_t)(seed >> 32);
+    a.key0 = k0;
+    a.key1 = k1;
+    for (int r = 0; r < 10; ++r) {
+        a.rk[2 * r] = k0;
+        a.rk[2 * r + 1] = k1;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+}
 
 // Layout helpers shared by host and kernels.
 __host__ __device__ constexpr int ising_words_per_row(int L) { return (L + 31) / 32; }

@@ -11,18 +11,32 @@
 //   -> accept iff T[b][c] == always or u < T[b][c]   (integer compare)
 //   -> flip / recolour, move the bin
 //   -> count the current bin in the block's shared-memory histogram.
-// Lattice rows live in HBM/L2 walker-interleaved (coalesced) and are streamed
-// through registers: each thread keeps the row above, the current row and
-// the row below, and prefetches the next one while it works on this one.
+//
+// Latency structure.  With p = 8192 walkers there is one warp per scheduler,
+// so nothing hides a walker's serial chain: the shared-memory threshold load
+// would sit between two consecutive accept decisions.  The sweep therefore
+// loads, for site x+1, both thresholds it can need -- the one for "site x
+// rejected" (same bin, left neighbour unchanged) and the one for "site x
+// accepted" (bin moved by site x's energy change, left neighbour flipped) --
+// while site x is being decided, and then selects one.  Every such index is the
+// bin of a configuration that can occur, so it is always inside the table.
+// Philox blocks are computed one group ahead, with the round keys read from
+// the kernel parameters.
+//
+// Shared memory holds one row of RS = C+1 words per bin: the C thresholds and
+// the bin's histogram counter, so one row offset addresses both.
+// Lattice rows live in HBM/L2 walker-interleaved (coalesced) and stream through
+// registers: the row above (final), the current row and the row below (old),
+// with the next row prefetched one row ahead.
 #include "muca_device.cuh"
 #include "muca_internal.h"
 
 namespace muca {
 
 template <int WR>
-__device__ __forceinline__ uint32_t bit_at(const uint32_t (&r)[WR], int pos)
+__device__ __forceinline__ int bit_at(const uint32_t (&r)[WR], int pos)
 {
-    return (r[pos >> 5] >> (pos & 31)) & 1u;
+    return (int)((r[pos >> 5] >> (pos & 31)) & 1u);
 }
 
 template <int WR>
@@ -31,18 +45,24 @@ __device__ __forceinline__ uint32_t nib_at(const uint32_t (&r)[WR], int x)
     return (r[(4 * x) >> 5] >> ((4 * x) & 31)) & 15u;
 }
 
+__device__ __forceinline__ uint32_t word_of(const uint4 &u, int j)
+{
+    return j == 0 ? u.x : (j == 1 ? u.y : (j == 2 ? u.z : u.w));
+}
+
 // One sweep of an Ising (MUCA in E) or multimagnetic (weight in M) walker.
 // Spin bit 1 means s = -1.  k = 4 - (number of anti-aligned neighbours), so
-// dE = 4(k-2); Ising column c = k, bin move k-2; MUMA column c = 5*bit + k,
-// bin (M+N)/2 moves by 2*bit-1.
+// dE = 4(k-2); Ising column c = k and the bin moves by k-2; MUMA column
+// c = 5*bit + k and the bin (M+N)/2 moves by 2*bit-1.
 template <int SYS, int L>
-__device__ __forceinline__ void ising_sweep(uint32_t *__restrict__ lat, int ps, int &b,
-                                            const uint32_t *__restrict__ sT, uint32_t *__restrict__ sH,
-                                            uint32_t g, uint32_t wid, uint32_t k0, uint32_t k1, int record)
+__device__ __forceinline__ void ising_sweep(uint32_t *__restrict__ lat, int ps, int &bR,
+                                            uint32_t *__restrict__ sTH, uint32_t g, uint32_t wid,
+                                            const uint32_t (&rk)[20], int record)
 {
     constexpr int WR = ising_words_per_row(L);
     constexpr int C = (SYS == kMuma) ? 10 : 5;
-    uint32_t up[WR], cur[WR], dn[WR], first[WR], nxt[WR];
+    constexpr int RS = C + 1;
+    uint32_t up[WR], cur[WR], dn[WR], first[WR], nxt[WR], old[WR];
 #pragma unroll
     for (int j = 0; j < WR; ++j) {
         up[j] = lat[((L - 1) * WR + j) * ps];
@@ -51,7 +71,7 @@ __device__ __forceinline__ void ising_sweep(uint32_t *__restrict__ lat, int ps, 
         first[j] = 0u;
         nxt[j] = 0u;
     }
-    int bC = b * C;
+    uint4 u_next = philox4x32_10_rk(make_uint4(0u, g, wid, kTagSweep), rk);
 #pragma unroll 1
     for (int y = 0; y < L; ++y) {
         if (y + 2 < L) {
@@ -59,33 +79,61 @@ __device__ __forceinline__ void ising_sweep(uint32_t *__restrict__ lat, int ps, 
             for (int j = 0; j < WR; ++j) nxt[j] = lat[((y + 2) * WR + j) * ps];
         }
 #pragma unroll
-        for (int gq = 0; gq < L / 4; ++gq) {
-            const uint4 u = philox4x32_10(make_uint4((uint32_t)(y * (L / 4) + gq), g, wid, kTagSweep), k0, k1);
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const int x = 4 * gq + j;
-                const uint32_t uw = j == 0 ? u.x : (j == 1 ? u.y : (j == 2 ? u.z : u.w));
-                const uint32_t s = bit_at<WR>(cur, x);
-                const int n1 = (int)(bit_at<WR>(cur, (x + L - 1) % L) + bit_at<WR>(cur, (x + 1) % L) +
-                                     bit_at<WR>(up, x) + bit_at<WR>(dn, x));
-                const int k = s ? n1 : 4 - n1;
-                int col, db;
-                if (SYS == kMuma) {
-                    col = 5 * (int)s + k;
-                    db = 2 * (int)s - 1;
-                } else {
-                    col = k;
-                    db = k - 2;
-                }
-                const uint32_t t = sT[bC + col];
-                if (t == kAlways || uw < t) {
-                    cur[x >> 5] ^= 1u << (x & 31);
-                    b += db;
-                    bC += db * C;
-                }
-                if (record == 0) atomicAdd(&sH[b], 1u);
+        for (int j = 0; j < WR; ++j) old[j] = cur[j];
+        // Columns and bin-row moves of site x for "left neighbour as it was"
+        // (c0, d0) and "left neighbour flipped" (c1, d1), from the row's old
+        // values; the right neighbour of the last site is site 0 of this row,
+        // already final.
+        auto site = [&](int x, int &c0, int &c1, int &d0, int &d1) {
+            const int s = bit_at<WR>(old, x);
+            const int l = bit_at<WR>(old, (x + L - 1) % L);
+            const int r = (x == L - 1) ? bit_at<WR>(cur, 0) : bit_at<WR>(old, x + 1);
+            const int n1 = l + r + bit_at<WR>(up, x) + bit_at<WR>(dn, x);
+            const int k0 = s ? n1 : 4 - n1;
+            const int k1 = k0 - 1 + 2 * (l ^ s);
+            if (SYS == kMuma) {
+                c0 = 5 * s + k0;
+                c1 = 5 * s + k1;
+                d0 = d1 = (2 * s - 1) * RS;
+            } else {
+                c0 = k0;
+                c1 = k1;
+                d0 = (k0 - 2) * RS;
+                d1 = (k1 - 2) * RS;
             }
+        };
+        int c0, c1, d0, d1;
+        site(0, c0, c1, d0, d1);
+        uint32_t T0 = sTH[bR + c0], T1 = 0u;
+        bool accP = false;
+        int dRp = 0;
+        uint4 u = u_next;
+#pragma unroll
+        for (int x = 0; x < L; ++x) {
+            if ((x & 3) == 0) {
+                u = u_next;
+                if (!(y == L - 1 && x == L - 4))
+                    u_next = philox4x32_10_rk(make_uint4((uint32_t)((y * L + x) / 4 + 1), g, wid, kTagSweep), rk);
+            }
+            const uint32_t uw = word_of(u, x & 3);
+            bR = accP ? bR + dRp : bR;
+            const int dR = accP ? d1 : d0;
+            const uint32_t T = accP ? T1 : T0;
+            if (x + 1 < L) {
+                int n0, n1c, e0, e1;
+                site(x + 1, n0, n1c, e0, e1);
+                T0 = sTH[bR + n0];
+                T1 = sTH[bR + dR + n1c];
+                d0 = e0;
+                d1 = e1;
+            }
+            const bool acc = (T == kAlways) || (uw < T);
+            if (acc) cur[x >> 5] ^= 1u << (x & 31);
+            if (record == 0) atomicAdd(&sTH[(acc ? bR + dR : bR) + C], 1u);
+            accP = acc;
+            dRp = dR;
         }
+        bR = accP ? bR + dRp : bR;
 #pragma unroll
         for (int j = 0; j < WR; ++j) lat[(y * WR + j) * ps] = cur[j];
         if (y == 0) {
@@ -99,20 +147,21 @@ __device__ __forceinline__ void ising_sweep(uint32_t *__restrict__ lat, int ps, 
             dn[j] = (y + 2 < L) ? nxt[j] : first[j];
         }
     }
-    if (record == 1) atomicAdd(&sH[b], 1u);
+    if (record == 1) atomicAdd(&sTH[bR + C], 1u);
 }
 
 // One sweep of a q-state Potts walker (4-bit spins).  Proposal: a uniform new
 // state different from the old one, new = (old + 1 + mulhi(u, q-1)) mod q.
 // dE = n_eq(old) - n_eq(new) in [-4, 4]; column dE+4; bin E+2N moves by dE.
+// The "left neighbour changed" candidate uses the left site's proposed colour.
 template <int L>
-__device__ __forceinline__ void potts_sweep(uint32_t *__restrict__ lat, int ps, int &b,
-                                            const uint32_t *__restrict__ sT, uint32_t *__restrict__ sH,
-                                            uint32_t g, uint32_t wid, uint32_t k0, uint32_t k1, int record,
-                                            uint32_t q)
+__device__ __forceinline__ void potts_sweep(uint32_t *__restrict__ lat, int ps, int &bR,
+                                            uint32_t *__restrict__ sTH, uint32_t g, uint32_t wid,
+                                            const uint32_t (&rk)[20], int record, uint32_t q)
 {
     constexpr int WR = potts_words_per_row(L);
-    uint32_t up[WR], cur[WR], dn[WR], first[WR], nxt[WR];
+    constexpr int RS = 10;
+    uint32_t up[WR], cur[WR], dn[WR], first[WR], nxt[WR], old[WR];
 #pragma unroll
     for (int j = 0; j < WR; ++j) {
         up[j] = lat[((L - 1) * WR + j) * ps];
@@ -122,7 +171,7 @@ __device__ __forceinline__ void potts_sweep(uint32_t *__restrict__ lat, int ps, 
         nxt[j] = 0u;
     }
     const uint32_t qm1 = q - 1u;
-    int b9 = b * 9;
+    uint4 u_next = philox4x32_10_rk(make_uint4(0u, g, wid, kTagSweep), rk);
 #pragma unroll 1
     for (int y = 0; y < L; ++y) {
         if (y + 2 < L) {
@@ -130,31 +179,64 @@ __device__ __forceinline__ void potts_sweep(uint32_t *__restrict__ lat, int ps, 
             for (int j = 0; j < WR; ++j) nxt[j] = lat[((y + 2) * WR + j) * ps];
         }
 #pragma unroll
-        for (int gp = 0; gp < L / 2; ++gp) {
-            const uint4 u = philox4x32_10(make_uint4((uint32_t)(y * (L / 2) + gp), g, wid, kTagSweep), k0, k1);
+        for (int j = 0; j < WR; ++j) old[j] = cur[j];
+        // Proposal and energy change of site x, for the left neighbour as it was
+        // (c0, d0) and recoloured to the left site's proposal lnw (c1, d1).
+        auto site = [&](int x, uint32_t uprop, uint32_t lnw, uint32_t &nw, int &c0, int &c1, int &d0, int &d1) {
+            const uint32_t o = nib_at<WR>(old, x);
+            const uint32_t nl = nib_at<WR>(old, (x + L - 1) % L);
+            const uint32_t nr = (x == L - 1) ? nib_at<WR>(cur, 0) : nib_at<WR>(old, x + 1);
+            const uint32_t nu = nib_at<WR>(up, x), nd = nib_at<WR>(dn, x);
+            uint32_t v = o + 1u + __umulhi(uprop, qm1);
+            v = (v >= q) ? v - q : v;
+            nw = v;
+            const int rest = (int)(nr == o) + (int)(nu == o) + (int)(nd == o) - (int)(nr == v) - (int)(nu == v) -
+                             (int)(nd == v);
+            const int dE0 = rest + (int)(nl == o) - (int)(nl == v);
+            const int dE1 = rest + (int)(lnw == o) - (int)(lnw == v);
+            c0 = dE0 + 4;
+            c1 = dE1 + 4;
+            d0 = dE0 * RS;
+            d1 = dE1 * RS;
+        };
+        uint4 u = u_next;
+        uint32_t nwc;
+        int c0, c1, d0, d1;
+        site(0, u.x, 0u, nwc, c0, c1, d0, d1);
+        uint32_t T0 = sTH[bR + c0], T1 = 0u;
+        bool accP = false;
+        int dRp = 0;
 #pragma unroll
-            for (int j = 0; j < 2; ++j) {
-                const int x = 2 * gp + j;
-                const uint32_t u_prop = j ? u.z : u.x;
-                const uint32_t u_acc = j ? u.w : u.y;
-                const uint32_t old = nib_at<WR>(cur, x);
-                const uint32_t nl = nib_at<WR>(cur, (x + L - 1) % L), nr = nib_at<WR>(cur, (x + 1) % L);
-                const uint32_t nu = nib_at<WR>(up, x), nd = nib_at<WR>(dn, x);
-                uint32_t nw = old + 1u + __umulhi(u_prop, qm1);
-                nw = (nw >= q) ? nw - q : nw;
-                const int eo = (int)(nl == old) + (int)(nr == old) + (int)(nu == old) + (int)(nd == old);
-                const int en = (int)(nl == nw) + (int)(nr == nw) + (int)(nu == nw) + (int)(nd == nw);
-                const int dE = eo - en;
-                const uint32_t t = sT[b9 + dE + 4];
-                if (t == kAlways || u_acc < t) {
-                    const int wi = (4 * x) >> 5, sh = (4 * x) & 31;
-                    cur[wi] = (cur[wi] & ~(15u << sh)) | (nw << sh);
-                    b += dE;
-                    b9 += 9 * dE;
-                }
-                if (record == 0) atomicAdd(&sH[b], 1u);
+        for (int x = 0; x < L; ++x) {
+            if ((x & 1) == 0) {
+                u = u_next;
+                if (!(y == L - 1 && x == L - 2))
+                    u_next = philox4x32_10_rk(make_uint4((uint32_t)((y * L + x) / 2 + 1), g, wid, kTagSweep), rk);
             }
+            const uint32_t u_acc = (x & 1) ? u.w : u.y;
+            bR = accP ? bR + dRp : bR;
+            const int dR = accP ? d1 : d0;
+            const uint32_t T = accP ? T1 : T0;
+            const uint32_t nw = nwc;
+            if (x + 1 < L) {
+                const uint32_t uprop = ((x + 1) & 1) ? u.z : u_next.x;
+                int n0, n1c, e0, e1;
+                site(x + 1, uprop, nw, nwc, n0, n1c, e0, e1);
+                T0 = sTH[bR + n0];
+                T1 = sTH[bR + dR + n1c];
+                d0 = e0;
+                d1 = e1;
+            }
+            const bool acc = (T == kAlways) || (u_acc < T);
+            if (acc) {
+                const int wi = (4 * x) >> 5, sh = (4 * x) & 31;
+                cur[wi] = (cur[wi] & ~(15u << sh)) | (nw << sh);
+            }
+            if (record == 0) atomicAdd(&sTH[(acc ? bR + dR : bR) + 9], 1u);
+            accP = acc;
+            dRp = dR;
         }
+        bR = accP ? bR + dRp : bR;
 #pragma unroll
         for (int j = 0; j < WR; ++j) lat[(y * WR + j) * ps] = cur[j];
         if (y == 0) {
@@ -168,22 +250,25 @@ __device__ __forceinline__ void potts_sweep(uint32_t *__restrict__ lat, int ps, 
             dn[j] = (y + 2 < L) ? nxt[j] : first[j];
         }
     }
-    if (record == 1) atomicAdd(&sH[b], 1u);
+    if (record == 1) atomicAdd(&sTH[bR + 9], 1u);
 }
 
-// The sweep kernel: stage the threshold table in shared memory, run the
-// walkers, flush the block histogram to its own uint64 slot every
-// `flush_every` sweeps (so no uint32 bin can overflow) and at the end.
+// The sweep kernel: stage the threshold table in shared memory (rows of C
+// thresholds + 1 histogram counter), run the walkers, flush the block
+// histogram to its own uint64 slot every `flush_every` sweeps (so no uint32
+// counter can overflow) and at the end.
 template <int SYS, int L>
 __global__ void __launch_bounds__(kMaxSweepBlock) k_sweep_spin(const SpinSweepArgs a)
 {
     constexpr int C = num_cols(SYS);
+    constexpr int RS = C + 1;
     extern __shared__ __align__(16) uint32_t smem[];
-    uint32_t *sT = smem;
-    uint32_t *sH = smem + (size_t)a.B * C;
+    uint32_t *sTH = smem;
     const int tid = threadIdx.x;
-    for (int i = tid; i < a.B * C; i += blockDim.x) sT[i] = a.T[i];
-    for (int i = tid; i < a.B; i += blockDim.x) sH[i] = 0u;
+    for (int i = tid; i < a.B * RS; i += blockDim.x) {
+        const int b = i / RS, c = i - (i / RS) * RS;
+        sTH[i] = (c < C) ? a.T[b * C + c] : 0u;
+    }
     __syncthreads();
 
     const int w = blockIdx.x * blockDim.x + tid;
@@ -191,7 +276,7 @@ __global__ void __launch_bounds__(kMaxSweepBlock) k_sweep_spin(const SpinSweepAr
     const uint32_t wid = (uint32_t)(w + a.walker_offset);
     const uint32_t g0 = (uint32_t)a.state->sweep_counter;
     uint32_t *lat = a.lattice + (active ? w : 0);
-    int b = active ? a.bin[w] : 0;
+    int bR = (active ? a.bin[w] : 0) * RS;
     unsigned long long *Hb = a.Hpart + (size_t)blockIdx.x * a.B;
 
     for (int64_t s0 = 0; s0 < a.sweeps; s0 += a.flush_every) {
@@ -201,22 +286,22 @@ __global__ void __launch_bounds__(kMaxSweepBlock) k_sweep_spin(const SpinSweepAr
             for (int64_t sw = s0; sw < s1; ++sw) {
                 const uint32_t g = g0 + (uint32_t)sw;
                 if (SYS == kPotts)
-                    potts_sweep<L>(lat, a.pstride, b, sT, sH, g, wid, a.key0, a.key1, a.record, (uint32_t)a.q);
+                    potts_sweep<L>(lat, a.pstride, bR, sTH, g, wid, a.rk, a.record, (uint32_t)a.q);
                 else
-                    ising_sweep<SYS, L>(lat, a.pstride, b, sT, sH, g, wid, a.key0, a.key1, a.record);
+                    ising_sweep<SYS, L>(lat, a.pstride, bR, sTH, g, wid, a.rk, a.record);
             }
         }
         __syncthreads();
-        for (int i = tid; i < a.B; i += blockDim.x) {
-            const uint32_t c = sH[i];
+        for (int b = tid; b < a.B; b += blockDim.x) {
+            const uint32_t c = sTH[b * RS + C];
             if (c) {
-                Hb[i] += c;
-                sH[i] = 0u;
+                Hb[b] += c;
+                sTH[b * RS + C] = 0u;
             }
         }
         __syncthreads();
     }
-    if (active) a.bin[w] = b;
+    if (active) a.bin[w] = bR / RS;
 }
 
 size_t spin_sweep_smem_bytes(int system, int B) { return (size_t)B * (num_cols(system) + 1) * sizeof(uint32_t); }
