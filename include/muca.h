@@ -149,6 +149,25 @@ int muca_get_walker_bins(muca_ctx *ctx, int32_t *host_out, int p);
 int muca_get_thresholds(muca_ctx *ctx, uint32_t *host_out, int64_t n);
 int muca_get_sweep_counter(muca_ctx *ctx, int64_t *host_out);
 
+/* Batching.  A batch advances several contexts together -- different systems,
+ * lattice sizes and walker counts, e.g. Ising L in {16..64} and q = 10 Potts
+ * L in {16..48} with 2048 walkers each -- so that systems too small to fill the
+ * GPU alone fill it together.  Each iteration of muca_batch_run is the paper's
+ * Fig. 1 step for every system at once: sweeps of all walkers of all systems in
+ * ONE persistent kernel launch over a tile list, then the merge, the
+ * accumulated-statistics recursion and the threshold rebuild for all systems
+ * (one launch each).  With use_graph != 0 all n_iter iterations are captured
+ * once into a CUDA graph (re-captured when n_iter or sweeps change) and
+ * launched as one graph.  Results are bit-identical to running each context on
+ * its own with muca_iterate + muca_merge_and_update: a walker's random stream
+ * depends only on (seed, walker, sweep).
+ * muca_batch_create: the contexts must use the same stream and stay alive
+ * until muca_batch_free; the batch owns a small device descriptor table.
+ * muca_batch_run: every context must have no unmerged sweeps (MUCA_ERR_STATE). */
+int muca_batch_create(muca_ctx *const *systems, int n, muca_batch **out);
+int muca_batch_run(muca_batch *batch, int n_iter, int64_t sweeps, int use_graph);
+int muca_batch_free(muca_batch *batch);
+
 /* Diagnostics: evaluate the library's deterministic binary64 exp (fn = 0) or
  * log (fn = 1) -- the functions the weight recursion and the threshold build
  * use -- on n host values, on the current device.  Synchronous. */

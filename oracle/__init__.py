@@ -99,9 +99,12 @@ def _bind_polymer(L):
     L.orc_poly_iterate_range.argtypes = [c.c_void_p, c.c_int64, c.c_int, c.c_int, c.c_int]
     L.orc_poly_advance.argtypes = [c.c_void_p, c.c_int64]
     L.orc_poly_update.argtypes = [c.c_void_p]
-    for name in ("orc_poly_get_lnW", "orc_poly_get_histogram", "orc_poly_get_coords",
+    for name in ("orc_poly_get_lnW", "orc_poly_get_lnW_sampled", "orc_poly_get_histogram", "orc_poly_get_coords",
                  "orc_poly_get_energy", "orc_poly_get_bins", "orc_poly_get_counters"):
         getattr(L, name).argtypes = [c.c_void_p, c.c_void_p]
+    L.orc_poly_set_beta.argtypes = [c.c_void_p, c.c_double]
+    L.orc_poly_refresh_energy.argtypes = [c.c_void_p]
+    L.orc_poly_refresh_energy.restype = c.c_double
     L.orc_poly_energy.argtypes = [c.c_int, c.c_void_p, c.c_int]
     L.orc_poly_energy.restype = c.c_double
     L.orc_poly_pair.argtypes = [c.c_double, c.c_int, c.c_int]
@@ -260,3 +263,76 @@ def tm_potts(L: int, q: int) -> list:
     out = np.zeros(2 * (2 * N + 1), dtype=np.uint64)
     assert lib().orc_tm_potts(L, q, _ptr(out)) == 0
     return _u128(out)
+
+
+class PolyRun:
+    """Oracle multicanonical run of a bead-spring polymer of N beads (p walkers)."""
+
+    def __init__(self, N: int, p: int, seed: int, e_lo: float, e_hi: float, K: float = 40.0, R: float = 1.5,
+                 record: int = 0, beta: float = 0.0):
+        self._lib = lib()
+        self.h = self._lib.orc_poly_create(N, p, seed, e_lo, e_hi, K, R, record)
+        if not self.h:
+            raise ValueError("oracle: bad polymer configuration")
+        self.N, self.p = N, p
+        self.B = self._lib.orc_poly_num_bins(self.h)
+        if beta > 0:
+            self._lib.orc_poly_set_beta(self.h, beta)
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            self._lib.orc_poly_free(self.h)
+            self.h = None
+
+    def init(self):
+        self._lib.orc_poly_init(self.h)
+
+    def iterate(self, sweeps: int, nthreads: int = 1):
+        self._lib.orc_poly_iterate(self.h, sweeps, nthreads)
+
+    def iterate_range(self, sweeps: int, w0: int, w1: int, nthreads: int = 1):
+        self._lib.orc_poly_iterate_range(self.h, sweeps, w0, w1, nthreads)
+
+    def advance(self, sweeps: int):
+        self._lib.orc_poly_advance(self.h, sweeps)
+
+    def update(self):
+        self._lib.orc_poly_update(self.h)
+
+    def refresh_energy(self) -> float:
+        return self._lib.orc_poly_refresh_energy(self.h)
+
+    def _get(self, name, n, dtype):
+        a = np.zeros(n, dtype=dtype)
+        getattr(self._lib, name)(self.h, _ptr(a))
+        return a
+
+    def lnW(self):
+        return self._get("orc_poly_get_lnW", self.B, np.float64)
+
+    def lnW_sampled(self):
+        return self._get("orc_poly_get_lnW_sampled", self.B, np.float64)
+
+    def histogram(self):
+        return self._get("orc_poly_get_histogram", self.B, np.uint64)
+
+    def coords(self):
+        return self._get("orc_poly_get_coords", self.p * self.N * 3, np.float64).reshape(self.p, self.N, 3)
+
+    def energy(self):
+        return self._get("orc_poly_get_energy", self.p, np.float64)
+
+    def bins(self):
+        return self._get("orc_poly_get_bins", self.p, np.int32)
+
+    def counters(self):
+        return self._get("orc_poly_get_counters", 2, np.int64)
+
+
+def poly_energy(X: np.ndarray) -> float:
+    X = np.ascontiguousarray(X, dtype=np.float64)
+    return lib().orc_poly_energy(X.shape[0], _ptr(X), 0)
+
+
+def poly_pair(r: float, sep: int) -> float:
+    return lib().orc_poly_pair(float(r), int(sep), 0)

@@ -79,6 +79,27 @@ int orc_bruteforce_potts(int L, int q, uint64_t *omega /* 2N+1, index E+2N */);
 int orc_tm_ising(int L, int track_m, uint64_t *out);
 int orc_tm_potts(int L, int q, uint64_t *out /* index E+2N */);
 
+/* Polymer (Eq. 7 reading, see polymer_oracle.c).  Handles are opaque. */
+void *orc_poly_create(int N, int p, uint64_t seed, double e_lo, double e_hi, double K, double R, int record);
+void orc_poly_free(void *h);
+int orc_poly_num_bins(void *h);
+void orc_poly_set_beta(void *h, double beta);
+void orc_poly_init(void *h);
+void orc_poly_iterate(void *h, int64_t sweeps, int nthreads);
+void orc_poly_iterate_range(void *h, int64_t sweeps, int w0, int w1, int nthreads);
+void orc_poly_advance(void *h, int64_t sweeps);
+void orc_poly_update(void *h);
+double orc_poly_refresh_energy(void *h);
+void orc_poly_get_lnW(void *h, double *out);
+void orc_poly_get_lnW_sampled(void *h, double *out);
+void orc_poly_get_histogram(void *h, uint64_t *out);
+void orc_poly_get_coords(void *h, double *out /* p*N*3 */);
+void orc_poly_get_energy(void *h, double *out /* p */);
+void orc_poly_get_bins(void *h, int32_t *out /* p */);
+void orc_poly_get_counters(void *h, int64_t *out /* {near-tie acceptances, bin-edge events} */);
+double orc_poly_energy(int N, const double *X, int unused);
+double orc_poly_pair(double r, int sep, int unused);
+
 #ifdef __cplusplus
 }
 #endif

@@ -1,0 +1,402 @@
+/*
+ * polymer_oracle.c -- plain CPU oracle of the multicanonical simulation of a
+ * single flexible bead-spring polymer (paper: polymer paragraph, Eq. 7).
+ * TEST INFRASTRUCTURE ONLY (tests, smoke check, CPU-baseline leg of the bench).
+ *
+ * Hamiltonian (reading of Eq. 7 with the benchmark's parameters):
+ *   E = sum_{|i-j| >= 2} V_LJ(r_ij) + sum_i V_FENE(r_{i,i+1})
+ *   V_LJ(r)   = 4 [(1/r)^12 - (1/r)^6] - V_LJ(rc),  r < rc = 2.5, else 0
+ *               (eps = sigma = 1, truncated and shifted)
+ *   V_FENE(r) = -(K/2) R^2 ln(1 - (r/R)^2),  r < R, else +infinity (move rejected)
+ *               (K = 40, R = 1.5, bond rest length 0)
+ * Move: beads i = 0..N-1 in order; bead i is displaced by
+ *   delta_a = (u_a - 2^31) * 1229 * 2^-44,  a = x, y, z,
+ * i.e. uniform in a cube of side 1229/4096 = 0.30005 on a dyadic grid of
+ * spacing 1229 * 2^-44, so every coordinate stays an exact binary64 value and
+ * any implementation that adds the same integers lands on the same bits.
+ * Random words: Philox4x32-10, counter (bead, global sweep, walker, tag 1),
+ * words 0..2 the displacement, word 3 the acceptance.
+ * Energy bins: b = floor((E - e_lo) * 10) (width 0.1); the window is
+ * 0 <= b < B.  Inside the window a move to E' is accepted iff b' is inside and
+ * (d >= 0 or u_3 < floor(2^32 exp(d))), d = ln W(b') - ln W(b); outside the
+ * window (walk-in after the start) a move is accepted iff it does not increase
+ * the distance of E to the window, and nothing is recorded.  In canonical mode
+ * (beta > 0) the weight is exp(-beta E) and there is no window.
+ * Initial chain: bead 0 at the origin; bead k = bead k-1 + u_hat, with u_hat a
+ * unit vector from Marsaglia's (1972) method on Philox tag-2 words, rounded
+ * to the 2^-44 grid; redrawn (up to 64 times) while any earlier bead lies
+ * closer than 0.9.
+ */
+#include <math.h>
+#include <pthread.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include "muca_oracle.h"
+
+#define POLY_TAG_SWEEP 1u
+#define POLY_TAG_INIT 2u
+#define POLY_STEP_Q 1229.0
+#define POLY_GRID 0x1p-44
+#define POLY_RC 2.5
+
+typedef struct {
+    int N, p, B, record;
+    uint64_t seed;
+    double e_lo, e_hi, K, R, beta;
+    int64_t sweep_counter;
+    double *X;       /* p*N*3 */
+    double *E;       /* p */
+    double *lnW, *lnW_sampled, *G, *lnR;
+    uint64_t *H_open, *H_last;
+    int64_t *events; /* p*2: [near-tie acceptances, bin-edge events] */
+} orc_poly;
+
+static double poly_lj(double r2)
+{
+    if (r2 >= POLY_RC * POLY_RC) return 0.0;
+    double ir2 = 1.0 / r2;
+    double ir6 = ir2 * ir2 * ir2;
+    double irc2 = 1.0 / (POLY_RC * POLY_RC);
+    double irc6 = irc2 * irc2 * irc2;
+    return 4.0 * (ir6 * ir6 - ir6) - 4.0 * (irc6 * irc6 - irc6);
+}
+
+static double poly_fene(double r2, double K, double R)
+{
+    if (r2 >= R * R) return INFINITY;
+    return -0.5 * K * R * R * log(1.0 - r2 / (R * R));
+}
+
+/* Pair energy at distance r for index separation sep (1 = bond, >= 2 = LJ). */
+double orc_poly_pair(double r, int sep, int unused)
+{
+    (void)unused;
+    double r2 = r * r;
+    return sep == 1 ? poly_fene(r2, 40.0, 1.5) : poly_lj(r2);
+}
+
+static double poly_pair2(const orc_poly *P, double r2, int sep)
+{
+    return sep == 1 ? poly_fene(r2, P->K, P->R) : poly_lj(r2);
+}
+
+static double poly_dist2(const double *a, const double *b)
+{
+    double dx = a[0] - b[0], dy = a[1] - b[1], dz = a[2] - b[2];
+    return dx * dx + dy * dy + dz * dz;
+}
+
+/* Energy of one configuration from scratch, pairs i < j in order. */
+double orc_poly_energy(int N, const double *X, int unused)
+{
+    (void)unused;
+    double E = 0.0;
+    for (int i = 0; i < N; ++i)
+        for (int j = i + 1; j < N; ++j) {
+            double r2 = poly_dist2(X + 3 * i, X + 3 * j);
+            E += (j - i == 1) ? poly_fene(r2, 40.0, 1.5) : poly_lj(r2);
+        }
+    return E;
+}
+
+static double poly_energy_P(const orc_poly *P, const double *X)
+{
+    double E = 0.0;
+    for (int i = 0; i < P->N; ++i)
+        for (int j = i + 1; j < P->N; ++j) E += poly_pair2(P, poly_dist2(X + 3 * i, X + 3 * j), j - i);
+    return E;
+}
+
+static int poly_bin(const orc_poly *P, double E) { return (int)floor((E - P->e_lo) * 10.0); }
+
+void *orc_poly_create(int N, int p, uint64_t seed, double e_lo, double e_hi, double K, double R, int record)
+{
+    if (N < 2 || p < 1 || !(e_hi > e_lo) || !(K > 0) || !(R > 0)) return NULL;
+    orc_poly *P = (orc_poly *)calloc(1, sizeof *P);
+    P->N = N;
+    P->p = p;
+    P->seed = seed;
+    P->e_lo = e_lo;
+    P->e_hi = e_hi;
+    P->K = K;
+    P->R = R;
+    P->record = record;
+    P->B = (int)floor((e_hi - e_lo) * 10.0 + 0.5);
+    if (P->B < 2) { free(P); return NULL; }
+    P->X = (double *)calloc((size_t)p * N * 3, sizeof(double));
+    P->E = (double *)calloc((size_t)p, sizeof(double));
+    P->lnW = (double *)calloc((size_t)P->B, sizeof(double));
+    P->lnW_sampled = (double *)calloc((size_t)P->B, sizeof(double));
+    P->G = (double *)calloc((size_t)P->B, sizeof(double));
+    P->lnR = (double *)calloc((size_t)P->B, sizeof(double));
+    P->H_open = (uint64_t *)calloc((size_t)P->B, sizeof(uint64_t));
+    P->H_last = (uint64_t *)calloc((size_t)P->B, sizeof(uint64_t));
+    P->events = (int64_t *)calloc((size_t)p * 2, sizeof(int64_t));
+    return P;
+}
+
+void orc_poly_free(void *h)
+{
+    orc_poly *P = (orc_poly *)h;
+    if (!P) return;
+    free(P->X); free(P->E); free(P->lnW); free(P->lnW_sampled); free(P->G); free(P->lnR);
+    free(P->H_open); free(P->H_last); free(P->events);
+    free(P);
+}
+
+int orc_poly_num_bins(void *h) { return ((orc_poly *)h)->B; }
+
+/* Canonical mode for the window pilot: weight exp(-beta E), no window. */
+void orc_poly_set_beta(void *h, double beta) { ((orc_poly *)h)->beta = beta; }
+
+static uint32_t poly_word(const orc_poly *P, uint32_t c0, uint32_t c1, uint32_t w, uint32_t tag, int k)
+{
+    uint32_t ctr[4] = {c0, c1, w, tag}, key[2] = {(uint32_t)(P->seed & 0xffffffffu), (uint32_t)(P->seed >> 32)}, out[4];
+    orc_philox4x32_10(ctr, key, out);
+    return out[k];
+}
+
+void orc_poly_init(void *h)
+{
+    orc_poly *P = (orc_poly *)h;
+    const int N = P->N;
+    uint32_t key[2] = {(uint32_t)(P->seed & 0xffffffffu), (uint32_t)(P->seed >> 32)};
+    for (int w = 0; w < P->p; ++w) {
+        double *X = P->X + (size_t)w * N * 3;
+        X[0] = X[1] = X[2] = 0.0;
+        uint32_t draw = 0; /* counts Philox blocks drawn for this walker */
+        for (int k = 1; k < N; ++k) {
+            double cand[3] = {0, 0, 0};
+            for (int attempt = 0; attempt < 64; ++attempt) {
+                /* Marsaglia: v1, v2 uniform in [-1, 1) with s = v1^2 + v2^2 < 1 */
+                double v1, v2, s;
+                for (;;) {
+                    uint32_t ctr[4] = {draw++, 0u, (uint32_t)w, POLY_TAG_INIT}, u[4];
+                    orc_philox4x32_10(ctr, key, u);
+                    v1 = (double)u[0] * 0x1p-31 - 1.0;
+                    v2 = (double)u[1] * 0x1p-31 - 1.0;
+                    s = v1 * v1 + v2 * v2;
+                    if (s < 1.0 && s > 0.0) break;
+                }
+                double f = 2.0 * sqrt(1.0 - s);
+                double uh[3] = {v1 * f, v2 * f, 1.0 - 2.0 * s};
+                for (int a = 0; a < 3; ++a) cand[a] = X[3 * (k - 1) + a] + nearbyint(uh[a] * 0x1p44) * POLY_GRID;
+                int ok = 1;
+                for (int j = 0; j < k - 1 && ok; ++j)
+                    if (poly_dist2(cand, X + 3 * j) < 0.81) ok = 0;
+                if (ok) break;
+            }
+            for (int a = 0; a < 3; ++a) X[3 * k + a] = cand[a];
+        }
+        P->E[w] = poly_energy_P(P, X);
+    }
+    for (int b = 0; b < P->B; ++b) {
+        P->lnW[b] = P->lnW_sampled[b] = P->G[b] = P->lnR[b] = 0.0;
+        P->H_open[b] = P->H_last[b] = 0;
+    }
+    P->sweep_counter = 0;
+}
+
+static double poly_window_dist(const orc_poly *P, double E)
+{
+    int b = poly_bin(P, E);
+    if (b >= 0 && b < P->B) return 0.0;
+    return (b < 0) ? (P->e_lo - E) : (E - P->e_hi);
+}
+
+static void poly_walker_sweeps(orc_poly *P, int w, int64_t g0, int64_t sweeps, uint64_t *hist)
+{
+    const int N = P->N;
+    double *X = P->X + (size_t)w * N * 3;
+    double E = P->E[w];
+    int64_t *ev = P->events + 2 * (size_t)w;
+    uint32_t key[2] = {(uint32_t)(P->seed & 0xffffffffu), (uint32_t)(P->seed >> 32)};
+    for (int64_t sw = 0; sw < sweeps; ++sw) {
+        uint32_t g = (uint32_t)(g0 + sw);
+        for (int i = 0; i < N; ++i) {
+            uint32_t ctr[4] = {(uint32_t)i, g, (uint32_t)w, POLY_TAG_SWEEP}, u[4];
+            orc_philox4x32_10(ctr, key, u);
+            double xn[3];
+            for (int a = 0; a < 3; ++a)
+                xn[a] = X[3 * i + a] + (double)((int64_t)u[a] - 2147483648LL) * POLY_STEP_Q * POLY_GRID;
+            double dE = 0.0;
+            int broken = 0;
+            for (int j = 0; j < N; ++j) {
+                if (j == i) continue;
+                int sep = abs(i - j);
+                double vn = poly_pair2(P, poly_dist2(xn, X + 3 * j), sep);
+                double vo = poly_pair2(P, poly_dist2(X + 3 * i, X + 3 * j), sep);
+                if (isinf(vn)) broken = 1;
+                dE += vn - vo;
+            }
+            int accept = 0;
+            double En = E + dE;
+            if (!broken) {
+                if (P->beta > 0.0) {
+                    double d = -P->beta * dE;
+                    accept = d >= 0.0 || (double)u[3] < floor(ldexp(orc_det_exp(d), 32));
+                } else {
+                    int b = poly_bin(P, E), bn = poly_bin(P, En);
+                    if (b >= 0 && b < P->B) {
+                        if (bn >= 0 && bn < P->B) {
+                            double d = P->lnW[bn] - P->lnW[b];
+                            if (d >= 0.0) {
+                                accept = 1;
+                            } else {
+                                double pa = orc_det_exp(d);
+                                accept = (double)u[3] < floor(ldexp(pa, 32));
+                                if (fabs((double)u[3] * 0x1p-32 - pa) < 1e-6) ev[0] += 1;
+                            }
+                            double edge = (En - P->e_lo) * 10.0;
+                            if (fabs(edge - nearbyint(edge)) < 1e-8) ev[1] += 1;
+                        }
+                    } else {
+                        accept = poly_window_dist(P, En) <= poly_window_dist(P, E);
+                    }
+                }
+            }
+            if (accept) {
+                for (int a = 0; a < 3; ++a) X[3 * i + a] = xn[a];
+                E = En;
+            }
+            if (P->record == 0 && P->beta <= 0.0) {
+                int b = poly_bin(P, E);
+                if (b >= 0 && b < P->B) hist[b] += 1;
+            }
+        }
+        if (P->record == 1 && P->beta <= 0.0) {
+            int b = poly_bin(P, E);
+            if (b >= 0 && b < P->B) hist[b] += 1;
+        }
+    }
+    P->E[w] = E;
+}
+
+typedef struct {
+    orc_poly *P;
+    int w0, w1;
+    int64_t g0, sweeps;
+    uint64_t *hist;
+} poly_job;
+
+static void *poly_job_main(void *arg)
+{
+    poly_job *j = (poly_job *)arg;
+    for (int w = j->w0; w < j->w1; ++w) poly_walker_sweeps(j->P, w, j->g0, j->sweeps, j->hist);
+    return NULL;
+}
+
+void orc_poly_iterate_range(void *h, int64_t sweeps, int w0, int w1, int nthreads)
+{
+    orc_poly *P = (orc_poly *)h;
+    if (w0 < 0) w0 = 0;
+    if (w1 > P->p) w1 = P->p;
+    if (w1 <= w0 || sweeps <= 0) return;
+    int nw = w1 - w0;
+    if (nthreads < 1) nthreads = 1;
+    if (nthreads > nw) nthreads = nw;
+    poly_job *jobs = (poly_job *)calloc((size_t)nthreads, sizeof *jobs);
+    pthread_t *th = (pthread_t *)calloc((size_t)nthreads, sizeof *th);
+    for (int t = 0; t < nthreads; ++t) {
+        jobs[t].P = P;
+        jobs[t].w0 = w0 + (int)((int64_t)nw * t / nthreads);
+        jobs[t].w1 = w0 + (int)((int64_t)nw * (t + 1) / nthreads);
+        jobs[t].g0 = P->sweep_counter;
+        jobs[t].sweeps = sweeps;
+        jobs[t].hist = (uint64_t *)calloc((size_t)P->B, sizeof(uint64_t));
+    }
+    if (nthreads == 1) {
+        poly_job_main(&jobs[0]);
+    } else {
+        for (int t = 0; t < nthreads; ++t) pthread_create(&th[t], NULL, poly_job_main, &jobs[t]);
+        for (int t = 0; t < nthreads; ++t) pthread_join(th[t], NULL);
+    }
+    for (int t = 0; t < nthreads; ++t) {
+        for (int b = 0; b < P->B; ++b) P->H_open[b] += jobs[t].hist[b];
+        free(jobs[t].hist);
+    }
+    free(jobs);
+    free(th);
+}
+
+void orc_poly_advance(void *h, int64_t sweeps) { ((orc_poly *)h)->sweep_counter += sweeps; }
+
+void orc_poly_iterate(void *h, int64_t sweeps, int nthreads)
+{
+    orc_poly_iterate_range(h, sweeps, 0, ((orc_poly *)h)->p, nthreads);
+    orc_poly_advance(h, sweeps);
+}
+
+/* Same accumulated-statistics recursion as the spin oracle, over all B bins. */
+void orc_poly_update(void *h)
+{
+    orc_poly *P = (orc_poly *)h;
+    const int B = P->B;
+    memcpy(P->lnW_sampled, P->lnW, sizeof(double) * B);
+    for (int k = 0; k + 1 < B; ++k) {
+        uint64_t h0 = P->H_open[k], h1 = P->H_open[k + 1];
+        if (h0 > 0 && h1 > 0) {
+            double a = (double)h0, c = (double)h1;
+            double g = (a * c) / (a + c);
+            P->G[k] = P->G[k] + g;
+            double kappa = g / P->G[k];
+            double diff = orc_det_log(a) - orc_det_log(c);
+            P->lnR[k] = P->lnR[k] + kappa * diff;
+        }
+    }
+    double acc = 0.0;
+    P->lnW[0] = acc;
+    for (int k = 0; k + 1 < B; ++k) {
+        acc = acc + P->lnR[k];
+        P->lnW[k + 1] = acc;
+    }
+    memcpy(P->H_last, P->H_open, sizeof(uint64_t) * B);
+    memset(P->H_open, 0, sizeof(uint64_t) * B);
+}
+
+/* Recompute every walker's energy from scratch (removes accumulated rounding);
+ * returns the largest |E_running - E_scratch|. */
+double orc_poly_refresh_energy(void *h)
+{
+    orc_poly *P = (orc_poly *)h;
+    double worst = 0.0;
+    for (int w = 0; w < P->p; ++w) {
+        double e = poly_energy_P(P, P->X + (size_t)w * P->N * 3);
+        double d = fabs(e - P->E[w]);
+        if (d > worst) worst = d;
+        P->E[w] = e;
+    }
+    return worst;
+}
+
+void orc_poly_get_lnW(void *h, double *out) { memcpy(out, ((orc_poly *)h)->lnW, sizeof(double) * ((orc_poly *)h)->B); }
+void orc_poly_get_lnW_sampled(void *h, double *out)
+{
+    memcpy(out, ((orc_poly *)h)->lnW_sampled, sizeof(double) * ((orc_poly *)h)->B);
+}
+void orc_poly_get_histogram(void *h, uint64_t *out)
+{
+    memcpy(out, ((orc_poly *)h)->H_last, sizeof(uint64_t) * ((orc_poly *)h)->B);
+}
+void orc_poly_get_coords(void *h, double *out)
+{
+    orc_poly *P = (orc_poly *)h;
+    memcpy(out, P->X, sizeof(double) * (size_t)P->p * P->N * 3);
+}
+void orc_poly_get_energy(void *h, double *out) { memcpy(out, ((orc_poly *)h)->E, sizeof(double) * ((orc_poly *)h)->p); }
+void orc_poly_get_bins(void *h, int32_t *out)
+{
+    orc_poly *P = (orc_poly *)h;
+    for (int w = 0; w < P->p; ++w) out[w] = poly_bin(P, P->E[w]);
+}
+void orc_poly_get_counters(void *h, int64_t *out)
+{
+    orc_poly *P = (orc_poly *)h;
+    out[0] = out[1] = 0;
+    for (int w = 0; w < P->p; ++w) {
+        out[0] += P->events[2 * w];
+        out[1] += P->events[2 * w + 1];
+    }
+}

@@ -23,7 +23,7 @@ __all__ = ["Muca", "MucaError", "ISING2D", "POTTS2D", "ISING2D_MUMA", "POLYMER3D
            "muca_get_histogram", "muca_get_flatness", "muca_get_reweight", "muca_get_state", "muca_set_state",
            "muca_get_spins", "muca_get_walker_bins", "muca_get_thresholds", "muca_get_sweep_counter",
            "muca_synchronize", "muca_free", "muca_last_error", "muca_det_math",
-           "muca_iterate_noalloc"]
+           "muca_iterate_noalloc", "muca_batch_create", "muca_batch_run", "muca_batch_free", "Batch"]
 
 
 def _p(a: np.ndarray):
@@ -140,6 +140,44 @@ def muca_iterate_noalloc(h, sweeps: int, dev_H_out: int):
     """Sweeps + merge into a caller-provided device buffer, with no device allocation
     (partial histograms in the library's static device array; see include/muca.h)."""
     check(load().muca_iterate_noalloc(h, sweeps, ctypes.c_void_p(dev_H_out)), "muca_iterate_noalloc")
+
+
+def muca_batch_create(handles):
+    arr = (ctypes.c_void_p * len(handles))(*[h.value if isinstance(h, ctypes.c_void_p) else h for h in handles])
+    b = ctypes.c_void_p()
+    check(load().muca_batch_create(arr, len(handles), ctypes.byref(b)), "muca_batch_create")
+    return b
+
+
+def muca_batch_run(b, n_iter: int, sweeps: int, use_graph: bool = True):
+    check(load().muca_batch_run(b, n_iter, sweeps, 1 if use_graph else 0), "muca_batch_run")
+
+
+def muca_batch_free(b):
+    check(load().muca_batch_free(b), "muca_batch_free")
+
+
+class Batch:
+    """Several Muca systems advanced together (one persistent sweep launch per iteration;
+    optionally the whole run as one CUDA graph)."""
+
+    def __init__(self, systems):
+        self.systems = list(systems)
+        self.h = muca_batch_create([s.h for s in self.systems])
+
+    def run(self, n_iter: int, sweeps: int, use_graph: bool = True):
+        muca_batch_run(self.h, n_iter, sweeps, use_graph)
+
+    def close(self):
+        if getattr(self, "h", None) is not None:
+            muca_batch_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def muca_synchronize(h):

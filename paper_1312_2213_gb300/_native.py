@@ -40,6 +40,9 @@ PROTOTYPES = {
     "muca_get_sweep_counter": (c_int, [c_vp, P(c_i64)]),
     "muca_det_math": (c_int, [c_int, c_vp, c_vp, c_i64]),
     "muca_iterate_noalloc": (c_int, [c_vp, c_i64, c_vp]),
+    "muca_batch_create": (c_int, [P(c_vp), c_int, P(c_vp)]),
+    "muca_batch_run": (c_int, [c_vp, c_int, c_i64, c_int]),
+    "muca_batch_free": (c_int, [c_vp]),
     "muca_synchronize": (c_int, [c_vp]),
     "muca_free": (c_int, [c_vp]),
 }

@@ -4,6 +4,7 @@
 // thread-local message.  No compute happens on the host.
 #include <cstdarg>
 #include <cstdio>
+#include <algorithm>
 #include <cstring>
 #include <mutex>
 #include <new>
@@ -53,6 +54,7 @@ struct muca_ctx {
     int pstride = 0, wpw = 0, nblk_max = 0;
     cudaStream_t stream = nullptr;
     bool owns_arena = false, started = false;
+    bool open = false;  // sweeps since the last merge (their partial histograms sit in Hpart)
     void *arena = nullptr;
     size_t arena_bytes = 0;
     uint32_t *lat = nullptr;
@@ -383,9 +385,11 @@ int muca_iterate(muca_ctx *c, int64_t sweeps)
     fill_round_keys(a, c->seed);
     a.record = c->record;
     a.walker_offset = c->walker_offset;
+    a.kind = sweep_kind(c->system, c->L);
     MUCA_CUDA(launch_spin_sweep(c->system, c->L, a, c->block, c->stream));
     MUCA_CUDA(launch_advance(c->state, sweeps, c->stream));
     c->started = true;
+    c->open = true;
     return MUCA_OK;
 }
 
@@ -397,6 +401,7 @@ int muca_merge_and_update(muca_ctx *c, int *is_flat)
     MUCA_CUDA(launch_recursion(a, c->stream));
     MUCA_CUDA(launch_thresholds(a, c->stream));
     c->started = true;
+    c->open = false;
     if (is_flat) {
         int f = 0;
         if (int rc = d2h(c, &f, &c->state->flat, sizeof(int))) return rc;
@@ -606,6 +611,7 @@ int muca_set_state(muca_ctx *c, const void *host_buf, size_t bytes)
     MUCA_CUDA(cudaMemcpyAsync(c->state, &h.dev, sizeof h.dev, cudaMemcpyHostToDevice, c->stream));
     MUCA_CUDA(cudaStreamSynchronize(c->stream));
     c->started = true;
+    c->open = true;
     return MUCA_OK;
 }
 
@@ -638,6 +644,232 @@ int muca_free(muca_ctx *c)
     if (c->owns_arena && c->arena) cudaFree(c->arena);
     delete c;
     if (e != cudaSuccess) return fail(MUCA_ERR_CUDA, "muca_free: %s", cudaGetErrorString(e));
+    return MUCA_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Batching: several systems (different models, lattice sizes, walker counts)
+// advance together.  One iteration is five launches for the whole batch -- a
+// persistent sweep over a tile list (system, first walker), the sweep-counter
+// advance, and the merge, recursion and threshold kernels over all systems --
+// and muca_batch_run can capture all n_iter iterations as one CUDA graph.
+// Small systems alone leave most of the GPU idle (2048 walkers are 64 warps
+// for 608 schedulers); in one launch they fill it together.
+struct muca_batch {
+    std::vector<muca_ctx *> sys;
+    int block = 128;
+    size_t smem = 0;
+    int ntiles = 0, max_bins = 0, max_nreach = 0, max_cells = 0;
+    void *dmem = nullptr;
+    SpinSweepArgs *d_sys = nullptr;
+    int2 *d_tiles = nullptr;
+    UpdateArgs *d_upd = nullptr;
+    DevState **d_states = nullptr;
+    std::vector<SpinSweepArgs> h_sys;
+    cudaStream_t ctx_stream = nullptr;  // the systems' stream (may be the legacy default stream)
+    cudaStream_t stream = nullptr;      // the batch's own stream (capturable)
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int g_iter = 0;
+    int64_t g_sweeps = 0;
+};
+
+namespace {
+
+SpinSweepArgs sweep_args(const muca_ctx *c, int64_t sweeps, int block)
+{
+    SpinSweepArgs a{};
+    a.T = c->T;
+    a.lattice = c->lat;
+    a.bin = c->bin;
+    a.Hpart = c->Hpart;
+    a.state = c->state;
+    a.p = c->p;
+    a.pstride = c->pstride;
+    a.B = c->B;
+    a.q = c->q;
+    a.sweeps = sweeps;
+    const unsigned long long per_sweep = (unsigned long long)block * (c->record == 0 ? (unsigned)c->N : 1u);
+    unsigned long long fe = 0xFFFFFFFFull / per_sweep;
+    if (fe < 1) fe = 1;
+    if (fe > (unsigned long long)sweeps) fe = (unsigned long long)sweeps;
+    a.flush_every = (int)(fe > 0x7fffffffull ? 0x7fffffffull : fe);
+    fill_round_keys(a, c->seed);
+    a.record = c->record;
+    a.walker_offset = c->walker_offset;
+    a.kind = sweep_kind(c->system, c->L);
+    return a;
+}
+
+int batch_enqueue_iteration(muca_batch *b, int64_t sweeps)
+{
+    const int n = (int)b->sys.size();
+    MUCA_CUDA(launch_sweep_batch(b->d_sys, b->d_tiles, b->ntiles, b->block, b->smem, b->stream));
+    MUCA_CUDA(launch_advance_batch(b->d_states, n, sweeps, b->stream));
+    MUCA_CUDA(launch_merge_batch(b->d_upd, n, b->max_bins, b->stream));
+    MUCA_CUDA(launch_recursion_batch(b->d_upd, n, b->max_nreach, b->stream));
+    MUCA_CUDA(launch_thresholds_batch(b->d_upd, n, b->max_cells, b->stream));
+    return MUCA_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int muca_batch_create(muca_ctx *const *systems, int n, muca_batch **out)
+{
+    if (!out) return fail(MUCA_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (!systems || n < 1) return fail(MUCA_ERR_ARG, "need at least one system");
+    for (int i = 0; i < n; ++i) {
+        if (!systems[i]) return fail(MUCA_ERR_ARG, "system %d is NULL", i);
+        if (systems[i]->stream != systems[0]->stream)
+            return fail(MUCA_ERR_ARG, "all systems of a batch must use the same stream");
+        if (systems[i]->system == kPolymer)
+            return fail(MUCA_ERR_ARG, "system %d: the polymer is not part of spin batches", i);
+        for (int j = 0; j < i; ++j)
+            if (systems[j] == systems[i]) return fail(MUCA_ERR_ARG, "system %d appears twice", i);
+    }
+    muca_batch *b = new (std::nothrow) muca_batch();
+    if (!b) return fail(MUCA_ERR_OOM, "host allocation failed");
+    b->sys.assign(systems, systems + n);
+    b->ctx_stream = systems[0]->stream;
+    if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming) != cudaSuccess) {
+        if (b->stream) cudaStreamDestroy(b->stream);
+        if (b->ev_in) cudaEventDestroy(b->ev_in);
+        delete b;
+        return fail(MUCA_ERR_CUDA, "muca_batch_create: cannot create stream/events");
+    }
+    // Heaviest systems first, so their tiles start in the first wave.
+    std::vector<int> order(n);
+    for (int i = 0; i < n; ++i) order[i] = i;
+    auto cost = [&](int i) { return (double)b->sys[i]->N * (b->sys[i]->system == kPotts ? 2.5 : 1.0); };
+    for (int i = 1; i < n; ++i)
+        for (int j = i; j > 0 && cost(order[j]) > cost(order[j - 1]); --j) std::swap(order[j], order[j - 1]);
+    std::vector<int2> tiles;
+    std::vector<UpdateArgs> upd(n);
+    std::vector<DevState *> states(n);
+    for (int i = 0; i < n; ++i) {
+        muca_ctx *c = b->sys[i];
+        b->smem = std::max(b->smem, spin_sweep_smem_bytes(c->system, c->B));
+        b->max_bins = std::max(b->max_bins, c->B);
+        b->max_nreach = std::max(b->max_nreach, c->nreach);
+        b->max_cells = std::max(b->max_cells, c->B * c->C);
+        upd[i] = update_args(c);
+        upd[i].nblocks = (c->p + b->block - 1) / b->block;
+        states[i] = c->state;
+    }
+    for (int i : order)
+        for (int w0 = 0; w0 < b->sys[i]->p; w0 += b->block) tiles.push_back(make_int2(i, w0));
+    b->ntiles = (int)tiles.size();
+    b->h_sys.resize(n);
+    const size_t sz_sys = align_up(sizeof(SpinSweepArgs) * n), sz_tiles = align_up(sizeof(int2) * tiles.size()),
+                 sz_upd = align_up(sizeof(UpdateArgs) * n), sz_st = align_up(sizeof(DevState *) * n);
+    cudaError_t e = cudaMalloc(&b->dmem, sz_sys + sz_tiles + sz_upd + sz_st);
+    if (e != cudaSuccess) {
+        cudaStreamDestroy(b->stream);
+        cudaEventDestroy(b->ev_in);
+        cudaEventDestroy(b->ev_out);
+        delete b;
+        return fail(MUCA_ERR_OOM, "muca_batch_create: %s", cudaGetErrorString(e));
+    }
+    char *base = (char *)b->dmem;
+    b->d_sys = (SpinSweepArgs *)base;
+    b->d_tiles = (int2 *)(base + sz_sys);
+    b->d_upd = (UpdateArgs *)(base + sz_sys + sz_tiles);
+    b->d_states = (DevState **)(base + sz_sys + sz_tiles + sz_upd);
+    e = cudaMemcpy(b->d_tiles, tiles.data(), sizeof(int2) * tiles.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(b->d_upd, upd.data(), sizeof(UpdateArgs) * n, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(b->d_states, states.data(), sizeof(DevState *) * n, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = prepare_sweep_batch(b->smem);
+    if (e == cudaSuccess) e = prepare_recursion_batch(b->max_nreach);
+    if (e != cudaSuccess) {
+        cudaFree(b->dmem);
+        cudaStreamDestroy(b->stream);
+        cudaEventDestroy(b->ev_in);
+        cudaEventDestroy(b->ev_out);
+        delete b;
+        return fail(MUCA_ERR_CUDA, "muca_batch_create: %s", cudaGetErrorString(e));
+    }
+    *out = b;
+    return MUCA_OK;
+}
+
+int muca_batch_run(muca_batch *b, int n_iter, int64_t sweeps, int use_graph)
+{
+    if (!b) return fail(MUCA_ERR_ARG, "batch is NULL");
+    if (n_iter < 1 || sweeps < 1) return fail(MUCA_ERR_ARG, "n_iter and sweeps must be >= 1");
+    const int n = (int)b->sys.size();
+    for (int i = 0; i < n; ++i)
+        if (b->sys[i]->open)
+            return fail(MUCA_ERR_STATE, "system %d has unmerged sweeps; call muca_merge_and_update first", i);
+    for (int i = 0; i < n; ++i) b->h_sys[i] = sweep_args(b->sys[i], sweeps, b->block);
+    // order the batch's own stream after the systems' earlier work
+    MUCA_CUDA(cudaEventRecord(b->ev_in, b->ctx_stream));
+    MUCA_CUDA(cudaStreamWaitEvent(b->stream, b->ev_in, 0));
+    MUCA_CUDA(cudaMemcpyAsync(b->d_sys, b->h_sys.data(), sizeof(SpinSweepArgs) * n, cudaMemcpyHostToDevice,
+                              b->stream));
+    // the flatness ratio may change between runs
+    std::vector<UpdateArgs> upd(n);
+    for (int i = 0; i < n; ++i) {
+        upd[i] = update_args(b->sys[i]);
+        upd[i].nblocks = (b->sys[i]->p + b->block - 1) / b->block;
+    }
+    MUCA_CUDA(cudaMemcpyAsync(b->d_upd, upd.data(), sizeof(UpdateArgs) * n, cudaMemcpyHostToDevice, b->stream));
+    if (use_graph) {
+        if (!b->exec || b->g_iter != n_iter || b->g_sweeps != sweeps) {
+            if (b->exec) {
+                cudaGraphExecDestroy(b->exec);
+                b->exec = nullptr;
+            }
+            // the host-side copies above stay outside the captured region
+            MUCA_CUDA(cudaStreamSynchronize(b->stream));
+            MUCA_CUDA(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+            int rc = MUCA_OK;
+            for (int it = 0; it < n_iter && rc == MUCA_OK; ++it) rc = batch_enqueue_iteration(b, sweeps);
+            cudaGraph_t graph = nullptr;
+            cudaError_t e = cudaStreamEndCapture(b->stream, &graph);
+            if (rc != MUCA_OK) {
+                if (graph) cudaGraphDestroy(graph);
+                return rc;
+            }
+            if (e != cudaSuccess) return fail(MUCA_ERR_CUDA, "graph capture: %s", cudaGetErrorString(e));
+            e = cudaGraphInstantiate(&b->exec, graph, 0);
+            cudaGraphDestroy(graph);
+            if (e != cudaSuccess) {
+                b->exec = nullptr;
+                return fail(MUCA_ERR_CUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(e));
+            }
+            b->g_iter = n_iter;
+            b->g_sweeps = sweeps;
+        }
+        MUCA_CUDA(cudaGraphLaunch(b->exec, b->stream));
+    } else {
+        for (int it = 0; it < n_iter; ++it)
+            if (int rc = batch_enqueue_iteration(b, sweeps)) return rc;
+    }
+    // and the systems' later work after the batch
+    MUCA_CUDA(cudaEventRecord(b->ev_out, b->stream));
+    MUCA_CUDA(cudaStreamWaitEvent(b->ctx_stream, b->ev_out, 0));
+    for (int i = 0; i < n; ++i) b->sys[i]->started = true;
+    return MUCA_OK;
+}
+
+int muca_batch_free(muca_batch *b)
+{
+    if (!b) return MUCA_OK;
+    cudaError_t e = cudaStreamSynchronize(b->stream);
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->dmem) cudaFree(b->dmem);
+    cudaStreamDestroy(b->stream);
+    cudaEventDestroy(b->ev_in);
+    cudaEventDestroy(b->ev_out);
+    delete b;
+    if (e != cudaSuccess) return fail(MUCA_ERR_CUDA, "muca_batch_free: %s", cudaGetErrorString(e));
     return MUCA_OK;
 }
 

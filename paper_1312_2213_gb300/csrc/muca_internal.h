@@ -39,6 +39,7 @@ struct SpinSweepArgs {
     int record;
     int walker_offset;       // global id of walker 0 (for sharding)
     uint32_t rk[20];         // Philox round keys (k0 + r*W0, k1 + r*W1), r = 0..9
+    int kind;                // system * 16 + L / 4 (dispatch key of the batched sweep)
 };
 
 // Philox round keys for a seed: round r uses (lo + r*W0, hi + r*W1).
@@ -69,6 +70,11 @@ __host__ __device__ constexpr int num_cols(int system) { return system == kPotts
 bool spin_sweep_supported(int system, int L);
 size_t spin_sweep_smem_bytes(int system, int B);
 cudaError_t launch_spin_sweep(int system, int L, const SpinSweepArgs &a, int block, cudaStream_t s);
+int sweep_kind(int system, int L);
+// Batched sweep: tiles[k] = (system index, first walker); all tiles use `block` threads.
+cudaError_t prepare_sweep_batch(size_t smem);
+cudaError_t launch_sweep_batch(const SpinSweepArgs *d_sys, const int2 *d_tiles, int ntiles, int block, size_t smem,
+                               cudaStream_t s);
 
 struct UpdateArgs {
     int system, B, nreach, nblocks, N, q, p, pstride, L;
@@ -81,6 +87,12 @@ struct UpdateArgs {
     DevState *state;
 };
 cudaError_t launch_merge(const UpdateArgs &a, cudaStream_t s);
+// Batched update kernels over n systems (argument arrays in device memory).
+cudaError_t launch_merge_batch(const UpdateArgs *d_args, int n, int max_bins, cudaStream_t s);
+cudaError_t launch_recursion_batch(const UpdateArgs *d_args, int n, int max_nreach, cudaStream_t s);
+cudaError_t prepare_recursion_batch(int max_nreach);
+cudaError_t launch_thresholds_batch(const UpdateArgs *d_args, int n, int max_cells, cudaStream_t s);
+cudaError_t launch_advance_batch(DevState *const *d_states, int n, int64_t sweeps, cudaStream_t s);
 cudaError_t launch_recursion(const UpdateArgs &a, cudaStream_t s);
 cudaError_t launch_thresholds(const UpdateArgs &a, cudaStream_t s);
 cudaError_t launch_advance(DevState *st, int64_t sweeps, cudaStream_t s);

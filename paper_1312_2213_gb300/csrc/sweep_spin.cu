@@ -20,8 +20,10 @@
 // accepted" (bin moved by site x's energy change, left neighbour flipped) --
 // while site x is being decided, and then selects one.  Every such index is the
 // bin of a configuration that can occur, so it is always inside the table.
-// Philox blocks are computed one group ahead, with the round keys read from
-// the kernel parameters.
+// Philox blocks are computed one group ahead (the block after a sweep's last
+// group is computed and discarded, which keeps the row one basic block), with
+// the round keys read from the kernel parameters; the recording mode is a
+// template parameter for the same reason.
 //
 // Shared memory holds one row of RS = C+1 words per bin: the C thresholds and
 // the bin's histogram counter, so one row offset addresses both.
@@ -54,10 +56,10 @@ __device__ __forceinline__ uint32_t word_of(const uint4 &u, int j)
 // Spin bit 1 means s = -1.  k = 4 - (number of anti-aligned neighbours), so
 // dE = 4(k-2); Ising column c = k and the bin moves by k-2; MUMA column
 // c = 5*bit + k and the bin (M+N)/2 moves by 2*bit-1.
-template <int SYS, int L>
+template <int SYS, int L, int RECORD>
 __device__ __forceinline__ void ising_sweep(uint32_t *__restrict__ lat, int ps, int &bR,
                                             uint32_t *__restrict__ sTH, uint32_t g, uint32_t wid,
-                                            const uint32_t (&rk)[20], int record)
+                                            const uint32_t (&rk)[20])
 {
     constexpr int WR = ising_words_per_row(L);
     constexpr int C = (SYS == kMuma) ? 10 : 5;
@@ -112,8 +114,7 @@ __device__ __forceinline__ void ising_sweep(uint32_t *__restrict__ lat, int ps, 
         for (int x = 0; x < L; ++x) {
             if ((x & 3) == 0) {
                 u = u_next;
-                if (!(y == L - 1 && x == L - 4))
-                    u_next = philox4x32_10_rk(make_uint4((uint32_t)((y * L + x) / 4 + 1), g, wid, kTagSweep), rk);
+                u_next = philox4x32_10_rk(make_uint4((uint32_t)((y * L + x) / 4 + 1), g, wid, kTagSweep), rk);
             }
             const uint32_t uw = word_of(u, x & 3);
             bR = accP ? bR + dRp : bR;
@@ -129,7 +130,7 @@ __device__ __forceinline__ void ising_sweep(uint32_t *__restrict__ lat, int ps, 
             }
             const bool acc = (T == kAlways) || (uw < T);
             if (acc) cur[x >> 5] ^= 1u << (x & 31);
-            if (record == 0) atomicAdd(&sTH[(acc ? bR + dR : bR) + C], 1u);
+            if (RECORD == 0) atomicAdd(&sTH[(acc ? bR + dR : bR) + C], 1u);
             accP = acc;
             dRp = dR;
         }
@@ -147,17 +148,17 @@ __device__ __forceinline__ void ising_sweep(uint32_t *__restrict__ lat, int ps, 
             dn[j] = (y + 2 < L) ? nxt[j] : first[j];
         }
     }
-    if (record == 1) atomicAdd(&sTH[bR + C], 1u);
+    if (RECORD == 1) atomicAdd(&sTH[bR + C], 1u);
 }
 
 // One sweep of a q-state Potts walker (4-bit spins).  Proposal: a uniform new
 // state different from the old one, new = (old + 1 + mulhi(u, q-1)) mod q.
 // dE = n_eq(old) - n_eq(new) in [-4, 4]; column dE+4; bin E+2N moves by dE.
 // The "left neighbour changed" candidate uses the left site's proposed colour.
-template <int L>
+template <int L, int RECORD>
 __device__ __forceinline__ void potts_sweep(uint32_t *__restrict__ lat, int ps, int &bR,
                                             uint32_t *__restrict__ sTH, uint32_t g, uint32_t wid,
-                                            const uint32_t (&rk)[20], int record, uint32_t q)
+                                            const uint32_t (&rk)[20], uint32_t q)
 {
     constexpr int WR = potts_words_per_row(L);
     constexpr int RS = 10;
@@ -210,8 +211,7 @@ __device__ __forceinline__ void potts_sweep(uint32_t *__restrict__ lat, int ps, 
         for (int x = 0; x < L; ++x) {
             if ((x & 1) == 0) {
                 u = u_next;
-                if (!(y == L - 1 && x == L - 2))
-                    u_next = philox4x32_10_rk(make_uint4((uint32_t)((y * L + x) / 2 + 1), g, wid, kTagSweep), rk);
+                u_next = philox4x32_10_rk(make_uint4((uint32_t)((y * L + x) / 2 + 1), g, wid, kTagSweep), rk);
             }
             const uint32_t u_acc = (x & 1) ? u.w : u.y;
             bR = accP ? bR + dRp : bR;
@@ -232,7 +232,7 @@ __device__ __forceinline__ void potts_sweep(uint32_t *__restrict__ lat, int ps, 
                 const int wi = (4 * x) >> 5, sh = (4 * x) & 31;
                 cur[wi] = (cur[wi] & ~(15u << sh)) | (nw << sh);
             }
-            if (record == 0) atomicAdd(&sTH[(acc ? bR + dR : bR) + 9], 1u);
+            if (RECORD == 0) atomicAdd(&sTH[(acc ? bR + dR : bR) + 9], 1u);
             accP = acc;
             dRp = dR;
         }
@@ -250,19 +250,19 @@ __device__ __forceinline__ void potts_sweep(uint32_t *__restrict__ lat, int ps, 
             dn[j] = (y + 2 < L) ? nxt[j] : first[j];
         }
     }
-    if (record == 1) atomicAdd(&sTH[bR + 9], 1u);
+    if (RECORD == 1) atomicAdd(&sTH[bR + 9], 1u);
 }
 
-// The sweep kernel: stage the threshold table in shared memory (rows of C
-// thresholds + 1 histogram counter), run the walkers, flush the block
-// histogram to its own uint64 slot every `flush_every` sweeps (so no uint32
-// counter can overflow) and at the end.
+// One thread block's share of a sweep launch: stage the threshold table in
+// shared memory (rows of C thresholds + 1 histogram counter), run walkers
+// [w0, w0 + blockDim.x) of the system, flush the block histogram to its
+// own uint64 slot `slot` every `flush_every` sweeps (so no uint32 counter can
+// overflow) and at the end.
 template <int SYS, int L>
-__global__ void __launch_bounds__(kMaxSweepBlock) k_sweep_spin(const SpinSweepArgs a)
+__device__ __forceinline__ void sweep_block(const SpinSweepArgs &a, int w0, int slot, uint32_t *smem)
 {
     constexpr int C = num_cols(SYS);
     constexpr int RS = C + 1;
-    extern __shared__ __align__(16) uint32_t smem[];
     uint32_t *sTH = smem;
     const int tid = threadIdx.x;
     for (int i = tid; i < a.B * RS; i += blockDim.x) {
@@ -271,24 +271,35 @@ __global__ void __launch_bounds__(kMaxSweepBlock) k_sweep_spin(const SpinSweepAr
     }
     __syncthreads();
 
-    const int w = blockIdx.x * blockDim.x + tid;
+    const int w = w0 + tid;
     const bool active = w < a.p;
     const uint32_t wid = (uint32_t)(w + a.walker_offset);
     const uint32_t g0 = (uint32_t)a.state->sweep_counter;
     uint32_t *lat = a.lattice + (active ? w : 0);
     int bR = (active ? a.bin[w] : 0) * RS;
-    unsigned long long *Hb = a.Hpart + (size_t)blockIdx.x * a.B;
+    unsigned long long *Hb = a.Hpart + (size_t)slot * a.B;
 
     for (int64_t s0 = 0; s0 < a.sweeps; s0 += a.flush_every) {
         const int64_t s1 = (a.sweeps < s0 + a.flush_every) ? a.sweeps : s0 + a.flush_every;
         if (active) {
+            if (a.record == 0) {
 #pragma unroll 1
-            for (int64_t sw = s0; sw < s1; ++sw) {
-                const uint32_t g = g0 + (uint32_t)sw;
-                if (SYS == kPotts)
-                    potts_sweep<L>(lat, a.pstride, bR, sTH, g, wid, a.rk, a.record, (uint32_t)a.q);
-                else
-                    ising_sweep<SYS, L>(lat, a.pstride, bR, sTH, g, wid, a.rk, a.record);
+                for (int64_t sw = s0; sw < s1; ++sw) {
+                    const uint32_t g = g0 + (uint32_t)sw;
+                    if (SYS == kPotts)
+                        potts_sweep<L, 0>(lat, a.pstride, bR, sTH, g, wid, a.rk, (uint32_t)a.q);
+                    else
+                        ising_sweep<SYS, L, 0>(lat, a.pstride, bR, sTH, g, wid, a.rk);
+                }
+            } else {
+#pragma unroll 1
+                for (int64_t sw = s0; sw < s1; ++sw) {
+                    const uint32_t g = g0 + (uint32_t)sw;
+                    if (SYS == kPotts)
+                        potts_sweep<L, 1>(lat, a.pstride, bR, sTH, g, wid, a.rk, (uint32_t)a.q);
+                    else
+                        ising_sweep<SYS, L, 1>(lat, a.pstride, bR, sTH, g, wid, a.rk);
+                }
             }
         }
         __syncthreads();
@@ -302,6 +313,55 @@ __global__ void __launch_bounds__(kMaxSweepBlock) k_sweep_spin(const SpinSweepAr
         __syncthreads();
     }
     if (active) a.bin[w] = bR / RS;
+}
+
+// One system per launch: block k runs walkers [k*blockDim.x, (k+1)*blockDim.x).
+template <int SYS, int L>
+__global__ void __launch_bounds__(kMaxSweepBlock) k_sweep_spin(const SpinSweepArgs a)
+{
+    extern __shared__ __align__(16) uint32_t smem[];
+    sweep_block<SYS, L>(a, blockIdx.x * blockDim.x, blockIdx.x, smem);
+}
+
+// Every system of a batch in one launch: block k runs the tile (system,
+// first walker) tiles[k]; the per-system arguments live in device memory.
+// The switch dispatches to the same block function as the one-system kernel,
+// so a walker's trajectory does not depend on how the launch is grouped.
+__global__ void __launch_bounds__(kMaxSweepBlock) k_sweep_batch(const SpinSweepArgs *__restrict__ sys,
+                                                                const int2 *__restrict__ tiles)
+{
+    extern __shared__ __align__(16) uint32_t smem[];
+    const int2 t = tiles[blockIdx.x];
+    const SpinSweepArgs a = sys[t.x];
+    const int slot = t.y / blockDim.x;
+    switch (a.kind) {
+#define MUCA_CASE(S, LL) \
+    case (S) * 16 + (LL) / 4: sweep_block<(S), (LL)>(a, t.y, slot, smem); break;
+#define MUCA_CASES(S) \
+    MUCA_CASE(S, 4) MUCA_CASE(S, 8) MUCA_CASE(S, 12) MUCA_CASE(S, 16) MUCA_CASE(S, 24) MUCA_CASE(S, 32) \
+    MUCA_CASE(S, 48) MUCA_CASE(S, 64)
+        MUCA_CASES(kIsing)
+        MUCA_CASES(kMuma)
+        MUCA_CASE(kPotts, 4) MUCA_CASE(kPotts, 8) MUCA_CASE(kPotts, 12) MUCA_CASE(kPotts, 16)
+        MUCA_CASE(kPotts, 24) MUCA_CASE(kPotts, 32) MUCA_CASE(kPotts, 48)
+#undef MUCA_CASES
+#undef MUCA_CASE
+    default: break;
+    }
+}
+
+int sweep_kind(int system, int L) { return system * 16 + L / 4; }
+
+cudaError_t launch_sweep_batch(const SpinSweepArgs *d_sys, const int2 *d_tiles, int ntiles, int block, size_t smem,
+                               cudaStream_t s)
+{
+    k_sweep_batch<<<ntiles, block, smem, s>>>(d_sys, d_tiles);
+    return cudaGetLastError();
+}
+
+cudaError_t prepare_sweep_batch(size_t smem)
+{
+    return cudaFuncSetAttribute(k_sweep_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 
 size_t spin_sweep_smem_bytes(int system, int B) { return (size_t)B * (num_cols(system) + 1) * sizeof(uint32_t); }

@@ -23,9 +23,8 @@ namespace muca {
 
 #define kNegInf (__longlong_as_double((long long)0xfff0000000000000ULL))
 
-__global__ void k_merge(const UpdateArgs a)
+__device__ __forceinline__ void merge_body(const UpdateArgs &a, int b)
 {
-    const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= a.B) return;
     unsigned long long s = 0ull;
     for (int k = 0; k < a.nblocks; ++k) {
@@ -36,15 +35,21 @@ __global__ void k_merge(const UpdateArgs a)
     a.H[b] = s;
 }
 
+__global__ void k_merge(const UpdateArgs a) { merge_body(a, blockIdx.x * blockDim.x + threadIdx.x); }
+
+__global__ void k_merge_batch(const UpdateArgs *__restrict__ arr)
+{
+    merge_body(arr[blockIdx.y], blockIdx.x * blockDim.x + threadIdx.x);
+}
+
 // Recursion over the ordered reachable bins r_0 < ... < r_{K-1}.  For each
 // neighbouring pair with h0 = H(r_k) > 0 and h1 = H(r_{k+1}) > 0:
 //   g = h0 h1 / (h0 + h1);  G_k += g;  kappa = g / G_k;
 //   lnR_k += kappa (ln h0 - ln h1),
 // then ln W(r_0) = 0 and ln W(r_{k+1}) = ln W(r_k) + lnR_k, summed in order by
 // one thread.  Pairs are independent, so the first part runs on all threads.
-__global__ void __launch_bounds__(1024) k_recursion(const UpdateArgs a)
+__device__ __forceinline__ void recursion_body(const UpdateArgs &a, double *sm)
 {
-    extern __shared__ double sm[];
     double *slog = sm;
     double *slnR = sm + a.nreach;
     __shared__ unsigned long long s_min, s_max, s_sum;
@@ -98,10 +103,22 @@ __global__ void __launch_bounds__(1024) k_recursion(const UpdateArgs a)
     }
 }
 
-__global__ void k_thresholds(const UpdateArgs a)
+__global__ void __launch_bounds__(1024) k_recursion(const UpdateArgs a)
+{
+    extern __shared__ double sm[];
+    recursion_body(a, sm);
+}
+
+__global__ void __launch_bounds__(1024) k_recursion_batch(const UpdateArgs *__restrict__ arr)
+{
+    extern __shared__ double sm[];
+    const UpdateArgs a = arr[blockIdx.y];
+    recursion_body(a, sm);
+}
+
+__device__ __forceinline__ void thresholds_body(const UpdateArgs &a, int i)
 {
     const int C = num_cols(a.system);
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= a.B * C) return;
     const int b = i / C, c = i - (i / C) * C;
     int b2, dE = 0;
@@ -129,7 +146,20 @@ __global__ void k_thresholds(const UpdateArgs a)
     a.T[i] = t;
 }
 
+__global__ void k_thresholds(const UpdateArgs a) { thresholds_body(a, blockIdx.x * blockDim.x + threadIdx.x); }
+
+__global__ void k_thresholds_batch(const UpdateArgs *__restrict__ arr)
+{
+    thresholds_body(arr[blockIdx.y], blockIdx.x * blockDim.x + threadIdx.x);
+}
+
 __global__ void k_advance(DevState *st, long long sweeps) { st->sweep_counter += (unsigned long long)sweeps; }
+
+__global__ void k_advance_batch(DevState *const *states, int n, long long sweeps)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) states[i]->sweep_counter += (unsigned long long)sweeps;
+}
 
 __global__ void k_init_weights(const UpdateArgs a)
 {
@@ -331,6 +361,37 @@ cudaError_t launch_thresholds(const UpdateArgs &a, cudaStream_t s)
 {
     const int n = a.B * num_cols(a.system);
     k_thresholds<<<(n + 255) / 256, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_merge_batch(const UpdateArgs *d_args, int n, int max_bins, cudaStream_t s)
+{
+    k_merge_batch<<<dim3((max_bins + 255) / 256, n), 256, 0, s>>>(d_args);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_recursion_batch(const UpdateArgs *d_args, int n, int max_nreach, cudaStream_t s)
+{
+    const size_t smem = (size_t)2 * max_nreach * sizeof(double);
+    k_recursion_batch<<<dim3(1, n), 1024, smem, s>>>(d_args);
+    return cudaGetLastError();
+}
+
+cudaError_t prepare_recursion_batch(int max_nreach)
+{
+    return cudaFuncSetAttribute(k_recursion_batch, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)((size_t)2 * max_nreach * sizeof(double)));
+}
+
+cudaError_t launch_thresholds_batch(const UpdateArgs *d_args, int n, int max_cells, cudaStream_t s)
+{
+    k_thresholds_batch<<<dim3((max_cells + 255) / 256, n), 256, 0, s>>>(d_args);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_advance_batch(DevState *const *d_states, int n, int64_t sweeps, cudaStream_t s)
+{
+    k_advance_batch<<<(n + 127) / 128, 128, 0, s>>>(d_states, n, (long long)sweeps);
     return cudaGetLastError();
 }
 

@@ -1,0 +1,78 @@
+"""Batched mode: several systems in one persistent sweep launch per iteration (and the whole
+run as one CUDA graph) give bit-identical results to running each context on its own, which in
+turn the oracle pins; one system is also compared with the oracle directly."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_1312_2213_gb300 as m
+from gpu_util import compare_state
+
+pytestmark = pytest.mark.gpu
+
+MIX = [(m.ISING2D, 16, 2, 100, 11, None), (m.POTTS2D, 16, 10, 70, 12, None), (m.ISING2D_MUMA, 8, 2, 50, 13, 0.4407),
+       (m.ISING2D, 32, 2, 40, 14, None), (m.POTTS2D, 24, 10, 33, 15, None), (m.ISING2D, 64, 2, 20, 16, None)]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def _make():
+    return [m.Muca(s, L, q, p, seed, beta=beta) for s, L, q, p, seed, beta in MIX]
+
+
+@pytest.mark.parametrize("use_graph", [False, True])
+def test_batch_equals_individual_runs(use_graph):
+    n_iter, sweeps = 3, 15
+    ref = _make()
+    for _ in range(n_iter):
+        for c in ref:
+            c.iterate(sweeps)
+            c.merge_and_update()
+    sys_ = _make()
+    b = m.Batch(sys_)
+    b.run(n_iter, sweeps, use_graph=use_graph)
+    b.run(2, sweeps, use_graph=use_graph)  # second run: graph re-captured for a new n_iter
+    for _ in range(2):
+        for c in ref:
+            c.iterate(sweeps)
+            c.merge_and_update()
+    for r, s in zip(ref, sys_):
+        np.testing.assert_array_equal(r.histogram(), s.histogram())
+        np.testing.assert_array_equal(r.lnW().view(np.uint64), s.lnW().view(np.uint64))
+        np.testing.assert_array_equal(r.spins(), s.spins())
+        np.testing.assert_array_equal(r.thresholds(), s.thresholds())
+        assert r.sweep_counter() == s.sweep_counter() == 5 * sweeps
+    b.close()
+
+
+def test_batch_graph_replay_matches_oracle():
+    sys_ = _make()
+    b = m.Batch(sys_)
+    for _ in range(2):
+        b.run(2, 10, use_graph=True)   # same graph replayed twice
+    s, L, q, p, seed, beta = MIX[1]
+    o = oracle.Run(s, L, q, p, seed, beta=beta or 0.0)
+    o.init()
+    for _ in range(4):
+        o.iterate(10, 8)
+        o.update()
+    compare_state(sys_[1], o, "batched Potts after 4 graph iterations")
+
+
+def test_batch_rejects_unmerged_and_duplicates():
+    sys_ = _make()[:2]
+    with pytest.raises(m.MucaError):
+        m.Batch([sys_[0], sys_[0]])
+    b = m.Batch(sys_)
+    sys_[0].iterate(3)
+    with pytest.raises(m.MucaError) as e:
+        b.run(1, 5)
+    assert e.value.code == -5
+    sys_[0].merge_and_update()
+    b.run(1, 5)
