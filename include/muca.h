@@ -47,7 +47,7 @@ enum {
     MUCA_ISING2D = 0,      /* H = -J sum_<ij> s_i s_j, L x L periodic, MUCA in E   */
     MUCA_POTTS2D = 1,      /* H = -J sum_<ij> delta(s_i,s_j), q states, MUCA in E  */
     MUCA_ISING2D_MUMA = 2, /* Ising at fixed beta, weight exp(-beta E) W(M), Eq. 3 */
-    MUCA_POLYMER3D = 3     /* FENE + Lennard-Jones chain, Eq. 7 (see muca_set_param) */
+    MUCA_POLYMER3D = 3     /* FENE + Lennard-Jones chain, Eq. 7, MUCA in E (see muca_set_param) */
 };
 
 typedef struct muca_ctx muca_ctx;     /* opaque, library-owned */
@@ -60,7 +60,9 @@ const char *muca_last_error(void);
  * (Fig. 1: "initialized in p independent realizations with the same weight
  * function").  L_or_N is the lattice side L (spins) or the bead count N
  * (polymer); q is the number of Potts states (ignored otherwise).
- * Spins: L even, 4 <= L <= 64 and L % 4 == 0; Potts 2 <= q <= 16, L <= 48.
+ * Spins: L in {4, 8, 12, 16, 24, 32, 48, 64}; Potts 2 <= q <= 16, L <= 48.
+ * Polymer: 2 <= N <= 128 beads; the walkers start as random walks of unit
+ * bonds and walk into the energy window before anything is recorded.
  * The walkers' initial states are drawn from the counter-based generator
  * keyed by `seed` (ln W = 0 everywhere, so the first iteration samples
  * beta = 0, where a random state is already in equilibrium: the paper
@@ -88,9 +90,11 @@ int muca_init_ex(muca_ctx **out, int system, int L_or_N, int q, int p, uint64_t 
  *                 walker w draws from the stream of walker w + offset, so the
  *                 union of the shards equals one context of all walkers;
  *                 re-draws the initial states; before the first iterate.
- *   Polymer only (before the first iterate): "e_lo", "e_hi", "bin_width",
- *   "step" (side of the displacement cube), "fene_K", "fene_R",
- *   "lj_cutoff".
+ *   Polymer only (before the first iterate): "e_lo", "e_hi" (the energy
+ *   window, bins of width 0.1, at most 32768 bins; default [2N, 6N)),
+ *   "fene_K", "fene_R" (default 40, 1.5).  Fixed: LJ eps = sigma = 1 cut at
+ *   2.5 and shifted, acting on beads |i-j| >= 2; FENE on bonds; single-bead
+ *   moves uniform in a cube of side 1229/4096 on a 2^-44 grid.
  * Unknown key or bad value: MUCA_ERR_ARG; too late: MUCA_ERR_STATE. */
 int muca_set_param(muca_ctx *ctx, const char *key, double value);
 
@@ -193,6 +197,14 @@ int muca_det_math(int fn, const double *host_in, double *host_out, int64_t n);
  * two contexts on the same device from two threads -- race and give wrong
  * histograms; serialise them. */
 int muca_iterate_noalloc(muca_ctx *ctx, int64_t sweeps, uint64_t *dev_H_out);
+
+/* Polymer: bead coordinates (p*N*3 doubles, walker-major, then bead, then
+ * x/y/z; exact values of the 2^-44 grid the moves live on) and, if host_energies
+ * is not NULL, the walkers' running energies (p doubles). */
+int muca_get_coords(muca_ctx *ctx, double *host_coords, int64_t n, double *host_energies, int p);
+/* Polymer: the largest difference between a running energy and its from-scratch
+ * recomputation seen at the refresh after each muca_iterate. */
+int muca_get_drift(muca_ctx *ctx, double *host_out);
 
 /* Wait for the context's stream. */
 int muca_synchronize(muca_ctx *ctx);

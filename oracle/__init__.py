@@ -103,6 +103,8 @@ def _bind_polymer(L):
                  "orc_poly_get_energy", "orc_poly_get_bins", "orc_poly_get_counters"):
         getattr(L, name).argtypes = [c.c_void_p, c.c_void_p]
     L.orc_poly_set_beta.argtypes = [c.c_void_p, c.c_double]
+    L.orc_poly_reweight.argtypes = [c.c_void_p, c.c_double, c.c_void_p, c.c_void_p]
+    L.orc_poly_get_walker_events.argtypes = [c.c_void_p, c.c_void_p]
     L.orc_poly_refresh_energy.argtypes = [c.c_void_p]
     L.orc_poly_refresh_energy.restype = c.c_double
     L.orc_poly_energy.argtypes = [c.c_int, c.c_void_p, c.c_int]
@@ -327,6 +329,15 @@ class PolyRun:
 
     def counters(self):
         return self._get("orc_poly_get_counters", 2, np.int64)
+
+    def walker_events(self):
+        return self._get("orc_poly_get_walker_events", 2 * self.p, np.int64).reshape(self.p, 2)
+
+    def reweight(self, beta: float):
+        out = np.zeros(4)
+        lnP = np.zeros(self.B)
+        self._lib.orc_poly_reweight(self.h, beta, _ptr(out), _ptr(lnP))
+        return out, lnP
 
 
 def poly_energy(X: np.ndarray) -> float:

@@ -97,6 +97,8 @@ void orc_poly_get_coords(void *h, double *out /* p*N*3 */);
 void orc_poly_get_energy(void *h, double *out /* p */);
 void orc_poly_get_bins(void *h, int32_t *out /* p */);
 void orc_poly_get_counters(void *h, int64_t *out /* {near-tie acceptances, bin-edge events} */);
+void orc_poly_reweight(void *h, double beta, double out[4], double *lnP /* nullable, B */);
+void orc_poly_get_walker_events(void *h, int64_t *out /* p*2 */);
 double orc_poly_energy(int N, const double *X, int unused);
 double orc_poly_pair(double r, int sep, int unused);
 

@@ -22,6 +22,9 @@
  * window (walk-in after the start) a move is accepted iff it does not increase
  * the distance of E to the window, and nothing is recorded.  In canonical mode
  * (beta > 0) the weight is exp(-beta E) and there is no window.
+ * After each call that runs sweeps, every chain is shifted so that bead 0 sits
+ * at the origin (an exact shift by a grid vector, so coordinates stay well
+ * inside the range where binary64 holds the grid exactly).
  * Initial chain: bead 0 at the origin; bead k = bead k-1 + u_hat, with u_hat a
  * unit vector from Marsaglia's (1972) method on Philox tag-2 words, rounded
  * to the 2^-44 grid; redrawn (up to 64 times) while any earlier bead lies
@@ -249,8 +252,10 @@ static void poly_walker_sweeps(orc_poly *P, int w, int64_t g0, int64_t sweeps, u
                                 accept = (double)u[3] < floor(ldexp(pa, 32));
                                 if (fabs((double)u[3] * 0x1p-32 - pa) < 1e-6) ev[0] += 1;
                             }
+                            /* a bin edge within 1e-4 of the new energy: an FP32 implementation of
+                             * the pair terms may bin this state differently */
                             double edge = (En - P->e_lo) * 10.0;
-                            if (fabs(edge - nearbyint(edge)) < 1e-8) ev[1] += 1;
+                            if (fabs(edge - nearbyint(edge)) < 1e-3) ev[1] += 1;
                         }
                     } else {
                         accept = poly_window_dist(P, En) <= poly_window_dist(P, E);
@@ -271,6 +276,10 @@ static void poly_walker_sweeps(orc_poly *P, int w, int64_t g0, int64_t sweeps, u
             if (b >= 0 && b < P->B) hist[b] += 1;
         }
     }
+    /* recentre on bead 0 (an exact shift by a grid vector: energies are unchanged) */
+    double c[3] = {X[0], X[1], X[2]};
+    for (int j = 0; j < N; ++j)
+        for (int a = 0; a < 3; ++a) X[3 * j + a] -= c[a];
     P->E[w] = E;
 }
 
@@ -399,4 +408,49 @@ void orc_poly_get_counters(void *h, int64_t *out)
         out[0] += P->events[2 * w];
         out[1] += P->events[2 * w + 1];
     }
+}
+
+/* Eq. (2) for the polymer with E at bin centres: out = {<E>, <E^2>, C_V per bead,
+ * ln of <exp(-beta E)> over the estimated density of states normalised to 1}. */
+void orc_poly_reweight(void *h, double beta, double out[4], double *lnP)
+{
+    orc_poly *P = (orc_poly *)h;
+    const int B = P->B;
+    double *x = (double *)malloc(sizeof(double) * B), *lo = (double *)malloc(sizeof(double) * B);
+    double m = -INFINITY, m2 = -INFINITY;
+    for (int b = 0; b < B; ++b) {
+        x[b] = lo[b] = -INFINITY;
+        if (P->H_last[b] == 0) continue;
+        lo[b] = log((double)P->H_last[b]) - P->lnW_sampled[b];
+        x[b] = lo[b] - beta * (P->e_lo + 0.1 * (b + 0.5));
+        if (x[b] > m) m = x[b];
+        if (lo[b] > m2) m2 = lo[b];
+    }
+    double z = 0.0, z2 = 0.0;
+    for (int b = 0; b < B; ++b)
+        if (x[b] > -INFINITY) {
+            z += exp(x[b] - m);
+            z2 += exp(lo[b] - m2);
+        }
+    double lse = m + log(z), a1 = 0.0, a2 = 0.0;
+    for (int b = 0; b < B; ++b) {
+        double lp = (x[b] > -INFINITY) ? x[b] - lse : -INFINITY;
+        if (lnP) lnP[b] = lp;
+        if (x[b] == -INFINITY) continue;
+        double E = P->e_lo + 0.1 * (b + 0.5), pr = exp(lp);
+        a1 += pr * E;
+        a2 += pr * E * E;
+    }
+    out[0] = a1;
+    out[1] = a2;
+    out[2] = beta * beta * (a2 - a1 * a1) / P->N;
+    out[3] = lse - (m2 + log(z2));
+    free(x);
+    free(lo);
+}
+
+void orc_poly_get_walker_events(void *h, int64_t *out)
+{
+    orc_poly *P = (orc_poly *)h;
+    memcpy(out, P->events, sizeof(int64_t) * 2 * (size_t)P->p);
 }

@@ -23,7 +23,7 @@ __all__ = ["Muca", "MucaError", "ISING2D", "POTTS2D", "ISING2D_MUMA", "POLYMER3D
            "muca_get_histogram", "muca_get_flatness", "muca_get_reweight", "muca_get_state", "muca_set_state",
            "muca_get_spins", "muca_get_walker_bins", "muca_get_thresholds", "muca_get_sweep_counter",
            "muca_synchronize", "muca_free", "muca_last_error", "muca_det_math",
-           "muca_iterate_noalloc", "muca_batch_create", "muca_batch_run", "muca_batch_free", "Batch"]
+           "muca_iterate_noalloc", "muca_get_coords", "muca_get_drift", "muca_batch_create", "muca_batch_run", "muca_batch_free", "Batch"]
 
 
 def _p(a: np.ndarray):
@@ -129,6 +129,17 @@ def muca_get_sweep_counter(h) -> int:
     return v.value
 
 
+def muca_get_coords(h, coords: np.ndarray, energies: np.ndarray | None = None):
+    check(load().muca_get_coords(h, _p(coords), coords.size, None if energies is None else _p(energies),
+                                 0 if energies is None else energies.size), "muca_get_coords")
+
+
+def muca_get_drift(h) -> float:
+    v = ctypes.c_double()
+    check(load().muca_get_drift(h, ctypes.byref(v)), "muca_get_drift")
+    return v.value
+
+
 def muca_det_math(fn: int, x: np.ndarray) -> np.ndarray:
     x = np.ascontiguousarray(x, dtype=np.float64)
     out = np.zeros_like(x)
@@ -194,7 +205,7 @@ class Muca:
 
     def __init__(self, system: int, L: int, q: int = 2, p: int = 64, seed: int = 1, *, beta: float | None = None,
                  record: int = 0, block: int | None = None, walker_offset: int = 0, stream=None,
-                 arena: str | None = None):
+                 arena: str | None = None, window: tuple | None = None):
         self.system, self.L, self.q, self.p, self.seed = system, L, q, p, seed
         self._arena = None
         if arena == "torch":
@@ -206,8 +217,7 @@ class Muca:
             self.h = muca_init_ex(system, L, q, p, seed, ptr, nbytes)
         else:
             self.h = muca_init(system, L, q, p, seed)
-        self.B = muca_num_bins(self.h)
-        self.N = L * L
+        self.N = L if system == POLYMER3D else L * L
         self.C = {ISING2D: 5, POTTS2D: 9, ISING2D_MUMA: 10}.get(system, 0)
         if stream is not None:
             muca_set_stream(self.h, int(getattr(stream, "cuda_stream", stream)))
@@ -219,6 +229,10 @@ class Muca:
             muca_set_param(self.h, "block", block)
         if walker_offset:
             muca_set_param(self.h, "walker_offset", walker_offset)
+        if window is not None:
+            muca_set_param(self.h, "e_lo", window[0])
+            muca_set_param(self.h, "e_hi", window[1])
+        self.B = muca_num_bins(self.h)
 
     def close(self):
         if getattr(self, "h", None) is not None:
@@ -292,6 +306,20 @@ class Muca:
 
     def sweep_counter(self) -> int:
         return muca_get_sweep_counter(self.h)
+
+    def coords(self) -> np.ndarray:
+        c = np.zeros(self.p * self.N * 3, dtype=np.float64)
+        muca_get_coords(self.h, c)
+        return c.reshape(self.p, self.N, 3)
+
+    def energies(self) -> np.ndarray:
+        c = np.zeros(self.p * self.N * 3, dtype=np.float64)
+        e = np.zeros(self.p, dtype=np.float64)
+        muca_get_coords(self.h, c, e)
+        return e
+
+    def drift(self) -> float:
+        return muca_get_drift(self.h)
 
     def get_state(self) -> np.ndarray:
         n = muca_get_state(self.h, None)

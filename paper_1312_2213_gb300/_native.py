@@ -38,6 +38,8 @@ PROTOTYPES = {
     "muca_get_walker_bins": (c_int, [c_vp, c_vp, c_int]),
     "muca_get_thresholds": (c_int, [c_vp, c_vp, c_i64]),
     "muca_get_sweep_counter": (c_int, [c_vp, P(c_i64)]),
+    "muca_get_coords": (c_int, [c_vp, c_vp, c_i64, c_vp, c_int]),
+    "muca_get_drift": (c_int, [c_vp, P(c_dbl)]),
     "muca_det_math": (c_int, [c_int, c_vp, c_vp, c_i64]),
     "muca_iterate_noalloc": (c_int, [c_vp, c_i64, c_vp]),
     "muca_batch_create": (c_int, [P(c_vp), c_int, P(c_vp)]),

@@ -41,7 +41,7 @@ constexpr size_t kAlign = 256;
 size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
 struct Layout {
-    size_t lat, bin, T, lnW, lnW_sampled, G, lnR, H, Hpart, rlist, reach, state, out, total;
+    size_t lat, bin, T, lnW, lnW_sampled, G, lnR, H, Hpart, rlist, reach, state, out, Eq, lnWq, total;
 };
 
 }  // namespace
@@ -66,6 +66,9 @@ struct muca_ctx {
     uint8_t *reach = nullptr;
     DevState *state = nullptr;
     double *out = nullptr;  // reweight outputs: 4 + B doubles
+    // polymer: energies and ln W in fixed point, window and FENE parameters
+    long long *Eq = nullptr, *lnWq = nullptr;
+    double e_lo = 0.0, e_hi = 0.0, fene_K = 40.0, fene_R = 1.5;
     std::vector<uint8_t> h_reach;
     std::vector<int32_t> h_rlist;
 };
@@ -75,7 +78,10 @@ namespace {
 bool valid_config(int system, int L, int q, int p, std::string &why)
 {
     if (p < 1) { why = "p must be >= 1"; return false; }
-    if (system == kPolymer) { why = "the polymer system is not available in this build"; return false; }
+    if (system == kPolymer) {
+        if (!polymer_supported(L)) { why = "polymer bead count must be in [2, 128]"; return false; }
+        return true;
+    }
     if (system != kIsing && system != kPotts && system != kMuma) { why = "unknown system"; return false; }
     if (system == kPotts && (q < 2 || q > 16)) { why = "Potts q must be in [2, 16]"; return false; }
     if (!spin_sweep_supported(system, L)) {
@@ -85,8 +91,27 @@ bool valid_config(int system, int L, int q, int p, std::string &why)
     return true;
 }
 
+// Polymer bins of width 0.1 over [e_lo, e_hi).
+int polymer_bins(double e_lo, double e_hi) { return (int)((e_hi - e_lo) * 10.0 + 0.5); }
+
 void fill_shape(muca_ctx *c, int system, int L, int q, int p)
 {
+    if (system == kPolymer) {
+        c->system = system;
+        c->L = L;
+        c->N = L;  // beads
+        c->q = 0;
+        c->p = p;
+        c->e_lo = 2.0 * L;  // default window; set "e_lo"/"e_hi" for the run's own
+        c->e_hi = 6.0 * L;
+        c->B = polymer_bins(c->e_lo, c->e_hi);
+        c->C = 0;
+        c->pstride = p;
+        c->wpw = 0;
+        c->nblk_max = 1;
+        c->block = 128;
+        return;
+    }
     c->system = system;
     c->L = L;
     c->q = (system == kPotts) ? q : 2;
@@ -107,7 +132,9 @@ void reachable_bins(muca_ctx *c)
 {
     const int N = c->N, B = c->B;
     c->h_reach.assign(B, 1);
-    if (c->system == kIsing) {
+    if (c->system == kPolymer) {
+        // every bin of the window
+    } else if (c->system == kIsing) {
         c->h_reach[1] = 0;
         c->h_reach[N - 1] = 0;
     } else if (c->system == kPotts) {
@@ -133,6 +160,26 @@ Layout plan(const muca_ctx *c)
         off += align_up(bytes);
         return o;
     };
+    if (c->system == kPolymer) {
+        const size_t Bc = kPolyMaxBins;
+        l.lat = take(sizeof(long long) * 3 * (size_t)c->N * c->p);
+        l.bin = take(sizeof(int32_t) * (size_t)c->p);
+        l.Eq = take(sizeof(long long) * (size_t)c->p);
+        l.T = take(0);
+        l.lnW = take(sizeof(double) * Bc);
+        l.lnW_sampled = take(sizeof(double) * Bc);
+        l.G = take(sizeof(double) * Bc);
+        l.lnR = take(sizeof(double) * Bc);
+        l.H = take(sizeof(unsigned long long) * Bc);
+        l.Hpart = take(sizeof(unsigned long long) * Bc);
+        l.lnWq = take(sizeof(long long) * Bc);
+        l.rlist = take(sizeof(int32_t) * Bc);
+        l.reach = take(Bc);
+        l.state = take(sizeof(DevState));
+        l.out = take(sizeof(double) * (4 + Bc));
+        l.total = off;
+        return l;
+    }
     l.lat = take(sizeof(uint32_t) * (size_t)c->wpw * c->pstride);
     l.bin = take(sizeof(int32_t) * (size_t)c->pstride);
     l.T = take(sizeof(uint32_t) * (size_t)c->B * c->C);
@@ -164,6 +211,8 @@ UpdateArgs update_args(const muca_ctx *c)
     a.L = c->L;
     a.beta = c->beta;
     a.flat_ratio = c->flat_ratio;
+    a.e_lo = c->e_lo;
+    if (c->system == kPolymer) a.nblocks = 1;  // the open histogram is one global slot
     a.reach = c->reach;
     a.rlist = c->rlist;
     a.Hpart = c->Hpart;
@@ -177,8 +226,65 @@ UpdateArgs update_args(const muca_ctx *c)
     return a;
 }
 
+PolyArgs poly_args(const muca_ctx *c, int64_t sweeps)
+{
+    PolyArgs a{};
+    a.X = (long long *)c->lat;
+    a.E = c->Eq;
+    a.bin = c->bin;
+    a.lnWq = c->lnWq;
+    a.H = c->Hpart;
+    a.state = c->state;
+    a.p = c->p;
+    a.N = c->N;
+    a.B = c->B;
+    a.record = c->record;
+    a.walker_offset = c->walker_offset;
+    a.elo_q = llrint(c->e_lo * 1099511627776.0);                      // e_lo * 2^40
+    a.ehi_q = a.elo_q + ((long long)c->B * 1099511627776LL + 9) / 10;  // first energy with bin >= B
+    a.fene_KR2_half = (float)(0.5 * c->fene_K * c->fene_R * c->fene_R);
+    a.fene_invR2 = (float)(1.0 / (c->fene_R * c->fene_R));
+    a.lj_rc2 = 6.25f;
+    const double irc6 = 1.0 / (6.25 * 6.25 * 6.25);
+    a.lj_shift = (float)(4.0 * (irc6 * irc6 - irc6));
+    a.sweeps = sweeps;
+    SpinSweepArgs keys{};
+    fill_round_keys(keys, c->seed);
+    a.key0 = keys.key0;
+    a.key1 = keys.key1;
+    for (int i = 0; i < 20; ++i) a.rk[i] = keys.rk[i];
+    return a;
+}
+
+// Upload the reachable list and reset the weights; for the polymer also
+// recompute every walker's energy and bin for the current window.
+int reset_weights(muca_ctx *c)
+{
+    reachable_bins(c);
+    MUCA_CUDA(cudaMemcpyAsync(c->reach, c->h_reach.data(), c->B, cudaMemcpyHostToDevice, c->stream));
+    MUCA_CUDA(cudaMemcpyAsync(c->rlist, c->h_rlist.data(), sizeof(int32_t) * c->nreach, cudaMemcpyHostToDevice,
+                              c->stream));
+    UpdateArgs a = update_args(c);
+    MUCA_CUDA(launch_init_lnW(a, c->stream));
+    if (c->system == kPolymer) {
+        PolyArgs pa = poly_args(c, 0);
+        MUCA_CUDA(launch_poly_energy(pa, 0, c->stream));
+        MUCA_CUDA(launch_poly_lnwq(c->lnW, c->lnWq, c->B, c->stream));
+    } else {
+        MUCA_CUDA(launch_thresholds(a, c->stream));
+    }
+    MUCA_CUDA(cudaStreamSynchronize(c->stream));
+    return MUCA_OK;
+}
+
 int init_walkers(muca_ctx *c)
 {
+    if (c->system == kPolymer) {
+        PolyArgs pa = poly_args(c, 0);
+        MUCA_CUDA(launch_poly_init(pa, c->stream));
+        MUCA_CUDA(launch_poly_energy(pa, 0, c->stream));
+        return MUCA_OK;
+    }
     MUCA_CUDA(launch_init_spins(c->system, c->L, c->q, c->p, c->pstride, (uint32_t)(c->seed & 0xffffffffu),
                                 (uint32_t)(c->seed >> 32), c->walker_offset, c->lat, c->bin, c->stream));
     return MUCA_OK;
@@ -201,18 +307,14 @@ int setup(muca_ctx *c)
     c->reach = (uint8_t *)(base + l.reach);
     c->state = (DevState *)(base + l.state);
     c->out = (double *)(base + l.out);
-    reachable_bins(c);
+    if (c->system == kPolymer) {
+        c->Eq = (long long *)(base + l.Eq);
+        c->lnWq = (long long *)(base + l.lnWq);
+    }
     MUCA_CUDA(cudaMemsetAsync(c->arena, 0, l.total, c->stream));
-    MUCA_CUDA(cudaMemcpyAsync(c->reach, c->h_reach.data(), c->B, cudaMemcpyHostToDevice, c->stream));
-    MUCA_CUDA(cudaMemcpyAsync(c->rlist, c->h_rlist.data(), sizeof(int32_t) * c->nreach, cudaMemcpyHostToDevice,
-                              c->stream));
-    UpdateArgs a = update_args(c);
-    MUCA_CUDA(launch_init_lnW(a, c->stream));
     int rc = init_walkers(c);
     if (rc) return rc;
-    MUCA_CUDA(launch_thresholds(a, c->stream));
-    MUCA_CUDA(cudaStreamSynchronize(c->stream));
-    return MUCA_OK;
+    return reset_weights(c);
 }
 
 int create(muca_ctx **out, int system, int L, int q, int p, uint64_t seed, void *arena, size_t arena_bytes)
@@ -271,15 +373,45 @@ struct StateHeader {
     char magic[8];
     int32_t version, system, L, q, p, B, C, wpw, pstride, record, walker_offset;
     uint64_t seed;
-    double beta;
+    double beta, e_lo, e_hi, fene_K, fene_R;
     DevState dev;
 };
 
+// Device sections of a checkpoint, in order: walkers, bins, [polymer energies],
+// ln W, ln W sampled, G, lnR, merged H, open histogram, thresholds / ln W fixed point.
+struct Section {
+    void *dev;
+    size_t bytes;
+};
+
+std::vector<Section> state_sections(const muca_ctx *c)
+{
+    std::vector<Section> v;
+    const size_t B = (size_t)c->B;
+    if (c->system == kPolymer) {
+        v.push_back({c->lat, sizeof(long long) * 3 * (size_t)c->N * c->p});
+        v.push_back({c->bin, sizeof(int32_t) * (size_t)c->p});
+        v.push_back({c->Eq, sizeof(long long) * (size_t)c->p});
+    } else {
+        v.push_back({c->lat, sizeof(uint32_t) * (size_t)c->wpw * c->pstride});
+        v.push_back({c->bin, sizeof(int32_t) * (size_t)c->p});
+    }
+    v.push_back({c->lnW, sizeof(double) * B});
+    v.push_back({c->lnW_sampled, sizeof(double) * B});
+    v.push_back({c->G, sizeof(double) * B});
+    v.push_back({c->lnR, sizeof(double) * B});
+    v.push_back({c->H, sizeof(unsigned long long) * B});
+    v.push_back({nullptr, sizeof(unsigned long long) * B});  // open histogram (summed over block slots)
+    if (c->system == kPolymer) v.push_back({c->lnWq, sizeof(long long) * B});
+    else v.push_back({c->T, sizeof(uint32_t) * B * c->C});
+    return v;
+}
+
 size_t state_bytes(const muca_ctx *c)
 {
-    return sizeof(StateHeader) + sizeof(uint32_t) * (size_t)c->wpw * c->pstride + sizeof(int32_t) * (size_t)c->p +
-           sizeof(double) * 4 * (size_t)c->B + sizeof(unsigned long long) * 2 * (size_t)c->B +
-           sizeof(uint32_t) * (size_t)c->B * c->C;
+    size_t n = sizeof(StateHeader);
+    for (const Section &s : state_sections(c)) n += s.bytes;
+    return n;
 }
 
 }  // namespace
@@ -326,9 +458,30 @@ int muca_set_param(muca_ctx *c, const char *key, double v)
         if (locked) return fail(MUCA_ERR_STATE, "beta must be set before the first iterate");
         if (!(v == v) || v < 0.0) return fail(MUCA_ERR_ARG, "beta must be >= 0");
         c->beta = v;
+        if (c->system == kPolymer) return MUCA_OK;  // reweighting only
         UpdateArgs a = update_args(c);
         MUCA_CUDA(launch_thresholds(a, c->stream));
         return MUCA_OK;
+    }
+    if (k == "e_lo" || k == "e_hi" || k == "fene_K" || k == "fene_R") {
+        if (c->system != kPolymer) return fail(MUCA_ERR_ARG, "'%s' applies to the polymer only", key);
+        if (locked) return fail(MUCA_ERR_STATE, "%s must be set before the first iterate", key);
+        if (!(v == v) || v > 1e6 || v < -1e6) return fail(MUCA_ERR_ARG, "bad value for %s", key);
+        double lo = c->e_lo, hi = c->e_hi, K = c->fene_K, R = c->fene_R;
+        if (k == "e_lo") lo = v;
+        if (k == "e_hi") hi = v;
+        if (k == "fene_K") K = v;
+        if (k == "fene_R") R = v;
+        if (!(K > 0.0) || !(R > 0.0)) return fail(MUCA_ERR_ARG, "fene_K and fene_R must be > 0");
+        const int B = (hi > lo) ? polymer_bins(lo, hi) : 0;
+        if (B < 2 || B > kPolyMaxBins)
+            return fail(MUCA_ERR_RANGE, "window [%g, %g) gives %d bins of 0.1; need 2..%d", lo, hi, B, kPolyMaxBins);
+        c->e_lo = lo;
+        c->e_hi = hi;
+        c->fene_K = K;
+        c->fene_R = R;
+        c->B = B;
+        return reset_weights(c);
     }
     if (k == "record") {
         if (locked) return fail(MUCA_ERR_STATE, "record must be set before the first iterate");
@@ -349,7 +502,8 @@ int muca_set_param(muca_ctx *c, const char *key, double v)
         const long long o = (long long)v;
         if ((double)o != v || o < 0 || o + c->p > 0x7fffffffLL) return fail(MUCA_ERR_ARG, "bad walker_offset");
         c->walker_offset = (int)o;
-        return init_walkers(c);
+        if (int rc = init_walkers(c)) return rc;
+        return c->system == kPolymer ? reset_weights(c) : MUCA_OK;
     }
     return fail(MUCA_ERR_ARG, "unknown parameter '%s'", key);
 }
@@ -366,6 +520,17 @@ int muca_iterate(muca_ctx *c, int64_t sweeps)
 {
     if (int rc = check_ctx(c)) return rc;
     if (sweeps < 1) return fail(MUCA_ERR_ARG, "sweeps must be >= 1");
+    if (c->system == kPolymer) {
+        if (sweeps > 0x7fffffffLL / c->N) return fail(MUCA_ERR_RANGE, "too many sweeps in one call");
+        PolyArgs pa = poly_args(c, sweeps);
+        MUCA_CUDA(launch_poly_sweep(pa, c->block, c->stream));
+        MUCA_CUDA(launch_advance(c->state, sweeps, c->stream));
+        // refresh the running energies from scratch; the largest change is recorded
+        MUCA_CUDA(launch_poly_energy(pa, 1, c->stream));
+        c->started = true;
+        c->open = true;
+        return MUCA_OK;
+    }
     SpinSweepArgs a{};
     a.T = c->T;
     a.lattice = c->lat;
@@ -399,7 +564,11 @@ int muca_merge_and_update(muca_ctx *c, int *is_flat)
     UpdateArgs a = update_args(c);
     MUCA_CUDA(launch_merge(a, c->stream));
     MUCA_CUDA(launch_recursion(a, c->stream));
-    MUCA_CUDA(launch_thresholds(a, c->stream));
+    if (c->system == kPolymer) {
+        MUCA_CUDA(launch_poly_lnwq(c->lnW, c->lnWq, c->B, c->stream));
+    } else {
+        MUCA_CUDA(launch_thresholds(a, c->stream));
+    }
     c->started = true;
     c->open = false;
     if (is_flat) {
@@ -466,6 +635,7 @@ int muca_get_reweight(muca_ctx *c, double beta, double host_out[4], double *host
 int muca_get_spins(muca_ctx *c, int8_t *host_out, int64_t n)
 {
     if (int rc = check_ctx(c)) return rc;
+    if (c->system == kPolymer) return fail(MUCA_ERR_ARG, "the polymer has no spins; use muca_get_coords");
     if (!host_out || n != (int64_t)c->p * c->N) return fail(MUCA_ERR_ARG, "need p*L*L = %lld bytes",
                                                               (long long)c->p * c->N);
     int8_t *tmp = nullptr;
@@ -488,9 +658,40 @@ int muca_get_walker_bins(muca_ctx *c, int32_t *host_out, int p)
 int muca_get_thresholds(muca_ctx *c, uint32_t *host_out, int64_t n)
 {
     if (int rc = check_ctx(c)) return rc;
+    if (c->system == kPolymer) return fail(MUCA_ERR_ARG, "the polymer has no threshold table");
     if (!host_out || n != (int64_t)c->B * c->C) return fail(MUCA_ERR_ARG, "need B*C = %lld uint32",
                                                               (long long)c->B * c->C);
     return d2h(c, host_out, c->T, sizeof(uint32_t) * (size_t)n);
+}
+
+int muca_get_coords(muca_ctx *c, double *host_coords, int64_t n, double *host_energies, int p)
+{
+    if (int rc = check_ctx(c)) return rc;
+    if (c->system != kPolymer) return fail(MUCA_ERR_ARG, "coordinates exist for the polymer only");
+    if (!host_coords || n != (int64_t)c->p * c->N * 3) return fail(MUCA_ERR_ARG, "need p*N*3 = %lld doubles",
+                                                                      (long long)c->p * c->N * 3);
+    if (host_energies && p != c->p) return fail(MUCA_ERR_ARG, "need p = %d energies", c->p);
+    double *tmp = nullptr;
+    MUCA_CUDA(cudaMalloc(&tmp, sizeof(double) * ((size_t)n + c->p)));
+    PolyArgs pa = poly_args(c, 0);
+    cudaError_t e = launch_poly_unpack(pa, tmp, tmp + n, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(host_coords, tmp, sizeof(double) * (size_t)n, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess && host_energies)
+        e = cudaMemcpyAsync(host_energies, tmp + n, sizeof(double) * c->p, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    cudaFree(tmp);
+    if (e != cudaSuccess) return fail(MUCA_ERR_CUDA, "muca_get_coords: %s", cudaGetErrorString(e));
+    return MUCA_OK;
+}
+
+int muca_get_drift(muca_ctx *c, double *host_out)
+{
+    if (int rc = check_ctx(c)) return rc;
+    if (!host_out) return fail(MUCA_ERR_ARG, "out is NULL");
+    DevState st;
+    if (int rc = d2h(c, &st, c->state, sizeof st)) return rc;
+    *host_out = (double)st.drift_max_q * 0x1p-40;
+    return MUCA_OK;
 }
 
 int muca_get_sweep_counter(muca_ctx *c, int64_t *host_out)
@@ -515,8 +716,8 @@ int muca_get_state(muca_ctx *c, void *host_buf, size_t *bytes)
     if (*bytes < need) return fail(MUCA_ERR_ARG, "state buffer too small: need %zu bytes", need);
     char *p = (char *)host_buf;
     StateHeader h{};
-    memcpy(h.magic, "MUCAST1", 8);
-    h.version = 1;
+    memcpy(h.magic, "MUCAST2", 8);
+    h.version = 2;
     h.system = c->system;
     h.L = c->L;
     h.q = c->q;
@@ -529,36 +730,31 @@ int muca_get_state(muca_ctx *c, void *host_buf, size_t *bytes)
     h.walker_offset = c->walker_offset;
     h.seed = c->seed;
     h.beta = c->beta;
+    h.e_lo = c->e_lo;
+    h.e_hi = c->e_hi;
+    h.fene_K = c->fene_K;
+    h.fene_R = c->fene_R;
     if (int rc = d2h(c, &h.dev, c->state, sizeof h.dev)) return rc;
     memcpy(p, &h, sizeof h);
     p += sizeof h;
-    auto pull = [&](const void *dev, size_t n) -> int {
-        cudaError_t e = cudaMemcpyAsync(p, dev, n, cudaMemcpyDeviceToHost, c->stream);
-        if (e != cudaSuccess) return fail(MUCA_ERR_CUDA, "muca_get_state: %s", cudaGetErrorString(e));
-        p += n;
-        return MUCA_OK;
-    };
-    int rc = 0;
-    if ((rc = pull(c->lat, sizeof(uint32_t) * (size_t)c->wpw * c->pstride))) return rc;
-    if ((rc = pull(c->bin, sizeof(int32_t) * (size_t)c->p))) return rc;
-    if ((rc = pull(c->lnW, sizeof(double) * c->B))) return rc;
-    if ((rc = pull(c->lnW_sampled, sizeof(double) * c->B))) return rc;
-    if ((rc = pull(c->G, sizeof(double) * c->B))) return rc;
-    if ((rc = pull(c->lnR, sizeof(double) * c->B))) return rc;
-    if ((rc = pull(c->H, sizeof(unsigned long long) * c->B))) return rc;
-    // open histogram: sum of the block slots (integer, exact)
-    std::vector<unsigned long long> part((size_t)c->nblk_max * c->B), open(c->B, 0ull);
-    {
-        cudaError_t e = cudaMemcpyAsync(part.data(), c->Hpart, sizeof(unsigned long long) * part.size(),
-                                        cudaMemcpyDeviceToHost, c->stream);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
-        if (e != cudaSuccess) return fail(MUCA_ERR_CUDA, "muca_get_state: %s", cudaGetErrorString(e));
-        for (int k = 0; k < c->nblk_max; ++k)
-            for (int b = 0; b < c->B; ++b) open[b] += part[(size_t)k * c->B + b];
+    for (const Section &sec : state_sections(c)) {
+        if (sec.dev) {
+            cudaError_t e = cudaMemcpyAsync(p, sec.dev, sec.bytes, cudaMemcpyDeviceToHost, c->stream);
+            if (e != cudaSuccess) return fail(MUCA_ERR_CUDA, "muca_get_state: %s", cudaGetErrorString(e));
+        } else {
+            // open histogram: sum of the block slots (integer, exact)
+            const int slots = (c->system == kPolymer) ? 1 : c->nblk_max;
+            std::vector<unsigned long long> part((size_t)slots * c->B), open(c->B, 0ull);
+            cudaError_t e = cudaMemcpyAsync(part.data(), c->Hpart, sizeof(unsigned long long) * part.size(),
+                                            cudaMemcpyDeviceToHost, c->stream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+            if (e != cudaSuccess) return fail(MUCA_ERR_CUDA, "muca_get_state: %s", cudaGetErrorString(e));
+            for (int k = 0; k < slots; ++k)
+                for (int b = 0; b < c->B; ++b) open[b] += part[(size_t)k * c->B + b];
+            memcpy(p, open.data(), sec.bytes);
+        }
+        p += sec.bytes;
     }
-    memcpy(p, open.data(), sizeof(unsigned long long) * c->B);
-    p += sizeof(unsigned long long) * c->B;
-    if ((rc = pull(c->T, sizeof(uint32_t) * (size_t)c->B * c->C))) return rc;
     MUCA_CUDA(cudaStreamSynchronize(c->stream));
     *bytes = need;
     return MUCA_OK;
@@ -568,46 +764,64 @@ int muca_set_state(muca_ctx *c, const void *host_buf, size_t bytes)
 {
     if (int rc = check_ctx(c)) return rc;
     if (!host_buf) return fail(MUCA_ERR_ARG, "buffer is NULL");
-    const size_t need = state_bytes(c);
-    if (bytes != need) return fail(MUCA_ERR_ARG, "state size %zu does not match this context (%zu)", bytes, need);
+    if (bytes < sizeof(StateHeader)) return fail(MUCA_ERR_ARG, "not a muca state buffer");
     StateHeader h;
     memcpy(&h, host_buf, sizeof h);
-    if (memcmp(h.magic, "MUCAST1", 8) != 0 || h.version != 1) return fail(MUCA_ERR_ARG, "not a muca state buffer");
-    if (h.system != c->system || h.L != c->L || h.q != c->q || h.p != c->p || h.B != c->B || h.C != c->C ||
-        h.wpw != c->wpw || h.pstride != c->pstride || h.seed != c->seed)
+    if (memcmp(h.magic, "MUCAST2", 8) != 0 || h.version != 2) return fail(MUCA_ERR_ARG, "not a muca state buffer");
+    if (h.system != c->system || h.L != c->L || h.q != c->q || h.p != c->p || h.C != c->C || h.wpw != c->wpw ||
+        h.pstride != c->pstride || h.seed != c->seed)
         return fail(MUCA_ERR_ARG, "state buffer was written by a different configuration");
+    if (c->system == kPolymer) {
+        if (h.B < 2 || h.B > kPolyMaxBins || h.B != polymer_bins(h.e_lo, h.e_hi))
+            return fail(MUCA_ERR_ARG, "state buffer: bad polymer window");
+    } else if (h.B != c->B) {
+        return fail(MUCA_ERR_ARG, "state buffer was written by a different configuration");
+    }
     if (h.record != 0 && h.record != 1) return fail(MUCA_ERR_ARG, "state buffer: bad record mode");
+    const int oldB = c->B;
+    c->B = h.B;  // the polymer window travels with the state
+    const size_t need = state_bytes(c);
+    if (bytes != need) {
+        c->B = oldB;
+        return fail(MUCA_ERR_ARG, "state size %zu does not match this context (%zu)", bytes, need);
+    }
     {
-        // every walker's bin indexes the shared-memory tables of the sweep kernel: check them here
-        const int32_t *bins = (const int32_t *)((const char *)host_buf + sizeof h +
-                                                sizeof(uint32_t) * (size_t)c->wpw * c->pstride);
+        // every walker's bin indexes shared-memory tables of the sweep kernels: check them here
+        const size_t off = sizeof h + state_sections(c)[0].bytes;
+        const int32_t *bins = (const int32_t *)((const char *)host_buf + off);
         for (int w = 0; w < c->p; ++w) {
             int32_t b;
             memcpy(&b, bins + w, sizeof b);
-            if (b < 0 || b >= c->B || !c->h_reach[b]) return fail(MUCA_ERR_ARG, "state buffer: walker %d has bin %d", w, b);
+            const bool ok = (c->system == kPolymer) ? (b >= -1 && b <= c->B)
+                                                    : (b >= 0 && b < c->B && c->h_reach[b]);
+            if (!ok) {
+                c->B = oldB;
+                return fail(MUCA_ERR_ARG, "state buffer: walker %d has bin %d", w, b);
+            }
         }
     }
     c->record = h.record;
     c->walker_offset = h.walker_offset;
     c->beta = h.beta;
+    c->e_lo = h.e_lo;
+    c->e_hi = h.e_hi;
+    c->fene_K = h.fene_K;
+    c->fene_R = h.fene_R;
+    if (c->system == kPolymer) {
+        reachable_bins(c);
+        MUCA_CUDA(cudaMemcpyAsync(c->reach, c->h_reach.data(), c->B, cudaMemcpyHostToDevice, c->stream));
+        MUCA_CUDA(cudaMemcpyAsync(c->rlist, c->h_rlist.data(), sizeof(int32_t) * c->nreach, cudaMemcpyHostToDevice,
+                                  c->stream));
+    }
+    const int slots = (c->system == kPolymer) ? 1 : c->nblk_max;
+    MUCA_CUDA(cudaMemsetAsync(c->Hpart, 0, sizeof(unsigned long long) * (size_t)slots * c->B, c->stream));
     const char *p = (const char *)host_buf + sizeof h;
-    auto push = [&](void *dev, size_t n) -> int {
-        cudaError_t e = cudaMemcpyAsync(dev, p, n, cudaMemcpyHostToDevice, c->stream);
+    for (const Section &sec : state_sections(c)) {
+        void *dst = sec.dev ? sec.dev : (void *)c->Hpart;  // open histogram -> slot 0
+        cudaError_t e = cudaMemcpyAsync(dst, p, sec.bytes, cudaMemcpyHostToDevice, c->stream);
         if (e != cudaSuccess) return fail(MUCA_ERR_CUDA, "muca_set_state: %s", cudaGetErrorString(e));
-        p += n;
-        return MUCA_OK;
-    };
-    int rc = 0;
-    if ((rc = push(c->lat, sizeof(uint32_t) * (size_t)c->wpw * c->pstride))) return rc;
-    if ((rc = push(c->bin, sizeof(int32_t) * (size_t)c->p))) return rc;
-    if ((rc = push(c->lnW, sizeof(double) * c->B))) return rc;
-    if ((rc = push(c->lnW_sampled, sizeof(double) * c->B))) return rc;
-    if ((rc = push(c->G, sizeof(double) * c->B))) return rc;
-    if ((rc = push(c->lnR, sizeof(double) * c->B))) return rc;
-    if ((rc = push(c->H, sizeof(unsigned long long) * c->B))) return rc;
-    MUCA_CUDA(cudaMemsetAsync(c->Hpart, 0, sizeof(unsigned long long) * (size_t)c->nblk_max * c->B, c->stream));
-    if ((rc = push(c->Hpart, sizeof(unsigned long long) * c->B))) return rc;  // open histogram -> slot 0
-    if ((rc = push(c->T, sizeof(uint32_t) * (size_t)c->B * c->C))) return rc;
+        p += sec.bytes;
+    }
     MUCA_CUDA(cudaMemcpyAsync(c->state, &h.dev, sizeof h.dev, cudaMemcpyHostToDevice, c->stream));
     MUCA_CUDA(cudaStreamSynchronize(c->stream));
     c->started = true;
@@ -922,6 +1136,7 @@ extern "C" int muca_iterate_noalloc(muca_ctx *c, int64_t sweeps, uint64_t *dev_H
     if (int rc = check_ctx(c)) return rc;
     if (sweeps < 1) return fail(MUCA_ERR_ARG, "sweeps must be >= 1");
     if (!dev_H_out) return fail(MUCA_ERR_ARG, "dev_H_out is NULL");
+    if (c->system == kPolymer) return fail(MUCA_ERR_ARG, "muca_iterate_noalloc: spin systems only");
     const size_t nblocks = (size_t)((c->p + c->block - 1) / c->block);
     const size_t need = nblocks * (size_t)c->B;
     if (need > kStaticHistSlots)

@@ -22,7 +22,8 @@ struct DevState {
     unsigned long long iteration;      // completed merge+update steps
     double flat_min, flat_mean, flat_max;
     int flat;
-    int pad;
+    int err;                           // non-zero: a device-side check failed
+    unsigned long long drift_max_q;    // polymer: largest |E_running - E_scratch| at a refresh (2^-40 units)
 };
 
 // Everything one spin sweep launch needs.  All pointers are device pointers.
@@ -76,9 +77,38 @@ cudaError_t prepare_sweep_batch(size_t smem);
 cudaError_t launch_sweep_batch(const SpinSweepArgs *d_sys, const int2 *d_tiles, int ntiles, int block, size_t smem,
                                cudaStream_t s);
 
+// Polymer (bead-spring chain, Eq. 7 reading).  Master coordinates are int64 on a
+// 2^-44 grid, walker-major and axis-major: X[(w*3 + a)*N + j]; energies are int64
+// in units of 2^-40; the window is [elo_q, elo_q + B/10) in the same units.
+constexpr int kPolyMaxBins = 32768;
+constexpr int kPolyMaxN = 128;
+constexpr long long kPolyStepQ = 1229;  // displacement grid units per unit of (u - 2^31)
+
+struct PolyArgs {
+    long long *X;
+    long long *E;
+    int32_t *bin;
+    const long long *lnWq;         // ln W in units of 2^-40
+    unsigned long long *H;         // open histogram (B counters)
+    DevState *state;
+    int p, N, B, record, walker_offset;
+    long long elo_q, ehi_q;        // window [elo_q, ehi_q): bins 0..B-1
+    float fene_KR2_half, fene_invR2, lj_rc2, lj_shift;
+    int64_t sweeps;
+    uint32_t key0, key1;
+    uint32_t rk[20];
+};
+bool polymer_supported(int N);
+cudaError_t launch_poly_init(const PolyArgs &a, cudaStream_t s);
+cudaError_t launch_poly_energy(const PolyArgs &a, int track_drift, cudaStream_t s);
+cudaError_t launch_poly_sweep(const PolyArgs &a, int block, cudaStream_t s);
+cudaError_t launch_poly_lnwq(const double *lnW, long long *lnWq, int B, cudaStream_t s);
+cudaError_t launch_poly_unpack(const PolyArgs &a, double *coords, double *energies, cudaStream_t s);
+
 struct UpdateArgs {
     int system, B, nreach, nblocks, N, q, p, pstride, L;
     double beta, flat_ratio;
+    double e_lo;  // polymer: energy of the window's lower edge
     const uint8_t *reach;
     const int32_t *rlist;
     unsigned long long *Hpart, *H;

@@ -1,0 +1,336 @@
+// polymer.cu -- multicanonical sweeps of a single flexible bead-spring polymer
+// (paper: polymer paragraph and Eq. 7; the benchmark's parameters: FENE bonds
+// K = 40, R = 1.5, Lennard-Jones 12-6 between beads |i-j| >= 2 with eps = sigma
+// = 1, cut at 2.5 and shifted; single-bead moves in a cube of side 0.3).
+//
+// One warp per walker.  The beads are visited in order; for bead i every lane
+// evaluates the old and the new pair energies with its partner beads
+// j = lane, lane + 32, ... in FP32 and keeps a compensated (Kahan) sum; the lane
+// sums are converted to 64-bit fixed point (2^-40 energy units) and added with
+// an exact integer warp reduction.  Nothing on the hot path uses FP64, whose
+// rate on GB300 is a small fraction of FP32.
+//
+// Exactness: master coordinates are int64 on a 2^-44 grid and a move adds
+// (u - 2^31) * 1229 grid units per axis (a cube of side 1229/4096 = 0.30005), so
+// the coordinates of an accepted move are exact and identical to any other
+// implementation that draws the same words.  The FP32 pair terms use shadows
+// relative to the walker's bead 0 at the start of each sweep.  The running
+// energy is an exact sum of the fixed-point energy changes; it is refreshed from
+// scratch after every iterate call, and the largest difference is recorded.
+// Acceptance inside the window: d = ln W(b') - ln W(b) from a fixed-point table,
+// accept iff d >= 0 or u < 2^32 exp(d) (FP32 exp); outside the window a move is
+// accepted iff it does not increase the distance to the window (walk-in).
+#include "muca_device.cuh"
+#include "muca_internal.h"
+
+namespace muca {
+
+bool polymer_supported(int N) { return N >= 2 && N <= kPolyMaxN; }
+
+__device__ __forceinline__ float lj_energy(float r2, const PolyArgs &a)
+{
+    const float ir2 = __frcp_rn(r2);
+    const float ir6 = ir2 * ir2 * ir2;
+    const float v = 4.0f * (ir6 * ir6 - ir6) - a.lj_shift;
+    return r2 < a.lj_rc2 ? v : 0.0f;
+}
+
+__device__ __forceinline__ float fene_energy(float r2, const PolyArgs &a)
+{
+    return -a.fene_KR2_half * log1pf(-r2 * a.fene_invR2);
+}
+
+__device__ __forceinline__ long long warp_sum_ll(long long q)
+{
+#pragma unroll
+    for (int off = 16; off; off >>= 1) q += __shfl_xor_sync(0xffffffffu, q, off);
+    return q;
+}
+
+__device__ __forceinline__ int poly_bin(long long E, const PolyArgs &a)
+{
+    const long long b = ((E - a.elo_q) * 10) >> 40;
+    return b < -1 ? -1 : (b > (long long)a.B ? a.B : (int)b);
+}
+
+// Random-walk initial chain (thread per walker): bead k = bead k-1 + unit vector
+// from Marsaglia's method on tag-2 Philox words, rounded to the grid, redrawn (up
+// to 64 times) while an earlier bead is closer than 0.9.  Binary64 with explicit
+// round-to-nearest operations (run once).
+__global__ void k_poly_init(const PolyArgs a)
+{
+    const int w = blockIdx.x * blockDim.x + threadIdx.x;
+    if (w >= a.p) return;
+    const int N = a.N;
+    const uint32_t wid = (uint32_t)(w + a.walker_offset);
+    long long *X = a.X + (size_t)w * 3 * N;
+    X[0] = X[N] = X[2 * N] = 0;
+    uint32_t draw = 0;
+    for (int k = 1; k < N; ++k) {
+        long long cand[3] = {0, 0, 0};
+        for (int attempt = 0; attempt < 64; ++attempt) {
+            double v1 = 0.0, v2 = 0.0, s = 0.5;
+            for (int tries = 0; tries < 4096; ++tries) {
+                const uint4 u = philox4x32_10(make_uint4(draw++, 0u, wid, kTagPolyInit), a.key0, a.key1);
+                v1 = __dsub_rn(__dmul_rn((double)u.x, 0x1p-31), 1.0);
+                v2 = __dsub_rn(__dmul_rn((double)u.y, 0x1p-31), 1.0);
+                s = __dadd_rn(__dmul_rn(v1, v1), __dmul_rn(v2, v2));
+                if (s < 1.0 && s > 0.0) break;
+            }
+            const double f = __dmul_rn(2.0, __dsqrt_rn(__dsub_rn(1.0, s)));
+            const double uh[3] = {__dmul_rn(v1, f), __dmul_rn(v2, f), __dsub_rn(1.0, __dmul_rn(2.0, s))};
+            for (int c = 0; c < 3; ++c) cand[c] = X[c * N + k - 1] + (long long)rint(__dmul_rn(uh[c], 0x1p44));
+            bool ok = true;
+            for (int j = 0; j < k - 1 && ok; ++j) {
+                const double dx = __dmul_rn((double)(cand[0] - X[j]), 0x1p-44);
+                const double dy = __dmul_rn((double)(cand[1] - X[N + j]), 0x1p-44);
+                const double dz = __dmul_rn((double)(cand[2] - X[2 * N + j]), 0x1p-44);
+                const double d2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+                if (d2 < 0.81) ok = false;
+            }
+            if (ok) break;
+        }
+        for (int c = 0; c < 3; ++c) X[c * N + k] = cand[c];
+    }
+}
+
+// Energy from scratch, one warp per walker (FP32 pairs relative to bead 0,
+// Kahan per lane, exact fixed-point warp sum).  With track != 0 the largest
+// change against the running energy is recorded in state->drift_max_q.
+__global__ void k_poly_energy(const PolyArgs a, int track)
+{
+    extern __shared__ __align__(16) float sh[];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, N = a.N;
+    const int w = blockIdx.x * (blockDim.x >> 5) + wib;
+    if (w >= a.p) return;
+    float *xs = sh + (size_t)wib * 3 * N;
+    const long long *X = a.X + (size_t)w * 3 * N;
+    const long long A0 = X[0], A1 = X[N], A2 = X[2 * N];
+    for (int j = lane; j < N; j += 32) {
+        xs[j] = (float)(X[j] - A0) * 0x1p-44f;
+        xs[N + j] = (float)(X[N + j] - A1) * 0x1p-44f;
+        xs[2 * N + j] = (float)(X[2 * N + j] - A2) * 0x1p-44f;
+    }
+    __syncwarp();
+    float s = 0.0f, c = 0.0f;
+    for (int i = 0; i < N; ++i) {
+        const float xi = xs[i], yi = xs[N + i], zi = xs[2 * N + i];
+        for (int j = lane; j < N; j += 32) {
+            if (j <= i) continue;
+            const float dx = xi - xs[j], dy = yi - xs[N + j], dz = zi - xs[2 * N + j];
+            const float r2 = dx * dx + dy * dy + dz * dz;
+            const float v = (j - i == 1) ? fene_energy(r2, a) : lj_energy(r2, a);
+            const float y = v - c;
+            const float t = s + y;
+            c = (t - s) - y;
+            s = t;
+        }
+    }
+    long long q = __float2ll_rn(s * 0x1p40f) - __float2ll_rn(c * 0x1p40f);
+    q = warp_sum_ll(q);
+    if (lane == 0) {
+        if (track) {
+            const long long d = q - a.E[w];
+            atomicMax(&a.state->drift_max_q, (unsigned long long)(d < 0 ? -d : d));
+        }
+        a.E[w] = q;
+        a.bin[w] = poly_bin(q, a);
+    }
+}
+
+// Sweeps: one warp per walker; the chain's master coordinates (int64) and FP32
+// shadows live in shared memory (36 N bytes per warp).
+template <int NPL, int RECORD>
+__global__ void __launch_bounds__(kMaxSweepBlock) k_sweep_polymer(const PolyArgs a)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, wpb = blockDim.x >> 5, N = a.N;
+    long long *Xs = (long long *)smem + (size_t)wib * 3 * N;
+    float *xs = (float *)(smem + (size_t)wpb * 3 * N * sizeof(long long)) + (size_t)wib * 3 * N;
+    const int w = blockIdx.x * wpb + wib;
+    if (w >= a.p) return;  // whole warps only; no block-wide barrier follows
+    const uint32_t wid = (uint32_t)(w + a.walker_offset);
+    long long *Xg = a.X + (size_t)w * 3 * N;
+    for (int t = lane; t < 3 * N; t += 32) Xs[t] = Xg[t];
+    long long E = a.E[w];
+    int b = poly_bin(E, a);
+    const uint32_t g0 = (uint32_t)a.state->sweep_counter;
+    const float R2 = 1.0f / a.fene_invR2;
+    __syncwarp();
+    for (int64_t sw = 0; sw < a.sweeps; ++sw) {
+        const uint32_t g = g0 + (uint32_t)sw;
+        const long long A0 = Xs[0], A1 = Xs[N], A2 = Xs[2 * N];
+        for (int j = lane; j < N; j += 32) {
+            xs[j] = (float)(Xs[j] - A0) * 0x1p-44f;
+            xs[N + j] = (float)(Xs[N + j] - A1) * 0x1p-44f;
+            xs[2 * N + j] = (float)(Xs[2 * N + j] - A2) * 0x1p-44f;
+        }
+        __syncwarp();
+#pragma unroll 1
+        for (int i = 0; i < N; ++i) {
+            const uint4 u = philox4x32_10_rk(make_uint4((uint32_t)i, g, wid, kTagSweep), a.rk);
+            const long long n0 = Xs[i] + ((long long)u.x - 2147483648LL) * kPolyStepQ;
+            const long long n1 = Xs[N + i] + ((long long)u.y - 2147483648LL) * kPolyStepQ;
+            const long long n2 = Xs[2 * N + i] + ((long long)u.z - 2147483648LL) * kPolyStepQ;
+            const float xo = xs[i], yo = xs[N + i], zo = xs[2 * N + i];
+            const float xn = (float)(n0 - A0) * 0x1p-44f, yn = (float)(n1 - A1) * 0x1p-44f,
+                        zn = (float)(n2 - A2) * 0x1p-44f;
+            float s = 0.0f, c = 0.0f;
+            bool broken = false;
+#pragma unroll
+            for (int k = 0; k < NPL; ++k) {
+                const int j = lane + 32 * k;
+                if (j < N && j != i) {
+                    const float xj = xs[j], yj = xs[N + j], zj = xs[2 * N + j];
+                    const float ax = xo - xj, ay = yo - yj, az = zo - zj;
+                    const float bx = xn - xj, by = yn - yj, bz = zn - zj;
+                    const float r2o = ax * ax + ay * ay + az * az;
+                    const float r2n = bx * bx + by * by + bz * bz;
+                    float vo, vn;
+                    if (j == i - 1 || j == i + 1) {
+                        const bool brk = !(r2n < R2);
+                        broken |= brk;
+                        vo = fene_energy(r2o, a);
+                        vn = brk ? vo : fene_energy(r2n, a);
+                    } else {
+                        vo = lj_energy(r2o, a);
+                        vn = lj_energy(r2n, a);
+                    }
+                    const float y = (vn - vo) - c;
+                    const float t = s + y;
+                    c = (t - s) - y;
+                    s = t;
+                }
+            }
+            broken = __any_sync(0xffffffffu, broken);
+            // |lane sum| >= 2^22 only for overlapping beads: such a move is rejected
+            const bool huge = __any_sync(0xffffffffu, !(fabsf(s) < 4194304.0f));
+            long long q = huge ? 0 : (__float2ll_rn(s * 0x1p40f) - __float2ll_rn(c * 0x1p40f));
+            q = warp_sum_ll(q);
+            const long long En = E + q;
+            const int bn = poly_bin(En, a);
+            bool acc = false;
+            if (!broken && !huge) {
+                if (b >= 0 && b < a.B) {
+                    if (bn >= 0 && bn < a.B) {
+                        const long long dq = __ldg(a.lnWq + bn) - __ldg(a.lnWq + b);
+                        if (dq >= 0) {
+                            acc = true;
+                        } else {
+                            const float thr = expf((float)dq * 0x1p-40f) * 4294967296.0f;
+                            acc = (float)u.w < thr;
+                        }
+                    }
+                } else {
+                    const long long dold = (b < 0) ? a.elo_q - E : E - a.ehi_q;
+                    const long long dnew = (bn < 0) ? a.elo_q - En : (bn >= a.B ? En - a.ehi_q : 0);
+                    acc = dnew <= dold;
+                }
+            }
+            if (acc) {
+                if (lane == 0) {
+                    Xs[i] = n0;
+                    Xs[N + i] = n1;
+                    Xs[2 * N + i] = n2;
+                    xs[i] = xn;
+                    xs[N + i] = yn;
+                    xs[2 * N + i] = zn;
+                }
+                E = En;
+                b = bn;
+            }
+            __syncwarp();
+            if (RECORD == 0 && lane == 0 && b >= 0 && b < a.B) atomicAdd(a.H + b, 1ull);
+        }
+        if (RECORD == 1 && lane == 0 && b >= 0 && b < a.B) atomicAdd(a.H + b, 1ull);
+    }
+    // recentre on bead 0 (an exact grid shift) and write back
+    const long long A0 = Xs[0], A1 = Xs[N], A2 = Xs[2 * N];
+    __syncwarp();
+    for (int t = lane; t < N; t += 32) {
+        Xg[t] = Xs[t] - A0;
+        Xg[N + t] = Xs[N + t] - A1;
+        Xg[2 * N + t] = Xs[2 * N + t] - A2;
+    }
+    if (lane == 0) {
+        a.E[w] = E;
+        a.bin[w] = b;
+    }
+}
+
+__global__ void k_poly_lnwq(const double *lnW, long long *lnWq, int B)
+{
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b < B) lnWq[b] = __double2ll_rn(__dmul_rn(lnW[b], 0x1p40));
+}
+
+__global__ void k_poly_unpack(const PolyArgs a, double *coords, double *energies)
+{
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long n = (long long)a.p * a.N;
+    if (t >= n) return;
+    const int w = (int)(t / a.N), j = (int)(t - (t / a.N) * a.N);
+    const long long *X = a.X + (size_t)w * 3 * a.N;
+    for (int c = 0; c < 3; ++c) coords[t * 3 + c] = (double)X[c * a.N + j] * 0x1p-44;
+    if (j == 0) energies[w] = (double)a.E[w] * 0x1p-40;
+}
+
+cudaError_t launch_poly_init(const PolyArgs &a, cudaStream_t s)
+{
+    k_poly_init<<<(a.p + 127) / 128, 128, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_poly_energy(const PolyArgs &a, int track_drift, cudaStream_t s)
+{
+    const int wpb = 4;
+    const size_t smem = (size_t)wpb * 3 * a.N * sizeof(float);
+    k_poly_energy<<<(a.p + wpb - 1) / wpb, wpb * 32, smem, s>>>(a, track_drift);
+    return cudaGetLastError();
+}
+
+template <int NPL>
+static cudaError_t launch_npl(const PolyArgs &a, int block, cudaStream_t s)
+{
+    const int wpb = block / 32;
+    const size_t smem = (size_t)wpb * 3 * a.N * (sizeof(long long) + sizeof(float));
+    const int nblk = (a.p + wpb - 1) / wpb;
+    cudaError_t e;
+    if (a.record == 0) {
+        e = cudaFuncSetAttribute(k_sweep_polymer<NPL, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        k_sweep_polymer<NPL, 0><<<nblk, block, smem, s>>>(a);
+    } else {
+        e = cudaFuncSetAttribute(k_sweep_polymer<NPL, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        k_sweep_polymer<NPL, 1><<<nblk, block, smem, s>>>(a);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_poly_sweep(const PolyArgs &a, int block, cudaStream_t s)
+{
+    const int npl = (a.N + 31) / 32;
+    switch (npl) {
+    case 1: return launch_npl<1>(a, block, s);
+    case 2: return launch_npl<2>(a, block, s);
+    case 3: return launch_npl<3>(a, block, s);
+    case 4: return launch_npl<4>(a, block, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_poly_lnwq(const double *lnW, long long *lnWq, int B, cudaStream_t s)
+{
+    k_poly_lnwq<<<(B + 255) / 256, 256, 0, s>>>(lnW, lnWq, B);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_poly_unpack(const PolyArgs &a, double *coords, double *energies, cudaStream_t s)
+{
+    const long long n = (long long)a.p * a.N;
+    k_poly_unpack<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(a, coords, energies);
+    return cudaGetLastError();
+}
+
+}  // namespace muca

@@ -257,6 +257,8 @@ __global__ void __launch_bounds__(1024) k_reweight(const UpdateArgs a, double be
             const double lnOmega = log((double)h) - a.lnW_sampled[b];
             if (a.system == kMuma) {
                 x = lnOmega;
+            } else if (a.system == kPolymer) {
+                x = lnOmega - beta * (a.e_lo + 0.1 * (b + 0.5));
             } else {
                 const double E = (a.system == kIsing) ? (double)(4 * b - 2 * N) : (double)(b - 2 * N);
                 x = lnOmega - beta * E;
@@ -293,6 +295,7 @@ __global__ void __launch_bounds__(1024) k_reweight(const UpdateArgs a, double be
             const double P = exp(lp);
             double v;
             if (a.system == kMuma) v = fabs((double)(2 * b - N));
+            else if (a.system == kPolymer) v = a.e_lo + 0.1 * (b + 0.5);
             else v = (a.system == kIsing) ? (double)(4 * b - 2 * N) : (double)(b - 2 * N);
             a1 += P * v;
             a2 += P * v * v;
@@ -309,10 +312,41 @@ __global__ void __launch_bounds__(1024) k_reweight(const UpdateArgs a, double be
         }
         __syncthreads();
     }
+    a1 = red[0];
+    a2 = red2[0];
+    // polymer: log-sum-exp of ln Omega itself (the normalisation of ln Z)
+    double lnNorm = 0.0;
+    if (a.system == kPolymer) {
+        __syncthreads();
+        double m2 = NEG_INF;
+        for (int b = tid; b < B; b += bs)
+            if (sx[b] > NEG_INF) m2 = fmax(m2, sx[b] + beta * (a.e_lo + 0.1 * (b + 0.5)));
+        red2[tid] = m2;
+        __syncthreads();
+        for (int st = bs / 2; st > 0; st >>= 1) {
+            if (tid < st) red2[tid] = fmax(red2[tid], red2[tid + st]);
+            __syncthreads();
+        }
+        m2 = red2[0];
+        __syncthreads();
+        double z2 = 0.0;
+        for (int b = tid; b < B; b += bs)
+            if (sx[b] > NEG_INF) z2 += exp(sx[b] + beta * (a.e_lo + 0.1 * (b + 0.5)) - m2);
+        red2[tid] = z2;
+        __syncthreads();
+        for (int st = bs / 2; st > 0; st >>= 1) {
+            if (tid < st) red2[tid] += red2[tid + st];
+            __syncthreads();
+        }
+        lnNorm = m2 + log(red2[0]);
+    }
     if (tid == 0) {
-        a1 = red[0];
-        a2 = red2[0];
-        if (a.system == kMuma) {
+        if (a.system == kPolymer) {
+            out4[0] = a1;
+            out4[1] = a2;
+            out4[2] = beta * beta * (a2 - a1 * a1) / N;
+            out4[3] = lse - lnNorm;
+        } else if (a.system == kMuma) {
             out4[0] = a1 / N;
             out4[1] = a2 / ((double)N * N);
             out4[2] = a.beta * N * (out4[1] - out4[0] * out4[0]);
