@@ -91,7 +91,7 @@ int muca_init_ex(muca_ctx **out, int system, int L_or_N, int q, int p, uint64_t 
  *                 union of the shards equals one context of all walkers;
  *                 re-draws the initial states; before the first iterate.
  *   Polymer only (before the first iterate): "e_lo", "e_hi" (the energy
- *   window, bins of width 0.1, at most 32768 bins; default [2N, 6N)),
+ *   window, bins of width 0.1, at most 12288 bins; default [2N, 6N)),
  *   "fene_K", "fene_R" (default 40, 1.5).  Fixed: LJ eps = sigma = 1 cut at
  *   2.5 and shifted, acting on beads |i-j| >= 2; FENE on bonds; single-bead
  *   moves uniform in a cube of side 1229/4096 on a 2^-44 grid.

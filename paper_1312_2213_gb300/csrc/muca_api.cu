@@ -240,8 +240,8 @@ PolyArgs poly_args(const muca_ctx *c, int64_t sweeps)
     a.B = c->B;
     a.record = c->record;
     a.walker_offset = c->walker_offset;
-    a.elo_q = llrint(c->e_lo * 1099511627776.0);                      // e_lo * 2^40
-    a.ehi_q = a.elo_q + ((long long)c->B * 1099511627776LL + 9) / 10;  // first energy with bin >= B
+    a.elo_q = llrint(c->e_lo * 4294967296.0);                      // e_lo * 2^32
+    a.ehi_q = a.elo_q + ((long long)c->B * 4294967296LL + 9) / 10;  // first energy with bin >= B
     a.fene_KR2_half = (float)(0.5 * c->fene_K * c->fene_R * c->fene_R);
     a.fene_invR2 = (float)(1.0 / (c->fene_R * c->fene_R));
     a.lj_rc2 = 6.25f;
@@ -690,7 +690,7 @@ int muca_get_drift(muca_ctx *c, double *host_out)
     if (!host_out) return fail(MUCA_ERR_ARG, "out is NULL");
     DevState st;
     if (int rc = d2h(c, &st, c->state, sizeof st)) return rc;
-    *host_out = (double)st.drift_max_q * 0x1p-40;
+    *host_out = (double)st.drift_max_q * 0x1p-32;
     return MUCA_OK;
 }
 

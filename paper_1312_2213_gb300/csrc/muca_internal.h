@@ -23,7 +23,7 @@ struct DevState {
     double flat_min, flat_mean, flat_max;
     int flat;
     int err;                           // non-zero: a device-side check failed
-    unsigned long long drift_max_q;    // polymer: largest |E_running - E_scratch| at a refresh (2^-40 units)
+    unsigned long long drift_max_q;    // polymer: largest |E_running - E_scratch| at a refresh (2^-32 units)
 };
 
 // Everything one spin sweep launch needs.  All pointers are device pointers.
@@ -79,8 +79,8 @@ cudaError_t launch_sweep_batch(const SpinSweepArgs *d_sys, const int2 *d_tiles, 
 
 // Polymer (bead-spring chain, Eq. 7 reading).  Master coordinates are int64 on a
 // 2^-44 grid, walker-major and axis-major: X[(w*3 + a)*N + j]; energies are int64
-// in units of 2^-40; the window is [elo_q, elo_q + B/10) in the same units.
-constexpr int kPolyMaxBins = 32768;
+// in units of 2^-32; the window is [elo_q, elo_q + B/10) in the same units.
+constexpr int kPolyMaxBins = 12288;  // the recursion stages 2 doubles a bin in shared memory
 constexpr int kPolyMaxN = 128;
 constexpr long long kPolyStepQ = 1229;  // displacement grid units per unit of (u - 2^31)
 
@@ -88,7 +88,7 @@ struct PolyArgs {
     long long *X;
     long long *E;
     int32_t *bin;
-    const long long *lnWq;         // ln W in units of 2^-40
+    const long long *lnWq;         // ln W in units of 2^-32
     unsigned long long *H;         // open histogram (B counters)
     DevState *state;
     int p, N, B, record, walker_offset;

@@ -6,7 +6,7 @@
 // One warp per walker.  The beads are visited in order; for bead i every lane
 // evaluates the old and the new pair energies with its partner beads
 // j = lane, lane + 32, ... in FP32 and keeps a compensated (Kahan) sum; the lane
-// sums are converted to 64-bit fixed point (2^-40 energy units) and added with
+// sums are converted to 64-bit fixed point (2^-32 energy units) and added with
 // an exact integer warp reduction.  Nothing on the hot path uses FP64, whose
 // rate on GB300 is a small fraction of FP32.
 //
@@ -14,7 +14,11 @@
 // (u - 2^31) * 1229 grid units per axis (a cube of side 1229/4096 = 0.30005), so
 // the coordinates of an accepted move are exact and identical to any other
 // implementation that draws the same words.  The FP32 pair terms use shadows
-// relative to the walker's bead 0 at the start of each sweep.  The running
+// relative to the walker's bead 0 at the start of each sweep, kept as unevaluated
+// float pairs (hi + lo): a difference (hi_i - hi_j) + (lo_i - lo_j) keeps the
+// separation of two beads to ~1e-7 of itself however far the chain extends, so
+// the rounding of FP32 energy changes stays unbiased when walk-in selects moves
+// by the sign of their energy change.  The running
 // energy is an exact sum of the fixed-point energy changes; it is refreshed from
 // scratch after every iterate call, and the largest difference is recorded.
 // Acceptance inside the window: d = ln W(b') - ln W(b) from a fixed-point table,
@@ -40,6 +44,15 @@ __device__ __forceinline__ float fene_energy(float r2, const PolyArgs &a)
     return -a.fene_KR2_half * log1pf(-r2 * a.fene_invR2);
 }
 
+// Offset on the 2^-44 grid as an unevaluated pair hi + lo of floats.
+__device__ __forceinline__ void grid_to_ff(long long d, float &hi, float &lo)
+{
+    hi = (float)d;
+    lo = (float)(d - (long long)hi);
+    hi *= 0x1p-44f;
+    lo *= 0x1p-44f;
+}
+
 __device__ __forceinline__ long long warp_sum_ll(long long q)
 {
 #pragma unroll
@@ -49,7 +62,7 @@ __device__ __forceinline__ long long warp_sum_ll(long long q)
 
 __device__ __forceinline__ int poly_bin(long long E, const PolyArgs &a)
 {
-    const long long b = ((E - a.elo_q) * 10) >> 40;
+    const long long b = ((E - a.elo_q) * 10) >> 32;
     return b < -1 ? -1 : (b > (long long)a.B ? a.B : (int)b);
 }
 
@@ -103,21 +116,24 @@ __global__ void k_poly_energy(const PolyArgs a, int track)
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, N = a.N;
     const int w = blockIdx.x * (blockDim.x >> 5) + wib;
     if (w >= a.p) return;
-    float *xs = sh + (size_t)wib * 3 * N;
+    float *xs = sh + (size_t)wib * 6 * N;  // hi[3N], lo[3N]
+    float *xl = xs + 3 * N;
     const long long *X = a.X + (size_t)w * 3 * N;
     const long long A0 = X[0], A1 = X[N], A2 = X[2 * N];
     for (int j = lane; j < N; j += 32) {
-        xs[j] = (float)(X[j] - A0) * 0x1p-44f;
-        xs[N + j] = (float)(X[N + j] - A1) * 0x1p-44f;
-        xs[2 * N + j] = (float)(X[2 * N + j] - A2) * 0x1p-44f;
+        grid_to_ff(X[j] - A0, xs[j], xl[j]);
+        grid_to_ff(X[N + j] - A1, xs[N + j], xl[N + j]);
+        grid_to_ff(X[2 * N + j] - A2, xs[2 * N + j], xl[2 * N + j]);
     }
     __syncwarp();
     float s = 0.0f, c = 0.0f;
     for (int i = 0; i < N; ++i) {
         const float xi = xs[i], yi = xs[N + i], zi = xs[2 * N + i];
+        const float li = xl[i], mi = xl[N + i], ni = xl[2 * N + i];
         for (int j = lane; j < N; j += 32) {
             if (j <= i) continue;
-            const float dx = xi - xs[j], dy = yi - xs[N + j], dz = zi - xs[2 * N + j];
+            const float dx = (xi - xs[j]) + (li - xl[j]), dy = (yi - xs[N + j]) + (mi - xl[N + j]),
+                        dz = (zi - xs[2 * N + j]) + (ni - xl[2 * N + j]);
             const float r2 = dx * dx + dy * dy + dz * dz;
             const float v = (j - i == 1) ? fene_energy(r2, a) : lj_energy(r2, a);
             const float y = v - c;
@@ -126,7 +142,7 @@ __global__ void k_poly_energy(const PolyArgs a, int track)
             s = t;
         }
     }
-    long long q = __float2ll_rn(s * 0x1p40f) - __float2ll_rn(c * 0x1p40f);
+    long long q = __float2ll_rn(s * 0x1p32f) - __float2ll_rn(c * 0x1p32f);
     q = warp_sum_ll(q);
     if (lane == 0) {
         if (track) {
@@ -138,15 +154,16 @@ __global__ void k_poly_energy(const PolyArgs a, int track)
     }
 }
 
-// Sweeps: one warp per walker; the chain's master coordinates (int64) and FP32
-// shadows live in shared memory (36 N bytes per warp).
+// Sweeps: one warp per walker; the chain's master coordinates (int64) and
+// float-pair shadows live in shared memory (48 N bytes per warp).
 template <int NPL, int RECORD>
 __global__ void __launch_bounds__(kMaxSweepBlock) k_sweep_polymer(const PolyArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, wpb = blockDim.x >> 5, N = a.N;
     long long *Xs = (long long *)smem + (size_t)wib * 3 * N;
-    float *xs = (float *)(smem + (size_t)wpb * 3 * N * sizeof(long long)) + (size_t)wib * 3 * N;
+    float *xs = (float *)(smem + (size_t)wpb * 3 * N * sizeof(long long)) + (size_t)wib * 6 * N;
+    float *xl = xs + 3 * N;
     const int w = blockIdx.x * wpb + wib;
     if (w >= a.p) return;  // whole warps only; no block-wide barrier follows
     const uint32_t wid = (uint32_t)(w + a.walker_offset);
@@ -161,9 +178,9 @@ __global__ void __launch_bounds__(kMaxSweepBlock) k_sweep_polymer(const PolyArgs
         const uint32_t g = g0 + (uint32_t)sw;
         const long long A0 = Xs[0], A1 = Xs[N], A2 = Xs[2 * N];
         for (int j = lane; j < N; j += 32) {
-            xs[j] = (float)(Xs[j] - A0) * 0x1p-44f;
-            xs[N + j] = (float)(Xs[N + j] - A1) * 0x1p-44f;
-            xs[2 * N + j] = (float)(Xs[2 * N + j] - A2) * 0x1p-44f;
+            grid_to_ff(Xs[j] - A0, xs[j], xl[j]);
+            grid_to_ff(Xs[N + j] - A1, xs[N + j], xl[N + j]);
+            grid_to_ff(Xs[2 * N + j] - A2, xs[2 * N + j], xl[2 * N + j]);
         }
         __syncwarp();
 #pragma unroll 1
@@ -173,8 +190,11 @@ __global__ void __launch_bounds__(kMaxSweepBlock) k_sweep_polymer(const PolyArgs
             const long long n1 = Xs[N + i] + ((long long)u.y - 2147483648LL) * kPolyStepQ;
             const long long n2 = Xs[2 * N + i] + ((long long)u.z - 2147483648LL) * kPolyStepQ;
             const float xo = xs[i], yo = xs[N + i], zo = xs[2 * N + i];
-            const float xn = (float)(n0 - A0) * 0x1p-44f, yn = (float)(n1 - A1) * 0x1p-44f,
-                        zn = (float)(n2 - A2) * 0x1p-44f;
+            const float lxo = xl[i], lyo = xl[N + i], lzo = xl[2 * N + i];
+            float xn, yn, zn, lxn, lyn, lzn;
+            grid_to_ff(n0 - A0, xn, lxn);
+            grid_to_ff(n1 - A1, yn, lyn);
+            grid_to_ff(n2 - A2, zn, lzn);
             float s = 0.0f, c = 0.0f;
             bool broken = false;
 #pragma unroll
@@ -182,8 +202,9 @@ __global__ void __launch_bounds__(kMaxSweepBlock) k_sweep_polymer(const PolyArgs
                 const int j = lane + 32 * k;
                 if (j < N && j != i) {
                     const float xj = xs[j], yj = xs[N + j], zj = xs[2 * N + j];
-                    const float ax = xo - xj, ay = yo - yj, az = zo - zj;
-                    const float bx = xn - xj, by = yn - yj, bz = zn - zj;
+                    const float ljx = xl[j], ljy = xl[N + j], ljz = xl[2 * N + j];
+                    const float ax = (xo - xj) + (lxo - ljx), ay = (yo - yj) + (lyo - ljy), az = (zo - zj) + (lzo - ljz);
+                    const float bx = (xn - xj) + (lxn - ljx), by = (yn - yj) + (lyn - ljy), bz = (zn - zj) + (lzn - ljz);
                     const float r2o = ax * ax + ay * ay + az * az;
                     const float r2n = bx * bx + by * by + bz * bz;
                     float vo, vn;
@@ -205,7 +226,7 @@ __global__ void __launch_bounds__(kMaxSweepBlock) k_sweep_polymer(const PolyArgs
             broken = __any_sync(0xffffffffu, broken);
             // |lane sum| >= 2^22 only for overlapping beads: such a move is rejected
             const bool huge = __any_sync(0xffffffffu, !(fabsf(s) < 4194304.0f));
-            long long q = huge ? 0 : (__float2ll_rn(s * 0x1p40f) - __float2ll_rn(c * 0x1p40f));
+            long long q = huge ? 0 : (__float2ll_rn(s * 0x1p32f) - __float2ll_rn(c * 0x1p32f));
             q = warp_sum_ll(q);
             const long long En = E + q;
             const int bn = poly_bin(En, a);
@@ -217,7 +238,7 @@ __global__ void __launch_bounds__(kMaxSweepBlock) k_sweep_polymer(const PolyArgs
                         if (dq >= 0) {
                             acc = true;
                         } else {
-                            const float thr = expf((float)dq * 0x1p-40f) * 4294967296.0f;
+                            const float thr = expf((float)dq * 0x1p-32f) * 4294967296.0f;
                             acc = (float)u.w < thr;
                         }
                     }
@@ -235,6 +256,9 @@ __global__ void __launch_bounds__(kMaxSweepBlock) k_sweep_polymer(const PolyArgs
                     xs[i] = xn;
                     xs[N + i] = yn;
                     xs[2 * N + i] = zn;
+                    xl[i] = lxn;
+                    xl[N + i] = lyn;
+                    xl[2 * N + i] = lzn;
                 }
                 E = En;
                 b = bn;
@@ -261,7 +285,7 @@ __global__ void __launch_bounds__(kMaxSweepBlock) k_sweep_polymer(const PolyArgs
 __global__ void k_poly_lnwq(const double *lnW, long long *lnWq, int B)
 {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
-    if (b < B) lnWq[b] = __double2ll_rn(__dmul_rn(lnW[b], 0x1p40));
+    if (b < B) lnWq[b] = __double2ll_rn(__dmul_rn(lnW[b], 0x1p32));
 }
 
 __global__ void k_poly_unpack(const PolyArgs a, double *coords, double *energies)
@@ -272,7 +296,7 @@ __global__ void k_poly_unpack(const PolyArgs a, double *coords, double *energies
     const int w = (int)(t / a.N), j = (int)(t - (t / a.N) * a.N);
     const long long *X = a.X + (size_t)w * 3 * a.N;
     for (int c = 0; c < 3; ++c) coords[t * 3 + c] = (double)X[c * a.N + j] * 0x1p-44;
-    if (j == 0) energies[w] = (double)a.E[w] * 0x1p-40;
+    if (j == 0) energies[w] = (double)a.E[w] * 0x1p-32;
 }
 
 cudaError_t launch_poly_init(const PolyArgs &a, cudaStream_t s)
@@ -284,7 +308,7 @@ cudaError_t launch_poly_init(const PolyArgs &a, cudaStream_t s)
 cudaError_t launch_poly_energy(const PolyArgs &a, int track_drift, cudaStream_t s)
 {
     const int wpb = 4;
-    const size_t smem = (size_t)wpb * 3 * a.N * sizeof(float);
+    const size_t smem = (size_t)wpb * 6 * a.N * sizeof(float);
     k_poly_energy<<<(a.p + wpb - 1) / wpb, wpb * 32, smem, s>>>(a, track_drift);
     return cudaGetLastError();
 }
@@ -293,7 +317,7 @@ template <int NPL>
 static cudaError_t launch_npl(const PolyArgs &a, int block, cudaStream_t s)
 {
     const int wpb = block / 32;
-    const size_t smem = (size_t)wpb * 3 * a.N * (sizeof(long long) + sizeof(float));
+    const size_t smem = (size_t)wpb * 3 * a.N * (sizeof(long long) + 2 * sizeof(float));
     const int nblk = (a.p + wpb - 1) / wpb;
     cudaError_t e;
     if (a.record == 0) {
