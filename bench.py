@@ -13,6 +13,10 @@ proposed single-spin update, accepted or not), whole job.
              (muca_set_state) and back out (muca_get_state) every step;
   roofline   the sweep kernel against the integer issue peak (SMs x 4 schedulers x 32 lanes x f_SM);
   cpu_baseline  the CPU oracle (all host cores) on a bounded sample of the same workload.
+  batched_mix   the uneven mix (2D Ising L in {16,24,32,48,64} and q=10 Potts L in {16,24,32,48},
+                2048 walkers each): one system per launch (plain) against all systems in one
+                persistent launch per iteration, and against the whole loop as one CUDA graph.
+  polymer       the bead-spring polymer, N in {13,32,64,128}, p = 4096, in its pilot windows.
 
 `--impl reference` times the CPU oracle itself as the reference arm.
 """
@@ -50,8 +54,95 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--sweeps", type=int, default=SWEEPS)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-sweeps", type=int, default=100, help="sweeps per system in the CPU sample")
+    ap.add_argument("--cpu-sweeps", type=int, default=400, help="sweeps per system in the CPU sample")
+    ap.add_argument("--no-extras", action="store_true", help="skip the batched-mix and polymer measurements")
+    ap.add_argument("--workload", default="all", choices=["all", "mix", "polymer"],
+                    help="mix / polymer: run only that measurement (for profiling)")
     return ap.parse_args()
+
+
+MIX = [(0, L, 2) for L in (16, 24, 32, 48, 64)] + [(1, L, 10) for L in (16, 24, 32, 48)]
+MIX_P = 2048
+
+
+def run_mix(m, torch, sweeps=1000, short_sweeps=10, short_iters=20):
+    """Plain (one system per launch, host loop) vs batched (one launch per iteration) vs graph."""
+    sites = sum(L * L for _, L, _ in MIX)
+
+    def make(seed0):
+        return [m.Muca(s_, L, q, MIX_P, seed0 + i, block=128) for i, (s_, L, q) in enumerate(MIX)]
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        fn()
+        b.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / 1e3
+
+    out = {"systems": "ising2d L=16,24,32,48,64 + potts2d q=10 L=16,24,32,48", "walkers_per_system": MIX_P}
+    # throughput regime: 1 iteration of `sweeps` sweeps
+    sysA = make(100)
+    for c in sysA:       # warm-up iteration
+        c.iterate(20)
+        c.merge_and_update()
+
+    def plain_iter(systems, sw):
+        for c in systems:
+            c.iterate(sw)
+            c.merge_and_update()
+
+    t_plain = timed(lambda: plain_iter(sysA, sweeps))
+    sysB = make(200)
+    batch = m.Batch(sysB)
+    batch.run(1, 20, use_graph=False)
+    t_batch = timed(lambda: batch.run(1, sweeps, use_graph=False))
+    batch.run(1, sweeps, use_graph=True)      # capture
+    t_graph = timed(lambda: batch.run(1, sweeps, use_graph=True))
+    att = MIX_P * sweeps * sites
+    out["throughput"] = {"sweeps_per_iteration": sweeps, "attempts_per_iteration": att,
+                         "plain_attempts_per_s": att / t_plain, "batched_attempts_per_s": att / t_batch,
+                         "graph_attempts_per_s": att / t_graph, "batched_over_plain": t_plain / t_batch,
+                         "graph_over_plain": t_plain / t_graph}
+    # short iterations: launch and host overheads dominate
+    t_plain_s = timed(lambda: [plain_iter(sysA, short_sweeps) for _ in range(short_iters)])
+    batch.run(short_iters, short_sweeps, use_graph=True)  # capture
+    t_graph_s = timed(lambda: batch.run(short_iters, short_sweeps, use_graph=True))
+    t_batch_s = timed(lambda: batch.run(short_iters, short_sweeps, use_graph=False))
+    att_s = MIX_P * short_sweeps * sites * short_iters
+    out["short_iterations"] = {"sweeps_per_iteration": short_sweeps, "iterations": short_iters,
+                               "plain_attempts_per_s": att_s / t_plain_s, "batched_attempts_per_s": att_s / t_batch_s,
+                               "graph_attempts_per_s": att_s / t_graph_s, "graph_over_plain": t_plain_s / t_graph_s}
+    batch.close()
+    for c in sysA + sysB:
+        c.close()
+    return out
+
+
+def run_polymer(m, torch, p=4096, budget_attempts=2.0e8):
+    import json as _json
+
+    W = _json.load(open(os.path.join(ROOT, "paper_1312_2213_gb300", "polymer_windows.json")))["windows"]
+    res = {"walkers": p, "windows": "pilot windows (paper_1312_2213_gb300/polymer_windows.json)", "chains": {}}
+    for N in (13, 32, 64, 128):
+        g = m.Muca(m.POLYMER3D, N, 0, p, 7, window=(W[str(N)]["e_lo"], W[str(N)]["e_hi"]))
+        for _ in range(2):
+            g.iterate(max(1, 200 // N))
+            g.merge_and_update()
+        sw = max(2, int(budget_attempts / (p * N)))
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        g.iterate(sw)
+        b.record()
+        torch.cuda.synchronize()
+        t = a.elapsed_time(b) / 1e3
+        att = p * sw * N
+        res["chains"][str(N)] = {"sweeps": sw, "attempts_per_s": att / t, "pair_evals_per_s": att * 2 * (N - 1) / t,
+                                 "energy_drift": g.drift()}
+        g.close()
+    return res
 
 
 def dist_env():
@@ -268,6 +359,9 @@ def run_ours(args):
                        "independent replicas, one per GPU"},
             "e2e": e2e, "gpu_launches": launches_per_step * args.steps, "roofline": roofline,
             "clocks": ck}
+    if not args.no_extras:
+        line["batched_mix"] = run_mix(m, torch)
+        line["polymer"] = run_polymer(m, torch)
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_sample(args.cpu_sweeps, 5)
     print(json.dumps(line), flush=True)
@@ -279,6 +373,14 @@ def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload != "all":
+        import torch
+
+        import paper_1312_2213_gb300 as m
+
+        m.load()
+        res = run_mix(m, torch) if args.workload == "mix" else run_polymer(m, torch)
+        print(json.dumps({"workload": args.workload, **res}), flush=True)
     else:
         run_ours(args)
 

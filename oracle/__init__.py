@@ -67,7 +67,8 @@ def lib():
             L.orc_is_flat.restype = ctypes.c_int
             L.orc_reweight.argtypes = [ctypes.c_void_p, ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p]
             for name in ("orc_reachable", "orc_get_lnW", "orc_get_lnW_sampled", "orc_get_histogram",
-                         "orc_get_thresholds", "orc_get_spins", "orc_get_bins", "orc_set_open_histogram"):
+                         "orc_get_thresholds", "orc_get_spins", "orc_get_bins", "orc_set_open_histogram",
+                         "orc_get_open_histogram"):
                 getattr(L, name).argtypes = [ctypes.c_void_p, ctypes.c_void_p]
             L.orc_get_sweep_counter.argtypes = [ctypes.c_void_p]
             L.orc_get_sweep_counter.restype = ctypes.c_int64
@@ -172,6 +173,9 @@ class Run:
         H = np.ascontiguousarray(np.asarray(H, dtype=np.uint64))
         assert H.shape == (self.B,)
         self._lib.orc_set_open_histogram(self.h, _ptr(H))
+
+    def open_histogram(self):
+        return self._get("orc_get_open_histogram", self.B, np.uint64)
 
     def is_flat(self, ratio: float = 0.5):
         st = np.zeros(3)

@@ -473,6 +473,7 @@ void orc_iterate(orc_run *r, int64_t sweeps, int nthreads)
 }
 
 void orc_set_open_histogram(orc_run *r, const uint64_t *H) { memcpy(r->H_open, H, sizeof(uint64_t) * r->B); }
+void orc_get_open_histogram(const orc_run *r, uint64_t *out) { memcpy(out, r->H_open, sizeof(uint64_t) * r->B); }
 
 /* a5 (reading R5) followed by a6. */
 void orc_update(orc_run *r)

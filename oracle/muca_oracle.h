@@ -54,6 +54,7 @@ void orc_advance(orc_run *r, int64_t sweeps);
 void orc_update(orc_run *r);
 /* Replace the open histogram (for recursion tests on hand-made histograms). */
 void orc_set_open_histogram(orc_run *r, const uint64_t *H);
+void orc_get_open_histogram(const orc_run *r, uint64_t *out);
 /* a7: 1 if every reachable bin of the last merged histogram is > 0 and
  * min/mean >= ratio.  stats = {min, mean, max} over reachable bins. */
 int orc_is_flat(const orc_run *r, double ratio, double stats[3]);
