@@ -85,6 +85,11 @@ int muca_init_ex(muca_ctx **out, int system, int L_or_N, int q, int p, uint64_t 
  *   "flat_ratio"  flatness criterion min H / mean H (default 0.5); any time.
  *   "block"       walkers per thread block of the sweep kernel (32..512,
  *                 multiple of 32); before the first iterate.
+ *   "pipeline"    spins: 1 (default) pairs every warp of walkers with a
+ *                 producer warp that computes their random numbers into a
+ *                 shared-memory ring (bounded waits; a wait that gives up makes
+ *                 the next synchronising call return MUCA_ERR_TIMEOUT); 0 runs
+ *                 one warp per 32 walkers.  Results are identical either way.
  *   "walker_offset" global id of this context's walker 0 when one system's
  *                 walkers are split over several contexts (e.g. one per GPU):
  *                 walker w draws from the stream of walker w + offset, so the
@@ -206,7 +211,8 @@ int muca_get_coords(muca_ctx *ctx, double *host_coords, int64_t n, double *host_
  * recomputation seen at the refresh after each muca_iterate. */
 int muca_get_drift(muca_ctx *ctx, double *host_out);
 
-/* Wait for the context's stream. */
+/* Wait for the context's stream; MUCA_ERR_TIMEOUT if a device-side bounded
+ * wait gave up since the context was created. */
 int muca_synchronize(muca_ctx *ctx);
 
 /* Release the context and (unless it came from muca_init_ex) its device memory. */

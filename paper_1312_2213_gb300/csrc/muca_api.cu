@@ -51,6 +51,7 @@ struct muca_ctx {
     uint64_t seed = 0;
     double beta = 0.0, flat_ratio = 0.5;
     int record = 0, block = 64, walker_offset = 0;
+    int pipeline = 1;  // spins: producer/consumer sweep (1) or one warp per walker group (0)
     int pstride = 0, wpw = 0, nblk_max = 0;
     cudaStream_t stream = nullptr;
     bool owns_arena = false, started = false;
@@ -361,11 +362,22 @@ int check_ctx(const muca_ctx *c)
     return MUCA_OK;
 }
 
+// Device-side checks (bounded waits) leave a flag in the device state; every
+// call that synchronises reports it.
+int check_device_flag(muca_ctx *c)
+{
+    int err = 0;
+    MUCA_CUDA(cudaMemcpyAsync(&err, &c->state->err, sizeof err, cudaMemcpyDeviceToHost, c->stream));
+    MUCA_CUDA(cudaStreamSynchronize(c->stream));
+    if (err) return fail(MUCA_ERR_TIMEOUT, "a bounded device wait gave up; the last iterations are invalid");
+    return MUCA_OK;
+}
+
 int d2h(muca_ctx *c, void *host, const void *dev, size_t bytes)
 {
     MUCA_CUDA(cudaMemcpyAsync(host, dev, bytes, cudaMemcpyDeviceToHost, c->stream));
     MUCA_CUDA(cudaStreamSynchronize(c->stream));
-    return MUCA_OK;
+    return check_device_flag(c);
 }
 
 // Checkpoint blob: fixed header, then the device sections in this order.
@@ -497,6 +509,11 @@ int muca_set_param(muca_ctx *c, const char *key, double v)
         c->block = b;
         return MUCA_OK;
     }
+    if (k == "pipeline") {
+        if (v != 0.0 && v != 1.0) return fail(MUCA_ERR_ARG, "pipeline must be 0 or 1");
+        c->pipeline = (int)v;
+        return MUCA_OK;
+    }
     if (k == "walker_offset") {
         if (locked) return fail(MUCA_ERR_STATE, "walker_offset must be set before the first iterate");
         const long long o = (long long)v;
@@ -551,7 +568,11 @@ int muca_iterate(muca_ctx *c, int64_t sweeps)
     a.record = c->record;
     a.walker_offset = c->walker_offset;
     a.kind = sweep_kind(c->system, c->L);
-    MUCA_CUDA(launch_spin_sweep(c->system, c->L, a, c->block, c->stream));
+    if (c->pipeline && spin_sweep_pc_fits(c->system, c->L, c->B, c->block)) {
+        MUCA_CUDA(launch_spin_sweep_pc(c->system, c->L, a, c->block, c->stream));
+    } else {
+        MUCA_CUDA(launch_spin_sweep(c->system, c->L, a, c->block, c->stream));
+    }
     MUCA_CUDA(launch_advance(c->state, sweeps, c->stream));
     c->started = true;
     c->open = true;
@@ -848,7 +869,7 @@ int muca_synchronize(muca_ctx *c)
 {
     if (int rc = check_ctx(c)) return rc;
     MUCA_CUDA(cudaStreamSynchronize(c->stream));
-    return MUCA_OK;
+    return check_device_flag(c);
 }
 
 int muca_free(muca_ctx *c)

@@ -72,6 +72,10 @@ bool spin_sweep_supported(int system, int L);
 size_t spin_sweep_smem_bytes(int system, int B);
 cudaError_t launch_spin_sweep(int system, int L, const SpinSweepArgs &a, int block, cudaStream_t s);
 int sweep_kind(int system, int L);
+// Producer/consumer form: `block` walkers a block, run by 2*block threads.
+bool spin_sweep_pc_fits(int system, int L, int B, int walkers_per_block);
+size_t spin_sweep_pc_smem_bytes(int system, int L, int B, int walkers_per_block);
+cudaError_t launch_spin_sweep_pc(int system, int L, const SpinSweepArgs &a, int block, cudaStream_t s);
 // Batched sweep: tiles[k] = (system index, first walker); all tiles use `block` threads.
 cudaError_t prepare_sweep_batch(size_t smem);
 cudaError_t launch_sweep_batch(const SpinSweepArgs *d_sys, const int2 *d_tiles, int ntiles, int block, size_t smem,

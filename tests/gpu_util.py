@@ -20,8 +20,10 @@ def compare_state(g, o, what=""):
     np.testing.assert_array_equal(g.histogram(), o.histogram(), err_msg="H " + what)
 
 
-def run_pair(system, L, q, p, seed, iters, sweeps, beta=0.0, record=0, block=None, nthreads=8, check_each=True):
+def run_pair(system, L, q, p, seed, iters, sweeps, beta=0.0, record=0, block=None, nthreads=8, check_each=True,
+             pipeline=1):
     g = m.Muca(system, L, q, p, seed, beta=beta if system == m.ISING2D_MUMA else None, record=record, block=block)
+    g.set_param("pipeline", pipeline)
     o = oracle.Run(system, L, q, p, seed, beta=beta, record=record)
     o.init()
     compare_state(g, o, "after init")

@@ -49,6 +49,14 @@ def test_iterations_bit_exact(system, L, q, p):
     run_pair(system, L, q, p, seed=1000 + L + q, iters=4, sweeps=sweeps, beta=0.4407, nthreads=NT)
 
 
+@pytest.mark.parametrize("system,L,q,p", [(m.ISING2D, 32, 2, 100), (m.POTTS2D, 16, 10, 70), (m.ISING2D_MUMA, 24, 2, 65),
+                                          (m.POTTS2D, 48, 8, 40), (m.ISING2D, 64, 2, 33)])
+def test_one_warp_form_bit_exact(system, L, q, p):
+    """pipeline = 0 (one warp runs its walkers' random numbers and chains) gives the same bits."""
+    run_pair(system, L, q, p, seed=77 + L, iters=3, sweeps=max(2, 3000 // (L * L)), beta=0.4407, nthreads=NT,
+             pipeline=0)
+
+
 def test_config_ising_L8_p64_full_length():
     """Ising L = 8, p = 64, 10 iterations of 1e4 sweeps: bit-exact at every iteration."""
     g, o = run_pair(m.ISING2D, 8, 2, 64, seed=1, iters=10, sweeps=10000, nthreads=NT)
