@@ -510,7 +510,7 @@ int muca_set_param(muca_ctx *c, const char *key, double v)
         return MUCA_OK;
     }
     if (k == "pipeline") {
-        if (v != 0.0 && v != 1.0) return fail(MUCA_ERR_ARG, "pipeline must be 0 or 1");
+        if (v != 0.0 && v != 1.0 && v != 2.0) return fail(MUCA_ERR_ARG, "pipeline must be 0, 1 or 2");
         c->pipeline = (int)v;
         return MUCA_OK;
     }
@@ -568,7 +568,9 @@ int muca_iterate(muca_ctx *c, int64_t sweeps)
     a.record = c->record;
     a.walker_offset = c->walker_offset;
     a.kind = sweep_kind(c->system, c->L);
-    if (c->pipeline && spin_sweep_pc_fits(c->system, c->L, c->B, c->block)) {
+    if (c->pipeline == 2 && spin_sweep_tn_fits(c->system, c->L, c->B, c->block)) {
+        MUCA_CUDA(launch_spin_sweep_tn(c->system, c->L, a, c->block, c->stream));
+    } else if (c->pipeline && spin_sweep_pc_fits(c->system, c->L, c->B, c->block)) {
         MUCA_CUDA(launch_spin_sweep_pc(c->system, c->L, a, c->block, c->stream));
     } else {
         MUCA_CUDA(launch_spin_sweep(c->system, c->L, a, c->block, c->stream));

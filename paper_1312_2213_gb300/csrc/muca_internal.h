@@ -76,6 +76,10 @@ int sweep_kind(int system, int L);
 bool spin_sweep_pc_fits(int system, int L, int B, int walkers_per_block);
 size_t spin_sweep_pc_smem_bytes(int system, int L, int B, int walkers_per_block);
 cudaError_t launch_spin_sweep_pc(int system, int L, const SpinSweepArgs &a, int block, cudaStream_t s);
+// Producer/consumer form with precomputed site codes (Ising, MUMA).
+bool spin_sweep_tn_fits(int system, int L, int B, int walkers_per_block);
+size_t spin_sweep_tn_smem_bytes(int system, int L, int B, int walkers_per_block);
+cudaError_t launch_spin_sweep_tn(int system, int L, const SpinSweepArgs &a, int block, cudaStream_t s);
 // Batched sweep: tiles[k] = (system index, first walker); all tiles use `block` threads.
 cudaError_t prepare_sweep_batch(size_t smem);
 cudaError_t launch_sweep_batch(const SpinSweepArgs *d_sys, const int2 *d_tiles, int ntiles, int block, size_t smem,

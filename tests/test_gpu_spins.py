@@ -57,6 +57,15 @@ def test_one_warp_form_bit_exact(system, L, q, p):
              pipeline=0)
 
 
+@pytest.mark.parametrize("system,L,p", [(m.ISING2D, 8, 64), (m.ISING2D, 16, 100), (m.ISING2D, 24, 70),
+                                        (m.ISING2D, 32, 130), (m.ISING2D, 48, 40), (m.ISING2D, 64, 35),
+                                        (m.ISING2D_MUMA, 8, 50), (m.ISING2D_MUMA, 32, 100), (m.ISING2D_MUMA, 48, 33)])
+def test_code_pipeline_bit_exact(system, L, p):
+    """pipeline = 2 (producer also computes the site column codes; threshold/next-bin pairs)."""
+    run_pair(system, L, 2, p, seed=500 + L, iters=4, sweeps=max(2, 4000 // (L * L)), beta=0.4407, nthreads=NT,
+             pipeline=2)
+
+
 def test_config_ising_L8_p64_full_length():
     """Ising L = 8, p = 64, 10 iterations of 1e4 sweeps: bit-exact at every iteration."""
     g, o = run_pair(m.ISING2D, 8, 2, 64, seed=1, iters=10, sweeps=10000, nthreads=NT)
