@@ -85,11 +85,15 @@ int muca_init_ex(muca_ctx **out, int system, int L_or_N, int q, int p, uint64_t 
  *   "flat_ratio"  flatness criterion min H / mean H (default 0.5); any time.
  *   "block"       walkers per thread block of the sweep kernel (32..512,
  *                 multiple of 32); before the first iterate.
- *   "pipeline"    spins: 1 (default) pairs every warp of walkers with a
- *                 producer warp that computes their random numbers into a
- *                 shared-memory ring (bounded waits; a wait that gives up makes
- *                 the next synchronising call return MUCA_ERR_TIMEOUT); 0 runs
- *                 one warp per 32 walkers.  Results are identical either way.
+ *   "pipeline"    spins: 2 (default) pairs every warp of walkers with a
+ *                 producer warp that computes their random numbers and, for
+ *                 Ising and MUMA, each site's neighbour code into a
+ *                 shared-memory ring; 1 does the same with random numbers
+ *                 only; 0 runs one warp per 32 walkers.  A form that does not
+ *                 fit the system, L, bin count or block falls back to the next
+ *                 lower one.  Ring hand-overs are bounded waits; a wait that
+ *                 gives up makes the next synchronising call return
+ *                 MUCA_ERR_TIMEOUT.  Results are identical in every form.
  *   "walker_offset" global id of this context's walker 0 when one system's
  *                 walkers are split over several contexts (e.g. one per GPU):
  *                 walker w draws from the stream of walker w + offset, so the

@@ -51,7 +51,7 @@ struct muca_ctx {
     uint64_t seed = 0;
     double beta = 0.0, flat_ratio = 0.5;
     int record = 0, block = 64, walker_offset = 0;
-    int pipeline = 1;  // spins: producer/consumer sweep (1) or one warp per walker group (0)
+    int pipeline = 2;  // spins: code form (2), producer/consumer (1) or one warp per walker group (0)
     int pstride = 0, wpw = 0, nblk_max = 0;
     cudaStream_t stream = nullptr;
     bool owns_arena = false, started = false;
@@ -568,9 +568,9 @@ int muca_iterate(muca_ctx *c, int64_t sweeps)
     a.record = c->record;
     a.walker_offset = c->walker_offset;
     a.kind = sweep_kind(c->system, c->L);
-    if (c->pipeline == 2 && spin_sweep_tn_fits(c->system, c->L, c->B, c->block)) {
+    if (c->pipeline >= 2 && spin_sweep_tn_fits(c->system, c->L, c->B, c->block)) {
         MUCA_CUDA(launch_spin_sweep_tn(c->system, c->L, a, c->block, c->stream));
-    } else if (c->pipeline && spin_sweep_pc_fits(c->system, c->L, c->B, c->block)) {
+    } else if (c->pipeline >= 1 && spin_sweep_pc_fits(c->system, c->L, c->B, c->block)) {
         MUCA_CUDA(launch_spin_sweep_pc(c->system, c->L, a, c->block, c->stream));
     } else {
         MUCA_CUDA(launch_spin_sweep(c->system, c->L, a, c->block, c->stream));

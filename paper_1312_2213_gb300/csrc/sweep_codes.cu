@@ -1,0 +1,723 @@
+// sweep_codes.cu -- producer/consumer form with precomputed site codes (Ising,
+// MUMA and Potts).
+#include "muca_device.cuh"
+#include "muca_internal.h"
+#include "sweep_common.cuh"
+
+namespace muca {
+
+// ---------------------------------------------------------------------------
+// Producer/consumer form with precomputed site codes (Ising and MUMA).
+// Shared memory holds the same threshold + histogram rows as above.  The
+// producer warp writes, per row, the walkers' random
+// words, their old row and, for every site, two column bytes: c0 for "left
+// neighbour as it was" and c1 for "left neighbour flipped", both without the up
+// neighbour (which only the consumer knows: the row above is final only after
+// the consumer has swept it) and, for the last site, without its right
+// neighbour (site 0 of the same row).  Four sites are handled at once with
+// bytewise arithmetic.  The consumer subtracts the up term (and the right term of
+// the last site), derives the bin moves from the two columns and runs the same
+// speculative chain as above.  (A variant that stored (threshold, next-row) pairs
+// to save the moves was slower: its 8-byte random loads doubled the bank
+// conflicts on the critical chain.)
+__device__ __forceinline__ uint32_t nib_to_bytes(uint32_t n)  // 4 bits -> 4 bytes of 0/1
+{
+    return (n * 0x00204081u) & 0x01010101u;
+}
+
+template <int L, int WR>
+__device__ __forceinline__ uint32_t row_nibble(const uint32_t (&r)[WR], int x)  // bits x..x+3 (x % 4 == 0)
+{
+    return (r[x >> 5] >> (x & 31)) & 15u;
+}
+
+template <int L, int WR>
+__device__ __forceinline__ uint32_t row_bit(const uint32_t (&r)[WR], int x)
+{
+    return (r[x >> 5] >> (x & 31)) & 1u;
+}
+
+template <int SYS, int L>
+__device__ __forceinline__ void produce_sweep_tn(uint32_t g, uint32_t wid, const uint32_t (&rk)[20],
+                                                 const uint32_t *__restrict__ lat, int ps, uint4 *ring_u,
+                                                 uint2 *ring_c, uint32_t *ring_r, unsigned long long *full,
+                                                 unsigned long long *empty, int &k, bool &bad)
+{
+    constexpr int WR = ising_words_per_row(L);
+    constexpr int G = L / 4;
+    constexpr size_t SU = (size_t)G * 32, SC = (size_t)G * 32, SR = (size_t)WR * 32;
+    // Rolling rows: o = row y (old), d = row y+1 (old; row 0 final for y = L-1), nn = row y+2
+    // prefetched one row ahead.  The producer runs at most kRing rows ahead of the
+    // consumer and L >= 2 kRing, so every row it reads has its value for this sweep
+    // (rows y, y+1, y+2 not yet swept; row 0 already swept when it is the last row's
+    // down neighbour).  The first two rows of a sweep are read after the first wait.
+    uint32_t o[WR], d[WR], nn[WR];
+#pragma unroll 1
+    for (int y = 0; y < L; ++y) {
+        const int slot = k % kRing;
+        if (!bad && !mbar_wait(&empty[slot], (unsigned)(((k / kRing) & 1) ^ 1))) bad = true;
+        if (y == 0) {
+#pragma unroll
+            for (int j = 0; j < WR; ++j) {
+                o[j] = lat[j * ps];
+                d[j] = lat[(WR + j) * ps];
+            }
+        }
+        const int y2 = (y + 2 < L) ? y + 2 : y + 2 - L;
+        if (y + 1 < L) {
+#pragma unroll
+            for (int j = 0; j < WR; ++j) nn[j] = lat[(y2 * WR + j) * ps];
+        }
+        uint4 *wu = ring_u + slot * SU;
+        uint2 *wc = ring_c + slot * SC;
+        uint32_t *wr = ring_r + slot * SR;
+#pragma unroll
+        for (int j = 0; j < WR; ++j) wr[j * 32] = o[j];
+#pragma unroll
+        for (int gq = 0; gq < G; ++gq) {
+            wu[gq * 32] = philox4x32_10_rk(make_uint4((uint32_t)(y * G + gq), g, wid, kTagSweep), rk);
+            const int x = 4 * gq;
+            const uint32_t s4 = row_nibble<L, WR>(o, x);
+            // left neighbours x-1..x+2 and right neighbours x+1..x+4 (periodic in x)
+            uint32_t l4 = (s4 << 1) & 15u, r4 = s4 >> 1;
+            l4 |= row_bit<L, WR>(o, (x + L - 1) % L);
+            if (x + 4 < L) r4 |= row_bit<L, WR>(o, x + 4) << 3;
+            else r4 |= ((s4 >> 3) & 1u) << 3;  // last site: right neighbour left out (anti = 0)
+            const uint32_t S = nib_to_bytes(s4);
+            const uint32_t A = nib_to_bytes(l4) ^ S;  // left anti-aligned
+            const uint32_t Bq = nib_to_bytes(r4) ^ S;
+            const uint32_t D = nib_to_bytes(row_nibble<L, WR>(d, x)) ^ S;
+            const uint32_t k0 = 0x04040404u - (A + Bq + D);  // 4 - anti-aligned (without up), per byte
+            const uint32_t k1 = k0 + 2u * A - 0x01010101u;   // left neighbour flipped
+            if (SYS == kMuma) {
+                const uint32_t s5 = S * 5u;
+                wc[gq * 32] = make_uint2(s5 + k0, s5 + k1);
+            } else {
+                wc[gq * 32] = make_uint2(k0, k1);
+            }
+        }
+        mbar_arrive(&full[slot]);
+        ++k;
+#pragma unroll
+        for (int j = 0; j < WR; ++j) {
+            o[j] = d[j];
+            d[j] = nn[j];
+        }
+    }
+}
+
+template <int SYS, int L, int RECORD>
+__device__ __forceinline__ void ising_sweep_tc(uint32_t *__restrict__ lat, int ps, int &bR, uint32_t *__restrict__ sTH,
+                                               const uint4 *__restrict__ ring_u, const uint2 *__restrict__ ring_c,
+                                               const uint32_t *__restrict__ ring_r, unsigned long long *full,
+                                               unsigned long long *empty, int &k, bool &bad)
+{
+    constexpr int WR = ising_words_per_row(L);
+    constexpr int C = (SYS == kMuma) ? 10 : 5;
+    constexpr int RS = C + 1;
+    constexpr int G = L / 4;
+    constexpr size_t SU = (size_t)G * 32, SC = (size_t)G * 32, SR = (size_t)WR * 32;
+    // bin-row move of an accepted flip, from its column: Ising (c - 2) rows,
+    // MUMA one row down for s = +1 (c < 5) and one up for s = -1
+    auto move = [](uint32_t c) -> int {
+        return (SYS == kMuma) ? ((c >= 5u) ? RS : -RS) : ((int)c - 2) * RS;
+    };
+    uint32_t up[WR], cur[WR];
+#pragma unroll
+    for (int j = 0; j < WR; ++j) up[j] = lat[((L - 1) * WR + j) * ps];
+#pragma unroll 1
+    for (int y = 0; y < L; ++y) {
+        const int slot = k % kRing;
+        if (!bad && !mbar_wait(&full[slot], (unsigned)((k / kRing) & 1))) bad = true;
+        const uint4 *ru = ring_u + slot * SU;
+        const uint2 *rc = ring_c + slot * SC;
+        const uint32_t *rr = ring_r + slot * SR;
+        uint32_t ua[WR];
+#pragma unroll
+        for (int j = 0; j < WR; ++j) {
+            cur[j] = rr[j * 32];
+            ua[j] = up[j] ^ cur[j];  // up neighbour anti-aligned
+        }
+        const uint32_t sLast = row_bit<L, WR>(cur, L - 1);
+        uint2 cd = rc[0];
+        {
+            const uint32_t u4 = nib_to_bytes(row_nibble<L, WR>(ua, 0));
+            cd.x -= u4;
+            cd.y -= u4;
+        }
+        uint2 cdn = cd;
+        const uint32_t c00 = cd.x & 0xffu;
+        uint32_t T0 = sTH[bR + (int)c00], T1 = 0u;
+        int d0 = move(c00), d1 = 0;
+        bool accP = false;
+        int dRp = 0;
+        uint4 u = make_uint4(0u, 0u, 0u, 0u);
+#pragma unroll
+        for (int x = 0; x < L; ++x) {
+            const int j4 = x & 3;
+            if (j4 == 0) {
+                u = ru[(x / 4) * 32];
+                cd = cdn;
+                if (x + 4 < L) {
+                    cdn = rc[(x / 4 + 1) * 32];
+                    const uint32_t u4 = nib_to_bytes(row_nibble<L, WR>(ua, x + 4));
+                    cdn.x -= u4;
+                    cdn.y -= u4;
+                }
+            }
+            const uint32_t uw = word_of(u, j4);
+            bR = accP ? bR + dRp : bR;
+            const int dR = accP ? d1 : d0;
+            const uint32_t T = accP ? T1 : T0;
+            if (x + 1 < L) {
+                const int jn = (x + 1) & 3;
+                const uint32_t wx = (jn == 0) ? cdn.x : cd.x, wy = (jn == 0) ? cdn.y : cd.y;
+                uint32_t c0 = (wx >> (8 * jn)) & 0xffu, c1 = (wy >> (8 * jn)) & 0xffu;
+                if (x + 1 == L - 1) {
+                    // the last site's right neighbour is site 0 of this row, final by now
+                    const uint32_t ra = row_bit<L, WR>(cur, 0) ^ sLast;
+                    c0 -= ra;
+                    c1 -= ra;
+                }
+                T0 = sTH[bR + (int)c0];
+                T1 = sTH[bR + dR + (int)c1];
+                d0 = move(c0);
+                d1 = move(c1);
+            }
+            const bool acc = (T == kAlways) || (uw < T);
+            if (acc) cur[x >> 5] ^= 1u << (x & 31);
+            if (RECORD == 0) atomicAdd(&sTH[(acc ? bR + dR : bR) + C], 1u);
+            accP = acc;
+            dRp = dR;
+        }
+        bR = accP ? bR + dRp : bR;
+#pragma unroll
+        for (int j = 0; j < WR; ++j) {
+            lat[(y * WR + j) * ps] = cur[j];
+            up[j] = cur[j];
+        }
+        mbar_arrive(&empty[slot]);  // after the row is stored: the producer reads it later
+        ++k;
+    }
+    if (RECORD == 1) atomicAdd(&sTH[bR + C], 1u);
+}
+
+__host__ __device__ constexpr size_t tn_ring_bytes(int L)
+{
+    return (size_t)kRing * ((size_t)(L / 4) * 32 * 16 + (size_t)(L / 4) * 32 * 8 + (size_t)((L + 31) / 32) * 32 * 4);
+}
+
+template <int SYS, int L>
+__device__ __forceinline__ void sweep_block_tn(const SpinSweepArgs &a, int w0, int slot_id, uint32_t *smem)
+{
+    constexpr int C = num_cols(SYS);
+    constexpr int RS = C + 1;
+    constexpr int G = L / 4;
+    const int ncw = blockDim.x / 64;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const bool producer = warp >= ncw;
+    const int pair = producer ? warp - ncw : warp;
+    uint32_t *sTH = smem;
+    const size_t th_bytes = ((size_t)a.B * RS * 4 + 15) / 16 * 16;
+    char *rbase = (char *)smem + th_bytes + (size_t)pair * tn_ring_bytes(L);
+    uint4 *ring_u = (uint4 *)rbase + lane;
+    uint2 *ring_c = (uint2 *)(rbase + (size_t)kRing * G * 32 * 16) + lane;
+    uint32_t *ring_r = (uint32_t *)(rbase + (size_t)kRing * (G * 32 * 16 + G * 32 * 8)) + lane;
+    unsigned long long *bars = (unsigned long long *)((char *)smem + th_bytes + (size_t)ncw * tn_ring_bytes(L));
+    unsigned long long *full = bars + (size_t)pair * 2 * kRing, *empty = full + kRing;
+
+    const int tid = threadIdx.x;
+    for (int i = tid; i < a.B * RS; i += blockDim.x) {
+        const int b = i / RS, c = i - (i / RS) * RS;
+        sTH[i] = (c < C) ? a.T[b * C + c] : 0u;
+    }
+    if (tid == 0)
+        for (int i = 0; i < ncw * 2 * kRing; ++i) mbar_init(bars + i, 32);
+    __syncthreads();
+
+    const int w = w0 + pair * 32 + lane;
+    const bool active = w < a.p;
+    const uint32_t wid = (uint32_t)(w + a.walker_offset);
+    const uint32_t g0 = (uint32_t)a.state->sweep_counter;
+    uint32_t *lat = a.lattice + (active ? w : 0);
+    int bR = (active ? a.bin[w] : 0) * RS;
+    unsigned long long *Hb = a.Hpart + (size_t)slot_id * a.B;
+    int k = 0;
+    bool bad = false;
+    for (int64_t s0 = 0; s0 < a.sweeps; s0 += a.flush_every) {
+        const int64_t s1 = (a.sweeps < s0 + a.flush_every) ? a.sweeps : s0 + a.flush_every;
+#pragma unroll 1
+        for (int64_t sw = s0; sw < s1; ++sw) {
+            const uint32_t g = g0 + (uint32_t)sw;
+            if (producer) {
+                produce_sweep_tn<SYS, L>(g, wid, a.rk, lat, a.pstride, ring_u, ring_c, ring_r, full, empty, k, bad);
+            } else if (active) {
+                if (a.record == 0)
+                    ising_sweep_tc<SYS, L, 0>(lat, a.pstride, bR, sTH, ring_u, ring_c, ring_r, full, empty, k, bad);
+                else
+                    ising_sweep_tc<SYS, L, 1>(lat, a.pstride, bR, sTH, ring_u, ring_c, ring_r, full, empty, k, bad);
+            } else {
+#pragma unroll 1
+                for (int y = 0; y < L; ++y) {
+                    const int slot = k % kRing;
+                    if (!bad && !mbar_wait(&full[slot], (unsigned)((k / kRing) & 1))) bad = true;
+                    mbar_arrive(&empty[slot]);
+                    ++k;
+                }
+            }
+        }
+        __syncthreads();
+        for (int b = tid; b < a.B; b += blockDim.x) {
+            const uint32_t c = sTH[b * RS + C];
+            if (c) {
+                Hb[b] += c;
+                sTH[b * RS + C] = 0u;
+            }
+        }
+        __syncthreads();
+    }
+    if (bad) atomicOr(const_cast<int *>(&a.state->err), 1);
+    if (!producer && active) a.bin[w] = bR / RS;
+}
+
+template <int SYS, int L>
+__global__ void __launch_bounds__(kMaxSweepBlock, 1) k_sweep_spin_tn(const SpinSweepArgs a)
+{
+    extern __shared__ __align__(16) uint32_t smem[];
+    sweep_block_tn<SYS, L>(a, blockIdx.x * (blockDim.x / 2), blockIdx.x, smem);
+}
+
+static int potts_tn_depth(int L, int B, int walkers_per_block);
+static size_t potts_tn_smem_bytes(int L, int RD, int B, int walkers_per_block);
+
+size_t spin_sweep_tn_smem_bytes(int system, int L, int B, int walkers_per_block)
+{
+    if (system == kPotts) {
+        const int rd = potts_tn_depth(L, B, walkers_per_block);
+        return potts_tn_smem_bytes(L, rd ? rd : 2, B, walkers_per_block);
+    }
+    const int ncw = walkers_per_block / 32;
+    return ((size_t)B * (num_cols(system) + 1) * 4 + 15) / 16 * 16 + (size_t)ncw * tn_ring_bytes(L) +
+           (size_t)ncw * 2 * kRing * sizeof(unsigned long long);
+}
+
+// ---------------------------------------------------------------------------
+// Code form for Potts.  The producer warp draws both words of every site and
+// makes the proposal v = (s + 1 + mulhi(u, q-1)) mod q itself.  Per row it
+// writes the acceptance words, the old and the proposed row (one byte a site)
+// and two code bytes a site, c = 4 + dE without the up neighbour: c0 with the
+// left neighbour as it was, c1 with the left neighbour recoloured to its own
+// proposal.  With ne(n, s) = [n != s], a neighbour n adds ne(n, v) - ne(n, s) to
+// dE; the producer evaluates it four sites at a time on bytes.  The consumer
+// adds the up neighbour's term the same way, four sites at a time, from the
+// final row above (kept in bytes), and the last site's right neighbour (site 0
+// of the same row, final by then) once a row.  The chain itself is the one of
+// the Ising code form.  RD is the ring depth in rows (4, or 2 where a deeper ring
+// does not fit next to the threshold table).
+__device__ __forceinline__ uint32_t ne_bytes(uint32_t a, uint32_t b)  // per byte [a != b], bytes < 16
+{
+    return (((a ^ b) + 0x0F0F0F0Fu) >> 4) & 0x01010101u;
+}
+
+__device__ __forceinline__ uint32_t nib_half_to_bytes(uint32_t w, int half)  // 4 nibbles -> 4 bytes
+{
+    const uint32_t t = __byte_perm(w, 0u, half ? 0x3322u : 0x1100u);
+    return (t & 0x000F000Fu) | ((t >> 4) & 0x0F000F00u);
+}
+
+__device__ __forceinline__ uint32_t bytes_to_nibs(uint32_t w0, uint32_t w1)  // 8 bytes (< 16) -> 8 nibbles
+{
+    return __byte_perm(w0 | (w0 >> 4), w1 | (w1 >> 4), 0x6420u);
+}
+
+// The producer runs a rolled loop over the row's nibble words (8 sites, 4
+// Philox blocks each); its old and down rows rotate through registers so that
+// word i is always element 0.  (A fully unrolled row was several times larger
+// than the instruction cache serves without fetch stalls.)
+template <int L, int RD>
+__device__ __forceinline__ void produce_sweep_potts_tn(uint32_t g, uint32_t wid, const uint32_t (&rk)[20],
+                                                       const uint32_t *__restrict__ lat, int ps, uint32_t q,
+                                                       uint4 *ring_u, uint2 *ring_c, uint2 *ring_op,
+                                                       unsigned long long *full, unsigned long long *empty, int &k,
+                                                       bool &bad)
+{
+    static_assert(L % 8 == 0, "whole nibble words a row");
+    constexpr int WR = L / 8;
+    constexpr size_t S = (size_t)(L / 4) * 32;
+    const uint32_t qm1 = q - 1u;
+    uint32_t o[WR], d[WR], nn[WR];
+#pragma unroll 1
+    for (int y = 0; y < L; ++y) {
+        const int slot = k % RD;
+        if (!bad && !mbar_wait(&empty[slot], (unsigned)(((k / RD) & 1) ^ 1))) bad = true;
+        if (y == 0) {
+#pragma unroll
+            for (int j = 0; j < WR; ++j) {
+                o[j] = lat[j * ps];
+                d[j] = lat[(WR + j) * ps];
+            }
+        }
+        const int y2 = (y + 2 < L) ? y + 2 : y + 2 - L;
+        if (y + 1 < L) {
+#pragma unroll
+            for (int j = 0; j < WR; ++j) nn[j] = lat[(y2 * WR + j) * ps];
+        }
+        uint4 *wu = ring_u + slot * S;
+        uint2 *wc = ring_c + slot * S;
+        uint2 *wop = ring_op + slot * S;
+        uint32_t ob_prev = nib_half_to_bytes(o[WR - 1], 1);  // sites L-4..L-1: left of site 0
+        uint32_t pprev = 0u;                                  // site 0's c1 is never used
+#pragma unroll 1
+        for (int i = 0; i < WR; ++i) {
+            const uint32_t on = o[1 % WR];  // next nibble word, cyclic
+            const uint32_t mask_last = (i == WR - 1) ? 0x00FFFFFFu : 0xFFFFFFFFu;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int j = 2 * i + h;
+                const uint32_t ob = nib_half_to_bytes(o[0], h);
+                const uint32_t ob_next = nib_half_to_bytes(h == 0 ? o[0] : on, h ^ 1);
+                const uint32_t db = nib_half_to_bytes(d[0], h);
+                const uint32_t base = (uint32_t)(y * (L / 2) + 2 * j);
+                const uint4 r0 = philox4x32_10_rk(make_uint4(base, g, wid, kTagSweep), rk);
+                const uint4 r1 = philox4x32_10_rk(make_uint4(base + 1u, g, wid, kTagSweep), rk);
+                wu[j * 32] = make_uint4(r0.y, r0.w, r1.y, r1.w);
+                const uint32_t up4[4] = {r0.x, r0.z, r1.x, r1.z};
+                uint32_t pb = 0u;
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    uint32_t v = ((ob >> (8 * e)) & 0xffu) + 1u + __umulhi(up4[e], qm1);
+                    v = (v >= q) ? v - q : v;
+                    pb |= v << (8 * e);
+                }
+                const uint32_t R = __funnelshift_r(ob, ob_next, 8);   // right neighbours (old)
+                const uint32_t Lo = __funnelshift_l(ob_prev, ob, 8);  // left neighbours (old)
+                const uint32_t Lp = __funnelshift_l(pprev, pb, 8);    // left neighbours (recoloured)
+                uint32_t nRp = ne_bytes(R, pb), nRo = ne_bytes(R, ob);
+                if (h == 1) {  // the row's last site: its right neighbour is added by the consumer
+                    nRp &= mask_last;
+                    nRo &= mask_last;
+                }
+                const uint32_t sp = 0x04040404u + nRp + ne_bytes(db, pb);
+                const uint32_t so = nRo + ne_bytes(db, ob);
+                // every byte stays in [1, 7] and no partial result borrows across bytes
+                const uint32_t c0 = sp + ne_bytes(Lo, pb) - so - ne_bytes(Lo, ob);
+                const uint32_t c1 = sp + ne_bytes(Lp, pb) - so - ne_bytes(Lp, ob);
+                wc[j * 32] = make_uint2(c0, c1);
+                wop[j * 32] = make_uint2(ob, pb);
+                ob_prev = ob;
+                pprev = pb;
+            }
+            const uint32_t o0 = o[0], d0 = d[0];
+#pragma unroll
+            for (int e = 0; e + 1 < WR; ++e) {
+                o[e] = o[e + 1];
+                d[e] = d[e + 1];
+            }
+            o[WR - 1] = o0;
+            d[WR - 1] = d0;
+        }
+        mbar_arrive(&full[slot]);
+        ++k;
+#pragma unroll
+        for (int j = 0; j < WR; ++j) {
+            o[j] = d[j];
+            d[j] = nn[j];
+        }
+    }
+}
+
+// The consumer runs a rolled loop over the row's byte words (4 sites each) and
+// peels the last word, which holds the last site's right-neighbour term.  The
+// final row above lives in a per-lane shared-memory row sU (bytes), rewritten
+// word by word as the current row completes.
+template <int L, int RD, int RECORD>
+__device__ __forceinline__ void potts_sweep_tc(uint32_t *__restrict__ lat, int ps, int &bR,
+                                               uint32_t *__restrict__ sTH, const uint4 *__restrict__ ring_u,
+                                               const uint2 *__restrict__ ring_c, const uint2 *__restrict__ ring_op,
+                                               uint32_t *__restrict__ sU, unsigned long long *full,
+                                               unsigned long long *empty, int &k, bool &bad)
+{
+    static_assert(L % 8 == 0, "whole nibble words a row");
+    constexpr int WR = L / 8;
+    constexpr int W4 = L / 4;
+    constexpr int RS = 10;
+    constexpr size_t S = (size_t)W4 * 32;
+    auto byte_of = [](uint32_t w, int i) -> int { return (int)((w >> (8 * i)) & 0xffu); };
+#pragma unroll 1
+    for (int y = 0; y < L; ++y) {
+        const int slot = k % RD;
+        if (!bad && !mbar_wait(&full[slot], (unsigned)((k / RD) & 1))) bad = true;
+        const uint4 *ru = ring_u + slot * S;
+        const uint2 *rc = ring_c + slot * S;
+        const uint2 *rop = ring_op + slot * S;
+        // code bytes of word j with the up neighbour's term added (bytes stay in [0, 8])
+        auto codes = [&](int j, uint2 op, uint32_t ubw) -> uint2 {
+            uint2 c = rc[j * 32];
+            const uint32_t np = ne_bytes(ubw, op.y), no = ne_bytes(ubw, op.x);
+            c.x = c.x + np - no;
+            c.y = c.y + np - no;
+            return c;
+        };
+        uint2 opn = rop[0];
+        uint2 cdn = codes(0, opn, sU[0]);
+        const int c00 = byte_of(cdn.x, 0);
+        uint32_t T0 = sTH[bR + c00], T1 = 0u;
+        int d0 = (c00 - 4) * RS, d1 = 0;
+        bool accP = false;
+        int dRp = 0;
+        // decide the current site (threshold T0 or T1 by the previous decision) and
+        // load both candidates of the next site, whose code bytes are n0 / n1
+        auto site = [&](uint32_t uw, int n0, int n1, uint32_t &am, int i) {
+            bR = accP ? bR + dRp : bR;
+            const int dR = accP ? d1 : d0;
+            const uint32_t T = accP ? T1 : T0;
+            T0 = sTH[bR + n0];
+            T1 = sTH[bR + dR + n1];
+            d0 = (n0 - 4) * RS;
+            d1 = (n1 - 4) * RS;
+            const bool acc = (T == kAlways) || (uw < T);
+            if (acc) am |= 0xffu << (8 * i);
+            if (RECORD == 0) atomicAdd(&sTH[(acc ? bR + dR : bR) + 9], 1u);
+            accP = acc;
+            dRp = dR;
+        };
+        uint32_t fprev = 0u;
+#pragma unroll 1
+        for (int j = 0; j < W4 - 1; ++j) {
+            const uint2 op = opn, cd = cdn;
+            const uint4 u = ru[j * 32];
+            opn = rop[(j + 1) * 32];
+            cdn = codes(j + 1, opn, sU[(j + 1) * 32]);
+            uint32_t am = 0u;
+            site(u.x, byte_of(cd.x, 1), byte_of(cd.y, 1), am, 0);
+            site(u.y, byte_of(cd.x, 2), byte_of(cd.y, 2), am, 1);
+            site(u.z, byte_of(cd.x, 3), byte_of(cd.y, 3), am, 2);
+            site(u.w, byte_of(cdn.x, 0), byte_of(cdn.y, 0), am, 3);
+            const uint32_t f = op.x ^ ((op.x ^ op.y) & am);
+            sU[j * 32] = f;
+            if (j & 1) lat[(y * WR + (j >> 1)) * ps] = bytes_to_nibs(fprev, f);
+            fprev = f;
+        }
+        {
+            constexpr int j = W4 - 1;
+            const uint2 op = opn, cd = cdn;
+            const uint4 u = ru[j * 32];
+            uint32_t am = 0u;
+            site(u.x, byte_of(cd.x, 1), byte_of(cd.y, 1), am, 0);
+            site(u.y, byte_of(cd.x, 2), byte_of(cd.y, 2), am, 1);
+            // the last site's right neighbour is site 0 of this row, final by now (word 0 is in sU)
+            const uint32_t f0 = sU[0] & 0xffu;
+            const int t = (int)(f0 != (op.y >> 24)) - (int)(f0 != (op.x >> 24));
+            site(u.z, byte_of(cd.x, 3) + t, byte_of(cd.y, 3) + t, am, 2);
+            // the last site: decision only
+            bR = accP ? bR + dRp : bR;
+            const int dR = accP ? d1 : d0;
+            const uint32_t T = accP ? T1 : T0;
+            const bool acc = (T == kAlways) || (u.w < T);
+            if (acc) am |= 0xff000000u;
+            if (RECORD == 0) atomicAdd(&sTH[(acc ? bR + dR : bR) + 9], 1u);
+            accP = acc;
+            dRp = dR;
+            const uint32_t f = op.x ^ ((op.x ^ op.y) & am);
+            sU[j * 32] = f;
+            lat[(y * WR + WR - 1) * ps] = bytes_to_nibs(fprev, f);
+        }
+        bR = accP ? bR + dRp : bR;
+        mbar_arrive(&empty[slot]);  // after the row is stored: the producer reads it later
+        ++k;
+    }
+    if (RECORD == 1) atomicAdd(&sTH[bR + 9], 1u);
+}
+
+// Shared memory a consumer warp owns: RD ring rows (acceptance words 16 B,
+// codes 8 B, old/proposed bytes 8 B, per group of 4 sites and lane) and its up row.
+__host__ __device__ constexpr size_t tnp_warp_bytes(int L, int RD)
+{
+    return (size_t)RD * (size_t)(L / 4) * 32 * (16 + 8 + 8) + (size_t)(L / 4) * 32 * 4;
+}
+
+template <int L, int RD>
+__device__ __forceinline__ void sweep_block_tnp(const SpinSweepArgs &a, int w0, int slot_id, uint32_t *smem)
+{
+    constexpr int C = 9;
+    constexpr int RS = C + 1;
+    constexpr size_t S = (size_t)(L / 4) * 32;
+    const int ncw = blockDim.x / 64;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const bool producer = warp >= ncw;
+    const int pair = producer ? warp - ncw : warp;
+    uint32_t *sTH = smem;
+    const size_t th_bytes = ((size_t)a.B * RS * 4 + 15) / 16 * 16;
+    char *rbase = (char *)smem + th_bytes + (size_t)pair * tnp_warp_bytes(L, RD);
+    uint4 *ring_u = (uint4 *)rbase + lane;
+    uint2 *ring_c = (uint2 *)(rbase + (size_t)RD * S * 16) + lane;
+    uint2 *ring_op = (uint2 *)(rbase + (size_t)RD * S * 24) + lane;
+    uint32_t *sU = (uint32_t *)(rbase + (size_t)RD * S * 32) + lane;
+    unsigned long long *bars = (unsigned long long *)((char *)smem + th_bytes + (size_t)ncw * tnp_warp_bytes(L, RD));
+    unsigned long long *full = bars + (size_t)pair * 2 * RD, *empty = full + RD;
+
+    const int tid = threadIdx.x;
+    for (int i = tid; i < a.B * RS; i += blockDim.x) {
+        const int b = i / RS, c = i - (i / RS) * RS;
+        sTH[i] = (c < C) ? a.T[b * C + c] : 0u;
+    }
+    if (tid == 0)
+        for (int i = 0; i < ncw * 2 * RD; ++i) mbar_init(bars + i, 32);
+    __syncthreads();
+
+    const int w = w0 + pair * 32 + lane;
+    const bool active = w < a.p;
+    const uint32_t wid = (uint32_t)(w + a.walker_offset);
+    const uint32_t g0 = (uint32_t)a.state->sweep_counter;
+    uint32_t *lat = a.lattice + (active ? w : 0);
+    int bR = (active ? a.bin[w] : 0) * RS;
+    unsigned long long *Hb = a.Hpart + (size_t)slot_id * a.B;
+    int k = 0;
+    bool bad = false;
+    if (!producer && active) {  // the row above row 0: row L-1 as the previous launch left it
+        constexpr int WR = L / 8;
+#pragma unroll
+        for (int j = 0; j < L / 4; ++j)
+            sU[j * 32] = nib_half_to_bytes(lat[((L - 1) * WR + (j >> 1)) * a.pstride], j & 1);
+    }
+    for (int64_t s0 = 0; s0 < a.sweeps; s0 += a.flush_every) {
+        const int64_t s1 = (a.sweeps < s0 + a.flush_every) ? a.sweeps : s0 + a.flush_every;
+#pragma unroll 1
+        for (int64_t sw = s0; sw < s1; ++sw) {
+            const uint32_t g = g0 + (uint32_t)sw;
+            if (producer) {
+                produce_sweep_potts_tn<L, RD>(g, wid, a.rk, lat, a.pstride, (uint32_t)a.q, ring_u, ring_c, ring_op,
+                                              full, empty, k, bad);
+            } else if (active) {
+                if (a.record == 0)
+                    potts_sweep_tc<L, RD, 0>(lat, a.pstride, bR, sTH, ring_u, ring_c, ring_op, sU, full, empty, k, bad);
+                else
+                    potts_sweep_tc<L, RD, 1>(lat, a.pstride, bR, sTH, ring_u, ring_c, ring_op, sU, full, empty, k, bad);
+            } else {
+#pragma unroll 1
+                for (int y = 0; y < L; ++y) {
+                    const int slot = k % RD;
+                    if (!bad && !mbar_wait(&full[slot], (unsigned)((k / RD) & 1))) bad = true;
+                    mbar_arrive(&empty[slot]);
+                    ++k;
+                }
+            }
+        }
+        __syncthreads();
+        for (int b = tid; b < a.B; b += blockDim.x) {
+            const uint32_t c = sTH[b * RS + C];
+            if (c) {
+                Hb[b] += c;
+                sTH[b * RS + C] = 0u;
+            }
+        }
+        __syncthreads();
+    }
+    if (bad) atomicOr(const_cast<int *>(&a.state->err), 1);
+    if (!producer && active) a.bin[w] = bR / RS;
+}
+
+template <int L, int RD>
+__global__ void __launch_bounds__(kMaxSweepBlock, 1) k_sweep_potts_tn(const SpinSweepArgs a)
+{
+    extern __shared__ __align__(16) uint32_t smem[];
+    sweep_block_tnp<L, RD>(a, blockIdx.x * (blockDim.x / 2), blockIdx.x, smem);
+}
+
+static size_t potts_tn_smem_bytes(int L, int RD, int B, int walkers_per_block)
+{
+    const int ncw = walkers_per_block / 32;
+    return ((size_t)B * 10 * 4 + 15) / 16 * 16 + (size_t)ncw * tnp_warp_bytes(L, RD) +
+           (size_t)ncw * 2 * RD * sizeof(unsigned long long);
+}
+
+// Deepest ring (4 or 2 rows) whose block fits in shared memory; 0 if none does.
+static int potts_tn_depth(int L, int B, int walkers_per_block)
+{
+    if (L < 8 || L > 48 || L % 8 != 0 || !sweep_L_supported(L)) return 0;
+    if (potts_tn_smem_bytes(L, 4, B, walkers_per_block) <= 227u * 1024u) return 4;
+    if (potts_tn_smem_bytes(L, 2, B, walkers_per_block) <= 227u * 1024u) return 2;
+    return 0;
+}
+
+
+template <int SYS, int L>
+static cudaError_t launch_one_tn(const SpinSweepArgs &a, int block, cudaStream_t s)
+{
+    const size_t smem = spin_sweep_tn_smem_bytes(SYS, L, a.B, block);
+    cudaError_t e = cudaFuncSetAttribute(k_sweep_spin_tn<SYS, L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int nblk = (a.p + block - 1) / block;
+    k_sweep_spin_tn<SYS, L><<<nblk, 2 * block, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <int SYS>
+static cudaError_t launch_sys_tn(int L, const SpinSweepArgs &a, int block, cudaStream_t s)
+{
+    switch (L) {
+    case 4: return launch_one_tn<SYS, 4>(a, block, s);
+    case 8: return launch_one_tn<SYS, 8>(a, block, s);
+    case 12: return launch_one_tn<SYS, 12>(a, block, s);
+    case 16: return launch_one_tn<SYS, 16>(a, block, s);
+    case 24: return launch_one_tn<SYS, 24>(a, block, s);
+    case 32: return launch_one_tn<SYS, 32>(a, block, s);
+    case 48: return launch_one_tn<SYS, 48>(a, block, s);
+    case 64: return launch_one_tn<SYS, 64>(a, block, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+bool spin_sweep_tn_fits(int system, int L, int B, int walkers_per_block)
+{
+    if (system == kPotts)
+        return walkers_per_block % 32 == 0 && 2 * walkers_per_block <= kMaxSweepBlock &&
+               potts_tn_depth(L, B, walkers_per_block) != 0;
+    return (system == kIsing || system == kMuma) && L >= 2 * kRing && walkers_per_block % 32 == 0 &&
+           2 * walkers_per_block <= kMaxSweepBlock &&
+           spin_sweep_tn_smem_bytes(system, L, B, walkers_per_block) <= 227u * 1024u;
+}
+
+template <int L, int RD>
+static cudaError_t launch_one_tnp(const SpinSweepArgs &a, int block, cudaStream_t s)
+{
+    const size_t smem = potts_tn_smem_bytes(L, RD, a.B, block);
+    cudaError_t e = cudaFuncSetAttribute(k_sweep_potts_tn<L, RD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int nblk = (a.p + block - 1) / block;
+    k_sweep_potts_tn<L, RD><<<nblk, 2 * block, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <int RD>
+static cudaError_t launch_potts_tn_rd(int L, const SpinSweepArgs &a, int block, cudaStream_t s)
+{
+    switch (L) {
+    case 8: return launch_one_tnp<8, RD>(a, block, s);
+    case 16: return launch_one_tnp<16, RD>(a, block, s);
+    case 24: return launch_one_tnp<24, RD>(a, block, s);
+    case 32: return launch_one_tnp<32, RD>(a, block, s);
+    case 48: return launch_one_tnp<48, RD>(a, block, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+static cudaError_t launch_potts_tn(int L, int rd, const SpinSweepArgs &a, int block, cudaStream_t s)
+{
+    if (rd == 4) return launch_potts_tn_rd<4>(L, a, block, s);
+    if (rd == 2) return launch_potts_tn_rd<2>(L, a, block, s);
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_spin_sweep_tn(int system, int L, const SpinSweepArgs &a, int block, cudaStream_t s)
+{
+    if (!spin_sweep_supported(system, L) || !spin_sweep_tn_fits(system, L, a.B, block)) return cudaErrorInvalidValue;
+    switch (system) {
+    case kIsing: return launch_sys_tn<kIsing>(L, a, block, s);
+    case kMuma: return launch_sys_tn<kMuma>(L, a, block, s);
+    case kPotts: return launch_potts_tn(L, potts_tn_depth(L, a.B, block), a, block, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace muca

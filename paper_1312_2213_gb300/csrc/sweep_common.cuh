@@ -1,0 +1,78 @@
+// sweep_common.cuh -- pieces shared by the three forms of the spin sweep
+// (one warp per walker group, producer/consumer, producer/consumer with site
+// codes): packed-row accessors, the bounded mbarrier hand-over and the
+// lattice sizes that have compiled kernels.
+#pragma once
+#include "muca_device.cuh"
+#include "muca_internal.h"
+
+namespace muca {
+
+// Lattice sizes with compiled sweep kernels.
+__host__ __device__ constexpr bool sweep_L_supported(int L)
+{
+    return L == 4 || L == 8 || L == 12 || L == 16 || L == 24 || L == 32 || L == 48 || L == 64;
+}
+
+template <int WR>
+__device__ __forceinline__ int bit_at(const uint32_t (&r)[WR], int pos)
+{
+    return (int)((r[pos >> 5] >> (pos & 31)) & 1u);
+}
+
+template <int WR>
+__device__ __forceinline__ uint32_t nib_at(const uint32_t (&r)[WR], int x)
+{
+    return (r[(4 * x) >> 5] >> ((4 * x) & 31)) & 15u;
+}
+
+__device__ __forceinline__ uint32_t word_of(const uint4 &u, int j)
+{
+    return j == 0 ? u.x : (j == 1 ? u.y : (j == 2 ? u.z : u.w));
+}
+
+// One sweep of an Ising (MUCA in E) or multimagnetic (weight in M) walker.
+// Spin bit 1 means s = -1.  k = 4 - (number of anti-aligned neighbours), so
+// dE = 4(k-2); Ising column c = k and the bin moves by k-2; MUMA column
+// c = 5*bit + k and the bin (M+N)/2 moves by 2*bit-1.
+
+// Ring depth (rows) of the producer/consumer forms and the bound on every
+// mbarrier wait: a wait that gives up sets the error flag instead of spinning on.
+constexpr int kRing = 4;
+constexpr int kSpinLimit = 1 << 20;
+
+__device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned long long *bar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(unsigned long long *bar)
+{
+    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(unsigned long long *bar, unsigned parity)
+{
+    unsigned ok;
+    asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+                 : "=r"(ok)
+                 : "r"(smem_u32(bar)), "r"(parity)
+                 : "memory");
+    return ok != 0;
+}
+
+// Bounded wait; returns false (and leaves the barrier alone) after kSpinLimit tries.
+__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity)
+{
+    for (int i = 0; i < kSpinLimit; ++i)
+        if (mbar_try(bar, parity)) return true;
+    return false;
+}
+
+// Consumer side of one Ising / MUMA sweep: as ising_sweep, with the random words
+// of row y read from ring slot (k % kRing).
+
+}  // namespace muca

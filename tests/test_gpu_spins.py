@@ -57,13 +57,26 @@ def test_one_warp_form_bit_exact(system, L, q, p):
              pipeline=0)
 
 
-@pytest.mark.parametrize("system,L,p", [(m.ISING2D, 8, 64), (m.ISING2D, 16, 100), (m.ISING2D, 24, 70),
-                                        (m.ISING2D, 32, 130), (m.ISING2D, 48, 40), (m.ISING2D, 64, 35),
-                                        (m.ISING2D_MUMA, 8, 50), (m.ISING2D_MUMA, 32, 100), (m.ISING2D_MUMA, 48, 33)])
-def test_code_pipeline_bit_exact(system, L, p):
-    """pipeline = 2 (producer also computes the site column codes; threshold/next-bin pairs)."""
-    run_pair(system, L, 2, p, seed=500 + L, iters=4, sweeps=max(2, 4000 // (L * L)), beta=0.4407, nthreads=NT,
-             pipeline=2)
+@pytest.mark.parametrize("system,L,q,p", [(m.ISING2D, 32, 2, 100), (m.POTTS2D, 16, 10, 70), (m.ISING2D_MUMA, 24, 2, 65),
+                                          (m.ISING2D, 64, 2, 33)])
+def test_random_pipeline_bit_exact(system, L, q, p):
+    """pipeline = 1 (producer warps compute the random numbers only) gives the same bits."""
+    run_pair(system, L, q, p, seed=91 + L, iters=3, sweeps=max(2, 3000 // (L * L)), beta=0.4407, nthreads=NT,
+             pipeline=1)
+
+
+@pytest.mark.parametrize("system,L,q,p,block", [
+    (m.ISING2D, 8, 2, 64, None), (m.ISING2D, 16, 2, 100, None), (m.ISING2D, 24, 2, 70, None),
+    (m.ISING2D, 32, 2, 130, None), (m.ISING2D, 48, 2, 40, None), (m.ISING2D, 64, 2, 35, None),
+    (m.ISING2D_MUMA, 8, 2, 50, None), (m.ISING2D_MUMA, 32, 2, 100, None), (m.ISING2D_MUMA, 48, 2, 33, None),
+    (m.POTTS2D, 8, 3, 64, None), (m.POTTS2D, 12, 5, 45, None), (m.POTTS2D, 16, 10, 100, None),
+    (m.POTTS2D, 24, 8, 70, None), (m.POTTS2D, 32, 8, 130, None), (m.POTTS2D, 32, 2, 40, None),
+    (m.POTTS2D, 48, 10, 40, 32)])
+def test_code_pipeline_bit_exact(system, L, q, p, block):
+    """pipeline = 2 (the producer also computes the per-site codes) gives the same bits; Potts L = 48
+    with 32 walkers a block runs the two-row ring, the others the four-row ring."""
+    run_pair(system, L, q, p, seed=500 + L + q, iters=4, sweeps=max(2, 4000 // (L * L)), beta=0.4407, nthreads=NT,
+             pipeline=2, block=block)
 
 
 def test_config_ising_L8_p64_full_length():
@@ -73,10 +86,13 @@ def test_config_ising_L8_p64_full_length():
     assert flat and g.merge_and_update is not None
 
 
-@pytest.mark.parametrize("record", [1])
-def test_record_per_sweep(record):
-    run_pair(m.ISING2D, 16, 2, 64, seed=5, iters=3, sweeps=50, record=record, nthreads=NT)
-    run_pair(m.POTTS2D, 16, 5, 64, seed=6, iters=3, sweeps=50, record=record, nthreads=NT)
+@pytest.mark.parametrize("pipeline", [0, 1, 2])
+def test_record_per_sweep(pipeline):
+    """record = 1 (one count per walker per sweep) in every form of the sweep."""
+    run_pair(m.ISING2D, 16, 2, 64, seed=5, iters=3, sweeps=50, record=1, nthreads=NT, pipeline=pipeline)
+    run_pair(m.POTTS2D, 16, 5, 64, seed=6, iters=3, sweeps=50, record=1, nthreads=NT, pipeline=pipeline)
+    run_pair(m.ISING2D_MUMA, 16, 2, 40, seed=7, iters=3, sweeps=50, beta=0.4407, record=1, nthreads=NT,
+             pipeline=pipeline)
 
 
 @pytest.mark.parametrize("block", [32, 96, 256, 512])
