@@ -37,7 +37,47 @@ __device__ __forceinline__ uint32_t row_bit(const uint32_t (&r)[WR], int x)
     return (r[x >> 5] >> (x & 31)) & 1u;
 }
 
-template <int SYS, int L>
+// Producer warps per consumer warp in the code forms.  One Philox4x32-10 block
+// costs a scheduler about 90 cycles of integer-multiply throughput and a single
+// warp reaches about 134 cycles a block, so one producer cannot keep up with its
+// consumer; the row's site groups are split over NP producers (on other
+// schedulers), which arrive together on the row's FULL barrier.
+constexpr int kCodeProducers = 2;
+
+template <int WR>
+__device__ __forceinline__ void rotate_words(uint32_t (&o)[WR])  // o[e] <- o[e+1], cyclic
+{
+    const uint32_t t = o[0];
+#pragma unroll
+    for (int e = 0; e + 1 < WR; ++e) o[e] = o[e + 1];
+    o[WR - 1] = t;
+}
+
+// Warp roles of a code-form block of one or two walker warps (ncw).  The block
+// has 4 ncw warps, laid out so that, with warp w issuing from scheduler w mod 4,
+// every consumer has a scheduler to itself (its serial chain is what sets the
+// pace) and the two producers of a consumer share another one:
+//   ncw = 1: [C0, idle, P0.0, P0.1]
+//   ncw = 2: [C0, C1, P0.0, P1.0, idle, idle, P0.1, P1.1]   (Pc.k: part k for consumer c)
+// Idle warps only take part in the block-wide barriers of the histogram flush.
+enum { kRoleConsumer = 0, kRoleProducer = 1, kRoleIdle = 2 };
+struct CodeRole {
+    int kind, pair, part;
+};
+__device__ __forceinline__ CodeRole code_role(int warp, int ncw)
+{
+    if (ncw == 1) {
+        if (warp == 0) return CodeRole{kRoleConsumer, 0, 0};
+        if (warp == 1) return CodeRole{kRoleIdle, 0, 0};
+        return CodeRole{kRoleProducer, 0, warp - 2};
+    }
+    const int sch = warp & 3, grp = warp >> 2;
+    if (sch < 2) return grp == 0 ? CodeRole{kRoleConsumer, sch, 0} : CodeRole{kRoleIdle, 0, 0};
+    return CodeRole{kRoleProducer, sch - 2, grp};
+}
+constexpr int kCodeWarpsPerWalkerWarp = 4;
+
+template <int SYS, int L, int PART>
 __device__ __forceinline__ void produce_sweep_tn(uint32_t g, uint32_t wid, const uint32_t (&rk)[20],
                                                  const uint32_t *__restrict__ lat, int ps, uint4 *ring_u,
                                                  uint2 *ring_c, uint32_t *ring_r, unsigned long long *full,
@@ -71,10 +111,13 @@ __device__ __forceinline__ void produce_sweep_tn(uint32_t g, uint32_t wid, const
         uint4 *wu = ring_u + slot * SU;
         uint2 *wc = ring_c + slot * SC;
         uint32_t *wr = ring_r + slot * SR;
+        if (PART == 0) {
 #pragma unroll
-        for (int j = 0; j < WR; ++j) wr[j * 32] = o[j];
+            for (int j = 0; j < WR; ++j) wr[j * 32] = o[j];
+        }
+        constexpr int g_lo = PART * G / kCodeProducers, g_hi = (PART + 1) * G / kCodeProducers;
 #pragma unroll
-        for (int gq = 0; gq < G; ++gq) {
+        for (int gq = g_lo; gq < g_hi; ++gq) {
             wu[gq * 32] = philox4x32_10_rk(make_uint4((uint32_t)(y * G + gq), g, wid, kTagSweep), rk);
             const int x = 4 * gq;
             const uint32_t s4 = row_nibble<L, WR>(o, x);
@@ -213,10 +256,12 @@ __device__ __forceinline__ void sweep_block_tn(const SpinSweepArgs &a, int w0, i
     constexpr int C = num_cols(SYS);
     constexpr int RS = C + 1;
     constexpr int G = L / 4;
-    const int ncw = blockDim.x / 64;
+    constexpr int NP = kCodeProducers;
+    const int ncw = blockDim.x / (32 * kCodeWarpsPerWalkerWarp);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const bool producer = warp >= ncw;
-    const int pair = producer ? warp - ncw : warp;
+    const CodeRole role = code_role(warp, ncw);
+    const bool producer = role.kind == kRoleProducer, consumer = role.kind == kRoleConsumer;
+    const int pair = role.pair, part = role.part;
     uint32_t *sTH = smem;
     const size_t th_bytes = ((size_t)a.B * RS * 4 + 15) / 16 * 16;
     char *rbase = (char *)smem + th_bytes + (size_t)pair * tn_ring_bytes(L);
@@ -231,8 +276,8 @@ __device__ __forceinline__ void sweep_block_tn(const SpinSweepArgs &a, int w0, i
         const int b = i / RS, c = i - (i / RS) * RS;
         sTH[i] = (c < C) ? a.T[b * C + c] : 0u;
     }
-    if (tid == 0)
-        for (int i = 0; i < ncw * 2 * kRing; ++i) mbar_init(bars + i, 32);
+    if (tid == 0)  // per pair: FULL[kRing] (NP producer warps arrive), EMPTY[kRing] (the consumer)
+        for (int i = 0; i < ncw * 2 * kRing; ++i) mbar_init(bars + i, ((i / kRing) % 2 == 0) ? 32 * NP : 32);
     __syncthreads();
 
     const int w = w0 + pair * 32 + lane;
@@ -250,13 +295,16 @@ __device__ __forceinline__ void sweep_block_tn(const SpinSweepArgs &a, int w0, i
         for (int64_t sw = s0; sw < s1; ++sw) {
             const uint32_t g = g0 + (uint32_t)sw;
             if (producer) {
-                produce_sweep_tn<SYS, L>(g, wid, a.rk, lat, a.pstride, ring_u, ring_c, ring_r, full, empty, k, bad);
-            } else if (active) {
+                if (part == 0)
+                    produce_sweep_tn<SYS, L, 0>(g, wid, a.rk, lat, a.pstride, ring_u, ring_c, ring_r, full, empty, k, bad);
+                else
+                    produce_sweep_tn<SYS, L, 1>(g, wid, a.rk, lat, a.pstride, ring_u, ring_c, ring_r, full, empty, k, bad);
+            } else if (consumer && active) {
                 if (a.record == 0)
                     ising_sweep_tc<SYS, L, 0>(lat, a.pstride, bR, sTH, ring_u, ring_c, ring_r, full, empty, k, bad);
                 else
                     ising_sweep_tc<SYS, L, 1>(lat, a.pstride, bR, sTH, ring_u, ring_c, ring_r, full, empty, k, bad);
-            } else {
+            } else if (consumer) {  // a consumer warp with no walkers keeps the barrier protocol
 #pragma unroll 1
                 for (int y = 0; y < L; ++y) {
                     const int slot = k % kRing;
@@ -277,14 +325,14 @@ __device__ __forceinline__ void sweep_block_tn(const SpinSweepArgs &a, int w0, i
         __syncthreads();
     }
     if (bad) atomicOr(const_cast<int *>(&a.state->err), 1);
-    if (!producer && active) a.bin[w] = bR / RS;
+    if (consumer && active) a.bin[w] = bR / RS;
 }
 
 template <int SYS, int L>
 __global__ void __launch_bounds__(kMaxSweepBlock, 1) k_sweep_spin_tn(const SpinSweepArgs a)
 {
     extern __shared__ __align__(16) uint32_t smem[];
-    sweep_block_tn<SYS, L>(a, blockIdx.x * (blockDim.x / 2), blockIdx.x, smem);
+    sweep_block_tn<SYS, L>(a, blockIdx.x * (blockDim.x / kCodeWarpsPerWalkerWarp), blockIdx.x, smem);
 }
 
 static int potts_tn_depth(int L, int B, int walkers_per_block);
@@ -334,7 +382,7 @@ __device__ __forceinline__ uint32_t bytes_to_nibs(uint32_t w0, uint32_t w1)  // 
 // Philox blocks each); its old and down rows rotate through registers so that
 // word i is always element 0.  (A fully unrolled row was several times larger
 // than the instruction cache serves without fetch stalls.)
-template <int L, int RD>
+template <int L, int RD, int PART>
 __device__ __forceinline__ void produce_sweep_potts_tn(uint32_t g, uint32_t wid, const uint32_t (&rk)[20],
                                                        const uint32_t *__restrict__ lat, int ps, uint32_t q,
                                                        uint4 *ring_u, uint2 *ring_c, uint2 *ring_op,
@@ -365,10 +413,27 @@ __device__ __forceinline__ void produce_sweep_potts_tn(uint32_t g, uint32_t wid,
         uint4 *wu = ring_u + slot * S;
         uint2 *wc = ring_c + slot * S;
         uint2 *wop = ring_op + slot * S;
-        uint32_t ob_prev = nib_half_to_bytes(o[WR - 1], 1);  // sites L-4..L-1: left of site 0
+        // this producer's nibble words [i0, i1); the arrays are rotated so that word i0 is element 0
+        constexpr int NP = kCodeProducers;
+        constexpr int i0 = (NP == 1 || PART == 0) ? 0 : (WR + 1) / 2;
+        constexpr int i1 = (NP == 2 && PART == 0) ? (WR + 1) / 2 : WR;
+#pragma unroll
+        for (int e = 0; e < i0; ++e) {
+            rotate_words<WR>(o);
+            rotate_words<WR>(d);
+        }
+        uint32_t ob_prev = nib_half_to_bytes(o[WR - 1], 1);  // the four sites left of word i0 (cyclic)
         uint32_t pprev = 0u;                                  // site 0's c1 is never used
+        if (i0 > 0) {
+            // proposal of site 8 i0 - 1 (the second site of its Philox block): the c1
+            // column of site 8 i0 has it as its recoloured left neighbour
+            const uint4 r = philox4x32_10_rk(make_uint4((uint32_t)(y * (L / 2) + 4 * i0 - 1), g, wid, kTagSweep), rk);
+            uint32_t v = (ob_prev >> 24) + 1u + __umulhi(r.z, qm1);
+            v = (v >= q) ? v - q : v;
+            pprev = v << 24;
+        }
 #pragma unroll 1
-        for (int i = 0; i < WR; ++i) {
+        for (int i = i0; i < i1; ++i) {
             const uint32_t on = o[1 % WR];  // next nibble word, cyclic
             const uint32_t mask_last = (i == WR - 1) ? 0x00FFFFFFu : 0xFFFFFFFFu;
 #pragma unroll
@@ -407,14 +472,13 @@ __device__ __forceinline__ void produce_sweep_potts_tn(uint32_t g, uint32_t wid,
                 ob_prev = ob;
                 pprev = pb;
             }
-            const uint32_t o0 = o[0], d0 = d[0];
+            rotate_words<WR>(o);
+            rotate_words<WR>(d);
+        }
 #pragma unroll
-            for (int e = 0; e + 1 < WR; ++e) {
-                o[e] = o[e + 1];
-                d[e] = d[e + 1];
-            }
-            o[WR - 1] = o0;
-            d[WR - 1] = d0;
+        for (int e = i1; e < WR; ++e) {  // back to word 0 first (WR rotations in all)
+            rotate_words<WR>(o);
+            rotate_words<WR>(d);
         }
         mbar_arrive(&full[slot]);
         ++k;
@@ -542,10 +606,12 @@ __device__ __forceinline__ void sweep_block_tnp(const SpinSweepArgs &a, int w0, 
     constexpr int C = 9;
     constexpr int RS = C + 1;
     constexpr size_t S = (size_t)(L / 4) * 32;
-    const int ncw = blockDim.x / 64;
+    constexpr int NP = kCodeProducers;
+    const int ncw = blockDim.x / (32 * kCodeWarpsPerWalkerWarp);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const bool producer = warp >= ncw;
-    const int pair = producer ? warp - ncw : warp;
+    const CodeRole role = code_role(warp, ncw);
+    const bool producer = role.kind == kRoleProducer, consumer = role.kind == kRoleConsumer;
+    const int pair = role.pair, part = role.part;
     uint32_t *sTH = smem;
     const size_t th_bytes = ((size_t)a.B * RS * 4 + 15) / 16 * 16;
     char *rbase = (char *)smem + th_bytes + (size_t)pair * tnp_warp_bytes(L, RD);
@@ -561,8 +627,8 @@ __device__ __forceinline__ void sweep_block_tnp(const SpinSweepArgs &a, int w0, 
         const int b = i / RS, c = i - (i / RS) * RS;
         sTH[i] = (c < C) ? a.T[b * C + c] : 0u;
     }
-    if (tid == 0)
-        for (int i = 0; i < ncw * 2 * RD; ++i) mbar_init(bars + i, 32);
+    if (tid == 0)  // per pair: FULL[RD] (NP producer warps arrive), EMPTY[RD] (the consumer)
+        for (int i = 0; i < ncw * 2 * RD; ++i) mbar_init(bars + i, ((i / RD) % 2 == 0) ? 32 * NP : 32);
     __syncthreads();
 
     const int w = w0 + pair * 32 + lane;
@@ -574,7 +640,7 @@ __device__ __forceinline__ void sweep_block_tnp(const SpinSweepArgs &a, int w0, 
     unsigned long long *Hb = a.Hpart + (size_t)slot_id * a.B;
     int k = 0;
     bool bad = false;
-    if (!producer && active) {  // the row above row 0: row L-1 as the previous launch left it
+    if (consumer && active) {  // the row above row 0: row L-1 as the previous launch left it
         constexpr int WR = L / 8;
 #pragma unroll
         for (int j = 0; j < L / 4; ++j)
@@ -586,14 +652,18 @@ __device__ __forceinline__ void sweep_block_tnp(const SpinSweepArgs &a, int w0, 
         for (int64_t sw = s0; sw < s1; ++sw) {
             const uint32_t g = g0 + (uint32_t)sw;
             if (producer) {
-                produce_sweep_potts_tn<L, RD>(g, wid, a.rk, lat, a.pstride, (uint32_t)a.q, ring_u, ring_c, ring_op,
-                                              full, empty, k, bad);
-            } else if (active) {
+                if (part == 0)
+                    produce_sweep_potts_tn<L, RD, 0>(g, wid, a.rk, lat, a.pstride, (uint32_t)a.q, ring_u, ring_c,
+                                                     ring_op, full, empty, k, bad);
+                else
+                    produce_sweep_potts_tn<L, RD, 1>(g, wid, a.rk, lat, a.pstride, (uint32_t)a.q, ring_u, ring_c,
+                                                     ring_op, full, empty, k, bad);
+            } else if (consumer && active) {
                 if (a.record == 0)
                     potts_sweep_tc<L, RD, 0>(lat, a.pstride, bR, sTH, ring_u, ring_c, ring_op, sU, full, empty, k, bad);
                 else
                     potts_sweep_tc<L, RD, 1>(lat, a.pstride, bR, sTH, ring_u, ring_c, ring_op, sU, full, empty, k, bad);
-            } else {
+            } else if (consumer) {
 #pragma unroll 1
                 for (int y = 0; y < L; ++y) {
                     const int slot = k % RD;
@@ -614,14 +684,14 @@ __device__ __forceinline__ void sweep_block_tnp(const SpinSweepArgs &a, int w0, 
         __syncthreads();
     }
     if (bad) atomicOr(const_cast<int *>(&a.state->err), 1);
-    if (!producer && active) a.bin[w] = bR / RS;
+    if (consumer && active) a.bin[w] = bR / RS;
 }
 
 template <int L, int RD>
 __global__ void __launch_bounds__(kMaxSweepBlock, 1) k_sweep_potts_tn(const SpinSweepArgs a)
 {
     extern __shared__ __align__(16) uint32_t smem[];
-    sweep_block_tnp<L, RD>(a, blockIdx.x * (blockDim.x / 2), blockIdx.x, smem);
+    sweep_block_tnp<L, RD>(a, blockIdx.x * (blockDim.x / kCodeWarpsPerWalkerWarp), blockIdx.x, smem);
 }
 
 static size_t potts_tn_smem_bytes(int L, int RD, int B, int walkers_per_block)
@@ -648,7 +718,7 @@ static cudaError_t launch_one_tn(const SpinSweepArgs &a, int block, cudaStream_t
     cudaError_t e = cudaFuncSetAttribute(k_sweep_spin_tn<SYS, L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const int nblk = (a.p + block - 1) / block;
-    k_sweep_spin_tn<SYS, L><<<nblk, 2 * block, smem, s>>>(a);
+    k_sweep_spin_tn<SYS, L><<<nblk, kCodeWarpsPerWalkerWarp * block, smem, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -671,10 +741,9 @@ static cudaError_t launch_sys_tn(int L, const SpinSweepArgs &a, int block, cudaS
 bool spin_sweep_tn_fits(int system, int L, int B, int walkers_per_block)
 {
     if (system == kPotts)
-        return walkers_per_block % 32 == 0 && 2 * walkers_per_block <= kMaxSweepBlock &&
-               potts_tn_depth(L, B, walkers_per_block) != 0;
-    return (system == kIsing || system == kMuma) && L >= 2 * kRing && walkers_per_block % 32 == 0 &&
-           2 * walkers_per_block <= kMaxSweepBlock &&
+        return (walkers_per_block == 32 || walkers_per_block == 64) && potts_tn_depth(L, B, walkers_per_block) != 0;
+    return (system == kIsing || system == kMuma) && L >= 2 * kRing &&
+           (walkers_per_block == 32 || walkers_per_block == 64) &&
            spin_sweep_tn_smem_bytes(system, L, B, walkers_per_block) <= 227u * 1024u;
 }
 
@@ -685,7 +754,7 @@ static cudaError_t launch_one_tnp(const SpinSweepArgs &a, int block, cudaStream_
     cudaError_t e = cudaFuncSetAttribute(k_sweep_potts_tn<L, RD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const int nblk = (a.p + block - 1) / block;
-    k_sweep_potts_tn<L, RD><<<nblk, 2 * block, smem, s>>>(a);
+    k_sweep_potts_tn<L, RD><<<nblk, kCodeWarpsPerWalkerWarp * block, smem, s>>>(a);
     return cudaGetLastError();
 }
 
