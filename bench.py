@@ -55,9 +55,9 @@ def parse():
     ap.add_argument("--sweeps", type=int, default=SWEEPS)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sweeps", type=int, default=400, help="sweeps per system in the CPU sample")
-    ap.add_argument("--no-extras", action="store_true", help="skip the batched-mix and polymer measurements")
-    ap.add_argument("--workload", default="all", choices=["all", "mix", "polymer"],
-                    help="mix / polymer: run only that measurement (for profiling)")
+    ap.add_argument("--no-extras", action="store_true", help="skip the batched-mix, Potts and polymer measurements")
+    ap.add_argument("--workload", default="all", choices=["all", "mix", "polymer", "potts"],
+                    help="mix / polymer / potts: run only that measurement (for profiling)")
     return ap.parse_args()
 
 
@@ -69,8 +69,8 @@ def run_mix(m, torch, sweeps=1000, short_sweeps=10, short_iters=20):
     """Plain (one system per launch, host loop) vs batched (one launch per iteration) vs graph."""
     sites = sum(L * L for _, L, _ in MIX)
 
-    def make(seed0):
-        return [m.Muca(s_, L, q, MIX_P, seed0 + i, block=128) for i, (s_, L, q) in enumerate(MIX)]
+    def make(seed0):  # default walkers per block: the plain path runs the fastest form that fits
+        return [m.Muca(s_, L, q, MIX_P, seed0 + i) for i, (s_, L, q) in enumerate(MIX)]
 
     def timed(fn):
         torch.cuda.synchronize()
@@ -118,6 +118,25 @@ def run_mix(m, torch, sweeps=1000, short_sweeps=10, short_iters=20):
     for c in sysA + sysB:
         c.close()
     return out
+
+
+def run_potts(m, torch, L=32, q=8, p=8192, sweeps=2000):
+    """Potts q = 8, L = 32, p = 8192 (the first-order Potts workload): one iteration of `sweeps` sweeps."""
+    g = m.Muca(m.POTTS2D, L, q, p, 11)
+    for _ in range(2):
+        g.iterate(50)
+        g.merge_and_update()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    g.iterate(sweeps)
+    b.record()
+    g.merge_and_update()
+    torch.cuda.synchronize()
+    t = a.elapsed_time(b) / 1e3
+    g.close()
+    att = p * sweeps * L * L
+    return {"L": L, "q": q, "walkers": p, "sweeps": sweeps, "attempts_per_s": att / t, "kernel_ms": t * 1e3}
 
 
 def run_polymer(m, torch, p=4096, budget_attempts=2.0e8):
@@ -346,7 +365,7 @@ def run_ours(args):
     achieved_tinst = P * sweeps * N * INSTR_PER_ATTEMPT / (sweep_ms / 1e3) / 1e12
     roofline = {"bound": "alu", "achieved": achieved_tinst, "peak": peak_tinst, "unit": "Tinst/s",
                 "frac": achieved_tinst / peak_tinst, "traffic": None,
-                "kernel": "k_sweep_spin (Ising L=32 MUCA/MUMA)", "kernel_ms": sweep_ms,
+                "kernel": "k_sweep_spin_tn (code form; Ising L=32 MUCA and MUMA)", "kernel_ms": sweep_ms,
                 "peak_basis": "%d SMs x 4 schedulers x 32 lanes x %.0f MHz (median sampled SM clock)" % (sms, f_mhz),
                 "instr_per_attempt": INSTR_PER_ATTEMPT}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -361,6 +380,7 @@ def run_ours(args):
             "clocks": ck}
     if not args.no_extras:
         line["batched_mix"] = run_mix(m, torch)
+        line["potts_q8_L32"] = run_potts(m, torch)
         line["polymer"] = run_polymer(m, torch)
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_sample(args.cpu_sweeps, 5)
@@ -379,7 +399,7 @@ def main():
         import paper_1312_2213_gb300 as m
 
         m.load()
-        res = run_mix(m, torch) if args.workload == "mix" else run_polymer(m, torch)
+        res = {"mix": run_mix, "polymer": run_polymer, "potts": run_potts}[args.workload](m, torch)
         print(json.dumps({"workload": args.workload, **res}), flush=True)
     else:
         run_ours(args)
