@@ -41,6 +41,11 @@ N = L * L
 # (10 rounds x 4 ops / 4 = 10), neighbour bits and count 8, table column and address 2,
 # threshold load 1, integer compare 2, flip/select 3, bin update 2, histogram atomic 1, loop 1.
 INSTR_PER_ATTEMPT = 30
+# DRAM bytes (read + write) per launch of the timed sweep kernel, from one ncu capture of the current
+# k_sweep_spin_tn build (dram__bytes_read.sum + dram__bytes_write.sum; mean of the Ising and MUMA
+# launches: 1.23 MB and 2.15 MB read, nothing written).  It is the walker state and does not grow
+# with the sweep count.  Set to None whenever the kernel changes until it is measured again.
+TRAFFIC_PER_LAUNCH = 1.69e6
 METRIC = "MUCA move attempts/s (Ising L=32 p=8192: MUCA in E + MUMA in M)"
 UNIT = "attempts/s"
 L2_FLUSH_BYTES = 256 << 20
@@ -364,7 +369,7 @@ def run_ours(args):
     peak_tinst = sms * 4 * 32 * f_mhz * 1e6 / 1e12
     achieved_tinst = P * sweeps * N * INSTR_PER_ATTEMPT / (sweep_ms / 1e3) / 1e12
     roofline = {"bound": "alu", "achieved": achieved_tinst, "peak": peak_tinst, "unit": "Tinst/s",
-                "frac": achieved_tinst / peak_tinst, "traffic": None,
+                "frac": achieved_tinst / peak_tinst, "traffic": TRAFFIC_PER_LAUNCH,
                 "kernel": "k_sweep_spin_tn (code form; Ising L=32 MUCA and MUMA)", "kernel_ms": sweep_ms,
                 "peak_basis": "%d SMs x 4 schedulers x 32 lanes x %.0f MHz (median sampled SM clock)" % (sms, f_mhz),
                 "instr_per_attempt": INSTR_PER_ATTEMPT}
