@@ -60,6 +60,25 @@ __device__ __forceinline__ long long warp_sum_ll(long long q)
     return q;
 }
 
+// llrint(t) for |t| < 2^62 without a 64-bit conversion instruction (those run on
+// the FP64 pipe, a small fraction of FP32 on GB300): below 2^31 a 32-bit rounding
+// conversion; above, t is an integer m * 2^e with e >= 8, rebuilt from its bits.
+__device__ __forceinline__ long long f2ll_exact(float t)
+{
+    const uint32_t b = __float_as_uint(t);
+    const int e = (int)((b >> 23) & 0xffu) - 150;
+    const long long m = (long long)((b & 0x7fffffu) | 0x800000u);
+    const long long big = (e >= 0 ? (m << (e & 63)) : 0);
+    return fabsf(t) < 2147483648.0f ? (long long)__float2int_rn(t) : ((b >> 31) ? -big : big);
+}
+
+// A 2^-32 fixed-point value as a float, from its two 32-bit halves (32-bit
+// conversions only).
+__device__ __forceinline__ float q32_to_float(long long v)
+{
+    return (float)(int)(v >> 32) + (float)(uint32_t)v * 0x1p-32f;
+}
+
 __device__ __forceinline__ int poly_bin(long long E, const PolyArgs &a)
 {
     const long long b = ((E - a.elo_q) * 10) >> 32;
@@ -164,6 +183,8 @@ __global__ void __launch_bounds__(kMaxSweepBlock) k_sweep_polymer(const PolyArgs
     long long *Xs = (long long *)smem + (size_t)wib * 3 * N;
     float *xs = (float *)(smem + (size_t)wpb * 3 * N * sizeof(long long)) + (size_t)wib * 6 * N;
     float *xl = xs + 3 * N;
+    // this sweep's Philox blocks, one per bead (lane l draws beads l, l+32, ...)
+    uint4 *su = (uint4 *)(smem + (size_t)wpb * 3 * N * (sizeof(long long) + 2 * sizeof(float))) + (size_t)wib * N;
     const int w = blockIdx.x * wpb + wib;
     if (w >= a.p) return;  // whole warps only; no block-wide barrier follows
     const uint32_t wid = (uint32_t)(w + a.walker_offset);
@@ -181,20 +202,25 @@ __global__ void __launch_bounds__(kMaxSweepBlock) k_sweep_polymer(const PolyArgs
             grid_to_ff(Xs[j] - A0, xs[j], xl[j]);
             grid_to_ff(Xs[N + j] - A1, xs[N + j], xl[N + j]);
             grid_to_ff(Xs[2 * N + j] - A2, xs[2 * N + j], xl[2 * N + j]);
+            su[j] = philox4x32_10_rk(make_uint4((uint32_t)j, g, wid, kTagSweep), a.rk);
         }
         __syncwarp();
 #pragma unroll 1
         for (int i = 0; i < N; ++i) {
-            const uint4 u = philox4x32_10_rk(make_uint4((uint32_t)i, g, wid, kTagSweep), a.rk);
-            const long long n0 = Xs[i] + ((long long)u.x - 2147483648LL) * kPolyStepQ;
-            const long long n1 = Xs[N + i] + ((long long)u.y - 2147483648LL) * kPolyStepQ;
-            const long long n2 = Xs[2 * N + i] + ((long long)u.z - 2147483648LL) * kPolyStepQ;
+            const uint4 u = su[i];
+            // move (u - 2^31) * 1229 grid units per axis: exact on the int64 master
+            // coordinates; the float-pair shadow moves by the same amount in FP32
+            // (the shadows are rebuilt exactly from the masters every sweep)
+            const int sx = (int)(u.x ^ 0x80000000u), sy = (int)(u.y ^ 0x80000000u), sz = (int)(u.z ^ 0x80000000u);
+            const long long n0 = Xs[i] + (long long)sx * kPolyStepQ;
+            const long long n1 = Xs[N + i] + (long long)sy * kPolyStepQ;
+            const long long n2 = Xs[2 * N + i] + (long long)sz * kPolyStepQ;
             const float xo = xs[i], yo = xs[N + i], zo = xs[2 * N + i];
             const float lxo = xl[i], lyo = xl[N + i], lzo = xl[2 * N + i];
-            float xn, yn, zn, lxn, lyn, lzn;
-            grid_to_ff(n0 - A0, xn, lxn);
-            grid_to_ff(n1 - A1, yn, lyn);
-            grid_to_ff(n2 - A2, zn, lzn);
+            constexpr float kStep = (float)kPolyStepQ * 0x1p-44f;
+            const float dx = (float)sx * kStep, dy = (float)sy * kStep, dz = (float)sz * kStep;
+            const float xn = xo + dx, yn = yo + dy, zn = zo + dz;
+            const float lxn = lxo + ((xo - xn) + dx), lyn = lyo + ((yo - yn) + dy), lzn = lzo + ((zo - zn) + dz);
             float s = 0.0f, c = 0.0f;
             bool broken = false;
 #pragma unroll
@@ -226,7 +252,7 @@ __global__ void __launch_bounds__(kMaxSweepBlock) k_sweep_polymer(const PolyArgs
             broken = __any_sync(0xffffffffu, broken);
             // |lane sum| >= 2^22 only for overlapping beads: such a move is rejected
             const bool huge = __any_sync(0xffffffffu, !(fabsf(s) < 4194304.0f));
-            long long q = huge ? 0 : (__float2ll_rn(s * 0x1p32f) - __float2ll_rn(c * 0x1p32f));
+            long long q = huge ? 0 : (f2ll_exact(s * 0x1p32f) - f2ll_exact(c * 0x1p32f));
             q = warp_sum_ll(q);
             const long long En = E + q;
             const int bn = poly_bin(En, a);
@@ -238,7 +264,7 @@ __global__ void __launch_bounds__(kMaxSweepBlock) k_sweep_polymer(const PolyArgs
                         if (dq >= 0) {
                             acc = true;
                         } else {
-                            const float thr = expf((float)dq * 0x1p-32f) * 4294967296.0f;
+                            const float thr = expf(q32_to_float(dq)) * 4294967296.0f;
                             acc = (float)u.w < thr;
                         }
                     }
@@ -317,7 +343,7 @@ template <int NPL>
 static cudaError_t launch_npl(const PolyArgs &a, int block, cudaStream_t s)
 {
     const int wpb = block / 32;
-    const size_t smem = (size_t)wpb * 3 * a.N * (sizeof(long long) + 2 * sizeof(float));
+    const size_t smem = (size_t)wpb * a.N * (3 * (sizeof(long long) + 2 * sizeof(float)) + sizeof(uint4));
     const int nblk = (a.p + wpb - 1) / wpb;
     cudaError_t e;
     if (a.record == 0) {
