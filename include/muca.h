@@ -83,8 +83,10 @@ int muca_init_ex(muca_ctx **out, int system, int L_or_N, int q, int p, uint64_t 
  *   "record"      0 = count the current bin after every attempt (default),
  *                 1 = once per sweep; before the first iterate.
  *   "flat_ratio"  flatness criterion min H / mean H (default 0.5); any time.
- *   "block"       walkers per thread block of the sweep kernel (32..512,
- *                 multiple of 32); before the first iterate.
+ *   "block"       spins: walkers per thread block of the sweep kernel (32..512,
+ *                 multiple of 32; default 64; the code form runs for 32 or 64);
+ *                 polymer: threads per block (default 256).  Before the first
+ *                 iterate.
  *   "pipeline"    spins: 2 (default) pairs every warp of walkers with a
  *                 producer warp that computes their random numbers and, for
  *                 Ising and MUMA, each site's neighbour code into a
@@ -99,6 +101,11 @@ int muca_init_ex(muca_ctx **out, int system, int L_or_N, int q, int p, uint64_t 
  *                 walker w draws from the stream of walker w + offset, so the
  *                 union of the shards equals one context of all walkers;
  *                 re-draws the initial states; before the first iterate.
+ *   "lanes"       polymer: lanes of a warp per walker in the sweep, 8, 16 or 32
+ *                 (32/lanes walkers share a warp); 0 (default) means 16.  The pair terms are
+ *                 FP32 and their grouping over lanes changes their rounding, so
+ *                 runs with different values agree within the FP32 tolerance,
+ *                 not bit for bit.  Any time.
  *   Polymer only (before the first iterate): "e_lo", "e_hi" (the energy
  *   window, bins of width 0.1, at most 12288 bins; default [2N, 6N)),
  *   "fene_K", "fene_R" (default 40, 1.5).  Fixed: LJ eps = sigma = 1 cut at

@@ -51,6 +51,7 @@ struct muca_ctx {
     uint64_t seed = 0;
     double beta = 0.0, flat_ratio = 0.5;
     int record = 0, block = 64, walker_offset = 0;
+    int lanes = 0;     // polymer: lanes per walker in the sweep (8, 16, 32; 0 = chosen by N)
     int pipeline = 2;  // spins: code form (2), producer/consumer (1) or one warp per walker group (0)
     int pstride = 0, wpw = 0, nblk_max = 0;
     cudaStream_t stream = nullptr;
@@ -110,7 +111,7 @@ void fill_shape(muca_ctx *c, int system, int L, int q, int p)
         c->pstride = p;
         c->wpw = 0;
         c->nblk_max = 1;
-        c->block = 128;
+        c->block = 256;
         return;
     }
     c->system = system;
@@ -241,6 +242,7 @@ PolyArgs poly_args(const muca_ctx *c, int64_t sweeps)
     a.B = c->B;
     a.record = c->record;
     a.walker_offset = c->walker_offset;
+    a.lanes = c->lanes;
     a.elo_q = llrint(c->e_lo * 4294967296.0);                      // e_lo * 2^32
     a.ehi_q = a.elo_q + ((long long)c->B * 4294967296LL + 9) / 10;  // first energy with bin >= B
     a.fene_KR2_half = (float)(0.5 * c->fene_K * c->fene_R * c->fene_R);
@@ -512,6 +514,12 @@ int muca_set_param(muca_ctx *c, const char *key, double v)
     if (k == "pipeline") {
         if (v != 0.0 && v != 1.0 && v != 2.0) return fail(MUCA_ERR_ARG, "pipeline must be 0, 1 or 2");
         c->pipeline = (int)v;
+        return MUCA_OK;
+    }
+    if (k == "lanes") {
+        if (c->system != kPolymer) return fail(MUCA_ERR_ARG, "lanes applies to the polymer only");
+        if (v != 0.0 && v != 8.0 && v != 16.0 && v != 32.0) return fail(MUCA_ERR_ARG, "lanes must be 0, 8, 16 or 32");
+        c->lanes = (int)v;
         return MUCA_OK;
     }
     if (k == "walker_offset") {

@@ -100,6 +100,7 @@ struct PolyArgs {
     unsigned long long *H;         // open histogram (B counters)
     DevState *state;
     int p, N, B, record, walker_offset;
+    int lanes;                     // lanes per walker in the sweep (8, 16, 32; 0 = by N)
     long long elo_q, ehi_q;        // window [elo_q, ehi_q): bins 0..B-1
     float fene_KR2_half, fene_invR2, lj_rc2, lj_shift;
     int64_t sweeps;
@@ -110,6 +111,7 @@ bool polymer_supported(int N);
 cudaError_t launch_poly_init(const PolyArgs &a, cudaStream_t s);
 cudaError_t launch_poly_energy(const PolyArgs &a, int track_drift, cudaStream_t s);
 cudaError_t launch_poly_sweep(const PolyArgs &a, int block, cudaStream_t s);
+int poly_lanes(int N, int requested);
 cudaError_t launch_poly_lnwq(const double *lnW, long long *lnWq, int B, cudaStream_t s);
 cudaError_t launch_poly_unpack(const PolyArgs &a, double *coords, double *energies, cudaStream_t s);
 

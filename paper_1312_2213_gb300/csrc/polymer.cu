@@ -173,35 +173,58 @@ __global__ void k_poly_energy(const PolyArgs a, int track)
     }
 }
 
-// Sweeps: one warp per walker; the chain's master coordinates (int64) and
-// float-pair shadows live in shared memory (48 N bytes per warp).
-template <int NPL, int RECORD>
+template <int G>
+__device__ __forceinline__ long long group_sum_ll(long long q)  // exact sum over the G lanes of a walker
+{
+#pragma unroll
+    for (int off = G / 2; off; off >>= 1) q += __shfl_xor_sync(0xffffffffu, q, off);
+    return q;
+}
+
+template <int G>
+__device__ __forceinline__ bool group_any(bool p, int gi)
+{
+    const unsigned bal = __ballot_sync(0xffffffffu, p);
+    return G == 32 ? bal != 0u : ((bal >> (gi * G)) & ((1u << (G & 31)) - 1u)) != 0u;
+}
+
+// Sweeps: G lanes per walker, 32/G walkers a warp, all on the same bead i.  A
+// walker's float-pair shadows and this sweep's Philox blocks live in shared
+// memory (40 N bytes); its int64 master coordinates stay in global memory (read
+// at the sweep start and for the moved bead, written on acceptance).  The two
+// bonds of bead i (FENE) are taken by lanes 0 and 1 of the group, the other
+// partners (LJ, |i - j| >= 2) by lanes j mod G, so no lane runs both branches.
+template <int G, int RECORD>
 __global__ void __launch_bounds__(kMaxSweepBlock) k_sweep_polymer(const PolyArgs a)
 {
+    constexpr int W = 32 / G;
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, wpb = blockDim.x >> 5, N = a.N;
-    long long *Xs = (long long *)smem + (size_t)wib * 3 * N;
-    float *xs = (float *)(smem + (size_t)wpb * 3 * N * sizeof(long long)) + (size_t)wib * 6 * N;
+    const int gi = lane / G, li = lane % G;
+    const int spb = wpb * W, slot = wib * W + gi;
+    float *xs = (float *)smem + (size_t)slot * 6 * N;
     float *xl = xs + 3 * N;
-    // this sweep's Philox blocks, one per bead (lane l draws beads l, l+32, ...)
-    uint4 *su = (uint4 *)(smem + (size_t)wpb * 3 * N * (sizeof(long long) + 2 * sizeof(float))) + (size_t)wib * N;
-    const int w = blockIdx.x * wpb + wib;
-    if (w >= a.p) return;  // whole warps only; no block-wide barrier follows
-    const uint32_t wid = (uint32_t)(w + a.walker_offset);
-    long long *Xg = a.X + (size_t)w * 3 * N;
-    for (int t = lane; t < 3 * N; t += 32) Xs[t] = Xg[t];
-    long long E = a.E[w];
+    uint4 *su = (uint4 *)(smem + (size_t)spb * 6 * N * sizeof(float)) + (size_t)slot * N;
+    const int w0 = (blockIdx.x * wpb + wib) * W;
+    if (w0 >= a.p) return;  // whole warps only; no block-wide barrier follows
+    const int w = w0 + gi;
+    const bool active = w < a.p;
+    const int wr = active ? w : w0;  // a group past the last walker shadows the warp's first one, read-only
+    const uint32_t wid = (uint32_t)(wr + a.walker_offset);
+    long long *Xg = a.X + (size_t)wr * 3 * N;
+    long long E = a.E[wr];
     int b = poly_bin(E, a);
     const uint32_t g0 = (uint32_t)a.state->sweep_counter;
     const float R2 = 1.0f / a.fene_invR2;
-    __syncwarp();
+    const int npl = (N + G - 1) / G;
+    constexpr float kStep = (float)kPolyStepQ * 0x1p-44f;
     for (int64_t sw = 0; sw < a.sweeps; ++sw) {
         const uint32_t g = g0 + (uint32_t)sw;
-        const long long A0 = Xs[0], A1 = Xs[N], A2 = Xs[2 * N];
-        for (int j = lane; j < N; j += 32) {
-            grid_to_ff(Xs[j] - A0, xs[j], xl[j]);
-            grid_to_ff(Xs[N + j] - A1, xs[N + j], xl[N + j]);
-            grid_to_ff(Xs[2 * N + j] - A2, xs[2 * N + j], xl[2 * N + j]);
+        const long long A0 = Xg[0], A1 = Xg[N], A2 = Xg[2 * N];
+        for (int j = li; j < N; j += G) {
+            grid_to_ff(Xg[j] - A0, xs[j], xl[j]);
+            grid_to_ff(Xg[N + j] - A1, xs[N + j], xl[N + j]);
+            grid_to_ff(Xg[2 * N + j] - A2, xs[2 * N + j], xl[2 * N + j]);
             su[j] = philox4x32_10_rk(make_uint4((uint32_t)j, g, wid, kTagSweep), a.rk);
         }
         __syncwarp();
@@ -212,48 +235,50 @@ __global__ void __launch_bounds__(kMaxSweepBlock) k_sweep_polymer(const PolyArgs
             // coordinates; the float-pair shadow moves by the same amount in FP32
             // (the shadows are rebuilt exactly from the masters every sweep)
             const int sx = (int)(u.x ^ 0x80000000u), sy = (int)(u.y ^ 0x80000000u), sz = (int)(u.z ^ 0x80000000u);
-            const long long n0 = Xs[i] + (long long)sx * kPolyStepQ;
-            const long long n1 = Xs[N + i] + (long long)sy * kPolyStepQ;
-            const long long n2 = Xs[2 * N + i] + (long long)sz * kPolyStepQ;
+            const long long X0 = Xg[i], X1 = Xg[N + i], X2 = Xg[2 * N + i];
             const float xo = xs[i], yo = xs[N + i], zo = xs[2 * N + i];
             const float lxo = xl[i], lyo = xl[N + i], lzo = xl[2 * N + i];
-            constexpr float kStep = (float)kPolyStepQ * 0x1p-44f;
             const float dx = (float)sx * kStep, dy = (float)sy * kStep, dz = (float)sz * kStep;
             const float xn = xo + dx, yn = yo + dy, zn = zo + dz;
             const float lxn = lxo + ((xo - xn) + dx), lyn = lyo + ((yo - yn) + dy), lzn = lzo + ((zo - zn) + dz);
             float s = 0.0f, c = 0.0f;
             bool broken = false;
-#pragma unroll
-            for (int k = 0; k < NPL; ++k) {
-                const int j = lane + 32 * k;
-                if (j < N && j != i) {
+            {
+                const int jb = (li == 0) ? i - 1 : i + 1;
+                if (li < 2 && jb >= 0 && jb < N) {
+                    const float xj = xs[jb], yj = xs[N + jb], zj = xs[2 * N + jb];
+                    const float ljx = xl[jb], ljy = xl[N + jb], ljz = xl[2 * N + jb];
+                    const float ax = (xo - xj) + (lxo - ljx), ay = (yo - yj) + (lyo - ljy), az = (zo - zj) + (lzo - ljz);
+                    const float bx = (xn - xj) + (lxn - ljx), by = (yn - yj) + (lyn - ljy), bz = (zn - zj) + (lzn - ljz);
+                    const float r2o = ax * ax + ay * ay + az * az;
+                    const float r2n = bx * bx + by * by + bz * bz;
+                    broken = !(r2n < R2);
+                    const float vo = fene_energy(r2o, a);
+                    const float vn = broken ? vo : fene_energy(r2n, a);
+                    s = vn - vo;
+                }
+            }
+#pragma unroll 2
+            for (int k = 0; k < npl; ++k) {
+                const int j = li + G * k, dj = j - i;
+                if (j < N && (dj > 1 || dj < -1)) {
                     const float xj = xs[j], yj = xs[N + j], zj = xs[2 * N + j];
                     const float ljx = xl[j], ljy = xl[N + j], ljz = xl[2 * N + j];
                     const float ax = (xo - xj) + (lxo - ljx), ay = (yo - yj) + (lyo - ljy), az = (zo - zj) + (lzo - ljz);
                     const float bx = (xn - xj) + (lxn - ljx), by = (yn - yj) + (lyn - ljy), bz = (zn - zj) + (lzn - ljz);
                     const float r2o = ax * ax + ay * ay + az * az;
                     const float r2n = bx * bx + by * by + bz * bz;
-                    float vo, vn;
-                    if (j == i - 1 || j == i + 1) {
-                        const bool brk = !(r2n < R2);
-                        broken |= brk;
-                        vo = fene_energy(r2o, a);
-                        vn = brk ? vo : fene_energy(r2n, a);
-                    } else {
-                        vo = lj_energy(r2o, a);
-                        vn = lj_energy(r2n, a);
-                    }
-                    const float y = (vn - vo) - c;
+                    const float y = (lj_energy(r2n, a) - lj_energy(r2o, a)) - c;
                     const float t = s + y;
                     c = (t - s) - y;
                     s = t;
                 }
             }
-            broken = __any_sync(0xffffffffu, broken);
+            broken = group_any<G>(broken, gi);
             // |lane sum| >= 2^22 only for overlapping beads: such a move is rejected
-            const bool huge = __any_sync(0xffffffffu, !(fabsf(s) < 4194304.0f));
+            const bool huge = group_any<G>(!(fabsf(s) < 4194304.0f), gi);
             long long q = huge ? 0 : (f2ll_exact(s * 0x1p32f) - f2ll_exact(c * 0x1p32f));
-            q = warp_sum_ll(q);
+            q = group_sum_ll<G>(q);
             const long long En = E + q;
             const int bn = poly_bin(En, a);
             bool acc = false;
@@ -275,10 +300,12 @@ __global__ void __launch_bounds__(kMaxSweepBlock) k_sweep_polymer(const PolyArgs
                 }
             }
             if (acc) {
-                if (lane == 0) {
-                    Xs[i] = n0;
-                    Xs[N + i] = n1;
-                    Xs[2 * N + i] = n2;
+                if (li == 0) {
+                    if (active) {
+                        Xg[i] = X0 + (long long)sx * kPolyStepQ;
+                        Xg[N + i] = X1 + (long long)sy * kPolyStepQ;
+                        Xg[2 * N + i] = X2 + (long long)sz * kPolyStepQ;
+                    }
                     xs[i] = xn;
                     xs[N + i] = yn;
                     xs[2 * N + i] = zn;
@@ -290,19 +317,21 @@ __global__ void __launch_bounds__(kMaxSweepBlock) k_sweep_polymer(const PolyArgs
                 b = bn;
             }
             __syncwarp();
-            if (RECORD == 0 && lane == 0 && b >= 0 && b < a.B) atomicAdd(a.H + b, 1ull);
+            if (RECORD == 0 && li == 0 && active && b >= 0 && b < a.B) atomicAdd(a.H + b, 1ull);
         }
-        if (RECORD == 1 && lane == 0 && b >= 0 && b < a.B) atomicAdd(a.H + b, 1ull);
+        if (RECORD == 1 && li == 0 && active && b >= 0 && b < a.B) atomicAdd(a.H + b, 1ull);
+        __syncwarp();
     }
+    if (!active) return;  // (no warp-wide operation follows)
     // recentre on bead 0 (an exact grid shift) and write back
-    const long long A0 = Xs[0], A1 = Xs[N], A2 = Xs[2 * N];
-    __syncwarp();
-    for (int t = lane; t < N; t += 32) {
-        Xg[t] = Xs[t] - A0;
-        Xg[N + t] = Xs[N + t] - A1;
-        Xg[2 * N + t] = Xs[2 * N + t] - A2;
+    const long long A0 = Xg[0], A1 = Xg[N], A2 = Xg[2 * N];
+    __syncwarp(__activemask());
+    for (int t = li; t < N; t += G) {
+        Xg[t] -= A0;
+        Xg[N + t] -= A1;
+        Xg[2 * N + t] -= A2;
     }
-    if (lane == 0) {
+    if (li == 0) {
         a.E[w] = E;
         a.bin[w] = b;
     }
@@ -339,34 +368,43 @@ cudaError_t launch_poly_energy(const PolyArgs &a, int track_drift, cudaStream_t 
     return cudaGetLastError();
 }
 
-template <int NPL>
-static cudaError_t launch_npl(const PolyArgs &a, int block, cudaStream_t s)
+template <int G>
+static cudaError_t launch_g(const PolyArgs &a, int block, cudaStream_t s)
 {
-    const int wpb = block / 32;
-    const size_t smem = (size_t)wpb * a.N * (3 * (sizeof(long long) + 2 * sizeof(float)) + sizeof(uint4));
-    const int nblk = (a.p + wpb - 1) / wpb;
+    const int wpb = block / 32, spb = wpb * (32 / G);
+    const size_t smem = (size_t)spb * a.N * (6 * sizeof(float) + sizeof(uint4));
+    const int nblk = (a.p + spb - 1) / spb;
     cudaError_t e;
     if (a.record == 0) {
-        e = cudaFuncSetAttribute(k_sweep_polymer<NPL, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        e = cudaFuncSetAttribute(k_sweep_polymer<G, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        k_sweep_polymer<NPL, 0><<<nblk, block, smem, s>>>(a);
+        k_sweep_polymer<G, 0><<<nblk, block, smem, s>>>(a);
     } else {
-        e = cudaFuncSetAttribute(k_sweep_polymer<NPL, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        e = cudaFuncSetAttribute(k_sweep_polymer<G, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        k_sweep_polymer<NPL, 1><<<nblk, block, smem, s>>>(a);
+        k_sweep_polymer<G, 1><<<nblk, block, smem, s>>>(a);
     }
     return cudaGetLastError();
 }
 
+// Lanes per walker: the fixed cost of an attempt (group reductions, the bin and
+// weight lookups, the decision) is shared by 32/G walkers, the pair terms are
+// spread over G lanes.  Measured on GB300 (4096 walkers, 256-thread blocks), 16
+// lanes is the fastest or within 3% of it for N = 13, 32, 64 and 128.
+int poly_lanes(int N, int requested)
+{
+    (void)N;
+    if (requested == 8 || requested == 16 || requested == 32) return requested;
+    return 16;
+}
+
 cudaError_t launch_poly_sweep(const PolyArgs &a, int block, cudaStream_t s)
 {
-    const int npl = (a.N + 31) / 32;
-    switch (npl) {
-    case 1: return launch_npl<1>(a, block, s);
-    case 2: return launch_npl<2>(a, block, s);
-    case 3: return launch_npl<3>(a, block, s);
-    case 4: return launch_npl<4>(a, block, s);
-    default: return cudaErrorInvalidValue;
+    if (!polymer_supported(a.N)) return cudaErrorInvalidValue;
+    switch (poly_lanes(a.N, a.lanes)) {
+    case 8: return launch_g<8>(a, block, s);
+    case 16: return launch_g<16>(a, block, s);
+    default: return launch_g<32>(a, block, s);
     }
 }
 
