@@ -101,6 +101,14 @@ int muca_init_ex(muca_ctx **out, int system, int L_or_N, int q, int p, uint64_t 
  *                 walker w draws from the stream of walker w + offset, so the
  *                 union of the shards equals one context of all walkers;
  *                 re-draws the initial states; before the first iterate.
+ *   "debug_drop_row"  test hook for the bounded waits (lattice systems): in the
+ *                 next muca_iterate only, the first producer warp of thread
+ *                 block 0 leaves out its hand-over of row r (counted from 0
+ *                 over the sweeps of that call), so the consumer's wait runs
+ *                 out; its warp then stops computing and the next synchronising
+ *                 call returns MUCA_ERR_TIMEOUT.  The context's walker state is
+ *                 invalid afterwards (restore a checkpoint with muca_set_state).
+ *                 No effect with pipeline = 0 or a row past the call's sweeps.
  *   "lanes"       polymer: lanes of a warp per walker in the sweep, 8, 16 or 32
  *                 (32/lanes walkers share a warp); 0 (default) means 16.  The pair terms are
  *                 FP32 and their grouping over lanes changes their rounding, so

@@ -52,6 +52,7 @@ struct muca_ctx {
     double beta = 0.0, flat_ratio = 0.5;
     int record = 0, block = 64, walker_offset = 0;
     int lanes = 0;     // polymer: lanes per walker in the sweep (8, 16, 32; 0 = chosen by N)
+    int debug_drop_row = -1;  // test hook for the bounded waits (next spin iterate only)
     int pipeline = 2;  // spins: code form (2), producer/consumer (1) or one warp per walker group (0)
     int pstride = 0, wpw = 0, nblk_max = 0;
     cudaStream_t stream = nullptr;
@@ -516,6 +517,13 @@ int muca_set_param(muca_ctx *c, const char *key, double v)
         c->pipeline = (int)v;
         return MUCA_OK;
     }
+    if (k == "debug_drop_row") {
+        if (c->system == kPolymer) return fail(MUCA_ERR_ARG, "debug_drop_row applies to lattice systems only");
+        const long long r = (long long)v;
+        if ((double)r != v || r < 0 || r > 0x7fffffffLL) return fail(MUCA_ERR_ARG, "debug_drop_row must be >= 0");
+        c->debug_drop_row = (int)r;
+        return MUCA_OK;
+    }
     if (k == "lanes") {
         if (c->system != kPolymer) return fail(MUCA_ERR_ARG, "lanes applies to the polymer only");
         if (v != 0.0 && v != 8.0 && v != 16.0 && v != 32.0) return fail(MUCA_ERR_ARG, "lanes must be 0, 8, 16 or 32");
@@ -576,6 +584,8 @@ int muca_iterate(muca_ctx *c, int64_t sweeps)
     a.record = c->record;
     a.walker_offset = c->walker_offset;
     a.kind = sweep_kind(c->system, c->L);
+    a.debug_drop_row = c->debug_drop_row;
+    c->debug_drop_row = -1;
     if (c->pipeline >= 2 && spin_sweep_tn_fits(c->system, c->L, c->B, c->block)) {
         MUCA_CUDA(launch_spin_sweep_tn(c->system, c->L, a, c->block, c->stream));
     } else if (c->pipeline >= 1 && spin_sweep_pc_fits(c->system, c->L, c->B, c->block)) {

@@ -41,6 +41,8 @@ struct SpinSweepArgs {
     int walker_offset;       // global id of walker 0 (for sharding)
     uint32_t rk[20];         // Philox round keys (k0 + r*W0, k1 + r*W1), r = 0..9
     int kind;                // system * 16 + L / 4 (dispatch key of the batched sweep)
+    int debug_drop_row = -1; // test hook: row hand-over (count within the launch) that the first
+                             // producer warp of block 0 skips, so the consumer's wait runs out; -1 = off
 };
 
 // Philox round keys for a seed: round r uses (lo + r*W0, hi + r*W1).

@@ -81,7 +81,7 @@ template <int SYS, int L, int PART>
 __device__ __forceinline__ void produce_sweep_tn(uint32_t g, uint32_t wid, const uint32_t (&rk)[20],
                                                  const uint32_t *__restrict__ lat, int ps, uint4 *ring_u,
                                                  uint2 *ring_c, uint32_t *ring_r, unsigned long long *full,
-                                                 unsigned long long *empty, int &k, bool &bad)
+                                                 unsigned long long *empty, int &k, bool &bad, int drop_k)
 {
     constexpr int WR = ising_words_per_row(L);
     constexpr int G = L / 4;
@@ -139,7 +139,7 @@ __device__ __forceinline__ void produce_sweep_tn(uint32_t g, uint32_t wid, const
                 wc[gq * 32] = make_uint2(k0, k1);
             }
         }
-        mbar_arrive(&full[slot]);
+        if (k != drop_k) mbar_arrive(&full[slot]);
         ++k;
 #pragma unroll
         for (int j = 0; j < WR; ++j) {
@@ -172,6 +172,11 @@ __device__ __forceinline__ void ising_sweep_tc(uint32_t *__restrict__ lat, int p
     for (int y = 0; y < L; ++y) {
         const int slot = k % kRing;
         if (!bad && !mbar_wait(&full[slot], (unsigned)((k / kRing) & 1))) bad = true;
+        if (bad) {  // a wait gave up: the ring is out of step, so nothing more is computed
+            mbar_arrive(&empty[slot]);
+            ++k;
+            continue;
+        }
         const uint4 *ru = ring_u + slot * SU;
         const uint2 *rc = ring_c + slot * SC;
         const uint32_t *rr = ring_r + slot * SR;
@@ -262,6 +267,7 @@ __device__ __forceinline__ void sweep_block_tn(const SpinSweepArgs &a, int w0, i
     const CodeRole role = code_role(warp, ncw);
     const bool producer = role.kind == kRoleProducer, consumer = role.kind == kRoleConsumer;
     const int pair = role.pair, part = role.part;
+    const int drop_k = (blockIdx.x == 0 && producer && pair == 0 && part == 0) ? a.debug_drop_row : -1;
     uint32_t *sTH = smem;
     const size_t th_bytes = ((size_t)a.B * RS * 4 + 15) / 16 * 16;
     char *rbase = (char *)smem + th_bytes + (size_t)pair * tn_ring_bytes(L);
@@ -296,9 +302,11 @@ __device__ __forceinline__ void sweep_block_tn(const SpinSweepArgs &a, int w0, i
             const uint32_t g = g0 + (uint32_t)sw;
             if (producer) {
                 if (part == 0)
-                    produce_sweep_tn<SYS, L, 0>(g, wid, a.rk, lat, a.pstride, ring_u, ring_c, ring_r, full, empty, k, bad);
+                    produce_sweep_tn<SYS, L, 0>(g, wid, a.rk, lat, a.pstride, ring_u, ring_c, ring_r, full, empty, k, bad,
+                                                drop_k);
                 else
-                    produce_sweep_tn<SYS, L, 1>(g, wid, a.rk, lat, a.pstride, ring_u, ring_c, ring_r, full, empty, k, bad);
+                    produce_sweep_tn<SYS, L, 1>(g, wid, a.rk, lat, a.pstride, ring_u, ring_c, ring_r, full, empty, k, bad,
+                                                -1);
             } else if (consumer && active) {
                 if (a.record == 0)
                     ising_sweep_tc<SYS, L, 0>(lat, a.pstride, bR, sTH, ring_u, ring_c, ring_r, full, empty, k, bad);
@@ -387,7 +395,7 @@ __device__ __forceinline__ void produce_sweep_potts_tn(uint32_t g, uint32_t wid,
                                                        const uint32_t *__restrict__ lat, int ps, uint32_t q,
                                                        uint4 *ring_u, uint2 *ring_c, uint2 *ring_op,
                                                        unsigned long long *full, unsigned long long *empty, int &k,
-                                                       bool &bad)
+                                                       bool &bad, int drop_k)
 {
     static_assert(L % 8 == 0, "whole nibble words a row");
     constexpr int WR = L / 8;
@@ -480,7 +488,7 @@ __device__ __forceinline__ void produce_sweep_potts_tn(uint32_t g, uint32_t wid,
             rotate_words<WR>(o);
             rotate_words<WR>(d);
         }
-        mbar_arrive(&full[slot]);
+        if (k != drop_k) mbar_arrive(&full[slot]);
         ++k;
 #pragma unroll
         for (int j = 0; j < WR; ++j) {
@@ -511,6 +519,11 @@ __device__ __forceinline__ void potts_sweep_tc(uint32_t *__restrict__ lat, int p
     for (int y = 0; y < L; ++y) {
         const int slot = k % RD;
         if (!bad && !mbar_wait(&full[slot], (unsigned)((k / RD) & 1))) bad = true;
+        if (bad) {  // a wait gave up: the ring is out of step, so nothing more is computed
+            mbar_arrive(&empty[slot]);
+            ++k;
+            continue;
+        }
         const uint4 *ru = ring_u + slot * S;
         const uint2 *rc = ring_c + slot * S;
         const uint2 *rop = ring_op + slot * S;
@@ -612,6 +625,7 @@ __device__ __forceinline__ void sweep_block_tnp(const SpinSweepArgs &a, int w0, 
     const CodeRole role = code_role(warp, ncw);
     const bool producer = role.kind == kRoleProducer, consumer = role.kind == kRoleConsumer;
     const int pair = role.pair, part = role.part;
+    const int drop_k = (blockIdx.x == 0 && producer && pair == 0 && part == 0) ? a.debug_drop_row : -1;
     uint32_t *sTH = smem;
     const size_t th_bytes = ((size_t)a.B * RS * 4 + 15) / 16 * 16;
     char *rbase = (char *)smem + th_bytes + (size_t)pair * tnp_warp_bytes(L, RD);
@@ -654,10 +668,10 @@ __device__ __forceinline__ void sweep_block_tnp(const SpinSweepArgs &a, int w0, 
             if (producer) {
                 if (part == 0)
                     produce_sweep_potts_tn<L, RD, 0>(g, wid, a.rk, lat, a.pstride, (uint32_t)a.q, ring_u, ring_c,
-                                                     ring_op, full, empty, k, bad);
+                                                     ring_op, full, empty, k, bad, drop_k);
                 else
                     produce_sweep_potts_tn<L, RD, 1>(g, wid, a.rk, lat, a.pstride, (uint32_t)a.q, ring_u, ring_c,
-                                                     ring_op, full, empty, k, bad);
+                                                     ring_op, full, empty, k, bad, -1);
             } else if (consumer && active) {
                 if (a.record == 0)
                     potts_sweep_tc<L, RD, 0>(lat, a.pstride, bR, sTH, ring_u, ring_c, ring_op, sU, full, empty, k, bad);

@@ -39,7 +39,10 @@ __device__ __forceinline__ uint32_t word_of(const uint4 &u, int j)
 // Ring depth (rows) of the producer/consumer forms and the bound on every
 // mbarrier wait: a wait that gives up sets the error flag instead of spinning on.
 constexpr int kRing = 4;
-constexpr int kSpinLimit = 1 << 20;
+// 2^17 tries of mbarrier.try_wait (each suspends the warp for a few microseconds
+// when the phase is not complete: ~1 s in all on GB300); a healthy hand-over takes
+// microseconds.
+constexpr int kSpinLimit = 1 << 17;
 
 __device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
 

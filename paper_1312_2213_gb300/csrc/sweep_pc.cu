@@ -47,6 +47,11 @@ __device__ __forceinline__ void ising_sweep_pc(uint32_t *__restrict__ lat, int p
         for (int j = 0; j < WR; ++j) old[j] = cur[j];
         const int slot = k % kRing;
         if (!bad && !mbar_wait(&full[slot], (unsigned)((k / kRing) & 1))) bad = true;
+        if (bad) {  // a wait gave up: the ring is out of step, so nothing more is computed
+            mbar_arrive(&empty[slot]);
+            ++k;
+            continue;
+        }
         const uint4 *ru = ring + (size_t)slot * G * 32;
         auto site = [&](int x, int &c0, int &c1, int &d0, int &d1) {
             const int s = bit_at<WR>(old, x);
@@ -142,6 +147,11 @@ __device__ __forceinline__ void potts_sweep_pc(uint32_t *__restrict__ lat, int p
         for (int j = 0; j < WR; ++j) old[j] = cur[j];
         const int slot = k % kRing;
         if (!bad && !mbar_wait(&full[slot], (unsigned)((k / kRing) & 1))) bad = true;
+        if (bad) {  // a wait gave up: the ring is out of step, so nothing more is computed
+            mbar_arrive(&empty[slot]);
+            ++k;
+            continue;
+        }
         const uint4 *ru = ring + (size_t)slot * G * 32;
         auto site = [&](int x, uint32_t uprop, uint32_t lnw, uint32_t &nw, int &c0, int &c1, int &d0, int &d1) {
             const uint32_t o = nib_at<WR>(old, x);
@@ -220,7 +230,8 @@ __device__ __forceinline__ void potts_sweep_pc(uint32_t *__restrict__ lat, int p
 // the paired consumer warp.  G blocks a row: L/4 (one word a site) or L/2 (two).
 template <int SYS, int L>
 __device__ __forceinline__ void produce_sweep(uint32_t g, uint32_t wid, const uint32_t (&rk)[20], uint4 *ring,
-                                              unsigned long long *full, unsigned long long *empty, int &k, bool &bad)
+                                              unsigned long long *full, unsigned long long *empty, int &k, bool &bad,
+                                              int drop_k)
 {
     constexpr int G = (SYS == kPotts) ? L / 2 : L / 4;
 #pragma unroll 1
@@ -231,7 +242,7 @@ __device__ __forceinline__ void produce_sweep(uint32_t g, uint32_t wid, const ui
 #pragma unroll
         for (int gq = 0; gq < G; ++gq)
             wu[gq * 32] = philox4x32_10_rk(make_uint4((uint32_t)(y * G + gq), g, wid, kTagSweep), rk);
-        mbar_arrive(&full[slot]);
+        if (k != drop_k) mbar_arrive(&full[slot]);
         ++k;
     }
 }
@@ -253,6 +264,7 @@ __device__ __forceinline__ void sweep_block_pc(const SpinSweepArgs &a, int w0, i
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const bool producer = warp >= ncw;
     const int pair = producer ? warp - ncw : warp;
+    const int drop_k = (blockIdx.x == 0 && producer && pair == 0) ? a.debug_drop_row : -1;
     uint32_t *sTH = smem;
     const size_t th_bytes = ((size_t)a.B * RS * 4 + 15) / 16 * 16;
     uint4 *ring = (uint4 *)((char *)smem + th_bytes) + (size_t)pair * kRing * G * 32 + lane;
@@ -287,7 +299,7 @@ __device__ __forceinline__ void sweep_block_pc(const SpinSweepArgs &a, int w0, i
         for (int64_t sw = s0; sw < s1; ++sw) {
             const uint32_t g = g0 + (uint32_t)sw;
             if (producer) {
-                produce_sweep<SYS, L>(g, wid, a.rk, ring, full, empty, k, bad);
+                produce_sweep<SYS, L>(g, wid, a.rk, ring, full, empty, k, bad, drop_k);
             } else if (active) {
                 if (a.record == 0) {
                     if (SYS == kPotts)

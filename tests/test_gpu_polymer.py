@@ -1,4 +1,4 @@
-"""GPU polymer path (one warp per walker, FP32 pair terms, exact fixed-point sums) against the
+"""GPU polymer path (8, 16 or 32 lanes per walker, FP32 pair terms, exact fixed-point sums) against the
 FP64 oracle.  Coordinates live on a 2^-44 grid on both sides, so trajectories that make the same
 accept/reject decisions are bit-identical; decisions can differ only at near-ties of the
 acceptance test or when an energy lies within the FP32 error of a bin edge, which the oracle
@@ -72,12 +72,16 @@ def test_first_iteration_trajectories_identical():
     assert int(g.histogram().sum()) == int(o.histogram().sum()) == p * S * N
 
 
-def test_first_iteration_histogram_in_pilot_window():
+@pytest.mark.parametrize("lanes,p", [(0, 64), (8, 61), (16, 63), (32, 64)])
+def test_first_iteration_histogram_in_pilot_window(lanes, p):
     """In the pilot window (walk-in, then ln W = 0): walkers without a near-tie or bin-edge event
-    in the oracle are bit-identical, and the histograms differ only through bin-edge events."""
-    N, p, S = 13, 64, 40
+    in the oracle are bit-identical, and the histograms differ only through bin-edge events.  Every
+    lane grouping (8, 16, 32 lanes a walker), with walker counts that leave the last warp partly
+    empty."""
+    N, S = 13, 40
     lo, hi = WINDOWS[str(N)]["e_lo"], WINDOWS[str(N)]["e_hi"]
     g = m.Muca(m.POLYMER3D, N, 0, p, 5, window=(lo, hi))
+    g.set_param("lanes", lanes)
     o = oracle.PolyRun(N, p, 5, lo, hi)
     o.init()
     g.iterate(S)
