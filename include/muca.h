@@ -101,6 +101,13 @@ int muca_init_ex(muca_ctx **out, int system, int L_or_N, int q, int p, uint64_t 
  *                 walker w draws from the stream of walker w + offset, so the
  *                 union of the shards equals one context of all walkers;
  *                 re-draws the initial states; before the first iterate.
+ *   "observables" Ising, before the first iterate: 1 records per-sweep sums of
+ *                 |M| and M^2 per energy bin (see muca_get_observables).
+ *   "recursion"   lattice systems, before the first iterate: the weight update,
+ *                 0 (default) = accumulated statistics in log form (the paper's
+ *                 method), 1 = the paper's simple rule W(n+1)(E) = W(n)(E)/H(n)(E)
+ *                 in log form over the reachable bins (an unvisited bin keeps
+ *                 its weight, ln W(r_0) = 0).
  *   "debug_drop_row"  test hook for the bounded waits (lattice systems): in the
  *                 next muca_iterate only, the first producer warp of thread
  *                 block 0 leaves out its hand-over of row r (counted from 0
@@ -160,6 +167,17 @@ int muca_get_flatness(muca_ctx *ctx, double host_stats[3]);
  *   susceptibility per site, ln P(M=0) - ln P(M=N)}.
  * host_lnP (nullable, B doubles) receives ln P(b). */
 int muca_get_reweight(muca_ctx *ctx, double beta, double host_out[4], double *host_lnP);
+
+/* Observables (Ising with "observables" = 1; the paper's Eq. (2) for an
+ * observable O that is not a function of the energy): after every sweep each
+ * walker adds one sample, |M| and M^2 to three uint64 sums of its current
+ * energy bin; each muca_merge_and_update closes the sums with the weights they
+ * were sampled with.  host_out = {<|M|>/N, <M^2>/N^2, beta N (<M^2>/N^2 -
+ * (<|M|>/N)^2)} at beta (NaN if no samples); host_sums (nullable, 3*nbins
+ * uint64: samples, sum |M|, sum M^2 per bin) receives the sums.
+ * Not recorded by muca_iterate_noalloc or in batches.
+ * Errors: MUCA_ERR_STATE if observables are off, MUCA_ERR_ARG on bad lengths. */
+int muca_get_observables(muca_ctx *ctx, double beta, double host_out[3], uint64_t *host_sums, int nbins);
 
 /* Checkpoint: the complete state (walkers, weights, recursion state, counters).
  * Call with host_buf == NULL to get the size in *bytes.  muca_set_state

@@ -59,6 +59,12 @@ def lib():
             for name in ("orc_num_bins", "orc_num_cols", "orc_num_sites"):
                 getattr(L, name).argtypes = [ctypes.c_void_p]
                 getattr(L, name).restype = ctypes.c_int
+            L.orc_set_recursion.argtypes = [ctypes.c_void_p, ctypes.c_int]
+            L.orc_set_observables.argtypes = [ctypes.c_void_p, ctypes.c_int]
+            L.orc_get_observables.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
+            L.orc_reweight_obs.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                                           ctypes.c_double, ctypes.c_void_p]
+            L.orc_reweight_observables.argtypes = [ctypes.c_void_p, ctypes.c_double, ctypes.c_void_p]
             L.orc_iterate.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int]
             L.orc_iterate_range.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_int,
                                             ctypes.c_int]
@@ -139,11 +145,14 @@ def det_log(x: float) -> float:
 class Run:
     """One oracle MUCA/MUMA run: p walkers sharing one ln W (Fig. 1 scheme)."""
 
-    def __init__(self, system: int, L: int, q: int, p: int, seed: int, beta: float = 0.0, record: int = 0):
+    def __init__(self, system: int, L: int, q: int, p: int, seed: int, beta: float = 0.0, record: int = 0,
+                 recursion: int = 0, observables: int = 0):
         self._lib = lib()
         self.h = self._lib.orc_create(system, L, q, p, seed, beta, record)
         if not self.h:
             raise ValueError("oracle: unsupported configuration")
+        self._lib.orc_set_recursion(self.h, recursion)
+        self._lib.orc_set_observables(self.h, observables)
         self.system, self.L, self.q, self.p, self.seed = system, L, q, p, seed
         self.B = self._lib.orc_num_bins(self.h)
         self.K = self._lib.orc_num_cols(self.h)
@@ -168,6 +177,17 @@ class Run:
 
     def update(self):
         self._lib.orc_update(self.h)
+
+    def observable_sums(self) -> np.ndarray:
+        """Per-bin sums (samples, |M|, M^2) of the last update, shape (B, 3)."""
+        a = np.zeros(3 * self.B, dtype=np.uint64)
+        self._lib.orc_get_observables(self.h, _ptr(a))
+        return a.reshape(self.B, 3)
+
+    def reweight_observables(self, beta: float) -> np.ndarray:
+        out = np.zeros(3, dtype=np.float64)
+        self._lib.orc_reweight_observables(self.h, beta, _ptr(out))
+        return out
 
     def set_open_histogram(self, H):
         H = np.ascontiguousarray(np.asarray(H, dtype=np.uint64))
@@ -216,6 +236,17 @@ class Run:
 
     def sweep_counter(self) -> int:
         return int(self._lib.orc_get_sweep_counter(self.h))
+
+
+def reweight_obs(N: int, sums: np.ndarray, lnW_sampled: np.ndarray, beta: float) -> np.ndarray:
+    """Eq. (2) on per-bin sums (samples, |M|, M^2) of an Ising run (reading R9)."""
+    sums = np.ascontiguousarray(np.asarray(sums, dtype=np.uint64).reshape(-1))
+    lw = np.ascontiguousarray(np.asarray(lnW_sampled, dtype=np.float64))
+    B = lw.size
+    assert sums.size == 3 * B
+    out = np.zeros(3, dtype=np.float64)
+    lib().orc_reweight_obs(B, N, _ptr(sums), _ptr(lw), beta, _ptr(out))
+    return out
 
 
 def bruteforce_ising(L: int) -> np.ndarray:

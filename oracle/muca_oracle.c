@@ -36,6 +36,14 @@
  *         lnR_k += kappa * (ln h0 - ln h1);
  *      then ln W(r_0) = 0, ln W(r_{k+1}) = ln W(r_k) + lnR_k summed in order.
  *      The first iteration with data has kappa = 1: the plain W/H update.
+ *   R5' plain update (selectable, recursion = 1), the paper's simple rule
+ *      W(n+1)(E) = W(n)(E) / H(n)(E) in log form over the reachable bins:
+ *         x_k = ln W(r_k) - ln max(H(r_k), 1),  ln W(r_k) <- x_k - x_0,
+ *      so an unvisited bin keeps its weight (H = 0 is taken as H = 1) and
+ *      ln W(r_0) = 0 as in R5.
+ *   R9 observables (Ising, optional): after each sweep every walker adds 1,
+ *      |M| and M^2 (M = sum of its spins) to three sums of its current bin;
+ *      Eq. (2) then reweights them with the weights they were sampled with.
  *   R6 reachable bins (even L >= 4, periodic): Ising has no state with
  *      exactly 2 or 2N-2 broken bonds; Potts (q >= 3) none with 1, 2, 3 or 5
  *      broken bonds; q = 2 Potts follows Ising.  Unreachable bins get
@@ -174,6 +182,9 @@ struct orc_run {
     uint64_t seed;
     double beta;
     int record;
+    int recursion; /* 0: R5 accumulated statistics, 1: R5' plain W/H */
+    int observables;            /* R9 on/off (Ising) */
+    uint64_t *O_open, *O_last;  /* 3 per bin: samples, sum |M|, sum M^2 */
     int64_t sweep_counter;
     int8_t *spin;       /* p*N: Ising/MUMA +-1, Potts 0..q-1 */
     int32_t *bin;       /* p: current bin of each walker */
@@ -246,6 +257,8 @@ orc_run *orc_create(int system, int L, int q, int p, uint64_t seed, double beta,
     r->lnR = (double *)calloc((size_t)r->B, sizeof(double));
     r->H_open = (uint64_t *)calloc((size_t)r->B, sizeof(uint64_t));
     r->H_last = (uint64_t *)calloc((size_t)r->B, sizeof(uint64_t));
+    r->O_open = (uint64_t *)calloc((size_t)r->B * 3, sizeof(uint64_t));
+    r->O_last = (uint64_t *)calloc((size_t)r->B * 3, sizeof(uint64_t));
     r->T = (uint32_t *)calloc((size_t)r->B * r->K, sizeof(uint32_t));
     orc_compute_reachable(r);
     return r;
@@ -257,6 +270,7 @@ void orc_free(orc_run *r)
     free(r->spin); free(r->bin); free(r->reach); free(r->rlist);
     free(r->lnW); free(r->lnW_sampled); free(r->G); free(r->lnR);
     free(r->H_open); free(r->H_last); free(r->T);
+    free(r->O_open); free(r->O_last);
     free(r);
 }
 
@@ -352,7 +366,7 @@ void orc_init(orc_run *r)
 }
 
 /* a2 + a3 for one walker: `sweeps` sweeps starting at global sweep g0. */
-static void orc_walker_sweeps(const orc_run *r, int w, int64_t g0, int64_t sweeps, uint64_t *hist)
+static void orc_walker_sweeps(const orc_run *r, int w, int64_t g0, int64_t sweeps, uint64_t *hist, uint64_t *obs)
 {
     const int L = r->L, N = r->N, K = r->K;
     int8_t *s = r->spin + (size_t)w * N;
@@ -413,6 +427,13 @@ static void orc_walker_sweeps(const orc_run *r, int w, int64_t g0, int64_t sweep
             if (r->record == 0) hist[b] += 1;
         }
         if (r->record == 1) hist[b] += 1;
+        if (obs) { /* R9 */
+            int64_t M = 0;
+            for (int i = 0; i < N; ++i) M += s[i];
+            obs[3 * (size_t)b] += 1;
+            obs[3 * (size_t)b + 1] += (uint64_t)(M < 0 ? -M : M);
+            obs[3 * (size_t)b + 2] += (uint64_t)(M * M);
+        }
     }
     r->bin[w] = b;
 }
@@ -421,13 +442,13 @@ typedef struct {
     const orc_run *r;
     int w0, w1;
     int64_t g0, sweeps;
-    uint64_t *hist;
+    uint64_t *hist, *obs;
 } orc_job;
 
 static void *orc_job_main(void *arg)
 {
     orc_job *j = (orc_job *)arg;
-    for (int w = j->w0; w < j->w1; ++w) orc_walker_sweeps(j->r, w, j->g0, j->sweeps, j->hist);
+    for (int w = j->w0; w < j->w1; ++w) orc_walker_sweeps(j->r, w, j->g0, j->sweeps, j->hist, j->obs);
     return NULL;
 }
 
@@ -448,6 +469,8 @@ void orc_iterate_range(orc_run *r, int64_t sweeps, int w0, int w1, int nthreads)
         jobs[t].g0 = r->sweep_counter;
         jobs[t].sweeps = sweeps;
         jobs[t].hist = (uint64_t *)calloc((size_t)r->B, sizeof(uint64_t));
+        jobs[t].obs = (r->observables && r->system == ORC_ISING) ? (uint64_t *)calloc((size_t)r->B * 3, sizeof(uint64_t))
+                                                                  : NULL;
     }
     if (nthreads == 1) {
         orc_job_main(&jobs[0]);
@@ -459,6 +482,10 @@ void orc_iterate_range(orc_run *r, int64_t sweeps, int w0, int w1, int nthreads)
     for (int t = 0; t < nthreads; ++t) {
         for (int b = 0; b < r->B; ++b) r->H_open[b] += jobs[t].hist[b];
         free(jobs[t].hist);
+        if (jobs[t].obs) {
+            for (size_t i = 0; i < (size_t)r->B * 3; ++i) r->O_open[i] += jobs[t].obs[i];
+            free(jobs[t].obs);
+        }
     }
     free(jobs);
     free(th);
@@ -475,11 +502,63 @@ void orc_iterate(orc_run *r, int64_t sweeps, int nthreads)
 void orc_set_open_histogram(orc_run *r, const uint64_t *H) { memcpy(r->H_open, H, sizeof(uint64_t) * r->B); }
 void orc_get_open_histogram(const orc_run *r, uint64_t *out) { memcpy(out, r->H_open, sizeof(uint64_t) * r->B); }
 
-/* a5 (reading R5) followed by a6. */
+void orc_set_recursion(orc_run *r, int mode) { r->recursion = mode; }
+void orc_set_observables(orc_run *r, int on) { r->observables = on; }
+void orc_get_observables(const orc_run *r, uint64_t *out) { memcpy(out, r->O_last, sizeof(uint64_t) * 3 * r->B); }
+
+/* Eq. (2) with per-bin sums (R9): <O>_beta = sum_b S_O(b) e^{-beta E_b} / W(b) over
+ * sum_b n(b) e^{-beta E_b} / W(b), W the weights the samples were taken with, E_b
+ * the Ising energy of bin b (4b - 2N).  out = {<|M|>/N, <M^2>/N^2, beta N
+ * (<M^2>/N^2 - (<|M|>/N)^2)}; NaN if no bin has samples. */
+void orc_reweight_obs(int B, int N, const uint64_t *sums, const double *lnW_sampled, double beta, double out[3])
+{
+    double m = -INFINITY;
+    for (int b = 0; b < B; ++b)
+        if (sums[3 * b] > 0) {
+            double x = -beta * (double)(4 * b - 2 * N) - lnW_sampled[b];
+            if (x > m) m = x;
+        }
+    if (m == -INFINITY) { out[0] = out[1] = out[2] = NAN; return; }
+    double z = 0.0, a1 = 0.0, a2 = 0.0;
+    for (int b = 0; b < B; ++b) {
+        if (sums[3 * b] == 0) continue;
+        double f = exp(-beta * (double)(4 * b - 2 * N) - lnW_sampled[b] - m);
+        z += f * (double)sums[3 * b];
+        a1 += f * (double)sums[3 * b + 1];
+        a2 += f * (double)sums[3 * b + 2];
+    }
+    out[0] = a1 / z / N;
+    out[1] = a2 / z / ((double)N * N);
+    out[2] = beta * N * (out[1] - out[0] * out[0]);
+}
+
+void orc_reweight_observables(const orc_run *r, double beta, double out[3])
+{
+    orc_reweight_obs(r->B, r->N, r->O_last, r->lnW_sampled, beta, out);
+}
+
+/* a5 (reading R5, or R5' when selected) followed by a6. */
 void orc_update(orc_run *r)
 {
     const int Kr = r->nreach;
     memcpy(r->lnW_sampled, r->lnW, sizeof(double) * r->B);
+    memcpy(r->O_last, r->O_open, sizeof(uint64_t) * 3 * r->B);
+    memset(r->O_open, 0, sizeof(uint64_t) * 3 * r->B);
+    if (r->recursion == 1) {
+        /* R5': x_k = ln W(r_k) - ln max(H(r_k), 1); ln W(r_k) = x_k - x_0 */
+        double x0 = 0.0;
+        for (int k = 0; k < Kr; ++k) {
+            uint64_t h = r->H_open[r->rlist[k]];
+            double lh = h > 0 ? orc_det_log((double)h) : 0.0;
+            double x = r->lnW_sampled[r->rlist[k]] - lh;
+            if (k == 0) x0 = x;
+            r->lnW[r->rlist[k]] = x - x0;
+        }
+        memcpy(r->H_last, r->H_open, sizeof(uint64_t) * r->B);
+        memset(r->H_open, 0, sizeof(uint64_t) * r->B);
+        orc_build_thresholds(r);
+        return;
+    }
     for (int k = 0; k + 1 < Kr; ++k) {
         uint64_t h0 = r->H_open[r->rlist[k]], h1 = r->H_open[r->rlist[k + 1]];
         if (h0 > 0 && h1 > 0) {

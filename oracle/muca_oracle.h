@@ -52,6 +52,14 @@ void orc_iterate_range(orc_run *r, int64_t sweeps, int w0, int w1, int nthreads)
 void orc_advance(orc_run *r, int64_t sweeps);
 /* a5+a6: merge -> accumulated-statistics recursion in log form -> new thresholds. */
 void orc_update(orc_run *r);
+/* Select the weight update: 0 = accumulated statistics (R5, default),
+ * 1 = the plain W/H rule (R5'). */
+void orc_set_recursion(orc_run *r, int mode);
+/* Observables (Ising, reading R9): per-sweep sums of 1, |M|, M^2 per bin. */
+void orc_set_observables(orc_run *r, int on);
+void orc_get_observables(const orc_run *r, uint64_t *out); /* 3*B, last update */
+void orc_reweight_obs(int B, int N, const uint64_t *sums, const double *lnW_sampled, double beta, double out[3]);
+void orc_reweight_observables(const orc_run *r, double beta, double out[3]);
 /* Replace the open histogram (for recursion tests on hand-made histograms). */
 void orc_set_open_histogram(orc_run *r, const uint64_t *H);
 void orc_get_open_histogram(const orc_run *r, uint64_t *out);

@@ -20,7 +20,8 @@ SYSTEM_NAMES = {ISING2D: "ising2d", POTTS2D: "potts2d", ISING2D_MUMA: "ising2d_m
 __all__ = ["Muca", "MucaError", "ISING2D", "POTTS2D", "ISING2D_MUMA", "POLYMER3D", "library_path", "load",
            "muca_init", "muca_init_ex", "muca_workspace_size", "muca_set_param", "muca_set_stream",
            "muca_iterate", "muca_merge_and_update", "muca_num_bins", "muca_get_lnW", "muca_get_lnW_sampled",
-           "muca_get_histogram", "muca_get_flatness", "muca_get_reweight", "muca_get_state", "muca_set_state",
+           "muca_get_histogram", "muca_get_flatness", "muca_get_reweight", "muca_get_observables",
+           "muca_get_state", "muca_set_state",
            "muca_get_spins", "muca_get_walker_bins", "muca_get_thresholds", "muca_get_sweep_counter",
            "muca_synchronize", "muca_free", "muca_last_error", "muca_det_math",
            "muca_iterate_noalloc", "muca_get_coords", "muca_get_drift", "muca_batch_create", "muca_batch_run", "muca_batch_free", "Batch"]
@@ -95,6 +96,12 @@ def muca_get_histogram(h, out: np.ndarray):
 
 def muca_get_flatness(h, out: np.ndarray):
     check(load().muca_get_flatness(h, _p(out)), "muca_get_flatness")
+
+
+def muca_get_observables(h, beta: float, out: np.ndarray, sums: np.ndarray | None = None):
+    n = 0 if sums is None else sums.size // 3
+    check(load().muca_get_observables(h, float(beta), _p(out), None if sums is None else _p(sums), n),
+          "muca_get_observables")
 
 
 def muca_get_reweight(h, beta: float, out: np.ndarray, lnP: np.ndarray | None = None):
@@ -288,6 +295,14 @@ class Muca:
         lnP = np.zeros(self.B, dtype=np.float64)
         muca_get_reweight(self.h, beta, out, lnP)
         return out, lnP
+
+    def observables(self, beta: float):
+        """Eq. (2) for |M| and M^2 (Ising with observables on): ({<|M|>/N, <M^2>/N^2, chi per
+        site}, per-bin sums of shape (B, 3))."""
+        out = np.zeros(3, dtype=np.float64)
+        sums = np.zeros(3 * self.B, dtype=np.uint64)
+        muca_get_observables(self.h, beta, out, sums)
+        return out, sums.reshape(self.B, 3)
 
     def spins(self) -> np.ndarray:
         a = np.zeros(self.p * self.N, dtype=np.int8)

@@ -41,7 +41,7 @@ constexpr size_t kAlign = 256;
 size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
 struct Layout {
-    size_t lat, bin, T, lnW, lnW_sampled, G, lnR, H, Hpart, rlist, reach, state, out, Eq, lnWq, total;
+    size_t lat, bin, T, lnW, lnW_sampled, G, lnR, H, Hpart, rlist, reach, state, out, Eq, lnWq, obs, total;
 };
 
 }  // namespace
@@ -53,6 +53,9 @@ struct muca_ctx {
     int record = 0, block = 64, walker_offset = 0;
     int lanes = 0;     // polymer: lanes per walker in the sweep (8, 16, 32; 0 = chosen by N)
     int debug_drop_row = -1;  // test hook for the bounded waits (next spin iterate only)
+    int recursion = 0;        // weight update: 0 accumulated statistics, 1 plain W/H
+    int observables = 0;      // Ising: per-sweep sums of 1, |M|, M^2 per bin
+    unsigned long long *obs = nullptr;  // [0, 3B): sums being filled, [3B, 6B): of the last update
     int pipeline = 2;  // spins: code form (2), producer/consumer (1) or one warp per walker group (0)
     int pstride = 0, wpw = 0, nblk_max = 0;
     cudaStream_t stream = nullptr;
@@ -196,6 +199,7 @@ Layout plan(const muca_ctx *c)
     l.reach = take((size_t)c->B);
     l.state = take(sizeof(DevState));
     l.out = take(sizeof(double) * (4 + (size_t)c->B));
+    l.obs = take(sizeof(unsigned long long) * 6 * (size_t)c->B);
     l.total = off;
     return l;
 }
@@ -215,6 +219,7 @@ UpdateArgs update_args(const muca_ctx *c)
     a.beta = c->beta;
     a.flat_ratio = c->flat_ratio;
     a.e_lo = c->e_lo;
+    a.recursion = c->recursion;
     if (c->system == kPolymer) a.nblocks = 1;  // the open histogram is one global slot
     a.reach = c->reach;
     a.rlist = c->rlist;
@@ -314,6 +319,8 @@ int setup(muca_ctx *c)
     if (c->system == kPolymer) {
         c->Eq = (long long *)(base + l.Eq);
         c->lnWq = (long long *)(base + l.lnWq);
+    } else {
+        c->obs = (unsigned long long *)(base + l.obs);
     }
     MUCA_CUDA(cudaMemsetAsync(c->arena, 0, l.total, c->stream));
     int rc = init_walkers(c);
@@ -417,8 +424,12 @@ std::vector<Section> state_sections(const muca_ctx *c)
     v.push_back({c->lnR, sizeof(double) * B});
     v.push_back({c->H, sizeof(unsigned long long) * B});
     v.push_back({nullptr, sizeof(unsigned long long) * B});  // open histogram (summed over block slots)
-    if (c->system == kPolymer) v.push_back({c->lnWq, sizeof(long long) * B});
-    else v.push_back({c->T, sizeof(uint32_t) * B * c->C});
+    if (c->system == kPolymer) {
+        v.push_back({c->lnWq, sizeof(long long) * B});
+    } else {
+        v.push_back({c->T, sizeof(uint32_t) * B * c->C});
+        v.push_back({c->obs, sizeof(unsigned long long) * 6 * B});  // observable sums (open, last)
+    }
     return v;
 }
 
@@ -517,6 +528,20 @@ int muca_set_param(muca_ctx *c, const char *key, double v)
         c->pipeline = (int)v;
         return MUCA_OK;
     }
+    if (k == "observables") {
+        if (c->system != kIsing) return fail(MUCA_ERR_ARG, "observables are recorded for the Ising system only");
+        if (locked) return fail(MUCA_ERR_STATE, "observables must be set before the first iterate");
+        if (v != 0.0 && v != 1.0) return fail(MUCA_ERR_ARG, "observables must be 0 or 1");
+        c->observables = (int)v;
+        return MUCA_OK;
+    }
+    if (k == "recursion") {
+        if (c->system == kPolymer) return fail(MUCA_ERR_ARG, "recursion applies to lattice systems only");
+        if (locked) return fail(MUCA_ERR_STATE, "recursion must be set before the first iterate");
+        if (v != 0.0 && v != 1.0) return fail(MUCA_ERR_ARG, "recursion must be 0 or 1");
+        c->recursion = (int)v;
+        return MUCA_OK;
+    }
     if (k == "debug_drop_row") {
         if (c->system == kPolymer) return fail(MUCA_ERR_ARG, "debug_drop_row applies to lattice systems only");
         const long long r = (long long)v;
@@ -584,6 +609,7 @@ int muca_iterate(muca_ctx *c, int64_t sweeps)
     a.record = c->record;
     a.walker_offset = c->walker_offset;
     a.kind = sweep_kind(c->system, c->L);
+    a.obs = (c->observables && c->system == kIsing) ? c->obs : nullptr;
     a.debug_drop_row = c->debug_drop_row;
     c->debug_drop_row = -1;
     if (c->pipeline >= 2 && spin_sweep_tn_fits(c->system, c->L, c->B, c->block)) {
@@ -609,6 +635,11 @@ int muca_merge_and_update(muca_ctx *c, int *is_flat)
         MUCA_CUDA(launch_poly_lnwq(c->lnW, c->lnWq, c->B, c->stream));
     } else {
         MUCA_CUDA(launch_thresholds(a, c->stream));
+        if (c->observables) {  // the sums just filled belong to the weights of this update
+            const size_t bytes = sizeof(unsigned long long) * 3 * (size_t)c->B;
+            MUCA_CUDA(cudaMemcpyAsync(c->obs + 3 * (size_t)c->B, c->obs, bytes, cudaMemcpyDeviceToDevice, c->stream));
+            MUCA_CUDA(cudaMemsetAsync(c->obs, 0, bytes, c->stream));
+        }
     }
     c->started = true;
     c->open = false;
@@ -670,6 +701,21 @@ int muca_get_reweight(muca_ctx *c, double beta, double host_out[4], double *host
     MUCA_CUDA(launch_reweight(a, beta, c->out, c->out + 4, c->stream));
     if (int rc = d2h(c, host_out, c->out, sizeof(double) * 4)) return rc;
     if (host_lnP) return d2h(c, host_lnP, c->out + 4, sizeof(double) * c->B);
+    return MUCA_OK;
+}
+
+int muca_get_observables(muca_ctx *c, double beta, double host_out[3], uint64_t *host_sums, int nbins)
+{
+    if (int rc = check_ctx(c)) return rc;
+    if (c->system != kIsing || !c->observables)
+        return fail(MUCA_ERR_STATE, "observables are not recorded (set \"observables\" = 1 on an Ising context)");
+    if (!host_out) return fail(MUCA_ERR_ARG, "out is NULL");
+    if (!(beta == beta)) return fail(MUCA_ERR_ARG, "beta is NaN");
+    if (host_sums && nbins != c->B) return fail(MUCA_ERR_ARG, "need a host buffer of 3 x %d uint64", c->B);
+    const unsigned long long *last = c->obs + 3 * (size_t)c->B;
+    MUCA_CUDA(launch_reweight_obs(last, c->lnW_sampled, c->B, c->N, beta, c->out, c->stream));
+    if (int rc = d2h(c, host_out, c->out, sizeof(double) * 3)) return rc;
+    if (host_sums) return d2h(c, host_sums, last, sizeof(unsigned long long) * 3 * (size_t)c->B);
     return MUCA_OK;
 }
 
@@ -757,8 +803,8 @@ int muca_get_state(muca_ctx *c, void *host_buf, size_t *bytes)
     if (*bytes < need) return fail(MUCA_ERR_ARG, "state buffer too small: need %zu bytes", need);
     char *p = (char *)host_buf;
     StateHeader h{};
-    memcpy(h.magic, "MUCAST2", 8);
-    h.version = 2;
+    memcpy(h.magic, "MUCAST3", 8);
+    h.version = 3;
     h.system = c->system;
     h.L = c->L;
     h.q = c->q;
@@ -808,7 +854,7 @@ int muca_set_state(muca_ctx *c, const void *host_buf, size_t bytes)
     if (bytes < sizeof(StateHeader)) return fail(MUCA_ERR_ARG, "not a muca state buffer");
     StateHeader h;
     memcpy(&h, host_buf, sizeof h);
-    if (memcmp(h.magic, "MUCAST2", 8) != 0 || h.version != 2) return fail(MUCA_ERR_ARG, "not a muca state buffer");
+    if (memcmp(h.magic, "MUCAST3", 8) != 0 || h.version != 3) return fail(MUCA_ERR_ARG, "not a muca state buffer");
     if (h.system != c->system || h.L != c->L || h.q != c->q || h.p != c->p || h.C != c->C || h.wpw != c->wpw ||
         h.pstride != c->pstride || h.seed != c->seed)
         return fail(MUCA_ERR_ARG, "state buffer was written by a different configuration");
@@ -984,6 +1030,8 @@ int muca_batch_create(muca_ctx *const *systems, int n, muca_batch **out)
             return fail(MUCA_ERR_ARG, "all systems of a batch must use the same stream");
         if (systems[i]->system == kPolymer)
             return fail(MUCA_ERR_ARG, "system %d: the polymer is not part of spin batches", i);
+        if (systems[i]->observables)
+            return fail(MUCA_ERR_ARG, "system %d records observables, which batches do not support", i);
         for (int j = 0; j < i; ++j)
             if (systems[j] == systems[i]) return fail(MUCA_ERR_ARG, "system %d appears twice", i);
     }

@@ -41,6 +41,7 @@ struct SpinSweepArgs {
     int walker_offset;       // global id of walker 0 (for sharding)
     uint32_t rk[20];         // Philox round keys (k0 + r*W0, k1 + r*W1), r = 0..9
     int kind;                // system * 16 + L / 4 (dispatch key of the batched sweep)
+    unsigned long long *obs = nullptr;  // Ising observables: per bin (samples, sum |M|, sum M^2), or null
     int debug_drop_row = -1; // test hook: row hand-over (count within the launch) that the first
                              // producer warp of block 0 skips, so the consumer's wait runs out; -1 = off
 };
@@ -121,6 +122,7 @@ struct UpdateArgs {
     int system, B, nreach, nblocks, N, q, p, pstride, L;
     double beta, flat_ratio;
     double e_lo;  // polymer: energy of the window's lower edge
+    int recursion;  // 0: accumulated statistics, 1: plain W/H
     const uint8_t *reach;
     const int32_t *rlist;
     unsigned long long *Hpart, *H;
@@ -145,5 +147,7 @@ cudaError_t launch_unpack_spins(int system, int L, int p, int pstride, const uin
                                 cudaStream_t s);
 cudaError_t launch_det_math(int fn, const double *in, double *out, long long n, cudaStream_t s);
 cudaError_t launch_reweight(const UpdateArgs &a, double beta, double *out4, double *lnP, cudaStream_t s);
+cudaError_t launch_reweight_obs(const unsigned long long *sums, const double *lnW_sampled, int B, int N, double beta,
+                                double *out3, cudaStream_t s);
 
 }  // namespace muca

@@ -153,8 +153,9 @@ template <int SYS, int L, int RECORD>
 __device__ __forceinline__ void ising_sweep_tc(uint32_t *__restrict__ lat, int ps, int &bR, uint32_t *__restrict__ sTH,
                                                const uint4 *__restrict__ ring_u, const uint2 *__restrict__ ring_c,
                                                const uint32_t *__restrict__ ring_r, unsigned long long *full,
-                                               unsigned long long *empty, int &k, bool &bad)
+                                               unsigned long long *empty, int &k, bool &bad, unsigned long long *obs)
 {
+    int pc = 0;  // -1 spins of the final rows (observables)
     constexpr int WR = ising_words_per_row(L);
     constexpr int C = (SYS == kMuma) ? 10 : 5;
     constexpr int RS = C + 1;
@@ -242,12 +243,14 @@ __device__ __forceinline__ void ising_sweep_tc(uint32_t *__restrict__ lat, int p
 #pragma unroll
         for (int j = 0; j < WR; ++j) {
             lat[(y * WR + j) * ps] = cur[j];
+            pc += __popc(cur[j]);
             up[j] = cur[j];
         }
         mbar_arrive(&empty[slot]);  // after the row is stored: the producer reads it later
         ++k;
     }
     if (RECORD == 1) atomicAdd(&sTH[bR + C], 1u);
+    if (SYS == kIsing && obs && !bad) record_observables(obs, bR / RS, L * L, pc);
 }
 
 __host__ __device__ constexpr size_t tn_ring_bytes(int L)
@@ -309,9 +312,11 @@ __device__ __forceinline__ void sweep_block_tn(const SpinSweepArgs &a, int w0, i
                                                 -1);
             } else if (consumer && active) {
                 if (a.record == 0)
-                    ising_sweep_tc<SYS, L, 0>(lat, a.pstride, bR, sTH, ring_u, ring_c, ring_r, full, empty, k, bad);
+                    ising_sweep_tc<SYS, L, 0>(lat, a.pstride, bR, sTH, ring_u, ring_c, ring_r, full, empty, k, bad,
+                                              a.obs);
                 else
-                    ising_sweep_tc<SYS, L, 1>(lat, a.pstride, bR, sTH, ring_u, ring_c, ring_r, full, empty, k, bad);
+                    ising_sweep_tc<SYS, L, 1>(lat, a.pstride, bR, sTH, ring_u, ring_c, ring_r, full, empty, k, bad,
+                                              a.obs);
             } else if (consumer) {  // a consumer warp with no walkers keeps the barrier protocol
 #pragma unroll 1
                 for (int y = 0; y < L; ++y) {

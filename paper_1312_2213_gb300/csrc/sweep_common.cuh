@@ -78,4 +78,15 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned pari
 // Consumer side of one Ising / MUMA sweep: as ising_sweep, with the random words
 // of row y read from ring slot (k % kRing).
 
+// Observables of an Ising walker after a sweep: one sample, |M| and M^2 added to
+// the sums of its bin; pc = number of -1 spins (set bits) of its lattice.
+__device__ __forceinline__ void record_observables(unsigned long long *obs, int bin, int N, int pc)
+{
+    const long long M = (long long)N - 2LL * pc;
+    unsigned long long *o = obs + 3 * (size_t)bin;
+    atomicAdd(o, 1ull);
+    atomicAdd(o + 1, (unsigned long long)(M < 0 ? -M : M));
+    atomicAdd(o + 2, (unsigned long long)(M * M));
+}
+
 }  // namespace muca

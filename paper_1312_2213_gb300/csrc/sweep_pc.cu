@@ -22,8 +22,9 @@ template <int SYS, int L, int RECORD>
 __device__ __forceinline__ void ising_sweep_pc(uint32_t *__restrict__ lat, int ps, int &bR,
                                                uint32_t *__restrict__ sTH, const uint4 *__restrict__ ring,
                                                unsigned long long *full, unsigned long long *empty, int &k,
-                                               bool &bad)
+                                               bool &bad, unsigned long long *obs)
 {
+    int pc = 0;  // -1 spins of the final rows (observables)
     constexpr int WR = ising_words_per_row(L);
     constexpr int C = (SYS == kMuma) ? 10 : 5;
     constexpr int RS = C + 1;
@@ -100,7 +101,10 @@ __device__ __forceinline__ void ising_sweep_pc(uint32_t *__restrict__ lat, int p
         }
         bR = accP ? bR + dRp : bR;
 #pragma unroll
-        for (int j = 0; j < WR; ++j) lat[(y * WR + j) * ps] = cur[j];
+        for (int j = 0; j < WR; ++j) {
+            lat[(y * WR + j) * ps] = cur[j];
+            pc += __popc(cur[j]);
+        }
         mbar_arrive(&empty[slot]);
         ++k;
         if (y == 0) {
@@ -115,6 +119,7 @@ __device__ __forceinline__ void ising_sweep_pc(uint32_t *__restrict__ lat, int p
         }
     }
     if (RECORD == 1) atomicAdd(&sTH[bR + C], 1u);
+    if (SYS == kIsing && obs && !bad) record_observables(obs, bR / RS, L * L, pc);
 }
 
 // Consumer side of one Potts sweep (two words a site: proposal, acceptance).
@@ -305,12 +310,12 @@ __device__ __forceinline__ void sweep_block_pc(const SpinSweepArgs &a, int w0, i
                     if (SYS == kPotts)
                         potts_sweep_pc<L, 0>(lat, a.pstride, bR, sTH, ring, full, empty, k, bad, (uint32_t)a.q);
                     else
-                        ising_sweep_pc<SYS, L, 0>(lat, a.pstride, bR, sTH, ring, full, empty, k, bad);
+                        ising_sweep_pc<SYS, L, 0>(lat, a.pstride, bR, sTH, ring, full, empty, k, bad, a.obs);
                 } else {
                     if (SYS == kPotts)
                         potts_sweep_pc<L, 1>(lat, a.pstride, bR, sTH, ring, full, empty, k, bad, (uint32_t)a.q);
                     else
-                        ising_sweep_pc<SYS, L, 1>(lat, a.pstride, bR, sTH, ring, full, empty, k, bad);
+                        ising_sweep_pc<SYS, L, 1>(lat, a.pstride, bR, sTH, ring, full, empty, k, bad, a.obs);
                 }
             } else {
                 // inactive consumer lane: keep the barrier protocol, do no work

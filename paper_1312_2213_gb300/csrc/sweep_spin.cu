@@ -39,8 +39,9 @@ namespace muca {
 template <int SYS, int L, int RECORD>
 __device__ __forceinline__ void ising_sweep(uint32_t *__restrict__ lat, int ps, int &bR,
                                             uint32_t *__restrict__ sTH, uint32_t g, uint32_t wid,
-                                            const uint32_t (&rk)[20])
+                                            const uint32_t (&rk)[20], unsigned long long *obs)
 {
+    int pc = 0;  // -1 spins of the final rows (observables)
     constexpr int WR = ising_words_per_row(L);
     constexpr int C = (SYS == kMuma) ? 10 : 5;
     constexpr int RS = C + 1;
@@ -116,7 +117,10 @@ __device__ __forceinline__ void ising_sweep(uint32_t *__restrict__ lat, int ps, 
         }
         bR = accP ? bR + dRp : bR;
 #pragma unroll
-        for (int j = 0; j < WR; ++j) lat[(y * WR + j) * ps] = cur[j];
+        for (int j = 0; j < WR; ++j) {
+            lat[(y * WR + j) * ps] = cur[j];
+            pc += __popc(cur[j]);
+        }
         if (y == 0) {
 #pragma unroll
             for (int j = 0; j < WR; ++j) first[j] = cur[j];
@@ -129,6 +133,7 @@ __device__ __forceinline__ void ising_sweep(uint32_t *__restrict__ lat, int ps, 
         }
     }
     if (RECORD == 1) atomicAdd(&sTH[bR + C], 1u);
+    if (SYS == kIsing && obs) record_observables(obs, bR / RS, L * L, pc);
 }
 
 // One sweep of a q-state Potts walker (4-bit spins).  Proposal: a uniform new
@@ -271,7 +276,7 @@ __device__ __forceinline__ void sweep_block(const SpinSweepArgs &a, int w0, int 
                     if (SYS == kPotts)
                         potts_sweep<L, 0>(lat, a.pstride, bR, sTH, g, wid, a.rk, (uint32_t)a.q);
                     else
-                        ising_sweep<SYS, L, 0>(lat, a.pstride, bR, sTH, g, wid, a.rk);
+                        ising_sweep<SYS, L, 0>(lat, a.pstride, bR, sTH, g, wid, a.rk, a.obs);
                 }
             } else {
 #pragma unroll 1
@@ -280,7 +285,7 @@ __device__ __forceinline__ void sweep_block(const SpinSweepArgs &a, int w0, int 
                     if (SYS == kPotts)
                         potts_sweep<L, 1>(lat, a.pstride, bR, sTH, g, wid, a.rk, (uint32_t)a.q);
                     else
-                        ising_sweep<SYS, L, 1>(lat, a.pstride, bR, sTH, g, wid, a.rk);
+                        ising_sweep<SYS, L, 1>(lat, a.pstride, bR, sTH, g, wid, a.rk, a.obs);
                 }
             }
         }

@@ -60,6 +60,7 @@ __device__ __forceinline__ void recursion_body(const UpdateArgs &a, double *sm)
         s_sum = 0ull;
     }
     for (int b = tid; b < a.B; b += bs) a.lnW_sampled[b] = a.lnW[b];
+    __syncthreads();  // lnW_sampled is the source of the plain update below
     unsigned long long mn = ~0ull, mx = 0ull, sum = 0ull;
     for (int k = tid; k < a.nreach; k += bs) {
         const unsigned long long h = a.H[a.rlist[k]];
@@ -72,6 +73,23 @@ __device__ __forceinline__ void recursion_body(const UpdateArgs &a, double *sm)
     atomicMin(&s_min, mn);
     atomicMax(&s_max, mx);
     atomicAdd(&s_sum, sum);
+    if (a.recursion == 1) {
+        // the plain rule W(n+1) = W(n)/H(n) in log form: x_k = ln W(r_k) - ln max(H(r_k), 1),
+        // ln W(r_k) = x_k - x_0 (an unvisited bin keeps its weight)
+        const double x0 = __dsub_rn(a.lnW_sampled[a.rlist[0]], slog[0]);
+        for (int k = tid; k < a.nreach; k += bs)
+            a.lnW[a.rlist[k]] = __dsub_rn(__dsub_rn(a.lnW_sampled[a.rlist[k]], slog[k]), x0);
+        __syncthreads();
+        if (tid == 0) {
+            const double mean = __ddiv_rn(__ull2double_rn(s_sum), (double)a.nreach);
+            a.state->flat_min = __ull2double_rn(s_min);
+            a.state->flat_mean = mean;
+            a.state->flat_max = __ull2double_rn(s_max);
+            a.state->flat = (s_min > 0ull) && (__ddiv_rn(__ull2double_rn(s_min), mean) >= a.flat_ratio);
+            a.state->iteration += 1ull;
+        }
+        return;
+    }
     for (int k = tid; k + 1 < a.nreach; k += bs) {
         const unsigned long long h0 = a.H[a.rlist[k]], h1 = a.H[a.rlist[k + 1]];
         double r = a.lnR[k];
@@ -462,6 +480,68 @@ cudaError_t launch_reweight(const UpdateArgs &a, double beta, double *out4, doub
     cudaError_t e = cudaFuncSetAttribute(k_reweight, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     k_reweight<<<1, 1024, smem, s>>>(a, beta, out4, lnP);
+    return cudaGetLastError();
+}
+
+// Eq. (2) with per-bin sums of an Ising run (samples n, sum |M|, sum M^2 per bin):
+// <O>_beta = sum_b S_O(b) e^{x_b} / sum_b n(b) e^{x_b}, x_b = -beta E_b - ln W(b),
+// E_b = 4b - 2N, W the weights the sums were sampled with.  One block; out =
+// {<|M|>/N, <M^2>/N^2, beta N (<M^2>/N^2 - (<|M|>/N)^2)}, NaN without samples.
+__global__ void __launch_bounds__(256) k_reweight_obs(const unsigned long long *__restrict__ sums,
+                                                      const double *__restrict__ lnW, int B, int N, double beta,
+                                                      double *out)
+{
+    __shared__ double red[4][256];
+    const int t = threadIdx.x;
+    double m = -INFINITY;
+    for (int b = t; b < B; b += 256)
+        if (sums[3 * b] > 0ull) m = fmax(m, -beta * (double)(4 * b - 2 * N) - lnW[b]);
+    red[0][t] = m;
+    __syncthreads();
+    for (int o = 128; o; o >>= 1) {
+        if (t < o) red[0][t] = fmax(red[0][t], red[0][t + o]);
+        __syncthreads();
+    }
+    const double mx = red[0][0];
+    __syncthreads();
+    double z = 0.0, a1 = 0.0, a2 = 0.0;
+    if (mx > -INFINITY) {
+        for (int b = t; b < B; b += 256) {
+            if (sums[3 * b] == 0ull) continue;
+            const double f = exp(-beta * (double)(4 * b - 2 * N) - lnW[b] - mx);
+            z += f * (double)sums[3 * b];
+            a1 += f * (double)sums[3 * b + 1];
+            a2 += f * (double)sums[3 * b + 2];
+        }
+    }
+    red[1][t] = z;
+    red[2][t] = a1;
+    red[3][t] = a2;
+    __syncthreads();
+    for (int o = 128; o; o >>= 1) {
+        if (t < o) {
+            red[1][t] += red[1][t + o];
+            red[2][t] += red[2][t + o];
+            red[3][t] += red[3][t + o];
+        }
+        __syncthreads();
+    }
+    if (t == 0) {
+        if (!(mx > -INFINITY)) {
+            out[0] = out[1] = out[2] = NAN;
+        } else {
+            const double m1 = red[2][0] / red[1][0] / N, m2 = red[3][0] / red[1][0] / ((double)N * N);
+            out[0] = m1;
+            out[1] = m2;
+            out[2] = beta * N * (m2 - m1 * m1);
+        }
+    }
+}
+
+cudaError_t launch_reweight_obs(const unsigned long long *sums, const double *lnW_sampled, int B, int N, double beta,
+                                double *out3, cudaStream_t s)
+{
+    k_reweight_obs<<<1, 256, 0, s>>>(sums, lnW_sampled, B, N, beta, out3);
     return cudaGetLastError();
 }
 

@@ -21,11 +21,13 @@ def compare_state(g, o, what=""):
 
 
 def run_pair(system, L, q, p, seed, iters, sweeps, beta=0.0, record=0, block=None, nthreads=8, check_each=True,
-             pipeline=None):
+             pipeline=None, recursion=0):
     g = m.Muca(system, L, q, p, seed, beta=beta if system == m.ISING2D_MUMA else None, record=record, block=block)
     if pipeline is not None:
         g.set_param("pipeline", pipeline)
-    o = oracle.Run(system, L, q, p, seed, beta=beta, record=record)
+    if recursion:
+        g.set_param("recursion", recursion)
+    o = oracle.Run(system, L, q, p, seed, beta=beta, record=record, recursion=recursion)
     o.init()
     compare_state(g, o, "after init")
     for it in range(iters):

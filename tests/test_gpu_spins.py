@@ -79,6 +79,14 @@ def test_code_pipeline_bit_exact(system, L, q, p, block):
              pipeline=2, block=block)
 
 
+@pytest.mark.parametrize("system,L,q,p", [(m.ISING2D, 16, 2, 64), (m.POTTS2D, 16, 8, 70), (m.ISING2D_MUMA, 16, 2, 40),
+                                          (m.ISING2D, 32, 2, 100)])
+def test_plain_recursion_bit_exact(system, L, q, p):
+    """recursion = 1 (the plain W/H update) matches the oracle bit for bit at every iteration."""
+    run_pair(system, L, q, p, seed=123 + L, iters=5, sweeps=max(2, 3000 // (L * L)), beta=0.4407, nthreads=NT,
+             recursion=1)
+
+
 def test_config_ising_L8_p64_full_length():
     """Ising L = 8, p = 64, 10 iterations of 1e4 sweeps: bit-exact at every iteration."""
     g, o = run_pair(m.ISING2D, 8, 2, 64, seed=1, iters=10, sweeps=10000, nthreads=NT)
@@ -226,3 +234,34 @@ def test_errors_are_reported_not_raised_in_c():
 def test_p_equals_one_and_tiny_lattice():
     run_pair(m.ISING2D, 4, 2, 1, seed=8, iters=3, sweeps=200, nthreads=1)
     run_pair(m.POTTS2D, 4, 16, 1, seed=8, iters=3, sweeps=200, nthreads=1)
+
+
+@pytest.mark.parametrize("pipeline,L,p", [(0, 8, 64), (1, 16, 70), (2, 16, 70), (2, 32, 100)])
+def test_observables_bit_exact(pipeline, L, p):
+    """Per-sweep sums of 1, |M| and M^2 per energy bin (Ising) match the oracle bit for bit in
+    every sweep form, and the Eq. 2 reweighting of them agrees to rounding."""
+    S = max(2, 2000 // (L * L))
+    g = m.Muca(m.ISING2D, L, 2, p, 41)
+    g.set_param("pipeline", pipeline)
+    g.set_param("observables", 1)
+    o = oracle.Run(0, L, 2, p, 41, observables=1)
+    o.init()
+    for _ in range(3):
+        g.iterate(S)
+        g.merge_and_update()
+        o.iterate(S, NT)
+        o.update()
+        out, sums = g.observables(0.4)
+        np.testing.assert_array_equal(sums, o.observable_sums())
+        assert int(sums[:, 0].sum()) == p * S
+        np.testing.assert_allclose(out, o.reweight_observables(0.4), rtol=1e-12, atol=0)
+    compare_state(g, o, "with observables")
+
+
+def test_observables_refused_where_not_recorded():
+    g = m.Muca(m.POTTS2D, 8, 3, 8, 1)
+    with pytest.raises(m.MucaError):
+        g.set_param("observables", 1)
+    h = m.Muca(m.ISING2D, 8, 2, 8, 1)
+    with pytest.raises(m.MucaError):
+        h.observables(0.4)

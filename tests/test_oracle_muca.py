@@ -127,6 +127,63 @@ def test_first_update_is_plain_w_over_h(orc):
     assert np.ptp(d) < 1e-12 * 30
 
 
+def test_plain_update_is_w_over_h_every_iteration(orc):
+    """recursion = 1 (the paper's simple rule W(n+1) = W(n)/H(n), log form): after two updates
+    ln W = -ln H1 - ln H2 up to the constant that puts ln W(r_0) at 0; an empty bin (H = 0 taken
+    as 1) keeps its weight; unreachable bins stay at -inf."""
+    rng = np.random.default_rng(3)
+    r = orc.Run(0, 4, 2, 1, 1, recursion=1)
+    r.init()
+    reach = r.reachable()
+    idx = np.nonzero(reach)[0]
+    H1 = np.zeros(r.B, dtype=np.uint64); H1[idx] = rng.integers(1, 10**6, idx.size)
+    H2 = np.zeros(r.B, dtype=np.uint64); H2[idx] = rng.integers(1, 10**6, idx.size)
+    H2[idx[4]] = 0
+    r.set_open_histogram(H1); r.update()
+    r.set_open_histogram(H2); r.update()
+    lh = np.log(H1[idx].astype(float)) + np.log(np.maximum(H2[idx], 1).astype(float))
+    want = -(lh - lh[0])
+    np.testing.assert_allclose(r.lnW()[idx], want, rtol=0, atol=1e-11)
+    assert np.all(np.isneginf(r.lnW()[~reach]))
+    assert r.lnW()[idx[0]] == 0.0
+
+
+def test_plain_and_accumulated_updates_agree_on_the_first_update(orc):
+    """With every reachable bin visited, the first accumulated-statistics update (kappa = 1)
+    and the plain rule give the same weights (up to rounding order)."""
+    rng = np.random.default_rng(4)
+    H = None
+    out = []
+    for mode in (0, 1):
+        r = orc.Run(1, 4, 3, 1, 1, recursion=mode)
+        r.init()
+        reach = r.reachable()
+        if H is None:
+            H = np.zeros(r.B, dtype=np.uint64)
+            H[reach] = rng.integers(1, 10**9, reach.sum())
+        r.set_open_histogram(H)
+        r.update()
+        out.append(r.lnW()[reach])
+    np.testing.assert_allclose(out[0], out[1], rtol=0, atol=1e-10)
+
+
+def test_plain_update_reaches_the_fixed_point_of_an_ideal_histogram(orc):
+    """If the histogram is exactly Omega(E) W(E) (ideal sampling), one plain update gives
+    ln W = -ln Omega + const: the sign and the bookkeeping of the rule (exact Omega of the
+    4x4 Ising lattice by brute force)."""
+    r = orc.Run(0, 4, 2, 1, 1, recursion=1)
+    r.init()
+    omega = orc.bruteforce_ising(4).astype(float)
+    reach = r.reachable()
+    H = np.zeros(r.B, dtype=np.uint64)
+    H[reach] = (omega[reach] * 1000).astype(np.uint64)  # W = 1 initially
+    r.set_open_histogram(H)
+    r.update()
+    idx = np.nonzero(reach)[0]
+    lo = np.log(omega[idx])
+    np.testing.assert_allclose(r.lnW()[idx], -(lo - lo[0]), rtol=0, atol=1e-11)
+
+
 def test_recursion_is_a_weighted_mean_of_naive_estimates(orc):
     """After two updates each neighbour ratio lnR is the g-weighted mean of the two naive
     estimates R^(n) + ln h0 - ln h1, with g = h0 h1/(h0+h1) (accumulated statistics)."""
@@ -279,3 +336,68 @@ def test_multimagnetic_converges_to_exact_P_of_M(orc):
         P = np.exp(lnPM - lnPM.max()); P /= P.sum()
     absM = np.abs(2 * np.arange(N + 1) - N)
     assert out[0] == pytest.approx((P * absM).sum() / N, rel=0.02)
+
+
+def _canonical_m_moments(orc, L, beta):
+    """Exact <|M|>/N and <M^2>/N^2 at beta from the brute-force Omega(E, M)."""
+    om = orc.bruteforce_ising_EM(L).astype(float)
+    N = L * L
+    E = 4.0 * np.arange(N + 1) - 2 * N
+    M = 2.0 * np.arange(N + 1) - N
+    w = om * np.exp(-beta * (E - E.min()))[:, None]
+    z = w.sum()
+    return (w * np.abs(M)[None, :]).sum() / z / N, (w * (M ** 2)[None, :]).sum() / z / N ** 2
+
+
+@pytest.mark.parametrize("beta", [0.0, 0.3, 0.4407, 0.8])
+def test_observable_reweighting_is_eq2(orc, beta):
+    """Eq. 2 on per-bin sums: with sums that are exact expectations under any weights W
+    (n(b) = c W(b) Omega(b), S_|M|(b) = c W(b) sum_M Omega(b, M)|M|, ...), the reweighted moments
+    equal the exact canonical ones of the 4x4 Ising lattice."""
+    L, N = 4, 16
+    om = orc.bruteforce_ising_EM(L).astype(float)
+    M = 2.0 * np.arange(N + 1) - N
+    rng = np.random.default_rng(5)
+    lnW = rng.uniform(-3, 3, N + 1)
+    scale = 2.0 ** 20
+    sums = np.zeros((N + 1, 3), dtype=np.uint64)
+    # integer sums need the factor c e^{lnW} Omega to be integral: choose W so that it is
+    for b in range(N + 1):
+        if om[b].sum() == 0:
+            continue
+        f = np.round(scale * np.exp(lnW[b]))
+        lnW[b] = np.log(f / scale)
+        sums[b] = [f * om[b].sum(), f * (om[b] * np.abs(M)).sum(), f * (om[b] * M ** 2).sum()]
+    got = orc.reweight_obs(N, sums, lnW, beta)
+    m1, m2 = _canonical_m_moments(orc, L, beta)
+    assert abs(got[0] - m1) < 1e-12 and abs(got[1] - m2) < 1e-12
+    assert abs(got[2] - beta * N * (m2 - m1 ** 2)) < 1e-10
+
+
+def test_observable_sums_follow_the_lattices(orc):
+    """Per-sweep sums (reading R9): over one sweep of p walkers the sample count is p, and
+    after the sweep the sums equal |M| and M^2 of the final lattices in their final bins."""
+    r = orc.Run(0, 8, 2, 12, 7, observables=1)
+    r.init()
+    r.iterate(1, 1)
+    r.update()
+    S = r.observable_sums()
+    s = r.spins().astype(np.int64)
+    Mw = s.sum(axis=(1, 2))
+    want = np.zeros(S.shape, dtype=np.int64)
+    for w, b in enumerate(r.bins()):
+        want[b] += np.array([1, abs(Mw[w]), Mw[w] ** 2], dtype=np.int64)
+    np.testing.assert_array_equal(S.astype(np.int64), want)
+
+
+def test_observables_at_low_temperature_from_a_muca_run(orc):
+    """A short multicanonical run of the 4x4 Ising lattice: the reweighted <|M|>/N at
+    beta = 0.6 is within 3% of the exact value (statistical check of the whole chain)."""
+    r = orc.Run(0, 4, 2, 64, 11, observables=1)
+    r.init()
+    for _ in range(12):
+        r.iterate(400, NT)
+        r.update()
+    got = r.reweight_observables(0.6)
+    m1, _ = _canonical_m_moments(orc, 4, 0.6)
+    assert abs(got[0] - m1) < 0.03 * m1
