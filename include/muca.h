@@ -116,6 +116,12 @@ int muca_init_ex(muca_ctx **out, int system, int L_or_N, int q, int p, uint64_t 
  *                 call returns MUCA_ERR_TIMEOUT.  The context's walker state is
  *                 invalid afterwards (restore a checkpoint with muca_set_state).
  *                 No effect with pipeline = 0 or a row past the call's sweeps.
+ *   "model"       polymer, before the first iterate: 0 (default) = the benchmark
+ *                 parameters (FENE K = 40, R = 1.5, rest length 0; LJ sigma = 1 cut
+ *                 at 2.5 and shifted), 1 = the paper's own parameters of Eq. (7)
+ *                 (FENE with K = 40, r0 = 0.7, r_max = 1; LJ sigma = 2^(-1/6) r0,
+ *                 no cutoff).  Redraws the initial chains (bond length r0 in
+ *                 model 1); travels with muca_get_state.
  *   "lanes"       polymer: lanes of a warp per walker in the sweep, 8, 16 or 32
  *                 (32/lanes walkers share a warp); 0 (default) means 16.  The pair terms are
  *                 FP32 and their grouping over lanes changes their rounding, so

@@ -110,6 +110,7 @@ def _bind_polymer(L):
                  "orc_poly_get_energy", "orc_poly_get_bins", "orc_poly_get_counters"):
         getattr(L, name).argtypes = [c.c_void_p, c.c_void_p]
     L.orc_poly_set_beta.argtypes = [c.c_void_p, c.c_double]
+    L.orc_poly_set_model.argtypes = [c.c_void_p, c.c_int]
     L.orc_poly_reweight.argtypes = [c.c_void_p, c.c_double, c.c_void_p, c.c_void_p]
     L.orc_poly_get_walker_events.argtypes = [c.c_void_p, c.c_void_p]
     L.orc_poly_refresh_energy.argtypes = [c.c_void_p]
@@ -306,7 +307,7 @@ class PolyRun:
     """Oracle multicanonical run of a bead-spring polymer of N beads (p walkers)."""
 
     def __init__(self, N: int, p: int, seed: int, e_lo: float, e_hi: float, K: float = 40.0, R: float = 1.5,
-                 record: int = 0, beta: float = 0.0):
+                 record: int = 0, beta: float = 0.0, model: int = 0):
         self._lib = lib()
         self.h = self._lib.orc_poly_create(N, p, seed, e_lo, e_hi, K, R, record)
         if not self.h:
@@ -315,6 +316,8 @@ class PolyRun:
         self.B = self._lib.orc_poly_num_bins(self.h)
         if beta > 0:
             self._lib.orc_poly_set_beta(self.h, beta)
+        if model:
+            self._lib.orc_poly_set_model(self.h, model)
 
     def __del__(self):
         if getattr(self, "h", None):
@@ -375,10 +378,10 @@ class PolyRun:
         return out, lnP
 
 
-def poly_energy(X: np.ndarray) -> float:
+def poly_energy(X: np.ndarray, model: int = 0) -> float:
     X = np.ascontiguousarray(X, dtype=np.float64)
-    return lib().orc_poly_energy(X.shape[0], _ptr(X), 0)
+    return lib().orc_poly_energy(X.shape[0], _ptr(X), model)
 
 
-def poly_pair(r: float, sep: int) -> float:
-    return lib().orc_poly_pair(float(r), int(sep), 0)
+def poly_pair(r: float, sep: int, model: int = 0) -> float:
+    return lib().orc_poly_pair(float(r), int(sep), int(model))

@@ -66,3 +66,24 @@ def fene_dimer_omega(e_edges, K: float, R: float, dps: int = 40):
         for a, b in zip(e_edges[:-1], e_edges[1:]):
             vols.append(float(4 * mpmath.pi / 3 * (r_of(b) ** 3 - r_of(a) ** 3)))
         return vols
+
+
+def fene_shifted_dimer_omega(e_edges, K: float, R: float, r0: float, dps: int = 40):
+    """Relative binned density of states of a FENE dimer with rest length r0 (the paper's
+    Eq. 7 bond), V(r) = -(K/2) R^2 ln(1 - ((r - r0)/R)^2) for |r - r0| < R, r0 > R.
+
+    V < E on the shell r0 - R t(E) < r < r0 + R t(E), t(E) = sqrt(1 - exp(-2E/(K R^2))), whose
+    volume is (4 pi / 3)[(r0 + R t)^3 - (r0 - R t)^3]; a bin [E_a, E_b) holds the difference.
+    """
+    with mpmath.workdps(dps):
+        KR2 = mpmath.mpf(K) * mpmath.mpf(R) ** 2
+        r0m, Rm = mpmath.mpf(r0), mpmath.mpf(R)
+
+        def vol(E):
+            E = mpmath.mpf(E)
+            if E <= 0:
+                return mpmath.mpf(0)
+            t = mpmath.sqrt(1 - mpmath.exp(-2 * E / KR2))
+            return 4 * mpmath.pi / 3 * ((r0m + Rm * t) ** 3 - (r0m - Rm * t) ** 3)
+
+        return [float(vol(b) - vol(a)) for a, b in zip(e_edges[:-1], e_edges[1:])]

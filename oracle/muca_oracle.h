@@ -93,6 +93,7 @@ void *orc_poly_create(int N, int p, uint64_t seed, double e_lo, double e_hi, dou
 void orc_poly_free(void *h);
 int orc_poly_num_bins(void *h);
 void orc_poly_set_beta(void *h, double beta);
+void orc_poly_set_model(void *h, int model); /* 1: the paper's parameters (Eq. 7); before init */
 void orc_poly_init(void *h);
 void orc_poly_iterate(void *h, int64_t sweeps, int nthreads);
 void orc_poly_iterate_range(void *h, int64_t sweeps, int w0, int w1, int nthreads);
@@ -108,8 +109,8 @@ void orc_poly_get_bins(void *h, int32_t *out /* p */);
 void orc_poly_get_counters(void *h, int64_t *out /* {near-tie acceptances, bin-edge events} */);
 void orc_poly_reweight(void *h, double beta, double out[4], double *lnP /* nullable, B */);
 void orc_poly_get_walker_events(void *h, int64_t *out /* p*2 */);
-double orc_poly_energy(int N, const double *X, int unused);
-double orc_poly_pair(double r, int sep, int unused);
+double orc_poly_energy(int N, const double *X, int model); /* model 0 benchmark, 1 paper */
+double orc_poly_pair(double r, int sep, int model);
 
 #ifdef __cplusplus
 }

@@ -25,10 +25,15 @@
  * After each call that runs sweeps, every chain is shifted so that bead 0 sits
  * at the origin (an exact shift by a grid vector, so coordinates stay well
  * inside the range where binary64 holds the grid exactly).
- * Initial chain: bead 0 at the origin; bead k = bead k-1 + u_hat, with u_hat a
- * unit vector from Marsaglia's (1972) method on Philox tag-2 words, rounded
+ * Initial chain: bead 0 at the origin; bead k = bead k-1 + b0 u_hat, with u_hat
+ * a unit vector from Marsaglia's (1972) method on Philox tag-2 words, rounded
  * to the 2^-44 grid; redrawn (up to 64 times) while any earlier bead lies
- * closer than 0.9.
+ * closer than 0.9 b0 (b0 = 1 here, the rest length 0.7 in model 1).
+ *
+ * Model 1 (the paper's own parameters of Eq. 7): the same sums with
+ *   V_LJ(r)   = 4 [(sigma/r)^12 - (sigma/r)^6], sigma = 2^(-1/6) r0, no cutoff,
+ *   V_FENE(r) = -(K/2) R^2 ln(1 - ((r - r0)/R)^2), |r - r0| < R, else +infinity,
+ *   K = 40, r0 = 0.7, R = r_max - r0 = 0.3 (r_max = 1).
  */
 #include <math.h>
 #include <pthread.h>
@@ -43,11 +48,15 @@
 #define POLY_STEP_Q 1229.0
 #define POLY_GRID 0x1p-44
 #define POLY_RC 2.5
+#define POLY_PAPER_R0 0.7
+#define POLY_PAPER_R 0.3
 
 typedef struct {
     int N, p, B, record;
     uint64_t seed;
     double e_lo, e_hi, K, R, beta;
+    int model;        /* 0: benchmark parameters, 1: the paper's (Eq. 7) */
+    double r0, sigma2; /* model 1: FENE rest length, LJ sigma^2 */
     int64_t sweep_counter;
     double *X;       /* p*N*3 */
     double *E;       /* p */
@@ -72,16 +81,37 @@ static double poly_fene(double r2, double K, double R)
     return -0.5 * K * R * R * log(1.0 - r2 / (R * R));
 }
 
-/* Pair energy at distance r for index separation sep (1 = bond, >= 2 = LJ). */
-double orc_poly_pair(double r, int sep, int unused)
+/* Model 1 (Eq. 7 with the paper's parameters). */
+static double poly_paper_sigma2(void) { return POLY_PAPER_R0 * POLY_PAPER_R0 * pow(2.0, -1.0 / 3.0); }
+
+static double poly_lj_paper(double r2, double sigma2)
 {
-    (void)unused;
-    double r2 = r * r;
+    double s2 = sigma2 / r2;
+    double s6 = s2 * s2 * s2;
+    return 4.0 * (s6 * s6 - s6);
+}
+
+static double poly_fene_paper(double r2, double K, double R, double r0)
+{
+    double x = (sqrt(r2) - r0) / R;
+    if (!(fabs(x) < 1.0)) return INFINITY;
+    return -0.5 * K * R * R * log(1.0 - x * x);
+}
+
+static double poly_pair_model(double r2, int sep, int model)
+{
+    if (model == 1)
+        return sep == 1 ? poly_fene_paper(r2, 40.0, POLY_PAPER_R, POLY_PAPER_R0) : poly_lj_paper(r2, poly_paper_sigma2());
     return sep == 1 ? poly_fene(r2, 40.0, 1.5) : poly_lj(r2);
 }
 
+/* Pair energy at distance r for index separation sep (1 = bond, >= 2 = LJ);
+ * model 0 benchmark, 1 the paper's parameters. */
+double orc_poly_pair(double r, int sep, int model) { return poly_pair_model(r * r, sep, model); }
+
 static double poly_pair2(const orc_poly *P, double r2, int sep)
 {
+    if (P->model == 1) return sep == 1 ? poly_fene_paper(r2, P->K, P->R, P->r0) : poly_lj_paper(r2, P->sigma2);
     return sep == 1 ? poly_fene(r2, P->K, P->R) : poly_lj(r2);
 }
 
@@ -92,15 +122,11 @@ static double poly_dist2(const double *a, const double *b)
 }
 
 /* Energy of one configuration from scratch, pairs i < j in order. */
-double orc_poly_energy(int N, const double *X, int unused)
+double orc_poly_energy(int N, const double *X, int model)
 {
-    (void)unused;
     double E = 0.0;
     for (int i = 0; i < N; ++i)
-        for (int j = i + 1; j < N; ++j) {
-            double r2 = poly_dist2(X + 3 * i, X + 3 * j);
-            E += (j - i == 1) ? poly_fene(r2, 40.0, 1.5) : poly_lj(r2);
-        }
+        for (int j = i + 1; j < N; ++j) E += poly_pair_model(poly_dist2(X + 3 * i, X + 3 * j), j - i, model);
     return E;
 }
 
@@ -154,6 +180,20 @@ int orc_poly_num_bins(void *h) { return ((orc_poly *)h)->B; }
 /* Canonical mode for the window pilot: weight exp(-beta E), no window. */
 void orc_poly_set_beta(void *h, double beta) { ((orc_poly *)h)->beta = beta; }
 
+/* Model 1: the paper's parameters (K = 40, r0 = 0.7, r_max = 1, LJ without cutoff);
+ * before orc_poly_init. */
+void orc_poly_set_model(void *h, int model)
+{
+    orc_poly *P = (orc_poly *)h;
+    P->model = model;
+    if (model == 1) {
+        P->K = 40.0;
+        P->R = POLY_PAPER_R;
+        P->r0 = POLY_PAPER_R0;
+        P->sigma2 = poly_paper_sigma2();
+    }
+}
+
 static uint32_t poly_word(const orc_poly *P, uint32_t c0, uint32_t c1, uint32_t w, uint32_t tag, int k)
 {
     uint32_t ctr[4] = {c0, c1, w, tag}, key[2] = {(uint32_t)(P->seed & 0xffffffffu), (uint32_t)(P->seed >> 32)}, out[4];
@@ -165,6 +205,8 @@ void orc_poly_init(void *h)
 {
     orc_poly *P = (orc_poly *)h;
     const int N = P->N;
+    const double b0 = (P->model == 1) ? POLY_PAPER_R0 : 1.0;  /* initial bond length */
+    const double d2min = (P->model == 1) ? 0.3969 : 0.81;      /* (0.9 b0)^2 */
     uint32_t key[2] = {(uint32_t)(P->seed & 0xffffffffu), (uint32_t)(P->seed >> 32)};
     for (int w = 0; w < P->p; ++w) {
         double *X = P->X + (size_t)w * N * 3;
@@ -185,10 +227,11 @@ void orc_poly_init(void *h)
                 }
                 double f = 2.0 * sqrt(1.0 - s);
                 double uh[3] = {v1 * f, v2 * f, 1.0 - 2.0 * s};
-                for (int a = 0; a < 3; ++a) cand[a] = X[3 * (k - 1) + a] + nearbyint(uh[a] * 0x1p44) * POLY_GRID;
+                for (int a = 0; a < 3; ++a)
+                    cand[a] = X[3 * (k - 1) + a] + nearbyint((uh[a] * b0) * 0x1p44) * POLY_GRID;
                 int ok = 1;
                 for (int j = 0; j < k - 1 && ok; ++j)
-                    if (poly_dist2(cand, X + 3 * j) < 0.81) ok = 0;
+                    if (poly_dist2(cand, X + 3 * j) < d2min) ok = 0;
                 if (ok) break;
             }
             for (int a = 0; a < 3; ++a) X[3 * k + a] = cand[a];

@@ -2,6 +2,7 @@
 // lays out the device arena, turns every C call into kernel launches on the
 // context's stream, and maps CUDA errors onto MUCA_ERR_* codes with a
 // thread-local message.  No compute happens on the host.
+#include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <algorithm>
@@ -52,6 +53,7 @@ struct muca_ctx {
     double beta = 0.0, flat_ratio = 0.5;
     int record = 0, block = 64, walker_offset = 0;
     int lanes = 0;     // polymer: lanes per walker in the sweep (8, 16, 32; 0 = chosen by N)
+    int model = 0;     // polymer: 0 benchmark parameters, 1 the paper's (Eq. 7)
     int debug_drop_row = -1;  // test hook for the bounded waits (next spin iterate only)
     int recursion = 0;        // weight update: 0 accumulated statistics, 1 plain W/H
     int observables = 0;      // Ising: per-sweep sums of 1, |M|, M^2 per bin
@@ -251,11 +253,30 @@ PolyArgs poly_args(const muca_ctx *c, int64_t sweeps)
     a.lanes = c->lanes;
     a.elo_q = llrint(c->e_lo * 4294967296.0);                      // e_lo * 2^32
     a.ehi_q = a.elo_q + ((long long)c->B * 4294967296LL + 9) / 10;  // first energy with bin >= B
-    a.fene_KR2_half = (float)(0.5 * c->fene_K * c->fene_R * c->fene_R);
-    a.fene_invR2 = (float)(1.0 / (c->fene_R * c->fene_R));
-    a.lj_rc2 = 6.25f;
-    const double irc6 = 1.0 / (6.25 * 6.25 * 6.25);
-    a.lj_shift = (float)(4.0 * (irc6 * irc6 - irc6));
+    a.model = c->model;
+    if (c->model == 1) {  // the paper's parameters of Eq. 7: K = 40, r0 = 0.7, r_max = 1, no LJ cutoff
+        const double K = 40.0, r0 = 0.7, R = 0.3;
+        a.fene_KR2_half = (float)(0.5 * K * R * R);
+        a.fene_invR2 = (float)(1.0 / (R * R));
+        a.fene_r0 = (float)r0;
+        a.fene_invR = (float)(1.0 / R);
+        a.lj_sigma2 = (float)(r0 * r0 * std::pow(2.0, -1.0 / 3.0));
+        a.lj_rc2 = INFINITY;
+        a.lj_shift = 0.0f;
+        a.init_bond = r0;
+        a.init_d2min = 0.3969;  // (0.9 r0)^2
+    } else {
+        a.fene_KR2_half = (float)(0.5 * c->fene_K * c->fene_R * c->fene_R);
+        a.fene_invR2 = (float)(1.0 / (c->fene_R * c->fene_R));
+        a.fene_r0 = 0.0f;
+        a.fene_invR = (float)(1.0 / c->fene_R);
+        a.lj_sigma2 = 1.0f;
+        a.lj_rc2 = 6.25f;
+        const double irc6 = 1.0 / (6.25 * 6.25 * 6.25);
+        a.lj_shift = (float)(4.0 * (irc6 * irc6 - irc6));
+        a.init_bond = 1.0;
+        a.init_d2min = 0.81;  // (0.9 b0)^2
+    }
     a.sweeps = sweeps;
     SpinSweepArgs keys{};
     fill_round_keys(keys, c->seed);
@@ -393,7 +414,7 @@ int d2h(muca_ctx *c, void *host, const void *dev, size_t bytes)
 // Checkpoint blob: fixed header, then the device sections in this order.
 struct StateHeader {
     char magic[8];
-    int32_t version, system, L, q, p, B, C, wpw, pstride, record, walker_offset;
+    int32_t version, system, L, q, p, B, C, wpw, pstride, record, walker_offset, model;
     uint64_t seed;
     double beta, e_lo, e_hi, fene_K, fene_R;
     DevState dev;
@@ -548,6 +569,14 @@ int muca_set_param(muca_ctx *c, const char *key, double v)
         if ((double)r != v || r < 0 || r > 0x7fffffffLL) return fail(MUCA_ERR_ARG, "debug_drop_row must be >= 0");
         c->debug_drop_row = (int)r;
         return MUCA_OK;
+    }
+    if (k == "model") {
+        if (c->system != kPolymer) return fail(MUCA_ERR_ARG, "model applies to the polymer only");
+        if (locked) return fail(MUCA_ERR_STATE, "model must be set before the first iterate");
+        if (v != 0.0 && v != 1.0) return fail(MUCA_ERR_ARG, "model must be 0 or 1");
+        c->model = (int)v;
+        if (int rc = init_walkers(c)) return rc;  // the initial chains depend on the bond length
+        return reset_weights(c);
     }
     if (k == "lanes") {
         if (c->system != kPolymer) return fail(MUCA_ERR_ARG, "lanes applies to the polymer only");
@@ -815,6 +844,7 @@ int muca_get_state(muca_ctx *c, void *host_buf, size_t *bytes)
     h.pstride = c->pstride;
     h.record = c->record;
     h.walker_offset = c->walker_offset;
+    h.model = c->model;
     h.seed = c->seed;
     h.beta = c->beta;
     h.e_lo = c->e_lo;
@@ -865,6 +895,7 @@ int muca_set_state(muca_ctx *c, const void *host_buf, size_t bytes)
         return fail(MUCA_ERR_ARG, "state buffer was written by a different configuration");
     }
     if (h.record != 0 && h.record != 1) return fail(MUCA_ERR_ARG, "state buffer: bad record mode");
+    if (h.model != 0 && h.model != 1) return fail(MUCA_ERR_ARG, "state buffer: bad polymer model");
     const int oldB = c->B;
     c->B = h.B;  // the polymer window travels with the state
     const size_t need = state_bytes(c);
@@ -894,6 +925,7 @@ int muca_set_state(muca_ctx *c, const void *host_buf, size_t bytes)
     c->e_hi = h.e_hi;
     c->fene_K = h.fene_K;
     c->fene_R = h.fene_R;
+    c->model = h.model;
     if (c->system == kPolymer) {
         reachable_bins(c);
         MUCA_CUDA(cudaMemcpyAsync(c->reach, c->h_reach.data(), c->B, cudaMemcpyHostToDevice, c->stream));

@@ -33,7 +33,7 @@ bool polymer_supported(int N) { return N >= 2 && N <= kPolyMaxN; }
 
 __device__ __forceinline__ float lj_energy(float r2, const PolyArgs &a)
 {
-    const float ir2 = __frcp_rn(r2);
+    const float ir2 = __frcp_rn(r2) * a.lj_sigma2;  // (sigma/r)^2; sigma = 1 in model 0
     const float ir6 = ir2 * ir2 * ir2;
     const float v = 4.0f * (ir6 * ir6 - ir6) - a.lj_shift;
     return r2 < a.lj_rc2 ? v : 0.0f;
@@ -41,7 +41,18 @@ __device__ __forceinline__ float lj_energy(float r2, const PolyArgs &a)
 
 __device__ __forceinline__ float fene_energy(float r2, const PolyArgs &a)
 {
+    if (a.model == 1) {  // rest length r0: -(K/2) R^2 ln(1 - ((r - r0)/R)^2)
+        const float x = (__fsqrt_rn(r2) - a.fene_r0) * a.fene_invR;
+        return -a.fene_KR2_half * log1pf(-x * x);
+    }
     return -a.fene_KR2_half * log1pf(-r2 * a.fene_invR2);
+}
+
+// A bond of squared length r2 is intact: r < R (model 0), |r - r0| < R (model 1).
+__device__ __forceinline__ bool fene_intact(float r2, const PolyArgs &a)
+{
+    if (a.model == 1) return fabsf((__fsqrt_rn(r2) - a.fene_r0) * a.fene_invR) < 1.0f;
+    return r2 < 1.0f / a.fene_invR2;
 }
 
 // Offset on the 2^-44 grid as an unevaluated pair hi + lo of floats.
@@ -111,14 +122,15 @@ __global__ void k_poly_init(const PolyArgs a)
             }
             const double f = __dmul_rn(2.0, __dsqrt_rn(__dsub_rn(1.0, s)));
             const double uh[3] = {__dmul_rn(v1, f), __dmul_rn(v2, f), __dsub_rn(1.0, __dmul_rn(2.0, s))};
-            for (int c = 0; c < 3; ++c) cand[c] = X[c * N + k - 1] + (long long)rint(__dmul_rn(uh[c], 0x1p44));
+            for (int c = 0; c < 3; ++c)
+                cand[c] = X[c * N + k - 1] + (long long)rint(__dmul_rn(__dmul_rn(uh[c], a.init_bond), 0x1p44));
             bool ok = true;
             for (int j = 0; j < k - 1 && ok; ++j) {
                 const double dx = __dmul_rn((double)(cand[0] - X[j]), 0x1p-44);
                 const double dy = __dmul_rn((double)(cand[1] - X[N + j]), 0x1p-44);
                 const double dz = __dmul_rn((double)(cand[2] - X[2 * N + j]), 0x1p-44);
                 const double d2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
-                if (d2 < 0.81) ok = false;
+                if (d2 < a.init_d2min) ok = false;
             }
             if (ok) break;
         }
@@ -215,7 +227,6 @@ __global__ void __launch_bounds__(kMaxSweepBlock) k_sweep_polymer(const PolyArgs
     long long E = a.E[wr];
     int b = poly_bin(E, a);
     const uint32_t g0 = (uint32_t)a.state->sweep_counter;
-    const float R2 = 1.0f / a.fene_invR2;
     const int npl = (N + G - 1) / G;
     constexpr float kStep = (float)kPolyStepQ * 0x1p-44f;
     for (int64_t sw = 0; sw < a.sweeps; ++sw) {
@@ -252,7 +263,7 @@ __global__ void __launch_bounds__(kMaxSweepBlock) k_sweep_polymer(const PolyArgs
                     const float bx = (xn - xj) + (lxn - ljx), by = (yn - yj) + (lyn - ljy), bz = (zn - zj) + (lzn - ljz);
                     const float r2o = ax * ax + ay * ay + az * az;
                     const float r2n = bx * bx + by * by + bz * bz;
-                    broken = !(r2n < R2);
+                    broken = !fene_intact(r2n, a);
                     const float vo = fene_energy(r2o, a);
                     const float vn = broken ? vo : fene_energy(r2n, a);
                     s = vn - vo;

@@ -15,7 +15,9 @@ import paper_1312_2213_gb300 as m
 
 pytestmark = pytest.mark.gpu
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-WINDOWS = json.load(open(os.path.join(ROOT, "paper_1312_2213_gb300", "polymer_windows.json")))["windows"]
+_WJ = json.load(open(os.path.join(ROOT, "paper_1312_2213_gb300", "polymer_windows.json")))
+WINDOWS = _WJ["windows"]
+PAPER_WINDOWS = _WJ["paper_model"]["windows"]
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -26,13 +28,13 @@ def _gpu():
         pytest.skip("no CUDA device")
 
 
-def energy_scale(X):
+def energy_scale(X, model=0):
     """Sum over pairs of |pair energy| (the scale of the FP32 rounding of an energy)."""
     N = X.shape[0]
     s = 0.0
     for i in range(N):
         for j in range(i + 1, N):
-            s += abs(oracle.poly_pair(float(np.linalg.norm(X[i] - X[j])), j - i))
+            s += abs(oracle.poly_pair(float(np.linalg.norm(X[i] - X[j])), j - i, model))
     return s
 
 
@@ -187,3 +189,57 @@ def test_polymer_argument_errors():
         g.spins()
     with pytest.raises(m.MucaError):
         g.set_param("fene_R", -1.0)
+
+
+@pytest.mark.parametrize("N", [40, 80])
+def test_paper_model_init_bit_exact(N):
+    """Model 1 (the paper's Eq. 7 parameters): initial chains with bonds r0 = 0.7 are bit-identical
+    to the oracle's, energies within the FP32 tolerance."""
+    p = 24
+    lo, hi = PAPER_WINDOWS[str(N)]["e_lo"], PAPER_WINDOWS[str(N)]["e_hi"]
+    g = m.Muca(m.POLYMER3D, N, 0, p, 23, window=(lo, hi))
+    g.set_param("model", 1)
+    o = oracle.PolyRun(N, p, 23, lo, hi, model=1)
+    o.init()
+    np.testing.assert_array_equal(g.coords(), o.coords())
+    ge, oe = g.energies(), o.energy()
+    for w in range(0, p, 5):
+        assert abs(ge[w] - oe[w]) <= 1e-6 * energy_scale(o.coords()[w], 1) + 1e-9
+
+
+def test_paper_model_first_iteration_in_pilot_window():
+    """Model 1, N = 40, in its pilot window (walk-in, then ln W = 0): walkers without a near-tie or
+    bin-edge event in the oracle are bit-identical; the energy refresh drift stays small."""
+    N, p, S = 40, 48, 12
+    lo, hi = PAPER_WINDOWS[str(N)]["e_lo"], PAPER_WINDOWS[str(N)]["e_hi"]
+    g = m.Muca(m.POLYMER3D, N, 0, p, 29, window=(lo, hi))
+    g.set_param("model", 1)
+    o = oracle.PolyRun(N, p, 29, lo, hi, model=1)
+    o.init()
+    g.iterate(S)
+    g.merge_and_update()
+    o.iterate(S, 8)
+    o.update()
+    clean = o.walker_events().sum(axis=1) == 0
+    same = np.all(g.coords() == o.coords(), axis=(1, 2))
+    assert clean.mean() > 0.5 and np.all(same[clean])
+    assert g.drift() < 1e-3
+    ge, oe = g.energies(), o.energy()
+    X = o.coords()
+    for w in np.nonzero(clean)[0][:8]:
+        assert abs(ge[w] - oe[w]) <= 1e-6 * energy_scale(X[w], 1) + 1e-9
+
+
+def test_paper_model_state_round_trip():
+    """The model travels with the checkpoint."""
+    g = m.Muca(m.POLYMER3D, 40, 0, 8, 3, window=(PAPER_WINDOWS["40"]["e_lo"], PAPER_WINDOWS["40"]["e_hi"]))
+    g.set_param("model", 1)
+    g.iterate(3)
+    g.merge_and_update()
+    st = g.get_state()
+    h = m.Muca(m.POLYMER3D, 40, 0, 8, 3)
+    h.set_state(st)
+    np.testing.assert_array_equal(g.coords(), h.coords())
+    g.iterate(2)
+    h.iterate(2)
+    np.testing.assert_array_equal(g.coords(), h.coords())

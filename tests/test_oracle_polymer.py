@@ -84,3 +84,75 @@ def test_fene_dimer_density_of_states(orc):
     le = np.log(omega[seen])
     off = np.median(le - lo)
     assert np.max(np.abs(lo + off - le)) < 0.15
+
+
+def test_paper_model_pair_potentials(orc):
+    """Model 1 (Eq. 7 with K = 40, r0 = 0.7, r_max = 1): LJ zero at sigma = 2^(-1/6) r0 and
+    minimum -1 at r0 with zero slope; FENE zero at r0, symmetric about it, (K/2) R^2 ln 2 at
+    |r - r0| = R/sqrt(2), infinite at r0 +- R; no cutoff (LJ nonzero at r = 3)."""
+    r0, R, K = 0.7, 0.3, 40.0
+    sigma = 2.0 ** (-1.0 / 6.0) * r0
+    assert abs(orc.poly_pair(sigma, 2, 1)) < 1e-13
+    assert abs(orc.poly_pair(r0, 2, 1) + 1.0) < 1e-13
+    h = 1e-6
+    assert abs(orc.poly_pair(r0 + h, 2, 1) - orc.poly_pair(r0 - h, 2, 1)) < 1e-9
+    assert orc.poly_pair(r0 * 1.01, 2, 1) > -1.0 and orc.poly_pair(r0 * 0.99, 2, 1) > -1.0
+    assert orc.poly_pair(3.0, 2, 1) < 0.0
+    assert abs(orc.poly_pair(r0, 1, 1)) < 1e-15
+    d = R / math.sqrt(2.0)
+    want = 0.5 * K * R * R * math.log(2.0)
+    assert abs(orc.poly_pair(r0 + d, 1, 1) - want) < 1e-12
+    assert abs(orc.poly_pair(r0 - d, 1, 1) - want) < 1e-12
+    assert math.isinf(orc.poly_pair(r0 + R, 1, 1)) and math.isinf(orc.poly_pair(r0 - R, 1, 1))
+
+
+def test_paper_model_straight_chain_energy(orc):
+    """A straight chain with bonds r0: every bond contributes 0 and each pair at distance k r0
+    (k >= 2) contributes 4[(sigma/(k r0))^12 - (sigma/(k r0))^6] = 4[(1/2) k^-12 - ... ]:
+    with sigma^6 = r0^6 / 2 the pair term is 4[k^-12/4 - k^-6/2] = k^-12 - 2 k^-6."""
+    N, r0 = 12, 0.7
+    X = np.zeros((N, 3))
+    X[:, 0] = r0 * np.arange(N)
+    want = sum((N - k) * (k ** -12.0 - 2.0 * k ** -6.0) for k in range(2, N))
+    assert abs(orc.poly_energy(X, 1) - want) < 1e-12
+
+
+def test_paper_model_init_bonds(orc):
+    """Initial chains of model 1: bonds of length r0 = 0.7 (to the grid rounding), no bead
+    closer than 0.9 r0 to an earlier one, finite energy."""
+    P = orc.PolyRun(40, 6, 5, -1e6, 1e6, model=1)
+    P.init()
+    X = P.coords()
+    b = np.linalg.norm(np.diff(X, axis=1), axis=2)
+    assert np.all(np.abs(b - 0.7) < 1e-12)
+    for w in range(X.shape[0]):
+        d = np.linalg.norm(X[w][:, None, :] - X[w][None, :, :], axis=2)
+        iu = np.triu_indices(40, 2)
+        assert d[iu].min() >= 0.63 - 1e-12
+        assert abs(P.energy()[w] - orc.poly_energy(X[w], 1)) < 1e-9
+
+
+def test_paper_model_dimer_density_of_states(orc):
+    """N = 2 in model 1: the binned density of states of the shifted FENE bond against the closed
+    form (4 pi/3)[(r0 + R t)^3 - (r0 - R t)^3], t = sqrt(1 - exp(-2E/(K R^2))).  The top bins are
+    shells ~1e-3 thick that walkers enter rarely; with no thermalisation between iterations a
+    3000-sweep iteration still carries the previous weights' distribution there (up to 0.1 in
+    ln Omega), so the estimate comes from a final 30000-sweep iteration."""
+    e_lo, e_hi = 0.0, 6.0
+    P = orc.PolyRun(2, 64, 13, e_lo, e_hi, model=1)
+    P.init()
+    for _ in range(14):
+        P.iterate(3000, 8)
+        P.update()
+    P.iterate(30000, 8)
+    P.update()
+    edges = [e_lo + 0.1 * b for b in range(P.B + 1)]
+    omega = np.array(ex.fene_shifted_dimer_omega(edges, 40.0, 0.3, 0.7))
+    H = P.histogram().astype(float)
+    seen = H > 0
+    assert seen.mean() > 0.98
+    lo = np.log(H[seen]) - P.lnW_sampled()[seen]
+    le = np.log(omega[seen])
+    off = np.median(le - lo)
+    # each bin within 4 counting errors (1/sqrt(H)) plus the error of the fitted offset
+    assert np.all(np.abs(lo + off - le) < 4.0 / np.sqrt(H[seen]) + 0.03)
