@@ -34,6 +34,16 @@
  *   V_LJ(r)   = 4 [(sigma/r)^12 - (sigma/r)^6], sigma = 2^(-1/6) r0, no cutoff,
  *   V_FENE(r) = -(K/2) R^2 ln(1 - ((r - r0)/R)^2), |r - r0| < R, else +infinity,
  *   K = 40, r0 = 0.7, R = r_max - r0 = 0.3 (r_max = 1).
+ *
+ * Move set 1 (the paper combines single-bead shifts with spherical rotations):
+ * at bead i a second Philox block (counter (i, sweep, walker, tag 3)) picks the
+ * move: word 0 < 2^31 the shift above, else a spherical rotation.  The pivot is
+ * bead i+1 (i = 0), i-1 (i = N-1), otherwise i+1 if word 1 is odd, else i-1;
+ * bead i goes to pivot + d n, d = |r_i - r_pivot|, n a unit vector from
+ * Marsaglia's method on (word 2, word 3) and, after a rejected pair, on the
+ * words of blocks (64 i + t, sweep, walker, tag 4), two pairs a block, at most
+ * 64 pairs (none accepted: the move is rejected).  Every step is a correctly
+ * rounded binary64 operation, and the offset is rounded to the grid.
  */
 #include <math.h>
 #include <pthread.h>
@@ -45,6 +55,8 @@
 
 #define POLY_TAG_SWEEP 1u
 #define POLY_TAG_INIT 2u
+#define POLY_TAG_MOVE 3u
+#define POLY_TAG_SPHERE 4u
 #define POLY_STEP_Q 1229.0
 #define POLY_GRID 0x1p-44
 #define POLY_RC 2.5
@@ -56,6 +68,7 @@ typedef struct {
     uint64_t seed;
     double e_lo, e_hi, K, R, beta;
     int model;        /* 0: benchmark parameters, 1: the paper's (Eq. 7) */
+    int moves;        /* 0: single-bead shifts, 1: shifts and spherical rotations */
     double r0, sigma2; /* model 1: FENE rest length, LJ sigma^2 */
     int64_t sweep_counter;
     double *X;       /* p*N*3 */
@@ -138,7 +151,15 @@ static double poly_energy_P(const orc_poly *P, const double *X)
     return E;
 }
 
-static int poly_bin(const orc_poly *P, double E) { return (int)floor((E - P->e_lo) * 10.0); }
+/* Bin of E, clamped to [-1, B] (below / above the window) so that energies far
+ * outside it (overlapping beads) cannot overflow the conversion. */
+static int poly_bin(const orc_poly *P, double E)
+{
+    double t = floor((E - P->e_lo) * 10.0);
+    if (!(t >= -1.0)) return -1;
+    if (t > (double)P->B) return P->B;
+    return (int)t;
+}
 
 void *orc_poly_create(int N, int p, uint64_t seed, double e_lo, double e_hi, double K, double R, int record)
 {
@@ -179,6 +200,41 @@ int orc_poly_num_bins(void *h) { return ((orc_poly *)h)->B; }
 
 /* Canonical mode for the window pilot: weight exp(-beta E), no window. */
 void orc_poly_set_beta(void *h, double beta) { ((orc_poly *)h)->beta = beta; }
+
+void orc_poly_set_moves(void *h, int moves) { ((orc_poly *)h)->moves = moves; }
+
+/* Spherical rotation of bead i of walker w (move set 1): the new position on
+ * the grid in xn, or 0 if Marsaglia's method found no point in 64 pairs. */
+static int poly_rotation(const orc_poly *P, const double *X, int i, int w, uint32_t g, const uint32_t m[4],
+                         double xn[3])
+{
+    const int N = P->N;
+    uint32_t key[2] = {(uint32_t)(P->seed & 0xffffffffu), (uint32_t)(P->seed >> 32)};
+    int pv = (i == 0) ? 1 : (i == N - 1) ? N - 2 : ((m[1] & 1u) ? i + 1 : i - 1);
+    double v1 = 0.0, v2 = 0.0, s = 0.0;
+    int found = 0;
+    uint32_t blk[4] = {0, 0, m[2], m[3]};
+    for (int t = 0; t < 64 && !found; ++t) {
+        if (t > 0 && (t & 1) == 1) {
+            uint32_t ctr[4] = {(uint32_t)(64 * i + (t >> 1)), g, (uint32_t)w, POLY_TAG_SPHERE};
+            orc_philox4x32_10(ctr, key, blk);
+        }
+        uint32_t a = (t == 0) ? m[2] : blk[(t & 1) ? 0 : 2];
+        uint32_t b = (t == 0) ? m[3] : blk[(t & 1) ? 1 : 3];
+        v1 = (double)a * 0x1p-31 - 1.0;
+        v2 = (double)b * 0x1p-31 - 1.0;
+        s = v1 * v1 + v2 * v2;
+        found = (s < 1.0 && s > 0.0);
+    }
+    if (!found) return 0;
+    double f = 2.0 * sqrt(1.0 - s);
+    double n[3] = {v1 * f, v2 * f, 1.0 - 2.0 * s};
+    const double *xp = X + 3 * pv, *xi = X + 3 * i;
+    double dx = xi[0] - xp[0], dy = xi[1] - xp[1], dz = xi[2] - xp[2];
+    double d = sqrt((dx * dx + dy * dy) + dz * dz);
+    for (int a = 0; a < 3; ++a) xn[a] = xp[a] + nearbyint((n[a] * d) * 0x1p44) * POLY_GRID;
+    return 1;
+}
 
 /* Model 1: the paper's parameters (K = 40, r0 = 0.7, r_max = 1, LJ without cutoff);
  * before orc_poly_init. */
@@ -264,11 +320,18 @@ static void poly_walker_sweeps(orc_poly *P, int w, int64_t g0, int64_t sweeps, u
         for (int i = 0; i < N; ++i) {
             uint32_t ctr[4] = {(uint32_t)i, g, (uint32_t)w, POLY_TAG_SWEEP}, u[4];
             orc_philox4x32_10(ctr, key, u);
-            double xn[3];
-            for (int a = 0; a < 3; ++a)
-                xn[a] = X[3 * i + a] + (double)((int64_t)u[a] - 2147483648LL) * POLY_STEP_Q * POLY_GRID;
+            double xn[3] = {X[3 * i], X[3 * i + 1], X[3 * i + 2]};
+            int rotation = 0, broken = 0;
+            if (P->moves == 1) {
+                uint32_t mc[4] = {(uint32_t)i, g, (uint32_t)w, POLY_TAG_MOVE}, mw[4];
+                orc_philox4x32_10(mc, key, mw);
+                rotation = mw[0] >= 0x80000000u;
+                if (rotation && !poly_rotation(P, X, i, w, g, mw, xn)) broken = 1; /* no point: rejected */
+            }
+            if (!rotation)
+                for (int a = 0; a < 3; ++a)
+                    xn[a] = X[3 * i + a] + (double)((int64_t)u[a] - 2147483648LL) * POLY_STEP_Q * POLY_GRID;
             double dE = 0.0;
-            int broken = 0;
             for (int j = 0; j < N; ++j) {
                 if (j == i) continue;
                 int sep = abs(i - j);
