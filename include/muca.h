@@ -122,6 +122,12 @@ int muca_init_ex(muca_ctx **out, int system, int L_or_N, int q, int p, uint64_t 
  *                 (FENE with K = 40, r0 = 0.7, r_max = 1; LJ sigma = 2^(-1/6) r0,
  *                 no cutoff).  Redraws the initial chains (bond length r0 in
  *                 model 1); travels with muca_get_state.
+ *   "moves"       polymer, before the first iterate: 0 (default) = single-bead
+ *                 shifts; 1 = the paper's combination of shifts with spherical
+ *                 rotations (each attempt picks one with probability 1/2; a
+ *                 rotation puts the bead on a uniform point of the sphere about a
+ *                 bonded neighbour, keeping that bond's length, computed in
+ *                 correctly rounded binary64 and rounded to the coordinate grid).
  *   "lanes"       polymer: lanes of a warp per walker in the sweep, 8, 16 or 32
  *                 (32/lanes walkers share a warp); 0 (default) means 16.  The pair terms are
  *                 FP32 and their grouping over lanes changes their rounding, so

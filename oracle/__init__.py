@@ -111,6 +111,7 @@ def _bind_polymer(L):
         getattr(L, name).argtypes = [c.c_void_p, c.c_void_p]
     L.orc_poly_set_beta.argtypes = [c.c_void_p, c.c_double]
     L.orc_poly_set_model.argtypes = [c.c_void_p, c.c_int]
+    L.orc_poly_set_moves.argtypes = [c.c_void_p, c.c_int]
     L.orc_poly_reweight.argtypes = [c.c_void_p, c.c_double, c.c_void_p, c.c_void_p]
     L.orc_poly_get_walker_events.argtypes = [c.c_void_p, c.c_void_p]
     L.orc_poly_refresh_energy.argtypes = [c.c_void_p]
@@ -307,7 +308,7 @@ class PolyRun:
     """Oracle multicanonical run of a bead-spring polymer of N beads (p walkers)."""
 
     def __init__(self, N: int, p: int, seed: int, e_lo: float, e_hi: float, K: float = 40.0, R: float = 1.5,
-                 record: int = 0, beta: float = 0.0, model: int = 0):
+                 record: int = 0, beta: float = 0.0, model: int = 0, moves: int = 0):
         self._lib = lib()
         self.h = self._lib.orc_poly_create(N, p, seed, e_lo, e_hi, K, R, record)
         if not self.h:
@@ -318,6 +319,8 @@ class PolyRun:
             self._lib.orc_poly_set_beta(self.h, beta)
         if model:
             self._lib.orc_poly_set_model(self.h, model)
+        if moves:
+            self._lib.orc_poly_set_moves(self.h, moves)
 
     def __del__(self):
         if getattr(self, "h", None):

@@ -94,6 +94,7 @@ void orc_poly_free(void *h);
 int orc_poly_num_bins(void *h);
 void orc_poly_set_beta(void *h, double beta);
 void orc_poly_set_model(void *h, int model); /* 1: the paper's parameters (Eq. 7); before init */
+void orc_poly_set_moves(void *h, int moves); /* 1: shifts and spherical rotations */
 void orc_poly_init(void *h);
 void orc_poly_iterate(void *h, int64_t sweeps, int nthreads);
 void orc_poly_iterate_range(void *h, int64_t sweeps, int w0, int w1, int nthreads);

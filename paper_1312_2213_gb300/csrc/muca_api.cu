@@ -54,6 +54,7 @@ struct muca_ctx {
     int record = 0, block = 64, walker_offset = 0;
     int lanes = 0;     // polymer: lanes per walker in the sweep (8, 16, 32; 0 = chosen by N)
     int model = 0;     // polymer: 0 benchmark parameters, 1 the paper's (Eq. 7)
+    int moves = 0;     // polymer: 0 single-bead shifts, 1 shifts and spherical rotations
     int debug_drop_row = -1;  // test hook for the bounded waits (next spin iterate only)
     int recursion = 0;        // weight update: 0 accumulated statistics, 1 plain W/H
     int observables = 0;      // Ising: per-sweep sums of 1, |M|, M^2 per bin
@@ -254,6 +255,7 @@ PolyArgs poly_args(const muca_ctx *c, int64_t sweeps)
     a.elo_q = llrint(c->e_lo * 4294967296.0);                      // e_lo * 2^32
     a.ehi_q = a.elo_q + ((long long)c->B * 4294967296LL + 9) / 10;  // first energy with bin >= B
     a.model = c->model;
+    a.moves = c->moves;
     if (c->model == 1) {  // the paper's parameters of Eq. 7: K = 40, r0 = 0.7, r_max = 1, no LJ cutoff
         const double K = 40.0, r0 = 0.7, R = 0.3;
         a.fene_KR2_half = (float)(0.5 * K * R * R);
@@ -568,6 +570,13 @@ int muca_set_param(muca_ctx *c, const char *key, double v)
         const long long r = (long long)v;
         if ((double)r != v || r < 0 || r > 0x7fffffffLL) return fail(MUCA_ERR_ARG, "debug_drop_row must be >= 0");
         c->debug_drop_row = (int)r;
+        return MUCA_OK;
+    }
+    if (k == "moves") {
+        if (c->system != kPolymer) return fail(MUCA_ERR_ARG, "moves applies to the polymer only");
+        if (locked) return fail(MUCA_ERR_STATE, "moves must be set before the first iterate");
+        if (v != 0.0 && v != 1.0) return fail(MUCA_ERR_ARG, "moves must be 0 or 1");
+        c->moves = (int)v;
         return MUCA_OK;
     }
     if (k == "model") {

@@ -21,6 +21,8 @@ constexpr uint32_t kPhiloxW1 = 0xBB67AE85u;
 constexpr uint32_t kTagInit = 0u;
 constexpr uint32_t kTagSweep = 1u;
 constexpr uint32_t kTagPolyInit = 2u;
+constexpr uint32_t kTagPolyMove = 3u;    // polymer move set 1: move choice, pivot, first sphere pair
+constexpr uint32_t kTagPolySphere = 4u;  // polymer move set 1: further sphere pairs
 
 __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1)
 {

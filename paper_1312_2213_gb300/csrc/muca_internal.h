@@ -107,6 +107,7 @@ struct PolyArgs {
     long long elo_q, ehi_q;        // window [elo_q, ehi_q): bins 0..B-1
     float fene_KR2_half, fene_invR2, lj_rc2, lj_shift;
     int model;                     // 0: benchmark parameters, 1: the paper's (Eq. 7)
+    int moves;                     // 0: single-bead shifts, 1: shifts and spherical rotations
     float fene_r0, fene_invR, lj_sigma2;  // model 1: rest length, 1/R, sigma^2 (model 0: 0, -, 1)
     double init_bond, init_d2min;  // initial bond length b0 and (0.9 b0)^2
     int64_t sweeps;

@@ -200,10 +200,49 @@ __device__ __forceinline__ bool group_any(bool p, int gi)
     return G == 32 ? bal != 0u : ((bal >> (gi * G)) & ((1u << (G & 31)) - 1u)) != 0u;
 }
 
+// Spherical rotation of bead i (move set 1): the pivot is a bonded neighbour,
+// the new position pivot + d n with d = |r_i - r_pivot| and n a unit vector from
+// Marsaglia's method on (m.z, m.w) and then on tag-4 blocks (64 i + t), two pairs
+// a block, at most 64 pairs.  Every step is a correctly rounded binary64
+// operation on exact grid values, so the new grid position is bit-identical to
+// any implementation that follows the same steps.  Returns false when no point
+// was found (the move is then rejected).
+__device__ bool poly_rotation(const long long *Xg, int N, int i, uint32_t g, uint32_t wid, const uint4 m,
+                              const uint32_t (&rk)[20], long long out[3])
+{
+    const int pv = (i == 0) ? 1 : (i == N - 1) ? N - 2 : ((m.y & 1u) ? i + 1 : i - 1);
+    double v1 = 0.0, v2 = 0.0, s = 0.0;
+    bool found = false;
+    uint4 blk = make_uint4(0u, 0u, m.z, m.w);
+    for (int t = 0; t < 64 && !found; ++t) {
+        if (t & 1) blk = philox4x32_10_rk(make_uint4((uint32_t)(64 * i + (t >> 1)), g, wid, kTagPolySphere), rk);
+        const uint32_t aw = (t == 0) ? m.z : ((t & 1) ? blk.x : blk.z);
+        const uint32_t bw = (t == 0) ? m.w : ((t & 1) ? blk.y : blk.w);
+        v1 = __dsub_rn(__dmul_rn((double)aw, 0x1p-31), 1.0);
+        v2 = __dsub_rn(__dmul_rn((double)bw, 0x1p-31), 1.0);
+        s = __dadd_rn(__dmul_rn(v1, v1), __dmul_rn(v2, v2));
+        found = s < 1.0 && s > 0.0;
+    }
+    if (!found) return false;
+    const double f = __dmul_rn(2.0, __dsqrt_rn(__dsub_rn(1.0, s)));
+    const double n[3] = {__dmul_rn(v1, f), __dmul_rn(v2, f), __dsub_rn(1.0, __dmul_rn(2.0, s))};
+    double dd[3];
+    long long P[3];
+    for (int c = 0; c < 3; ++c) {
+        P[c] = Xg[c * N + pv];
+        dd[c] = __dmul_rn((double)(Xg[c * N + i] - P[c]), 0x1p-44);
+    }
+    const double d = __dsqrt_rn(
+        __dadd_rn(__dadd_rn(__dmul_rn(dd[0], dd[0]), __dmul_rn(dd[1], dd[1])), __dmul_rn(dd[2], dd[2])));
+    for (int c = 0; c < 3; ++c) out[c] = P[c] + (long long)rint(__dmul_rn(__dmul_rn(n[c], d), 0x1p44));
+    return true;
+}
+
 // Sweeps: G lanes per walker, 32/G walkers a warp, all on the same bead i.  A
 // walker's float-pair shadows and this sweep's Philox blocks live in shared
-// memory (40 N bytes); its int64 master coordinates stay in global memory (read
-// at the sweep start and for the moved bead, written on acceptance).  The two
+// memory (40 N bytes, 56 N with rotations); its int64 master coordinates stay in
+// global memory (read at the sweep start and for the moved bead, written on
+// acceptance).  The two
 // bonds of bead i (FENE) are taken by lanes 0 and 1 of the group, the other
 // partners (LJ, |i - j| >= 2) by lanes j mod G, so no lane runs both branches.
 template <int G, int RECORD>
@@ -217,6 +256,7 @@ __global__ void __launch_bounds__(kMaxSweepBlock) k_sweep_polymer(const PolyArgs
     float *xs = (float *)smem + (size_t)slot * 6 * N;
     float *xl = xs + 3 * N;
     uint4 *su = (uint4 *)(smem + (size_t)spb * 6 * N * sizeof(float)) + (size_t)slot * N;
+    uint4 *sm = (uint4 *)(smem + (size_t)spb * N * (6 * sizeof(float) + sizeof(uint4))) + (size_t)slot * N;  // moves
     const int w0 = (blockIdx.x * wpb + wib) * W;
     if (w0 >= a.p) return;  // whole warps only; no block-wide barrier follows
     const int w = w0 + gi;
@@ -237,6 +277,7 @@ __global__ void __launch_bounds__(kMaxSweepBlock) k_sweep_polymer(const PolyArgs
             grid_to_ff(Xg[N + j] - A1, xs[N + j], xl[N + j]);
             grid_to_ff(Xg[2 * N + j] - A2, xs[2 * N + j], xl[2 * N + j]);
             su[j] = philox4x32_10_rk(make_uint4((uint32_t)j, g, wid, kTagSweep), a.rk);
+            if (a.moves) sm[j] = philox4x32_10_rk(make_uint4((uint32_t)j, g, wid, kTagPolyMove), a.rk);
         }
         __syncwarp();
 #pragma unroll 1
@@ -250,10 +291,28 @@ __global__ void __launch_bounds__(kMaxSweepBlock) k_sweep_polymer(const PolyArgs
             const float xo = xs[i], yo = xs[N + i], zo = xs[2 * N + i];
             const float lxo = xl[i], lyo = xl[N + i], lzo = xl[2 * N + i];
             const float dx = (float)sx * kStep, dy = (float)sy * kStep, dz = (float)sz * kStep;
-            const float xn = xo + dx, yn = yo + dy, zn = zo + dz;
-            const float lxn = lxo + ((xo - xn) + dx), lyn = lyo + ((yo - yn) + dy), lzn = lzo + ((zo - zn) + dz);
+            float xn = xo + dx, yn = yo + dy, zn = zo + dz;
+            float lxn = lxo + ((xo - xn) + dx), lyn = lyo + ((yo - yn) + dy), lzn = lzo + ((zo - zn) + dz);
+            long long n0 = X0 + (long long)sx * kPolyStepQ, n1 = X1 + (long long)sy * kPolyStepQ,
+                      n2 = X2 + (long long)sz * kPolyStepQ;
             float s = 0.0f, c = 0.0f;
             bool broken = false;
+            if (a.moves) {
+                const uint4 mv = sm[i];
+                if (mv.x >= 0x80000000u) {  // spherical rotation about a bonded neighbour
+                    long long nr[3];
+                    if (poly_rotation(Xg, N, i, g, wid, mv, a.rk, nr)) {
+                        n0 = nr[0];
+                        n1 = nr[1];
+                        n2 = nr[2];
+                        grid_to_ff(n0 - A0, xn, lxn);
+                        grid_to_ff(n1 - A1, yn, lyn);
+                        grid_to_ff(n2 - A2, zn, lzn);
+                    } else {
+                        broken = true;  // no point in 64 pairs: rejected
+                    }
+                }
+            }
             {
                 const int jb = (li == 0) ? i - 1 : i + 1;
                 if (li < 2 && jb >= 0 && jb < N) {
@@ -263,7 +322,7 @@ __global__ void __launch_bounds__(kMaxSweepBlock) k_sweep_polymer(const PolyArgs
                     const float bx = (xn - xj) + (lxn - ljx), by = (yn - yj) + (lyn - ljy), bz = (zn - zj) + (lzn - ljz);
                     const float r2o = ax * ax + ay * ay + az * az;
                     const float r2n = bx * bx + by * by + bz * bz;
-                    broken = !fene_intact(r2n, a);
+                    broken = broken || !fene_intact(r2n, a);
                     const float vo = fene_energy(r2o, a);
                     const float vn = broken ? vo : fene_energy(r2n, a);
                     s = vn - vo;
@@ -313,9 +372,9 @@ __global__ void __launch_bounds__(kMaxSweepBlock) k_sweep_polymer(const PolyArgs
             if (acc) {
                 if (li == 0) {
                     if (active) {
-                        Xg[i] = X0 + (long long)sx * kPolyStepQ;
-                        Xg[N + i] = X1 + (long long)sy * kPolyStepQ;
-                        Xg[2 * N + i] = X2 + (long long)sz * kPolyStepQ;
+                        Xg[i] = n0;
+                        Xg[N + i] = n1;
+                        Xg[2 * N + i] = n2;
                     }
                     xs[i] = xn;
                     xs[N + i] = yn;
@@ -383,7 +442,7 @@ template <int G>
 static cudaError_t launch_g(const PolyArgs &a, int block, cudaStream_t s)
 {
     const int wpb = block / 32, spb = wpb * (32 / G);
-    const size_t smem = (size_t)spb * a.N * (6 * sizeof(float) + sizeof(uint4));
+    const size_t smem = (size_t)spb * a.N * (6 * sizeof(float) + (a.moves ? 2 : 1) * sizeof(uint4));
     const int nblk = (a.p + spb - 1) / spb;
     cudaError_t e;
     if (a.record == 0) {

@@ -243,3 +243,25 @@ def test_paper_model_state_round_trip():
     g.iterate(2)
     h.iterate(2)
     np.testing.assert_array_equal(g.coords(), h.coords())
+
+
+@pytest.mark.parametrize("model,N", [(0, 13), (1, 40)])
+def test_rotation_moves_first_iteration_bit_exact(model, N):
+    """Move set 1 (shifts and spherical rotations, binary64 rotations rounded to the grid): walkers
+    without a near-tie or bin-edge event in the oracle follow bit-identical trajectories."""
+    p, S = 48, 12
+    W = PAPER_WINDOWS if model == 1 else WINDOWS
+    lo, hi = W[str(N)]["e_lo"], W[str(N)]["e_hi"]
+    g = m.Muca(m.POLYMER3D, N, 0, p, 31, window=(lo, hi))
+    g.set_param("model", model)
+    g.set_param("moves", 1)
+    o = oracle.PolyRun(N, p, 31, lo, hi, model=model, moves=1)
+    o.init()
+    g.iterate(S)
+    g.merge_and_update()
+    o.iterate(S, 8)
+    o.update()
+    clean = o.walker_events().sum(axis=1) == 0
+    same = np.all(g.coords() == o.coords(), axis=(1, 2))
+    assert clean.mean() > 0.5 and np.all(same[clean])
+    assert g.drift() < 1e-3 * max(1.0, N / 13)

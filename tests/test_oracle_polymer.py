@@ -156,3 +156,68 @@ def test_paper_model_dimer_density_of_states(orc):
     off = np.median(le - lo)
     # each bin within 4 counting errors (1/sqrt(H)) plus the error of the fitted offset
     assert np.all(np.abs(lo + off - le) < 4.0 / np.sqrt(H[seen]) + 0.03)
+
+
+@pytest.mark.parametrize("model", [0, 1])
+def test_rotation_moves_are_exact_and_energy_tracks(orc, model):
+    """Move set 1 (shifts and spherical rotations): coordinates stay on the 2^-44 grid and the
+    running energy equals the energy from scratch."""
+    N = 40 if model == 1 else 13
+    lo, hi = (-143.3, -4.2) if model == 1 else (33.3, 87.3)
+    P = orc.PolyRun(N, 8, 9, lo, hi, model=model, moves=1)
+    P.init()
+    for _ in range(3):
+        P.iterate(100, 8)
+        P.update()
+    X = P.coords()
+    assert np.all(X * 2.0 ** 44 == np.round(X * 2.0 ** 44))
+    E = P.energy()
+    for w in range(8):
+        assert E[w] == pytest.approx(orc.poly_energy(X[w], model), abs=1e-8)
+    assert P.refresh_energy() < 1e-8
+
+
+def test_rotation_directions_are_uniform(orc):
+    """N = 2 at beta -> 0 with rotations: every rotation keeps the bond length and puts the bond
+    on a uniform point of the sphere, so cos(theta) of the bond is uniform on [-1, 1] and its
+    azimuth uniform on [-pi, pi) (a wrong Marsaglia formula would bias either)."""
+    P = orc.PolyRun(2, 512, 21, -1e6, 1e6, beta=1e-12, moves=1)
+    P.init()
+    c, phi = [], []
+    for _ in range(40):
+        P.iterate(5, 8)
+        X = P.coords()
+        b = X[:, 1, :] - X[:, 0, :]
+        c.extend((b[:, 2] / np.linalg.norm(b, axis=1)).tolist())
+        phi.extend(np.arctan2(b[:, 1], b[:, 0]).tolist())
+    c, phi = np.array(c), np.array(phi)
+    hc, _ = np.histogram(c, bins=10, range=(-1, 1))
+    hp, _ = np.histogram(phi, bins=10, range=(-np.pi, np.pi))
+    for h in (hc, hp):
+        e = h.sum() / 10
+        assert ((h - e) ** 2 / e).sum() < 40  # 9 dof; samples are correlated, so a loose bound
+
+
+def test_rotation_keeps_the_dimer_density_of_states(orc):
+    """The shifted-FENE dimer (model 1) sampled with shifts and rotations reproduces the same
+    closed-form density of states (rotations keep the bond length; shifts make it ergodic).
+    Only half of the moves change the bond length here, so counts in the thin top shells are
+    correlated over longer times than 1/sqrt(H) assumes: the bound is 0.1 in ln Omega (three
+    seeds average to within 0.04 of the closed form in every bin)."""
+    e_lo, e_hi = 0.0, 6.0
+    P = orc.PolyRun(2, 64, 17, e_lo, e_hi, model=1, moves=1)
+    P.init()
+    for _ in range(14):
+        P.iterate(3000, 8)
+        P.update()
+    P.iterate(30000, 8)
+    P.update()
+    edges = [e_lo + 0.1 * b for b in range(P.B + 1)]
+    omega = np.array(ex.fene_shifted_dimer_omega(edges, 40.0, 0.3, 0.7))
+    H = P.histogram().astype(float)
+    seen = H > 0
+    assert seen.mean() > 0.98
+    lo = np.log(H[seen]) - P.lnW_sampled()[seen]
+    le = np.log(omega[seen])
+    off = np.median(le - lo)
+    assert np.max(np.abs(lo + off - le)) < 0.1
