@@ -158,6 +158,22 @@ int muca_iterate(muca_ctx *ctx, int64_t sweeps);
  * every reachable bin of H^(n) is non-zero and min/mean >= flat_ratio. */
 int muca_merge_and_update(muca_ctx *ctx, int *is_flat);
 
+/* Sharded runs: one system's walkers split over processes (typically one per
+ * GPU), the paper's Fig. 1 scheme with the histogram exchange as an all-reduce.
+ * Each shard is a context with the same system, L, q and seed, holding p_k
+ * walkers and "walker_offset" = the global id of its first walker.  After
+ * muca_iterate, muca_merge_open sums this shard's open histogram (its walkers'
+ * counts since the last update) into the caller's DEVICE buffer dev_H_out (B
+ * uint64, overwritten) and clears it in the context; the caller adds the
+ * buffers of all shards (e.g. torch.distributed.all_reduce) and muca_update_with
+ * closes the iteration on every shard with the summed histogram dev_H (the same
+ * recursion and thresholds as muca_merge_and_update), so all shards keep
+ * identical weights and together equal one context that holds all walkers.
+ * Observable sums (if recorded) stay per shard.  is_flat as in
+ * muca_merge_and_update.  Errors: MUCA_ERR_ARG on a NULL buffer. */
+int muca_merge_open(muca_ctx *ctx, uint64_t *dev_H_out);
+int muca_update_with(muca_ctx *ctx, const uint64_t *dev_H, int *is_flat);
+
 /* Number of histogram bins B of the context. */
 int muca_num_bins(const muca_ctx *ctx, int *nbins);
 

@@ -21,6 +21,7 @@ __all__ = ["Muca", "MucaError", "ISING2D", "POTTS2D", "ISING2D_MUMA", "POLYMER3D
            "muca_init", "muca_init_ex", "muca_workspace_size", "muca_set_param", "muca_set_stream",
            "muca_iterate", "muca_merge_and_update", "muca_num_bins", "muca_get_lnW", "muca_get_lnW_sampled",
            "muca_get_histogram", "muca_get_flatness", "muca_get_reweight", "muca_get_observables",
+           "muca_merge_open", "muca_update_with",
            "muca_get_state", "muca_set_state",
            "muca_get_spins", "muca_get_walker_bins", "muca_get_thresholds", "muca_get_sweep_counter",
            "muca_synchronize", "muca_free", "muca_last_error", "muca_det_math",
@@ -96,6 +97,17 @@ def muca_get_histogram(h, out: np.ndarray):
 
 def muca_get_flatness(h, out: np.ndarray):
     check(load().muca_get_flatness(h, _p(out)), "muca_get_flatness")
+
+
+def muca_merge_open(h, dev_ptr: int):
+    check(load().muca_merge_open(h, ctypes.c_void_p(dev_ptr)), "muca_merge_open")
+
+
+def muca_update_with(h, dev_ptr: int, want_flat: bool = False):
+    flat = ctypes.c_int(0)
+    check(load().muca_update_with(h, ctypes.c_void_p(dev_ptr), ctypes.byref(flat) if want_flat else None),
+          "muca_update_with")
+    return bool(flat.value) if want_flat else None
 
 
 def muca_get_observables(h, beta: float, out: np.ndarray, sums: np.ndarray | None = None):

@@ -33,6 +33,8 @@ PROTOTYPES = {
     "muca_get_flatness": (c_int, [c_vp, c_vp]),
     "muca_get_reweight": (c_int, [c_vp, c_dbl, c_vp, c_vp]),
     "muca_get_observables": (c_int, [c_vp, c_dbl, c_vp, c_vp, c_int]),
+    "muca_merge_open": (c_int, [c_vp, c_vp]),
+    "muca_update_with": (c_int, [c_vp, c_vp, c_vp]),
     "muca_get_state": (c_int, [c_vp, c_vp, P(c_sz)]),
     "muca_set_state": (c_int, [c_vp, c_vp, c_sz]),
     "muca_get_spins": (c_int, [c_vp, c_vp, c_i64]),

@@ -12,10 +12,24 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "muca.h"
 #include "muca_internal.h"
 
 using namespace muca;
+
+namespace {
+
+// NVTX range for the duration of a C call (visible in profilers; free otherwise).
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
+
+}  // namespace
 
 namespace {
 
@@ -614,6 +628,7 @@ int muca_set_stream(muca_ctx *c, void *stream)
 
 int muca_iterate(muca_ctx *c, int64_t sweeps)
 {
+    NvtxRange nvtx("muca_iterate");
     if (int rc = check_ctx(c)) return rc;
     if (sweeps < 1) return fail(MUCA_ERR_ARG, "sweeps must be >= 1");
     if (c->system == kPolymer) {
@@ -665,6 +680,7 @@ int muca_iterate(muca_ctx *c, int64_t sweeps)
 
 int muca_merge_and_update(muca_ctx *c, int *is_flat)
 {
+    NvtxRange nvtx("muca_merge_and_update");
     if (int rc = check_ctx(c)) return rc;
     UpdateArgs a = update_args(c);
     MUCA_CUDA(launch_merge(a, c->stream));
@@ -674,6 +690,45 @@ int muca_merge_and_update(muca_ctx *c, int *is_flat)
     } else {
         MUCA_CUDA(launch_thresholds(a, c->stream));
         if (c->observables) {  // the sums just filled belong to the weights of this update
+            const size_t bytes = sizeof(unsigned long long) * 3 * (size_t)c->B;
+            MUCA_CUDA(cudaMemcpyAsync(c->obs + 3 * (size_t)c->B, c->obs, bytes, cudaMemcpyDeviceToDevice, c->stream));
+            MUCA_CUDA(cudaMemsetAsync(c->obs, 0, bytes, c->stream));
+        }
+    }
+    c->started = true;
+    c->open = false;
+    if (is_flat) {
+        int f = 0;
+        if (int rc = d2h(c, &f, &c->state->flat, sizeof(int))) return rc;
+        *is_flat = f;
+    }
+    return MUCA_OK;
+}
+
+int muca_merge_open(muca_ctx *c, uint64_t *dev_H_out)
+{
+    NvtxRange nvtx("muca_merge_open");
+    if (int rc = check_ctx(c)) return rc;
+    if (!dev_H_out) return fail(MUCA_ERR_ARG, "dev_H_out is NULL");
+    UpdateArgs a = update_args(c);
+    a.H = (unsigned long long *)dev_H_out;  // block slots summed (and cleared) into the caller's buffer
+    MUCA_CUDA(launch_merge(a, c->stream));
+    return MUCA_OK;
+}
+
+int muca_update_with(muca_ctx *c, const uint64_t *dev_H, int *is_flat)
+{
+    NvtxRange nvtx("muca_update_with");
+    if (int rc = check_ctx(c)) return rc;
+    if (!dev_H) return fail(MUCA_ERR_ARG, "dev_H is NULL");
+    MUCA_CUDA(cudaMemcpyAsync(c->H, dev_H, sizeof(unsigned long long) * c->B, cudaMemcpyDeviceToDevice, c->stream));
+    UpdateArgs a = update_args(c);
+    MUCA_CUDA(launch_recursion(a, c->stream));
+    if (c->system == kPolymer) {
+        MUCA_CUDA(launch_poly_lnwq(c->lnW, c->lnWq, c->B, c->stream));
+    } else {
+        MUCA_CUDA(launch_thresholds(a, c->stream));
+        if (c->observables) {  // this shard's own sums (observables are not exchanged)
             const size_t bytes = sizeof(unsigned long long) * 3 * (size_t)c->B;
             MUCA_CUDA(cudaMemcpyAsync(c->obs + 3 * (size_t)c->B, c->obs, bytes, cudaMemcpyDeviceToDevice, c->stream));
             MUCA_CUDA(cudaMemsetAsync(c->obs, 0, bytes, c->stream));
@@ -1145,6 +1200,7 @@ int muca_batch_create(muca_ctx *const *systems, int n, muca_batch **out)
 
 int muca_batch_run(muca_batch *b, int n_iter, int64_t sweeps, int use_graph)
 {
+    NvtxRange nvtx(use_graph ? "muca_batch_run (graph)" : "muca_batch_run");
     if (!b) return fail(MUCA_ERR_ARG, "batch is NULL");
     if (n_iter < 1 || sweeps < 1) return fail(MUCA_ERR_ARG, "n_iter and sweeps must be >= 1");
     const int n = (int)b->sys.size();

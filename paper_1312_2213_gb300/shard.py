@@ -1,0 +1,61 @@
+"""One system whose walkers are split over processes, typically one per GPU: the paper's Fig. 1
+scheme with the per-iteration exchange as a single all-reduce of the histogram.
+
+Rank r of a group of size n runs walkers [r p / n, (r+1) p / n) of the system as a context with
+`walker_offset` set to its first walker, so its random streams are exactly those the walkers
+have in one context of all p.  After the sweeps each rank sums its open histogram into a device
+buffer (`muca_merge_open`), the buffers are added with `torch.distributed.all_reduce` (NCCL on
+the device buffer; other backends through a host copy), and every rank closes the iteration with
+the summed histogram (`muca_update_with`).  The ranks then hold identical weights, and together
+equal one context of all walkers bit for bit.
+
+A rank that fails is seen by the others as a failing collective.  The survivors can carry on in
+a new group (`set_group`): their walkers keep their state, and from then on the merge runs over
+the surviving walkers only.
+"""
+from __future__ import annotations
+
+import torch
+import torch.distributed as dist
+
+from . import Muca, muca_merge_open, muca_update_with
+
+
+def shard_range(p: int, rank: int, world: int) -> tuple[int, int]:
+    """Contiguous walker range [w0, w1) of a rank."""
+    return rank * p // world, (rank + 1) * p // world
+
+
+class ShardedMuca:
+    def __init__(self, system: int, L: int, q: int, p: int, seed: int, group=None, **kw):
+        self.group = group
+        rank, world = dist.get_rank(group), dist.get_world_size(group)
+        self.w0, self.w1 = shard_range(p, rank, world)
+        if self.w1 <= self.w0:
+            raise ValueError("more ranks than walkers")
+        self.ctx = Muca(system, L, q, self.w1 - self.w0, seed, walker_offset=self.w0, **kw)
+        self.B = self.ctx.B
+        self.buf = torch.zeros(self.B, dtype=torch.int64, device="cuda")
+
+    def set_group(self, group):
+        """Continue in another process group (e.g. the survivors after a rank failed)."""
+        self.group = group
+
+    def iterate(self, sweeps: int):
+        self.ctx.iterate(sweeps)
+
+    def merge_and_update(self, want_flat: bool = False):
+        """Sum the open histograms of all ranks and close the iteration on this rank."""
+        muca_merge_open(self.ctx.h, self.buf.data_ptr())
+        self.ctx.synchronize()  # the buffer is read by torch below
+        if dist.get_backend(self.group) == "nccl":
+            dist.all_reduce(self.buf, group=self.group)
+        else:
+            host = self.buf.cpu()
+            dist.all_reduce(host, group=self.group)
+            self.buf.copy_(host)
+        torch.cuda.synchronize()
+        return muca_update_with(self.ctx.h, self.buf.data_ptr(), want_flat)
+
+    def close(self):
+        self.ctx.close()
