@@ -248,6 +248,7 @@ class Muca:
             muca_set_param(self.h, "block", block)
         if walker_offset:
             muca_set_param(self.h, "walker_offset", walker_offset)
+        self.window = window
         if window is not None:
             muca_set_param(self.h, "e_lo", window[0])
             muca_set_param(self.h, "e_hi", window[1])
