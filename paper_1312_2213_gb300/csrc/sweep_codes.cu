@@ -10,7 +10,8 @@ namespace muca {
 // Producer/consumer form with precomputed site codes (Ising and MUMA).
 // Shared memory holds the same threshold + histogram rows as above.  The
 // producer warp writes, per row, the walkers' random
-// words, their old row and, for every site, two column bytes: c0 for "left
+// words (clamped, see clamp_words), their old row and, for every site, two column
+// bytes holding 4 c (byte offsets into a threshold row): c0 for "left
 // neighbour as it was" and c1 for "left neighbour flipped", both without the up
 // neighbour (which only the consumer knows: the row above is final only after
 // the consumer has swept it) and, for the last site, without its right
@@ -35,6 +36,19 @@ template <int L, int WR>
 __device__ __forceinline__ uint32_t row_bit(const uint32_t (&r)[WR], int x)
 {
     return (r[x >> 5] >> (x & 31)) & 1u;
+}
+
+// The random words handed to a code-form consumer are min(u, 2^32 - 2).  With
+// that clamp the acceptance "T == always or u < T" becomes the single compare
+// u' < T: for T = 2^32 - 1 (always) every u' is below it, and for any smaller T
+// the only changed word, 2^32 - 1, is rejected before and after.
+__device__ __forceinline__ uint4 clamp_words(uint4 u)
+{
+    u.x = min(u.x, 0xFFFFFFFEu);
+    u.y = min(u.y, 0xFFFFFFFEu);
+    u.z = min(u.z, 0xFFFFFFFEu);
+    u.w = min(u.w, 0xFFFFFFFEu);
+    return u;
 }
 
 // Producer warps per consumer warp in the code forms.  One Philox4x32-10 block
@@ -118,7 +132,7 @@ __device__ __forceinline__ void produce_sweep_tn(uint32_t g, uint32_t wid, const
         constexpr int g_lo = PART * G / kCodeProducers, g_hi = (PART + 1) * G / kCodeProducers;
 #pragma unroll
         for (int gq = g_lo; gq < g_hi; ++gq) {
-            wu[gq * 32] = philox4x32_10_rk(make_uint4((uint32_t)(y * G + gq), g, wid, kTagSweep), rk);
+            wu[gq * 32] = clamp_words(philox4x32_10_rk(make_uint4((uint32_t)(y * G + gq), g, wid, kTagSweep), rk));
             const int x = 4 * gq;
             const uint32_t s4 = row_nibble<L, WR>(o, x);
             // left neighbours x-1..x+2 and right neighbours x+1..x+4 (periodic in x)
@@ -130,10 +144,11 @@ __device__ __forceinline__ void produce_sweep_tn(uint32_t g, uint32_t wid, const
             const uint32_t A = nib_to_bytes(l4) ^ S;  // left anti-aligned
             const uint32_t Bq = nib_to_bytes(r4) ^ S;
             const uint32_t D = nib_to_bytes(row_nibble<L, WR>(d, x)) ^ S;
-            const uint32_t k0 = 0x04040404u - (A + Bq + D);  // 4 - anti-aligned (without up), per byte
-            const uint32_t k1 = k0 + 2u * A - 0x01010101u;   // left neighbour flipped
+            // columns as byte offsets (4 c) into a threshold row, per byte
+            const uint32_t k0 = (0x04040404u - (A + Bq + D)) << 2;  // 4 - anti-aligned (without up)
+            const uint32_t k1 = k0 + 8u * A - 0x04040404u;          // left neighbour flipped
             if (SYS == kMuma) {
-                const uint32_t s5 = S * 5u;
+                const uint32_t s5 = S * 20u;
                 wc[gq * 32] = make_uint2(s5 + k0, s5 + k1);
             } else {
                 wc[gq * 32] = make_uint2(k0, k1);
@@ -161,12 +176,20 @@ __device__ __forceinline__ void ising_sweep_tc(uint32_t *__restrict__ lat, int p
     constexpr int RS = C + 1;
     constexpr int G = L / 4;
     constexpr size_t SU = (size_t)G * 32, SC = (size_t)G * 32, SR = (size_t)WR * 32;
-    // bin-row move of an accepted flip, from its column: Ising (c - 2) rows,
-    // MUMA one row down for s = +1 (c < 5) and one up for s = -1
-    auto move = [](uint32_t c) -> int {
-        return (SYS == kMuma) ? ((c >= 5u) ? RS : -RS) : ((int)c - 2) * RS;
+    // The chain works in 32-bit shared-window byte addresses: bB = table base + 4 RS bin and the
+    // producer's columns are 4 c, so a threshold address is one add and the bin's histogram
+    // counter an immediate offset from the (already updated) bin address.
+    const int sbase = (int)__cvta_generic_to_shared(sTH);
+    auto th = [](int addr) -> uint32_t {
+        uint32_t v;
+        asm("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(addr));
+        return v;
     };
-    uint32_t up[WR], cur[WR];
+    // bin-row move of an accepted flip in bytes: Ising (c - 2) rows from the column,
+    // MUMA one row up for s = +1 and one down for s = -1 (the old spin of the site)
+    auto move = [](uint32_t cb) -> int { return ((int)cb - 8) * RS; };
+    int bB = sbase + bR * 4;
+    uint32_t up[WR], cur[WR], old[WR];
 #pragma unroll
     for (int j = 0; j < WR; ++j) up[j] = lat[((L - 1) * WR + j) * ps];
 #pragma unroll 1
@@ -185,21 +208,21 @@ __device__ __forceinline__ void ising_sweep_tc(uint32_t *__restrict__ lat, int p
 #pragma unroll
         for (int j = 0; j < WR; ++j) {
             cur[j] = rr[j * 32];
+            old[j] = cur[j];
             ua[j] = up[j] ^ cur[j];  // up neighbour anti-aligned
         }
         const uint32_t sLast = row_bit<L, WR>(cur, L - 1);
         uint2 cd = rc[0];
         {
-            const uint32_t u4 = nib_to_bytes(row_nibble<L, WR>(ua, 0));
+            const uint32_t u4 = nib_to_bytes(row_nibble<L, WR>(ua, 0)) << 2;
             cd.x -= u4;
             cd.y -= u4;
         }
         uint2 cdn = cd;
         const uint32_t c00 = cd.x & 0xffu;
-        uint32_t T0 = sTH[bR + (int)c00], T1 = 0u;
+        uint32_t T0 = th(bB + (int)c00), T1 = 0u;
         int d0 = move(c00), d1 = 0;
         bool accP = false;
-        int dRp = 0;
         uint4 u = make_uint4(0u, 0u, 0u, 0u);
 #pragma unroll
         for (int x = 0; x < L; ++x) {
@@ -209,37 +232,39 @@ __device__ __forceinline__ void ising_sweep_tc(uint32_t *__restrict__ lat, int p
                 cd = cdn;
                 if (x + 4 < L) {
                     cdn = rc[(x / 4 + 1) * 32];
-                    const uint32_t u4 = nib_to_bytes(row_nibble<L, WR>(ua, x + 4));
+                    const uint32_t u4 = nib_to_bytes(row_nibble<L, WR>(ua, x + 4)) << 2;
                     cdn.x -= u4;
                     cdn.y -= u4;
                 }
             }
             const uint32_t uw = word_of(u, j4);
-            bR = accP ? bR + dRp : bR;
-            const int dR = accP ? d1 : d0;
+            const int dR = (SYS == kMuma) ? (row_bit<L, WR>(old, x) ? 4 * RS : -4 * RS) : (accP ? d1 : d0);
             const uint32_t T = accP ? T1 : T0;
             if (x + 1 < L) {
                 const int jn = (x + 1) & 3;
                 const uint32_t wx = (jn == 0) ? cdn.x : cd.x, wy = (jn == 0) ? cdn.y : cd.y;
-                uint32_t c0 = (wx >> (8 * jn)) & 0xffu, c1 = (wy >> (8 * jn)) & 0xffu;
+                // byte jn of the packed codes (selector bytes 4 pick zeros)
+                uint32_t c0 = __byte_perm(wx, 0u, 0x4440u | (uint32_t)jn);
+                uint32_t c1 = __byte_perm(wy, 0u, 0x4440u | (uint32_t)jn);
                 if (x + 1 == L - 1) {
                     // the last site's right neighbour is site 0 of this row, final by now
-                    const uint32_t ra = row_bit<L, WR>(cur, 0) ^ sLast;
+                    const uint32_t ra = (row_bit<L, WR>(cur, 0) ^ sLast) << 2;
                     c0 -= ra;
                     c1 -= ra;
                 }
-                T0 = sTH[bR + (int)c0];
-                T1 = sTH[bR + dR + (int)c1];
-                d0 = move(c0);
-                d1 = move(c1);
+                T0 = th(bB + (int)c0);
+                T1 = th(bB + dR + (int)c1);
+                if (SYS != kMuma) {
+                    d0 = move(c0);
+                    d1 = move(c1);
+                }
             }
-            const bool acc = (T == kAlways) || (uw < T);
+            const bool acc = uw < T;  // the producer's clamp makes this "always or u < T"
             if (acc) cur[x >> 5] ^= 1u << (x & 31);
-            if (RECORD == 0) atomicAdd(&sTH[(acc ? bR + dR : bR) + C], 1u);
+            bB = acc ? bB + dR : bB;
+            if (RECORD == 0) asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(bB + 4 * C), "r"(1u) : "memory");
             accP = acc;
-            dRp = dR;
         }
-        bR = accP ? bR + dRp : bR;
 #pragma unroll
         for (int j = 0; j < WR; ++j) {
             lat[(y * WR + j) * ps] = cur[j];
@@ -249,6 +274,7 @@ __device__ __forceinline__ void ising_sweep_tc(uint32_t *__restrict__ lat, int p
         mbar_arrive(&empty[slot]);  // after the row is stored: the producer reads it later
         ++k;
     }
+    bR = (bB - sbase) / 4;
     if (RECORD == 1) atomicAdd(&sTH[bR + C], 1u);
     if (SYS == kIsing && obs && !bad) record_observables(obs, bR / RS, L * L, pc);
 }
@@ -458,7 +484,7 @@ __device__ __forceinline__ void produce_sweep_potts_tn(uint32_t g, uint32_t wid,
                 const uint32_t base = (uint32_t)(y * (L / 2) + 2 * j);
                 const uint4 r0 = philox4x32_10_rk(make_uint4(base, g, wid, kTagSweep), rk);
                 const uint4 r1 = philox4x32_10_rk(make_uint4(base + 1u, g, wid, kTagSweep), rk);
-                wu[j * 32] = make_uint4(r0.y, r0.w, r1.y, r1.w);
+                wu[j * 32] = clamp_words(make_uint4(r0.y, r0.w, r1.y, r1.w));
                 const uint32_t up4[4] = {r0.x, r0.z, r1.x, r1.z};
                 uint32_t pb = 0u;
 #pragma unroll
@@ -519,7 +545,18 @@ __device__ __forceinline__ void potts_sweep_tc(uint32_t *__restrict__ lat, int p
     constexpr int W4 = L / 4;
     constexpr int RS = 10;
     constexpr size_t S = (size_t)W4 * 32;
-    auto byte_of = [](uint32_t w, int i) -> int { return (int)((w >> (8 * i)) & 0xffu); };
+    // byte i of a packed word (selector bytes 4 pick zeros)
+    auto byte_of = [](uint32_t w, int i) -> int { return (int)__byte_perm(w, 0u, 0x4440u | (uint32_t)i); };
+    // As in the Ising consumer: 32-bit shared-window byte addresses (bB = table base + 4 RS bin,
+    // codes scaled to 4 c), clamped acceptance words, one compare.
+    const int sbase = (int)__cvta_generic_to_shared(sTH);
+    auto th = [](int addr) -> uint32_t {
+        uint32_t v;
+        asm("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(addr));
+        return v;
+    };
+    auto hist = [](int addr) { asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(addr), "r"(1u) : "memory"); };
+    int bB = sbase + bR * 4;
 #pragma unroll 1
     for (int y = 0; y < L; ++y) {
         const int slot = k % RD;
@@ -532,36 +569,35 @@ __device__ __forceinline__ void potts_sweep_tc(uint32_t *__restrict__ lat, int p
         const uint4 *ru = ring_u + slot * S;
         const uint2 *rc = ring_c + slot * S;
         const uint2 *rop = ring_op + slot * S;
-        // code bytes of word j with the up neighbour's term added (bytes stay in [0, 8])
+        // code bytes of word j with the up neighbour's term added (bytes stay in [0, 8]),
+        // scaled to byte offsets 4 c
         auto codes = [&](int j, uint2 op, uint32_t ubw) -> uint2 {
             uint2 c = rc[j * 32];
             const uint32_t np = ne_bytes(ubw, op.y), no = ne_bytes(ubw, op.x);
-            c.x = c.x + np - no;
-            c.y = c.y + np - no;
+            c.x = (c.x + np - no) << 2;
+            c.y = (c.y + np - no) << 2;
             return c;
         };
         uint2 opn = rop[0];
         uint2 cdn = codes(0, opn, sU[0]);
         const int c00 = byte_of(cdn.x, 0);
-        uint32_t T0 = sTH[bR + c00], T1 = 0u;
-        int d0 = (c00 - 4) * RS, d1 = 0;
+        uint32_t T0 = th(bB + c00), T1 = 0u;
+        int d0 = (c00 - 16) * RS, d1 = 0;  // bin-row move (c - 4) rows, in bytes
         bool accP = false;
-        int dRp = 0;
         // decide the current site (threshold T0 or T1 by the previous decision) and
         // load both candidates of the next site, whose code bytes are n0 / n1
         auto site = [&](uint32_t uw, int n0, int n1, uint32_t &am, int i) {
-            bR = accP ? bR + dRp : bR;
             const int dR = accP ? d1 : d0;
             const uint32_t T = accP ? T1 : T0;
-            T0 = sTH[bR + n0];
-            T1 = sTH[bR + dR + n1];
-            d0 = (n0 - 4) * RS;
-            d1 = (n1 - 4) * RS;
-            const bool acc = (T == kAlways) || (uw < T);
+            T0 = th(bB + n0);
+            T1 = th(bB + dR + n1);
+            d0 = (n0 - 16) * RS;
+            d1 = (n1 - 16) * RS;
+            const bool acc = uw < T;  // the producer's clamp makes this "always or u < T"
             if (acc) am |= 0xffu << (8 * i);
-            if (RECORD == 0) atomicAdd(&sTH[(acc ? bR + dR : bR) + 9], 1u);
+            bB = acc ? bB + dR : bB;
+            if (RECORD == 0) hist(bB + 4 * 9);
             accP = acc;
-            dRp = dR;
         };
         uint32_t fprev = 0u;
 #pragma unroll 1
@@ -590,24 +626,23 @@ __device__ __forceinline__ void potts_sweep_tc(uint32_t *__restrict__ lat, int p
             // the last site's right neighbour is site 0 of this row, final by now (word 0 is in sU)
             const uint32_t f0 = sU[0] & 0xffu;
             const int t = (int)(f0 != (op.y >> 24)) - (int)(f0 != (op.x >> 24));
-            site(u.z, byte_of(cd.x, 3) + t, byte_of(cd.y, 3) + t, am, 2);
+            site(u.z, byte_of(cd.x, 3) + 4 * t, byte_of(cd.y, 3) + 4 * t, am, 2);
             // the last site: decision only
-            bR = accP ? bR + dRp : bR;
             const int dR = accP ? d1 : d0;
             const uint32_t T = accP ? T1 : T0;
-            const bool acc = (T == kAlways) || (u.w < T);
+            const bool acc = u.w < T;
             if (acc) am |= 0xff000000u;
-            if (RECORD == 0) atomicAdd(&sTH[(acc ? bR + dR : bR) + 9], 1u);
+            bB = acc ? bB + dR : bB;
+            if (RECORD == 0) hist(bB + 4 * 9);
             accP = acc;
-            dRp = dR;
             const uint32_t f = op.x ^ ((op.x ^ op.y) & am);
             sU[j * 32] = f;
             lat[(y * WR + WR - 1) * ps] = bytes_to_nibs(fprev, f);
         }
-        bR = accP ? bR + dRp : bR;
         mbar_arrive(&empty[slot]);  // after the row is stored: the producer reads it later
         ++k;
     }
+    bR = (bB - sbase) / 4;
     if (RECORD == 1) atomicAdd(&sTH[bR + 9], 1u);
 }
 
