@@ -417,6 +417,18 @@ __device__ __forceinline__ uint32_t bytes_to_nibs(uint32_t w0, uint32_t w1)  // 
     return __byte_perm(w0 | (w0 >> 4), w1 | (w1 >> 4), 0x6420u);
 }
 
+// Potts producers: kPottsProducers parts per consumer.  Parts 0 and 1 share a
+// scheduler; part 2 runs on the consumer's scheduler in the two-walker-warp
+// layout (the idle warps of the Ising layout) or on a scheduler of its own in
+// the one-walker-warp layout, and takes about a third of the row's nibble words.
+// A part may own no words; it still waits and arrives on every row.
+constexpr int kPottsProducers = 3;
+__host__ __device__ constexpr int potts_part_begin(int WR, int part)
+{
+    // parts 0 / 1 / 2 own [0, n0), [n0, WR - n2), [WR - n2, WR) with n2 = (WR + 1) / 3
+    return part <= 0 ? 0 : part == 1 ? (WR - (WR + 1) / 3 + 1) / 2 : part == 2 ? WR - (WR + 1) / 3 : WR;
+}
+
 // The producer runs a rolled loop over the row's nibble words (8 sites, 4
 // Philox blocks each); its old and down rows rotate through registers so that
 // word i is always element 0.  (A fully unrolled row was several times larger
@@ -453,9 +465,7 @@ __device__ __forceinline__ void produce_sweep_potts_tn(uint32_t g, uint32_t wid,
         uint2 *wc = ring_c + slot * S;
         uint2 *wop = ring_op + slot * S;
         // this producer's nibble words [i0, i1); the arrays are rotated so that word i0 is element 0
-        constexpr int NP = kCodeProducers;
-        constexpr int i0 = (NP == 1 || PART == 0) ? 0 : (WR + 1) / 2;
-        constexpr int i1 = (NP == 2 && PART == 0) ? (WR + 1) / 2 : WR;
+        constexpr int i0 = potts_part_begin(WR, PART), i1 = potts_part_begin(WR, PART + 1);
 #pragma unroll
         for (int e = 0; e < i0; ++e) {
             rotate_words<WR>(o);
@@ -463,7 +473,7 @@ __device__ __forceinline__ void produce_sweep_potts_tn(uint32_t g, uint32_t wid,
         }
         uint32_t ob_prev = nib_half_to_bytes(o[WR - 1], 1);  // the four sites left of word i0 (cyclic)
         uint32_t pprev = 0u;                                  // site 0's c1 is never used
-        if (i0 > 0) {
+        if (i0 > 0 && i0 < i1) {
             // proposal of site 8 i0 - 1 (the second site of its Philox block): the c1
             // column of site 8 i0 has it as its recoloured left neighbour
             const uint4 r = philox4x32_10_rk(make_uint4((uint32_t)(y * (L / 2) + 4 * i0 - 1), g, wid, kTagSweep), rk);
@@ -659,10 +669,11 @@ __device__ __forceinline__ void sweep_block_tnp(const SpinSweepArgs &a, int w0, 
     constexpr int C = 9;
     constexpr int RS = C + 1;
     constexpr size_t S = (size_t)(L / 4) * 32;
-    constexpr int NP = kCodeProducers;
+    constexpr int NP = kPottsProducers;
     const int ncw = blockDim.x / (32 * kCodeWarpsPerWalkerWarp);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const CodeRole role = code_role(warp, ncw);
+    CodeRole role = code_role(warp, ncw);
+    if (role.kind == kRoleIdle) role = CodeRole{kRoleProducer, ncw == 1 ? 0 : (warp & 1), 2};
     const bool producer = role.kind == kRoleProducer, consumer = role.kind == kRoleConsumer;
     const int pair = role.pair, part = role.part;
     const int drop_k = (blockIdx.x == 0 && producer && pair == 0 && part == 0) ? a.debug_drop_row : -1;
@@ -709,8 +720,11 @@ __device__ __forceinline__ void sweep_block_tnp(const SpinSweepArgs &a, int w0, 
                 if (part == 0)
                     produce_sweep_potts_tn<L, RD, 0>(g, wid, a.rk, lat, a.pstride, (uint32_t)a.q, ring_u, ring_c,
                                                      ring_op, full, empty, k, bad, drop_k);
-                else
+                else if (part == 1)
                     produce_sweep_potts_tn<L, RD, 1>(g, wid, a.rk, lat, a.pstride, (uint32_t)a.q, ring_u, ring_c,
+                                                     ring_op, full, empty, k, bad, -1);
+                else
+                    produce_sweep_potts_tn<L, RD, 2>(g, wid, a.rk, lat, a.pstride, (uint32_t)a.q, ring_u, ring_c,
                                                      ring_op, full, empty, k, bad, -1);
             } else if (consumer && active) {
                 if (a.record == 0)
