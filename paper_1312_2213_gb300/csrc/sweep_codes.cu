@@ -73,7 +73,8 @@ __device__ __forceinline__ void rotate_words(uint32_t (&o)[WR])  // o[e] <- o[e+
 // pace) and the two producers of a consumer share another one:
 //   ncw = 1: [C0, idle, P0.0, P0.1]
 //   ncw = 2: [C0, C1, P0.0, P1.0, idle, idle, P0.1, P1.1]   (Pc.k: part k for consumer c)
-// Idle warps only take part in the block-wide barriers of the histogram flush.
+// Idle warps only take part in the block-wide barriers of the histogram flush
+// (the Potts form makes them a third producer part, see kPottsProducers).
 enum { kRoleConsumer = 0, kRoleProducer = 1, kRoleIdle = 2 };
 struct CodeRole {
     int kind, pair, part;
