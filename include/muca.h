@@ -207,6 +207,20 @@ int muca_get_reweight(muca_ctx *ctx, double beta, double host_out[4], double *ho
  * Errors: MUCA_ERR_STATE if observables are off, MUCA_ERR_ARG on bad lengths. */
 int muca_get_observables(muca_ctx *ctx, double beta, double host_out[3], uint64_t *host_sums, int nbins);
 
+/* Per-iteration metrics (no counterpart in the paper; the acceptance rate and
+ * the walkers' round trips between the energy extremes are the usual figures of
+ * merit of a multicanonical run).  Every sweep kernel counts the moves it
+ * accepts, and samples each walker's bin at the end of every sweep: a
+ * tunnelling event is an arrival at the lowest reachable bin when the highest
+ * was the last of the two visited, or the reverse (polymer: bins 0 and B-1 of
+ * the window).  Each update closes the counts of its iteration.  host_out =
+ * {accepted moves of the last closed iteration, its tunnelling events,
+ * accepted moves of all closed iterations, their tunnelling events, sweeps of
+ * the last closed iteration, closed iterations}; acceptance rate = out[0] /
+ * (p N out[4]).  A sharded context counts its own walkers.  Synchronises the
+ * context's stream. */
+int muca_get_metrics(muca_ctx *ctx, uint64_t host_out[6]);
+
 /* Checkpoint: the complete state (walkers, weights, recursion state, counters).
  * Call with host_buf == NULL to get the size in *bytes.  muca_set_state
  * restores a buffer produced by a context of the same configuration; resuming

@@ -74,7 +74,7 @@ def lib():
             L.orc_reweight.argtypes = [ctypes.c_void_p, ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p]
             for name in ("orc_reachable", "orc_get_lnW", "orc_get_lnW_sampled", "orc_get_histogram",
                          "orc_get_thresholds", "orc_get_spins", "orc_get_bins", "orc_set_open_histogram",
-                         "orc_get_open_histogram"):
+                         "orc_get_open_histogram", "orc_get_metrics"):
                 getattr(L, name).argtypes = [ctypes.c_void_p, ctypes.c_void_p]
             L.orc_get_sweep_counter.argtypes = [ctypes.c_void_p]
             L.orc_get_sweep_counter.restype = ctypes.c_int64
@@ -107,7 +107,7 @@ def _bind_polymer(L):
     L.orc_poly_advance.argtypes = [c.c_void_p, c.c_int64]
     L.orc_poly_update.argtypes = [c.c_void_p]
     for name in ("orc_poly_get_lnW", "orc_poly_get_lnW_sampled", "orc_poly_get_histogram", "orc_poly_get_coords",
-                 "orc_poly_get_energy", "orc_poly_get_bins", "orc_poly_get_counters"):
+                 "orc_poly_get_energy", "orc_poly_get_bins", "orc_poly_get_counters", "orc_poly_get_metrics"):
         getattr(L, name).argtypes = [c.c_void_p, c.c_void_p]
     L.orc_poly_set_beta.argtypes = [c.c_void_p, c.c_double]
     L.orc_poly_set_model.argtypes = [c.c_void_p, c.c_int]
@@ -238,6 +238,11 @@ class Run:
 
     def sweep_counter(self) -> int:
         return int(self._lib.orc_get_sweep_counter(self.h))
+
+    def metrics(self) -> np.ndarray:
+        """{accepted, tunnelling events} of the last closed iteration, the same totals over all
+        closed iterations, and the closed iteration's sweeps (uint64[5])."""
+        return self._get("orc_get_metrics", 5, np.uint64)
 
 
 def reweight_obs(N: int, sums: np.ndarray, lnW_sampled: np.ndarray, beta: float) -> np.ndarray:
@@ -373,6 +378,9 @@ class PolyRun:
 
     def walker_events(self):
         return self._get("orc_poly_get_walker_events", 2 * self.p, np.int64).reshape(self.p, 2)
+
+    def metrics(self) -> np.ndarray:
+        return self._get("orc_poly_get_metrics", 5, np.uint64)
 
     def reweight(self, beta: float):
         out = np.zeros(4)

@@ -193,6 +193,14 @@ struct orc_run {
     double *lnW, *lnW_sampled, *G, *lnR;
     uint64_t *H_open, *H_last;
     uint32_t *T; /* B*K */
+    /* metrics (no counterpart in the paper): per walker, accepted moves and
+     * tunnelling events of the open iteration, and which end of the reachable
+     * bins it visited last (0 none, 1 lowest, 2 highest), the bin sampled at
+     * the end of every sweep */
+    uint64_t *acc_w, *ev_w;
+    uint8_t *tun;
+    uint64_t m_last[2], m_total[2];
+    int64_t sweeps_last, sweep_at_update;
 };
 
 static int orc_valid(int system, int L, int q, int p)
@@ -260,6 +268,9 @@ orc_run *orc_create(int system, int L, int q, int p, uint64_t seed, double beta,
     r->O_open = (uint64_t *)calloc((size_t)r->B * 3, sizeof(uint64_t));
     r->O_last = (uint64_t *)calloc((size_t)r->B * 3, sizeof(uint64_t));
     r->T = (uint32_t *)calloc((size_t)r->B * r->K, sizeof(uint32_t));
+    r->acc_w = (uint64_t *)calloc((size_t)p, sizeof(uint64_t));
+    r->ev_w = (uint64_t *)calloc((size_t)p, sizeof(uint64_t));
+    r->tun = (uint8_t *)calloc((size_t)p, 1);
     orc_compute_reachable(r);
     return r;
 }
@@ -271,6 +282,7 @@ void orc_free(orc_run *r)
     free(r->lnW); free(r->lnW_sampled); free(r->G); free(r->lnR);
     free(r->H_open); free(r->H_last); free(r->T);
     free(r->O_open); free(r->O_last);
+    free(r->acc_w); free(r->ev_w); free(r->tun);
     free(r);
 }
 
@@ -362,6 +374,14 @@ void orc_init(orc_run *r)
         r->H_last[b] = 0;
     }
     r->sweep_counter = 0;
+    for (int w = 0; w < r->p; ++w) {
+        r->acc_w[w] = 0;
+        r->ev_w[w] = 0;
+        r->tun[w] = 0;
+    }
+    r->m_last[0] = r->m_last[1] = r->m_total[0] = r->m_total[1] = 0;
+    r->sweeps_last = 0;
+    r->sweep_at_update = 0;
     orc_build_thresholds(r);
 }
 
@@ -423,10 +443,19 @@ static void orc_walker_sweeps(const orc_run *r, int w, int64_t g0, int64_t sweep
             if (t == ORC_T_ALWAYS || u_acc < t) {
                 s[i] = new_s;
                 b += db;
+                r->acc_w[w] += 1;
             }
             if (r->record == 0) hist[b] += 1;
         }
         if (r->record == 1) hist[b] += 1;
+        /* tunnelling: the walker's bin at the end of the sweep against the two ends */
+        if (b == r->rlist[0]) {
+            if (r->tun[w] == 2) r->ev_w[w] += 1;
+            r->tun[w] = 1;
+        } else if (b == r->rlist[r->nreach - 1]) {
+            if (r->tun[w] == 1) r->ev_w[w] += 1;
+            r->tun[w] = 2;
+        }
         if (obs) { /* R9 */
             int64_t M = 0;
             for (int i = 0; i < N; ++i) M += s[i];
@@ -538,9 +567,37 @@ void orc_reweight_observables(const orc_run *r, double beta, double out[3])
 }
 
 /* a5 (reading R5, or R5' when selected) followed by a6. */
+/* Close the metrics of the iteration that the update ends. */
+static void orc_close_metrics(orc_run *r)
+{
+    uint64_t a = 0, e = 0;
+    for (int w = 0; w < r->p; ++w) {
+        a += r->acc_w[w];
+        e += r->ev_w[w];
+        r->acc_w[w] = 0;
+        r->ev_w[w] = 0;
+    }
+    r->m_last[0] = a;
+    r->m_last[1] = e;
+    r->m_total[0] += a;
+    r->m_total[1] += e;
+    r->sweeps_last = r->sweep_counter - r->sweep_at_update;
+    r->sweep_at_update = r->sweep_counter;
+}
+
+void orc_get_metrics(const orc_run *r, uint64_t out[5])
+{
+    out[0] = r->m_last[0];
+    out[1] = r->m_last[1];
+    out[2] = r->m_total[0];
+    out[3] = r->m_total[1];
+    out[4] = (uint64_t)r->sweeps_last;
+}
+
 void orc_update(orc_run *r)
 {
     const int Kr = r->nreach;
+    orc_close_metrics(r);
     memcpy(r->lnW_sampled, r->lnW, sizeof(double) * r->B);
     memcpy(r->O_last, r->O_open, sizeof(uint64_t) * 3 * r->B);
     memset(r->O_open, 0, sizeof(uint64_t) * 3 * r->B);

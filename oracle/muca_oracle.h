@@ -60,6 +60,12 @@ void orc_set_observables(orc_run *r, int on);
 void orc_get_observables(const orc_run *r, uint64_t *out); /* 3*B, last update */
 void orc_reweight_obs(int B, int N, const uint64_t *sums, const double *lnW_sampled, double beta, double out[3]);
 void orc_reweight_observables(const orc_run *r, double beta, double out[3]);
+/* Metrics of the last update: {accepted moves of the closed iteration, its
+ * tunnelling events (a walker's bin sampled at the end of every sweep arrives at
+ * the lowest reachable bin after the highest was the last end visited, or the
+ * reverse), accepted moves of all closed iterations, their tunnelling events,
+ * sweeps of the closed iteration}. */
+void orc_get_metrics(const orc_run *r, uint64_t out[5]);
 /* Replace the open histogram (for recursion tests on hand-made histograms). */
 void orc_set_open_histogram(orc_run *r, const uint64_t *H);
 void orc_get_open_histogram(const orc_run *r, uint64_t *out);
@@ -110,6 +116,7 @@ void orc_poly_get_bins(void *h, int32_t *out /* p */);
 void orc_poly_get_counters(void *h, int64_t *out /* {near-tie acceptances, bin-edge events} */);
 void orc_poly_reweight(void *h, double beta, double out[4], double *lnP /* nullable, B */);
 void orc_poly_get_walker_events(void *h, int64_t *out /* p*2 */);
+void orc_poly_get_metrics(void *h, uint64_t out[5]); /* as orc_get_metrics; ends: bins 0 and B-1 */
 double orc_poly_energy(int N, const double *X, int model); /* model 0 benchmark, 1 paper */
 double orc_poly_pair(double r, int sep, int model);
 

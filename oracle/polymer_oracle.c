@@ -76,6 +76,13 @@ typedef struct {
     double *lnW, *lnW_sampled, *G, *lnR;
     uint64_t *H_open, *H_last;
     int64_t *events; /* p*2: [near-tie acceptances, bin-edge events] */
+    /* metrics, as in the spin oracle: per walker accepted moves and tunnelling
+     * events (bins 0 and B-1, sampled at the end of every sweep) of the open
+     * iteration, and the end visited last (0 none, 1 bin 0, 2 bin B-1) */
+    uint64_t *acc_w, *ev_w;
+    uint8_t *tun;
+    uint64_t m_last[2], m_total[2];
+    int64_t sweeps_last, sweep_at_update;
 } orc_poly;
 
 static double poly_lj(double r2)
@@ -184,6 +191,9 @@ void *orc_poly_create(int N, int p, uint64_t seed, double e_lo, double e_hi, dou
     P->H_open = (uint64_t *)calloc((size_t)P->B, sizeof(uint64_t));
     P->H_last = (uint64_t *)calloc((size_t)P->B, sizeof(uint64_t));
     P->events = (int64_t *)calloc((size_t)p * 2, sizeof(int64_t));
+    P->acc_w = (uint64_t *)calloc((size_t)p, sizeof(uint64_t));
+    P->ev_w = (uint64_t *)calloc((size_t)p, sizeof(uint64_t));
+    P->tun = (uint8_t *)calloc((size_t)p, 1);
     return P;
 }
 
@@ -193,6 +203,7 @@ void orc_poly_free(void *h)
     if (!P) return;
     free(P->X); free(P->E); free(P->lnW); free(P->lnW_sampled); free(P->G); free(P->lnR);
     free(P->H_open); free(P->H_last); free(P->events);
+    free(P->acc_w); free(P->ev_w); free(P->tun);
     free(P);
 }
 
@@ -299,6 +310,12 @@ void orc_poly_init(void *h)
         P->H_open[b] = P->H_last[b] = 0;
     }
     P->sweep_counter = 0;
+    for (int w = 0; w < P->p; ++w) {
+        P->acc_w[w] = P->ev_w[w] = 0;
+        P->tun[w] = 0;
+    }
+    P->m_last[0] = P->m_last[1] = P->m_total[0] = P->m_total[1] = 0;
+    P->sweeps_last = P->sweep_at_update = 0;
 }
 
 static double poly_window_dist(const orc_poly *P, double E)
@@ -371,6 +388,7 @@ static void poly_walker_sweeps(orc_poly *P, int w, int64_t g0, int64_t sweeps, u
             if (accept) {
                 for (int a = 0; a < 3; ++a) X[3 * i + a] = xn[a];
                 E = En;
+                P->acc_w[w] += 1;
             }
             if (P->record == 0 && P->beta <= 0.0) {
                 int b = poly_bin(P, E);
@@ -380,6 +398,16 @@ static void poly_walker_sweeps(orc_poly *P, int w, int64_t g0, int64_t sweeps, u
         if (P->record == 1 && P->beta <= 0.0) {
             int b = poly_bin(P, E);
             if (b >= 0 && b < P->B) hist[b] += 1;
+        }
+        {
+            const int b = poly_bin(P, E);
+            if (b == 0) {
+                if (P->tun[w] == 2) P->ev_w[w] += 1;
+                P->tun[w] = 1;
+            } else if (b == P->B - 1) {
+                if (P->tun[w] == 1) P->ev_w[w] += 1;
+                P->tun[w] = 2;
+            }
         }
     }
     /* recentre on bead 0 (an exact shift by a grid vector: energies are unchanged) */
@@ -445,10 +473,34 @@ void orc_poly_iterate(void *h, int64_t sweeps, int nthreads)
 }
 
 /* Same accumulated-statistics recursion as the spin oracle, over all B bins. */
+void orc_poly_get_metrics(void *h, uint64_t out[5])
+{
+    orc_poly *P = (orc_poly *)h;
+    out[0] = P->m_last[0];
+    out[1] = P->m_last[1];
+    out[2] = P->m_total[0];
+    out[3] = P->m_total[1];
+    out[4] = (uint64_t)P->sweeps_last;
+}
+
 void orc_poly_update(void *h)
 {
     orc_poly *P = (orc_poly *)h;
     const int B = P->B;
+    {
+        uint64_t a = 0, e = 0;
+        for (int w = 0; w < P->p; ++w) {
+            a += P->acc_w[w];
+            e += P->ev_w[w];
+            P->acc_w[w] = P->ev_w[w] = 0;
+        }
+        P->m_last[0] = a;
+        P->m_last[1] = e;
+        P->m_total[0] += a;
+        P->m_total[1] += e;
+        P->sweeps_last = P->sweep_counter - P->sweep_at_update;
+        P->sweep_at_update = P->sweep_counter;
+    }
     memcpy(P->lnW_sampled, P->lnW, sizeof(double) * B);
     for (int k = 0; k + 1 < B; ++k) {
         uint64_t h0 = P->H_open[k], h1 = P->H_open[k + 1];

@@ -20,7 +20,7 @@ SYSTEM_NAMES = {ISING2D: "ising2d", POTTS2D: "potts2d", ISING2D_MUMA: "ising2d_m
 __all__ = ["Muca", "MucaError", "ISING2D", "POTTS2D", "ISING2D_MUMA", "POLYMER3D", "library_path", "load",
            "muca_init", "muca_init_ex", "muca_workspace_size", "muca_set_param", "muca_set_stream",
            "muca_iterate", "muca_merge_and_update", "muca_num_bins", "muca_get_lnW", "muca_get_lnW_sampled",
-           "muca_get_histogram", "muca_get_flatness", "muca_get_reweight", "muca_get_observables",
+           "muca_get_histogram", "muca_get_flatness", "muca_get_reweight", "muca_get_observables", "muca_get_metrics",
            "muca_merge_open", "muca_update_with",
            "muca_get_state", "muca_set_state",
            "muca_get_spins", "muca_get_walker_bins", "muca_get_thresholds", "muca_get_sweep_counter",
@@ -114,6 +114,10 @@ def muca_get_observables(h, beta: float, out: np.ndarray, sums: np.ndarray | Non
     n = 0 if sums is None else sums.size // 3
     check(load().muca_get_observables(h, float(beta), _p(out), None if sums is None else _p(sums), n),
           "muca_get_observables")
+
+
+def muca_get_metrics(h, out: np.ndarray):
+    check(load().muca_get_metrics(h, _p(out)), "muca_get_metrics")
 
 
 def muca_get_reweight(h, beta: float, out: np.ndarray, lnP: np.ndarray | None = None):
@@ -316,6 +320,18 @@ class Muca:
         sums = np.zeros(3 * self.B, dtype=np.uint64)
         muca_get_observables(self.h, beta, out, sums)
         return out, sums.reshape(self.B, 3)
+
+    def metrics(self) -> dict:
+        """Counts of the last closed iteration and of all closed iterations: accepted moves,
+        tunnelling events (arrivals at one end of the reachable bins after the other end, the bin
+        sampled at every sweep's end), the iteration's sweeps and its acceptance rate."""
+        a = np.zeros(6, dtype=np.uint64)
+        muca_get_metrics(self.h, a)
+        acc, ev, acc_t, ev_t, sw, it = (int(x) for x in a)
+        attempts = self.p * self.N * sw
+        return {"iteration": it, "accepted": acc, "tunnelling_events": ev, "sweeps": sw,
+                "acceptance_rate": acc / attempts if attempts else float("nan"),
+                "accepted_total": acc_t, "tunnelling_events_total": ev_t}
 
     def spins(self) -> np.ndarray:
         a = np.zeros(self.p * self.N, dtype=np.int8)

@@ -33,6 +33,7 @@ PROTOTYPES = {
     "muca_get_flatness": (c_int, [c_vp, c_vp]),
     "muca_get_reweight": (c_int, [c_vp, c_dbl, c_vp, c_vp]),
     "muca_get_observables": (c_int, [c_vp, c_dbl, c_vp, c_vp, c_int]),
+    "muca_get_metrics": (c_int, [c_vp, c_vp]),
     "muca_merge_open": (c_int, [c_vp, c_vp]),
     "muca_update_with": (c_int, [c_vp, c_vp, c_vp]),
     "muca_get_state": (c_int, [c_vp, c_vp, P(c_sz)]),

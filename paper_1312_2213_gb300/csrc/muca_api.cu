@@ -56,7 +56,7 @@ constexpr size_t kAlign = 256;
 size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
 struct Layout {
-    size_t lat, bin, T, lnW, lnW_sampled, G, lnR, H, Hpart, rlist, reach, state, out, Eq, lnWq, obs, total;
+    size_t lat, bin, T, lnW, lnW_sampled, G, lnR, H, Hpart, rlist, reach, state, out, Eq, lnWq, obs, metrics, tun, total;
 };
 
 }  // namespace
@@ -73,6 +73,8 @@ struct muca_ctx {
     int recursion = 0;        // weight update: 0 accumulated statistics, 1 plain W/H
     int observables = 0;      // Ising: per-sweep sums of 1, |M|, M^2 per bin
     unsigned long long *obs = nullptr;  // [0, 3B): sums being filled, [3B, 6B): of the last update
+    unsigned long long *metrics = nullptr;  // kMetricWords counters, see UpdateArgs::metrics
+    uint8_t *tun = nullptr;                 // [p] tunnelling state per walker
     int pipeline = 2;  // spins: code form (2), producer/consumer (1) or one warp per walker group (0)
     int pstride = 0, wpw = 0, nblk_max = 0;
     cudaStream_t stream = nullptr;
@@ -200,6 +202,8 @@ Layout plan(const muca_ctx *c)
         l.reach = take(Bc);
         l.state = take(sizeof(DevState));
         l.out = take(sizeof(double) * (4 + Bc));
+        l.metrics = take(sizeof(unsigned long long) * kMetricWords);
+        l.tun = take((size_t)c->p);
         l.total = off;
         return l;
     }
@@ -217,6 +221,8 @@ Layout plan(const muca_ctx *c)
     l.state = take(sizeof(DevState));
     l.out = take(sizeof(double) * (4 + (size_t)c->B));
     l.obs = take(sizeof(unsigned long long) * 6 * (size_t)c->B);
+    l.metrics = take(sizeof(unsigned long long) * kMetricWords);
+    l.tun = take((size_t)c->p);
     l.total = off;
     return l;
 }
@@ -237,6 +243,7 @@ UpdateArgs update_args(const muca_ctx *c)
     a.flat_ratio = c->flat_ratio;
     a.e_lo = c->e_lo;
     a.recursion = c->recursion;
+    a.metrics = c->metrics;
     if (c->system == kPolymer) a.nblocks = 1;  // the open histogram is one global slot
     a.reach = c->reach;
     a.rlist = c->rlist;
@@ -248,6 +255,36 @@ UpdateArgs update_args(const muca_ctx *c)
     a.lnR = c->lnR;
     a.T = c->T;
     a.state = c->state;
+    return a;
+}
+
+// Arguments of a spin sweep launch of `sweeps` sweeps with `block` walkers a block.
+SpinSweepArgs sweep_args(const muca_ctx *c, int64_t sweeps, int block)
+{
+    SpinSweepArgs a{};
+    a.T = c->T;
+    a.lattice = c->lat;
+    a.bin = c->bin;
+    a.Hpart = c->Hpart;
+    a.state = c->state;
+    a.p = c->p;
+    a.pstride = c->pstride;
+    a.B = c->B;
+    a.q = c->q;
+    a.sweeps = sweeps;
+    const unsigned long long per_sweep = (unsigned long long)block * (c->record == 0 ? (unsigned)c->N : 1u);
+    unsigned long long fe = 0xFFFFFFFFull / per_sweep;
+    if (fe < 1) fe = 1;
+    if (fe > (unsigned long long)sweeps) fe = (unsigned long long)sweeps;
+    a.flush_every = (int)(fe > 0x7fffffffull ? 0x7fffffffull : fe);
+    fill_round_keys(a, c->seed);
+    a.record = c->record;
+    a.walker_offset = c->walker_offset;
+    a.kind = sweep_kind(c->system, c->L);
+    a.metrics = c->metrics;
+    a.tun = c->tun;
+    a.bin_lo = c->h_rlist.front();
+    a.bin_hi = c->h_rlist.back();
     return a;
 }
 
@@ -294,6 +331,8 @@ PolyArgs poly_args(const muca_ctx *c, int64_t sweeps)
         a.init_d2min = 0.81;  // (0.9 b0)^2
     }
     a.sweeps = sweeps;
+    a.metrics = c->metrics;
+    a.tun = c->tun;
     SpinSweepArgs keys{};
     fill_round_keys(keys, c->seed);
     a.key0 = keys.key0;
@@ -325,6 +364,9 @@ int reset_weights(muca_ctx *c)
 
 int init_walkers(muca_ctx *c)
 {
+    // new walkers: no tunnelling history, no counts
+    MUCA_CUDA(cudaMemsetAsync(c->tun, 0, (size_t)c->p, c->stream));
+    MUCA_CUDA(cudaMemsetAsync(c->metrics, 0, sizeof(unsigned long long) * kMetricWords, c->stream));
     if (c->system == kPolymer) {
         PolyArgs pa = poly_args(c, 0);
         MUCA_CUDA(launch_poly_init(pa, c->stream));
@@ -353,6 +395,8 @@ int setup(muca_ctx *c)
     c->reach = (uint8_t *)(base + l.reach);
     c->state = (DevState *)(base + l.state);
     c->out = (double *)(base + l.out);
+    c->metrics = (unsigned long long *)(base + l.metrics);
+    c->tun = (uint8_t *)(base + l.tun);
     if (c->system == kPolymer) {
         c->Eq = (long long *)(base + l.Eq);
         c->lnWq = (long long *)(base + l.lnWq);
@@ -467,6 +511,8 @@ std::vector<Section> state_sections(const muca_ctx *c)
         v.push_back({c->T, sizeof(uint32_t) * B * c->C});
         v.push_back({c->obs, sizeof(unsigned long long) * 6 * B});  // observable sums (open, last)
     }
+    v.push_back({c->metrics, sizeof(unsigned long long) * kMetricWords});  // metrics counters
+    v.push_back({c->tun, (size_t)c->p});                                    // tunnelling states
     return v;
 }
 
@@ -642,26 +688,7 @@ int muca_iterate(muca_ctx *c, int64_t sweeps)
         c->open = true;
         return MUCA_OK;
     }
-    SpinSweepArgs a{};
-    a.T = c->T;
-    a.lattice = c->lat;
-    a.bin = c->bin;
-    a.Hpart = c->Hpart;
-    a.state = c->state;
-    a.p = c->p;
-    a.pstride = c->pstride;
-    a.B = c->B;
-    a.q = c->q;
-    a.sweeps = sweeps;
-    const unsigned long long per_sweep = (unsigned long long)c->block * (c->record == 0 ? (unsigned)c->N : 1u);
-    unsigned long long fe = 0xFFFFFFFFull / per_sweep;
-    if (fe < 1) fe = 1;
-    if (fe > (unsigned long long)sweeps) fe = (unsigned long long)sweeps;
-    a.flush_every = (int)(fe > 0x7fffffffull ? 0x7fffffffull : fe);
-    fill_round_keys(a, c->seed);
-    a.record = c->record;
-    a.walker_offset = c->walker_offset;
-    a.kind = sweep_kind(c->system, c->L);
+    SpinSweepArgs a = sweep_args(c, sweeps, c->block);
     a.obs = (c->observables && c->system == kIsing) ? c->obs : nullptr;
     a.debug_drop_row = c->debug_drop_row;
     c->debug_drop_row = -1;
@@ -797,6 +824,18 @@ int muca_get_reweight(muca_ctx *c, double beta, double host_out[4], double *host
     return MUCA_OK;
 }
 
+int muca_get_metrics(muca_ctx *c, uint64_t host_out[6])
+{
+    if (int rc = check_ctx(c)) return rc;
+    if (!host_out) return fail(MUCA_ERR_ARG, "host_out is NULL");
+    unsigned long long m[kMetricWords], it = 0;
+    MUCA_CUDA(cudaMemcpyAsync(&it, &c->state->iteration, sizeof it, cudaMemcpyDeviceToHost, c->stream));
+    if (int rc = d2h(c, m, c->metrics, sizeof m)) return rc;
+    for (int k = 0; k < 5; ++k) host_out[k] = m[2 + k];
+    host_out[5] = it;
+    return MUCA_OK;
+}
+
 int muca_get_observables(muca_ctx *c, double beta, double host_out[3], uint64_t *host_sums, int nbins)
 {
     if (int rc = check_ctx(c)) return rc;
@@ -896,8 +935,8 @@ int muca_get_state(muca_ctx *c, void *host_buf, size_t *bytes)
     if (*bytes < need) return fail(MUCA_ERR_ARG, "state buffer too small: need %zu bytes", need);
     char *p = (char *)host_buf;
     StateHeader h{};
-    memcpy(h.magic, "MUCAST3", 8);
-    h.version = 3;
+    memcpy(h.magic, "MUCAST4", 8);
+    h.version = 4;
     h.system = c->system;
     h.L = c->L;
     h.q = c->q;
@@ -948,7 +987,7 @@ int muca_set_state(muca_ctx *c, const void *host_buf, size_t bytes)
     if (bytes < sizeof(StateHeader)) return fail(MUCA_ERR_ARG, "not a muca state buffer");
     StateHeader h;
     memcpy(&h, host_buf, sizeof h);
-    if (memcmp(h.magic, "MUCAST3", 8) != 0 || h.version != 3) return fail(MUCA_ERR_ARG, "not a muca state buffer");
+    if (memcmp(h.magic, "MUCAST4", 8) != 0 || h.version != 4) return fail(MUCA_ERR_ARG, "not a muca state buffer");
     if (h.system != c->system || h.L != c->L || h.q != c->q || h.p != c->p || h.C != c->C || h.wpw != c->wpw ||
         h.pstride != c->pstride || h.seed != c->seed)
         return fail(MUCA_ERR_ARG, "state buffer was written by a different configuration");
@@ -1074,31 +1113,6 @@ struct muca_batch {
 };
 
 namespace {
-
-SpinSweepArgs sweep_args(const muca_ctx *c, int64_t sweeps, int block)
-{
-    SpinSweepArgs a{};
-    a.T = c->T;
-    a.lattice = c->lat;
-    a.bin = c->bin;
-    a.Hpart = c->Hpart;
-    a.state = c->state;
-    a.p = c->p;
-    a.pstride = c->pstride;
-    a.B = c->B;
-    a.q = c->q;
-    a.sweeps = sweeps;
-    const unsigned long long per_sweep = (unsigned long long)block * (c->record == 0 ? (unsigned)c->N : 1u);
-    unsigned long long fe = 0xFFFFFFFFull / per_sweep;
-    if (fe < 1) fe = 1;
-    if (fe > (unsigned long long)sweeps) fe = (unsigned long long)sweeps;
-    a.flush_every = (int)(fe > 0x7fffffffull ? 0x7fffffffull : fe);
-    fill_round_keys(a, c->seed);
-    a.record = c->record;
-    a.walker_offset = c->walker_offset;
-    a.kind = sweep_kind(c->system, c->L);
-    return a;
-}
 
 int batch_enqueue_iteration(muca_batch *b, int64_t sweeps)
 {
@@ -1334,25 +1348,8 @@ extern "C" int muca_iterate_noalloc(muca_ctx *c, int64_t sweeps, uint64_t *dev_H
     if (int rc = static_hist_ptr(&scratch)) return rc;
     // The array keeps whatever the previous call left in it: clear the slots used here.
     MUCA_CUDA(cudaMemsetAsync(scratch, 0, need * sizeof(unsigned long long), c->stream));
-    SpinSweepArgs a{};
-    a.T = c->T;
-    a.lattice = c->lat;
-    a.bin = c->bin;
+    SpinSweepArgs a = sweep_args(c, sweeps, c->block);
     a.Hpart = scratch;
-    a.state = c->state;
-    a.p = c->p;
-    a.pstride = c->pstride;
-    a.B = c->B;
-    a.q = c->q;
-    a.sweeps = sweeps;
-    const unsigned long long per_sweep = (unsigned long long)c->block * (c->record == 0 ? (unsigned)c->N : 1u);
-    unsigned long long fe = 0xFFFFFFFFull / per_sweep;
-    if (fe < 1) fe = 1;
-    if (fe > (unsigned long long)sweeps) fe = (unsigned long long)sweeps;
-    a.flush_every = (int)(fe > 0x7fffffffull ? 0x7fffffffull : fe);
-    fill_round_keys(a, c->seed);
-    a.record = c->record;
-    a.walker_offset = c->walker_offset;
     MUCA_CUDA(launch_spin_sweep(c->system, c->L, a, c->block, c->stream));
     MUCA_CUDA(launch_advance(c->state, sweeps, c->stream));
     UpdateArgs u = update_args(c);

@@ -124,4 +124,44 @@ __device__ inline double dm_log(double x)
     return __dadd_rn(__dmul_rn(ed, HI), __dadd_rn(__dmul_rn(ed, LO), lnm));
 }
 
+// Per-iteration metrics.  Accepted moves are counted from the rows themselves (an
+// accepted Ising flip changes one bit, an accepted Potts move one nibble, since the
+// proposal differs from the old colour) or per decision (polymer).  Tunnelling: a
+// walker's bin is sampled at the end of every sweep; an event is an arrival at the
+// lowest reachable bin when the highest was the last of the two visited, or the
+// reverse.  st: 0 neither visited yet, 1 lowest last, 2 highest last (r, r_lo, r_hi
+// in one unit: bins, or row offsets RS bin).
+__device__ __forceinline__ void tunnel_step(int r, int r_lo, int r_hi, int &st, unsigned &ev)
+{
+    if (r == r_lo) {
+        ev += (st == 2);
+        st = 1;
+    } else if (r == r_hi) {
+        ev += (st == 1);
+        st = 2;
+    }
+}
+
+// Changed 4-bit fields between two packed Potts words.
+__device__ __forceinline__ unsigned changed_nibbles(uint32_t a, uint32_t b)
+{
+    const uint32_t x = a ^ b;
+    return (unsigned)__popc((x | (x >> 1) | (x >> 2) | (x >> 3)) & 0x11111111u);
+}
+
+// Add a warp's counts to the context's open counters (accepted, tunnelling
+// events); every lane of the warp calls it.
+__device__ __forceinline__ void flush_metrics(unsigned long long *m, unsigned long long acc, unsigned ev)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        acc += __shfl_down_sync(0xffffffffu, acc, o);
+        ev += __shfl_down_sync(0xffffffffu, ev, o);
+    }
+    if ((threadIdx.x & 31) == 0 && m) {
+        if (acc) atomicAdd(&m[0], acc);
+        if (ev) atomicAdd(&m[1], (unsigned long long)ev);
+    }
+}
+
 }  // namespace muca

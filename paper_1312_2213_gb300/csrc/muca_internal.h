@@ -11,6 +11,7 @@ enum System { kIsing = 0, kPotts = 1, kMuma = 2, kPolymer = 3 };
 
 // Largest thread block of the sweep kernels (keeps up to 128 registers a thread).
 constexpr int kMaxSweepBlock = 512;
+constexpr int kMetricWords = 8;  // per-context metrics counters (see UpdateArgs::metrics)
 
 // Threshold meaning "always accept"; any other value t accepts iff u < t.
 constexpr uint32_t kAlways = 0xFFFFFFFFu;
@@ -44,6 +45,9 @@ struct SpinSweepArgs {
     unsigned long long *obs = nullptr;  // Ising observables: per bin (samples, sum |M|, sum M^2), or null
     int debug_drop_row = -1; // test hook: row hand-over (count within the launch) that the first
                              // producer warp of block 0 skips, so the consumer's wait runs out; -1 = off
+    unsigned long long *metrics = nullptr;  // open counters {accepted moves, tunnelling events}
+    uint8_t *tun = nullptr;  // [p] tunnelling state per walker (0 none, 1 lowest bin last, 2 highest)
+    int bin_lo = 0, bin_hi = 0;  // lowest and highest reachable bins
 };
 
 // Philox round keys for a seed: round r uses (lo + r*W0, hi + r*W1).
@@ -113,6 +117,8 @@ struct PolyArgs {
     int64_t sweeps;
     uint32_t key0, key1;
     uint32_t rk[20];
+    unsigned long long *metrics = nullptr;  // open counters {accepted moves, tunnelling events}
+    uint8_t *tun = nullptr;                 // [p] tunnelling state per walker
 };
 bool polymer_supported(int N);
 cudaError_t launch_poly_init(const PolyArgs &a, cudaStream_t s);
@@ -133,6 +139,10 @@ struct UpdateArgs {
     double *lnW, *lnW_sampled, *G, *lnR;
     uint32_t *T;
     DevState *state;
+    // metrics counters {open accepted, open tunnelling events, last accepted, last events,
+    // total accepted, total events, sweeps of the last iteration, sweep counter at the last
+    // update}; the recursion launch closes them (null: none)
+    unsigned long long *metrics;
 };
 cudaError_t launch_merge(const UpdateArgs &a, cudaStream_t s);
 // Batched update kernels over n systems (argument arrays in device memory).

@@ -268,6 +268,10 @@ __global__ void __launch_bounds__(kMaxSweepBlock) k_sweep_polymer(const PolyArgs
     int b = poly_bin(E, a);
     const uint32_t g0 = (uint32_t)a.state->sweep_counter;
     const int npl = (N + G - 1) / G;
+    // metrics: accepted moves and tunnelling between bins 0 and B-1 (group-uniform values)
+    unsigned long long nacc = 0;
+    unsigned ev = 0;
+    int tst = (active && a.tun) ? a.tun[w] : 0;
     constexpr float kStep = (float)kPolyStepQ * 0x1p-44f;
     for (int64_t sw = 0; sw < a.sweeps; ++sw) {
         const uint32_t g = g0 + (uint32_t)sw;
@@ -385,13 +389,18 @@ __global__ void __launch_bounds__(kMaxSweepBlock) k_sweep_polymer(const PolyArgs
                 }
                 E = En;
                 b = bn;
+                ++nacc;
             }
             __syncwarp();
             if (RECORD == 0 && li == 0 && active && b >= 0 && b < a.B) atomicAdd(a.H + b, 1ull);
         }
         if (RECORD == 1 && li == 0 && active && b >= 0 && b < a.B) atomicAdd(a.H + b, 1ull);
+        tunnel_step(b, 0, a.B - 1, tst, ev);
         __syncwarp();
     }
+    const bool lead = li == 0 && active;
+    flush_metrics(a.metrics, lead ? nacc : 0ull, lead ? ev : 0u);
+    if (lead && a.tun) a.tun[w] = (uint8_t)tst;
     if (!active) return;  // (no warp-wide operation follows)
     // recentre on bead 0 (an exact grid shift) and write back
     const long long A0 = Xg[0], A1 = Xg[N], A2 = Xg[2 * N];

@@ -169,7 +169,8 @@ template <int SYS, int L, int RECORD>
 __device__ __forceinline__ void ising_sweep_tc(uint32_t *__restrict__ lat, int ps, int &bR, uint32_t *__restrict__ sTH,
                                                const uint4 *__restrict__ ring_u, const uint2 *__restrict__ ring_c,
                                                const uint32_t *__restrict__ ring_r, unsigned long long *full,
-                                               unsigned long long *empty, int &k, bool &bad, unsigned long long *obs)
+                                               unsigned long long *empty, int &k, bool &bad, unsigned long long *obs,
+                                               unsigned &nacc)
 {
     int pc = 0;  // -1 spins of the final rows (observables)
     constexpr int WR = ising_words_per_row(L);
@@ -270,6 +271,7 @@ __device__ __forceinline__ void ising_sweep_tc(uint32_t *__restrict__ lat, int p
         for (int j = 0; j < WR; ++j) {
             lat[(y * WR + j) * ps] = cur[j];
             pc += __popc(cur[j]);
+            nacc += __popc(old[j] ^ cur[j]);
             up[j] = cur[j];
         }
         mbar_arrive(&empty[slot]);  // after the row is stored: the producer reads it later
@@ -325,6 +327,10 @@ __device__ __forceinline__ void sweep_block_tn(const SpinSweepArgs &a, int w0, i
     unsigned long long *Hb = a.Hpart + (size_t)slot_id * a.B;
     int k = 0;
     bool bad = false;
+    const int r_lo = a.bin_lo * RS, r_hi = a.bin_hi * RS;
+    int tst = (consumer && active && a.tun) ? a.tun[w] : 0;
+    unsigned ev = 0;
+    unsigned long long nacc = 0;
     for (int64_t s0 = 0; s0 < a.sweeps; s0 += a.flush_every) {
         const int64_t s1 = (a.sweeps < s0 + a.flush_every) ? a.sweeps : s0 + a.flush_every;
 #pragma unroll 1
@@ -338,12 +344,15 @@ __device__ __forceinline__ void sweep_block_tn(const SpinSweepArgs &a, int w0, i
                     produce_sweep_tn<SYS, L, 1>(g, wid, a.rk, lat, a.pstride, ring_u, ring_c, ring_r, full, empty, k, bad,
                                                 -1);
             } else if (consumer && active) {
+                unsigned na = 0;
                 if (a.record == 0)
                     ising_sweep_tc<SYS, L, 0>(lat, a.pstride, bR, sTH, ring_u, ring_c, ring_r, full, empty, k, bad,
-                                              a.obs);
+                                              a.obs, na);
                 else
                     ising_sweep_tc<SYS, L, 1>(lat, a.pstride, bR, sTH, ring_u, ring_c, ring_r, full, empty, k, bad,
-                                              a.obs);
+                                              a.obs, na);
+                nacc += na;
+                tunnel_step(bR, r_lo, r_hi, tst, ev);
             } else if (consumer) {  // a consumer warp with no walkers keeps the barrier protocol
 #pragma unroll 1
                 for (int y = 0; y < L; ++y) {
@@ -365,7 +374,11 @@ __device__ __forceinline__ void sweep_block_tn(const SpinSweepArgs &a, int w0, i
         __syncthreads();
     }
     if (bad) atomicOr(const_cast<int *>(&a.state->err), 1);
-    if (consumer && active) a.bin[w] = bR / RS;
+    if (consumer && active) {
+        a.bin[w] = bR / RS;
+        if (a.tun) a.tun[w] = (uint8_t)tst;
+    }
+    flush_metrics(a.metrics, nacc, ev);
 }
 
 template <int SYS, int L>
@@ -549,7 +562,7 @@ __device__ __forceinline__ void potts_sweep_tc(uint32_t *__restrict__ lat, int p
                                                uint32_t *__restrict__ sTH, const uint4 *__restrict__ ring_u,
                                                const uint2 *__restrict__ ring_c, const uint2 *__restrict__ ring_op,
                                                uint32_t *__restrict__ sU, unsigned long long *full,
-                                               unsigned long long *empty, int &k, bool &bad)
+                                               unsigned long long *empty, int &k, bool &bad, unsigned &nacc)
 {
     static_assert(L % 8 == 0, "whole nibble words a row");
     constexpr int WR = L / 8;
@@ -622,6 +635,7 @@ __device__ __forceinline__ void potts_sweep_tc(uint32_t *__restrict__ lat, int p
             site(u.y, byte_of(cd.x, 2), byte_of(cd.y, 2), am, 1);
             site(u.z, byte_of(cd.x, 3), byte_of(cd.y, 3), am, 2);
             site(u.w, byte_of(cdn.x, 0), byte_of(cdn.y, 0), am, 3);
+            nacc += (unsigned)__popc(am) >> 3;  // 0xff per accepted site
             const uint32_t f = op.x ^ ((op.x ^ op.y) & am);
             sU[j * 32] = f;
             if (j & 1) lat[(y * WR + (j >> 1)) * ps] = bytes_to_nibs(fprev, f);
@@ -646,6 +660,7 @@ __device__ __forceinline__ void potts_sweep_tc(uint32_t *__restrict__ lat, int p
             bB = acc ? bB + dR : bB;
             if (RECORD == 0) hist(bB + 4 * 9);
             accP = acc;
+            nacc += (unsigned)__popc(am) >> 3;
             const uint32_t f = op.x ^ ((op.x ^ op.y) & am);
             sU[j * 32] = f;
             lat[(y * WR + WR - 1) * ps] = bytes_to_nibs(fprev, f);
@@ -706,6 +721,10 @@ __device__ __forceinline__ void sweep_block_tnp(const SpinSweepArgs &a, int w0, 
     unsigned long long *Hb = a.Hpart + (size_t)slot_id * a.B;
     int k = 0;
     bool bad = false;
+    const int r_lo = a.bin_lo * RS, r_hi = a.bin_hi * RS;
+    int tst = (consumer && active && a.tun) ? a.tun[w] : 0;
+    unsigned ev = 0;
+    unsigned long long nacc = 0;
     if (consumer && active) {  // the row above row 0: row L-1 as the previous launch left it
         constexpr int WR = L / 8;
 #pragma unroll
@@ -728,10 +747,15 @@ __device__ __forceinline__ void sweep_block_tnp(const SpinSweepArgs &a, int w0, 
                     produce_sweep_potts_tn<L, RD, 2>(g, wid, a.rk, lat, a.pstride, (uint32_t)a.q, ring_u, ring_c,
                                                      ring_op, full, empty, k, bad, -1);
             } else if (consumer && active) {
+                unsigned na = 0;
                 if (a.record == 0)
-                    potts_sweep_tc<L, RD, 0>(lat, a.pstride, bR, sTH, ring_u, ring_c, ring_op, sU, full, empty, k, bad);
+                    potts_sweep_tc<L, RD, 0>(lat, a.pstride, bR, sTH, ring_u, ring_c, ring_op, sU, full, empty, k, bad,
+                                             na);
                 else
-                    potts_sweep_tc<L, RD, 1>(lat, a.pstride, bR, sTH, ring_u, ring_c, ring_op, sU, full, empty, k, bad);
+                    potts_sweep_tc<L, RD, 1>(lat, a.pstride, bR, sTH, ring_u, ring_c, ring_op, sU, full, empty, k, bad,
+                                             na);
+                nacc += na;
+                tunnel_step(bR, r_lo, r_hi, tst, ev);
             } else if (consumer) {
 #pragma unroll 1
                 for (int y = 0; y < L; ++y) {
@@ -753,7 +777,11 @@ __device__ __forceinline__ void sweep_block_tnp(const SpinSweepArgs &a, int w0, 
         __syncthreads();
     }
     if (bad) atomicOr(const_cast<int *>(&a.state->err), 1);
-    if (consumer && active) a.bin[w] = bR / RS;
+    if (consumer && active) {
+        a.bin[w] = bR / RS;
+        if (a.tun) a.tun[w] = (uint8_t)tst;
+    }
+    flush_metrics(a.metrics, nacc, ev);
 }
 
 template <int L, int RD>

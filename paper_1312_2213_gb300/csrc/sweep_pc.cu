@@ -22,7 +22,7 @@ template <int SYS, int L, int RECORD>
 __device__ __forceinline__ void ising_sweep_pc(uint32_t *__restrict__ lat, int ps, int &bR,
                                                uint32_t *__restrict__ sTH, const uint4 *__restrict__ ring,
                                                unsigned long long *full, unsigned long long *empty, int &k,
-                                               bool &bad, unsigned long long *obs)
+                                               bool &bad, unsigned long long *obs, unsigned &nacc)
 {
     int pc = 0;  // -1 spins of the final rows (observables)
     constexpr int WR = ising_words_per_row(L);
@@ -104,6 +104,7 @@ __device__ __forceinline__ void ising_sweep_pc(uint32_t *__restrict__ lat, int p
         for (int j = 0; j < WR; ++j) {
             lat[(y * WR + j) * ps] = cur[j];
             pc += __popc(cur[j]);
+            nacc += __popc(old[j] ^ cur[j]);
         }
         mbar_arrive(&empty[slot]);
         ++k;
@@ -127,7 +128,7 @@ template <int L, int RECORD>
 __device__ __forceinline__ void potts_sweep_pc(uint32_t *__restrict__ lat, int ps, int &bR,
                                                uint32_t *__restrict__ sTH, const uint4 *__restrict__ ring,
                                                unsigned long long *full, unsigned long long *empty, int &k,
-                                               bool &bad, uint32_t q)
+                                               bool &bad, uint32_t q, unsigned &nacc)
 {
     constexpr int WR = potts_words_per_row(L);
     constexpr int RS = 10;
@@ -214,7 +215,10 @@ __device__ __forceinline__ void potts_sweep_pc(uint32_t *__restrict__ lat, int p
         }
         bR = accP ? bR + dRp : bR;
 #pragma unroll
-        for (int j = 0; j < WR; ++j) lat[(y * WR + j) * ps] = cur[j];
+        for (int j = 0; j < WR; ++j) {
+            lat[(y * WR + j) * ps] = cur[j];
+            nacc += changed_nibbles(old[j], cur[j]);
+        }
         mbar_arrive(&empty[slot]);
         ++k;
         if (y == 0) {
@@ -295,6 +299,10 @@ __device__ __forceinline__ void sweep_block_pc(const SpinSweepArgs &a, int w0, i
     unsigned long long *Hb = a.Hpart + (size_t)slot_id * a.B;
     int k = 0;
     bool bad = false;
+    const int r_lo = a.bin_lo * RS, r_hi = a.bin_hi * RS;
+    int tst = (!producer && active && a.tun) ? a.tun[w] : 0;
+    unsigned ev = 0;
+    unsigned long long nacc = 0;
     // Inactive lanes (w >= p) run the same rows on walker 0's lattice copy in
     // registers only: they read but never store, so every lane arrives on every
     // barrier phase.
@@ -306,17 +314,20 @@ __device__ __forceinline__ void sweep_block_pc(const SpinSweepArgs &a, int w0, i
             if (producer) {
                 produce_sweep<SYS, L>(g, wid, a.rk, ring, full, empty, k, bad, drop_k);
             } else if (active) {
+                unsigned na = 0;
                 if (a.record == 0) {
                     if (SYS == kPotts)
-                        potts_sweep_pc<L, 0>(lat, a.pstride, bR, sTH, ring, full, empty, k, bad, (uint32_t)a.q);
+                        potts_sweep_pc<L, 0>(lat, a.pstride, bR, sTH, ring, full, empty, k, bad, (uint32_t)a.q, na);
                     else
-                        ising_sweep_pc<SYS, L, 0>(lat, a.pstride, bR, sTH, ring, full, empty, k, bad, a.obs);
+                        ising_sweep_pc<SYS, L, 0>(lat, a.pstride, bR, sTH, ring, full, empty, k, bad, a.obs, na);
                 } else {
                     if (SYS == kPotts)
-                        potts_sweep_pc<L, 1>(lat, a.pstride, bR, sTH, ring, full, empty, k, bad, (uint32_t)a.q);
+                        potts_sweep_pc<L, 1>(lat, a.pstride, bR, sTH, ring, full, empty, k, bad, (uint32_t)a.q, na);
                     else
-                        ising_sweep_pc<SYS, L, 1>(lat, a.pstride, bR, sTH, ring, full, empty, k, bad, a.obs);
+                        ising_sweep_pc<SYS, L, 1>(lat, a.pstride, bR, sTH, ring, full, empty, k, bad, a.obs, na);
                 }
+                nacc += na;
+                tunnel_step(bR, r_lo, r_hi, tst, ev);
             } else {
                 // inactive consumer lane: keep the barrier protocol, do no work
 #pragma unroll 1
@@ -339,7 +350,11 @@ __device__ __forceinline__ void sweep_block_pc(const SpinSweepArgs &a, int w0, i
         __syncthreads();
     }
     if (bad) atomicOr(const_cast<int *>(&a.state->err), 1);
-    if (!producer && active) a.bin[w] = bR / RS;
+    if (!producer && active) {
+        a.bin[w] = bR / RS;
+        if (a.tun) a.tun[w] = (uint8_t)tst;
+    }
+    flush_metrics(a.metrics, nacc, ev);
 }
 
 

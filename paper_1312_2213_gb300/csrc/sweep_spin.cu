@@ -39,7 +39,7 @@ namespace muca {
 template <int SYS, int L, int RECORD>
 __device__ __forceinline__ void ising_sweep(uint32_t *__restrict__ lat, int ps, int &bR,
                                             uint32_t *__restrict__ sTH, uint32_t g, uint32_t wid,
-                                            const uint32_t (&rk)[20], unsigned long long *obs)
+                                            const uint32_t (&rk)[20], unsigned long long *obs, unsigned &nacc)
 {
     int pc = 0;  // -1 spins of the final rows (observables)
     constexpr int WR = ising_words_per_row(L);
@@ -120,6 +120,7 @@ __device__ __forceinline__ void ising_sweep(uint32_t *__restrict__ lat, int ps, 
         for (int j = 0; j < WR; ++j) {
             lat[(y * WR + j) * ps] = cur[j];
             pc += __popc(cur[j]);
+            nacc += __popc(old[j] ^ cur[j]);
         }
         if (y == 0) {
 #pragma unroll
@@ -143,7 +144,7 @@ __device__ __forceinline__ void ising_sweep(uint32_t *__restrict__ lat, int ps, 
 template <int L, int RECORD>
 __device__ __forceinline__ void potts_sweep(uint32_t *__restrict__ lat, int ps, int &bR,
                                             uint32_t *__restrict__ sTH, uint32_t g, uint32_t wid,
-                                            const uint32_t (&rk)[20], uint32_t q)
+                                            const uint32_t (&rk)[20], uint32_t q, unsigned &nacc)
 {
     constexpr int WR = potts_words_per_row(L);
     constexpr int RS = 10;
@@ -223,7 +224,10 @@ __device__ __forceinline__ void potts_sweep(uint32_t *__restrict__ lat, int ps, 
         }
         bR = accP ? bR + dRp : bR;
 #pragma unroll
-        for (int j = 0; j < WR; ++j) lat[(y * WR + j) * ps] = cur[j];
+        for (int j = 0; j < WR; ++j) {
+            lat[(y * WR + j) * ps] = cur[j];
+            nacc += changed_nibbles(old[j], cur[j]);
+        }
         if (y == 0) {
 #pragma unroll
             for (int j = 0; j < WR; ++j) first[j] = cur[j];
@@ -265,6 +269,10 @@ __device__ __forceinline__ void sweep_block(const SpinSweepArgs &a, int w0, int 
     uint32_t *lat = a.lattice + (active ? w : 0);
     int bR = (active ? a.bin[w] : 0) * RS;
     unsigned long long *Hb = a.Hpart + (size_t)slot * a.B;
+    const int r_lo = a.bin_lo * RS, r_hi = a.bin_hi * RS;
+    int tst = (active && a.tun) ? a.tun[w] : 0;
+    unsigned ev = 0;
+    unsigned long long nacc = 0;
 
     for (int64_t s0 = 0; s0 < a.sweeps; s0 += a.flush_every) {
         const int64_t s1 = (a.sweeps < s0 + a.flush_every) ? a.sweeps : s0 + a.flush_every;
@@ -273,19 +281,25 @@ __device__ __forceinline__ void sweep_block(const SpinSweepArgs &a, int w0, int 
 #pragma unroll 1
                 for (int64_t sw = s0; sw < s1; ++sw) {
                     const uint32_t g = g0 + (uint32_t)sw;
+                    unsigned na = 0;
                     if (SYS == kPotts)
-                        potts_sweep<L, 0>(lat, a.pstride, bR, sTH, g, wid, a.rk, (uint32_t)a.q);
+                        potts_sweep<L, 0>(lat, a.pstride, bR, sTH, g, wid, a.rk, (uint32_t)a.q, na);
                     else
-                        ising_sweep<SYS, L, 0>(lat, a.pstride, bR, sTH, g, wid, a.rk, a.obs);
+                        ising_sweep<SYS, L, 0>(lat, a.pstride, bR, sTH, g, wid, a.rk, a.obs, na);
+                    nacc += na;
+                    tunnel_step(bR, r_lo, r_hi, tst, ev);
                 }
             } else {
 #pragma unroll 1
                 for (int64_t sw = s0; sw < s1; ++sw) {
                     const uint32_t g = g0 + (uint32_t)sw;
+                    unsigned na = 0;
                     if (SYS == kPotts)
-                        potts_sweep<L, 1>(lat, a.pstride, bR, sTH, g, wid, a.rk, (uint32_t)a.q);
+                        potts_sweep<L, 1>(lat, a.pstride, bR, sTH, g, wid, a.rk, (uint32_t)a.q, na);
                     else
-                        ising_sweep<SYS, L, 1>(lat, a.pstride, bR, sTH, g, wid, a.rk, a.obs);
+                        ising_sweep<SYS, L, 1>(lat, a.pstride, bR, sTH, g, wid, a.rk, a.obs, na);
+                    nacc += na;
+                    tunnel_step(bR, r_lo, r_hi, tst, ev);
                 }
             }
         }
@@ -299,7 +313,11 @@ __device__ __forceinline__ void sweep_block(const SpinSweepArgs &a, int w0, int 
         }
         __syncthreads();
     }
-    if (active) a.bin[w] = bR / RS;
+    if (active) {
+        a.bin[w] = bR / RS;
+        if (a.tun) a.tun[w] = (uint8_t)tst;
+    }
+    flush_metrics(a.metrics, nacc, ev);
 }
 
 // One system per launch: block k runs walkers [k*blockDim.x, (k+1)*blockDim.x).

@@ -121,10 +121,28 @@ __device__ __forceinline__ void recursion_body(const UpdateArgs &a, double *sm)
     }
 }
 
+// The iteration's metrics become the "last" ones (and are added to the totals);
+// the open counters restart.  Runs once per update, after the sweeps' atomics.
+__device__ __forceinline__ void close_metrics(const UpdateArgs &a)
+{
+    unsigned long long *m = a.metrics;
+    if (!m || threadIdx.x != 0) return;
+    m[2] = m[0];
+    m[3] = m[1];
+    m[4] += m[0];
+    m[5] += m[1];
+    const unsigned long long sc = a.state->sweep_counter;
+    m[6] = sc - m[7];
+    m[7] = sc;
+    m[0] = 0ull;
+    m[1] = 0ull;
+}
+
 __global__ void __launch_bounds__(1024) k_recursion(const UpdateArgs a)
 {
     extern __shared__ double sm[];
     recursion_body(a, sm);
+    close_metrics(a);
 }
 
 __global__ void __launch_bounds__(1024) k_recursion_batch(const UpdateArgs *__restrict__ arr)
@@ -132,6 +150,7 @@ __global__ void __launch_bounds__(1024) k_recursion_batch(const UpdateArgs *__re
     extern __shared__ double sm[];
     const UpdateArgs a = arr[blockIdx.y];
     recursion_body(a, sm);
+    close_metrics(a);
 }
 
 __device__ __forceinline__ void thresholds_body(const UpdateArgs &a, int i)

@@ -57,5 +57,22 @@ class ShardedMuca:
         torch.cuda.synchronize()
         return muca_update_with(self.ctx.h, self.buf.data_ptr(), want_flat)
 
+    def metrics(self) -> dict:
+        """The last closed iteration's metrics summed over the ranks of the group (each rank
+        counts its own walkers); the acceptance rate is over all walkers."""
+        d = self.ctx.metrics()
+        keys = ("accepted", "tunnelling_events", "accepted_total", "tunnelling_events_total")
+        t = torch.tensor([d[k] for k in keys] + [self.w1 - self.w0], dtype=torch.int64)
+        if dist.get_backend(self.group) == "nccl":
+            t = t.cuda()
+        dist.all_reduce(t, group=self.group)
+        t = t.cpu()
+        out = dict(d)
+        out.update({k: int(v) for k, v in zip(keys, t[:4])})
+        p = int(t[4])
+        attempts = p * self.ctx.N * d["sweeps"]
+        out["acceptance_rate"] = out["accepted"] / attempts if attempts else float("nan")
+        return out
+
     def close(self):
         self.ctx.close()

@@ -2,6 +2,7 @@
 on another rank, the exchange is a host all-reduce) each run half of the walkers through the C ABI
 (muca_merge_open + all-reduce + muca_update_with).  Weights, histograms and lattices must equal one
 context of all walkers bit for bit."""
+import json
 import os
 import socket
 import sys
@@ -49,6 +50,9 @@ def _rank_main(rank, world, port, out_dir, case):
     np.save(os.path.join(out_dir, "lnW_%d.npy" % rank), s.ctx.lnW())
     np.save(os.path.join(out_dir, "H_%d.npy" % rank), s.ctx.histogram())
     np.save(os.path.join(out_dir, "spins_%d.npy" % rank), s.ctx.spins())
+    met = s.metrics()  # summed over the ranks
+    with open(os.path.join(out_dir, "metrics_%d.json" % rank), "w") as f:
+        json.dump(met, f)
     dist.barrier()
     s.close()
     dist.destroy_process_group()
@@ -70,3 +74,10 @@ def test_two_shards_equal_one_context(tmp_path, case):
         np.testing.assert_array_equal(np.load(tmp_path / ("H_%d.npy" % rank)), g.histogram())
     spins = np.concatenate([np.load(tmp_path / ("spins_%d.npy" % r)) for r in range(world)])
     np.testing.assert_array_equal(spins, g.spins())
+    gm = g.metrics()
+    for rank in range(world):
+        with open(tmp_path / ("metrics_%d.json" % rank)) as f:
+            sm = json.load(f)
+        for k in ("accepted", "tunnelling_events", "accepted_total", "tunnelling_events_total", "sweeps",
+                  "iteration", "acceptance_rate"):
+            assert sm[k] == gm[k], k
