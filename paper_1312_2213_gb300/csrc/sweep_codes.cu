@@ -635,7 +635,7 @@ __device__ __forceinline__ void potts_sweep_tc(uint32_t *__restrict__ lat, int p
             site(u.y, byte_of(cd.x, 2), byte_of(cd.y, 2), am, 1);
             site(u.z, byte_of(cd.x, 3), byte_of(cd.y, 3), am, 2);
             site(u.w, byte_of(cdn.x, 0), byte_of(cdn.y, 0), am, 3);
-            nacc += (unsigned)__popc(am) >> 3;  // 0xff per accepted site
+            nacc += (unsigned)__popc(am);  // 0xff per accepted site: 8 x accepted (divided at the end)
             const uint32_t f = op.x ^ ((op.x ^ op.y) & am);
             sU[j * 32] = f;
             if (j & 1) lat[(y * WR + (j >> 1)) * ps] = bytes_to_nibs(fprev, f);
@@ -660,7 +660,7 @@ __device__ __forceinline__ void potts_sweep_tc(uint32_t *__restrict__ lat, int p
             bB = acc ? bB + dR : bB;
             if (RECORD == 0) hist(bB + 4 * 9);
             accP = acc;
-            nacc += (unsigned)__popc(am) >> 3;
+            nacc += (unsigned)__popc(am);
             const uint32_t f = op.x ^ ((op.x ^ op.y) & am);
             sU[j * 32] = f;
             lat[(y * WR + WR - 1) * ps] = bytes_to_nibs(fprev, f);
@@ -669,6 +669,7 @@ __device__ __forceinline__ void potts_sweep_tc(uint32_t *__restrict__ lat, int p
         ++k;
     }
     bR = (bB - sbase) / 4;
+    nacc >>= 3;
     if (RECORD == 1) atomicAdd(&sTH[bR + 9], 1u);
 }
 
