@@ -71,7 +71,7 @@ MIX_P = 2048
 
 
 def run_mix(m, torch, sweeps=1000, short_sweeps=10, short_iters=20):
-    """Plain (one system per launch, host loop) vs batched (one launch per iteration) vs graph."""
+    """Plain (one system per launch, host loop) vs batched (both batch forms) vs graph."""
     sites = sum(L * L for _, L, _ in MIX)
 
     def make(seed0):  # default walkers per block: the plain path runs the fastest form that fits
@@ -99,28 +99,40 @@ def run_mix(m, torch, sweeps=1000, short_sweeps=10, short_iters=20):
             c.merge_and_update()
 
     t_plain = timed(lambda: plain_iter(sysA, sweeps))
-    sysB = make(200)
-    batch = m.Batch(sysB)
-    batch.run(1, 20, use_graph=False)
-    t_batch = timed(lambda: batch.run(1, sweeps, use_graph=False))
-    batch.run(1, sweeps, use_graph=True)      # capture
-    t_graph = timed(lambda: batch.run(1, sweeps, use_graph=True))
+    t_plain_s = timed(lambda: [plain_iter(sysA, short_sweeps) for _ in range(short_iters)])
     att = MIX_P * sweeps * sites
-    out["throughput"] = {"sweeps_per_iteration": sweeps, "attempts_per_iteration": att,
+    att_s = MIX_P * short_sweeps * sites * short_iters
+    # batched forms: 0 = one persistent launch over all systems' tiles (one warp per 32 walkers),
+    # 1 = every system's own (code-form) sweep kernel side by side on forked streams
+    forms, made = {}, []
+    for form in (0, 1):
+        sysB = make(200 + 100 * form)
+        made += sysB
+        batch = m.Batch(sysB, form=form)
+        batch.run(1, 20, use_graph=False)
+        t_batch = timed(lambda: batch.run(1, sweeps, use_graph=False))
+        batch.run(1, sweeps, use_graph=True)      # capture
+        t_graph = timed(lambda: batch.run(1, sweeps, use_graph=True))
+        batch.run(short_iters, short_sweeps, use_graph=True)  # capture
+        t_graph_s = timed(lambda: batch.run(short_iters, short_sweeps, use_graph=True))
+        t_batch_s = timed(lambda: batch.run(short_iters, short_sweeps, use_graph=False))
+        batch.close()
+        forms[form] = (t_batch, t_graph, t_batch_s, t_graph_s)
+    best = min(forms, key=lambda f: forms[f][1])
+    t_batch, t_graph, t_batch_s, t_graph_s = forms[best]
+    out["throughput"] = {"sweeps_per_iteration": sweeps, "attempts_per_iteration": att, "batch_form": best,
                          "plain_attempts_per_s": att / t_plain, "batched_attempts_per_s": att / t_batch,
                          "graph_attempts_per_s": att / t_graph, "batched_over_plain": t_plain / t_batch,
-                         "graph_over_plain": t_plain / t_graph}
+                         "graph_over_plain": t_plain / t_graph,
+                         "by_form": {str(f): {"batched_attempts_per_s": att / v[0], "graph_attempts_per_s": att / v[1]}
+                                     for f, v in forms.items()}}
     # short iterations: launch and host overheads dominate
-    t_plain_s = timed(lambda: [plain_iter(sysA, short_sweeps) for _ in range(short_iters)])
-    batch.run(short_iters, short_sweeps, use_graph=True)  # capture
-    t_graph_s = timed(lambda: batch.run(short_iters, short_sweeps, use_graph=True))
-    t_batch_s = timed(lambda: batch.run(short_iters, short_sweeps, use_graph=False))
-    att_s = MIX_P * short_sweeps * sites * short_iters
-    out["short_iterations"] = {"sweeps_per_iteration": short_sweeps, "iterations": short_iters,
+    out["short_iterations"] = {"sweeps_per_iteration": short_sweeps, "iterations": short_iters, "batch_form": best,
                                "plain_attempts_per_s": att_s / t_plain_s, "batched_attempts_per_s": att_s / t_batch_s,
-                               "graph_attempts_per_s": att_s / t_graph_s, "graph_over_plain": t_plain_s / t_graph_s}
-    batch.close()
-    for c in sysA + sysB:
+                               "graph_attempts_per_s": att_s / t_graph_s, "graph_over_plain": t_plain_s / t_graph_s,
+                               "by_form": {str(f): {"batched_attempts_per_s": att_s / v[2],
+                                                    "graph_attempts_per_s": att_s / v[3]} for f, v in forms.items()}}
+    for c in sysA + made:
         c.close()
     return out
 

@@ -84,7 +84,8 @@ int muca_init_ex(muca_ctx **out, int system, int L_or_N, int q, int p, uint64_t 
  *                 1 = once per sweep; before the first iterate.
  *   "flat_ratio"  flatness criterion min H / mean H (default 0.5); any time.
  *   "block"       spins: walkers per thread block of the sweep kernel (32..512,
- *                 multiple of 32; default 64; the code form runs for 32 or 64);
+ *                 multiple of 32; default 64, or 32 where only that fits the
+ *                 code form; the code form runs for 32 or 64);
  *                 polymer: threads per block (default 256).  Before the first
  *                 iterate.
  *   "pipeline"    spins: 2 (default) pairs every warp of walkers with a
@@ -241,8 +242,8 @@ int muca_get_sweep_counter(muca_ctx *ctx, int64_t *host_out);
  * lattice sizes and walker counts, e.g. Ising L in {16..64} and q = 10 Potts
  * L in {16..48} with 2048 walkers each -- so that systems too small to fill the
  * GPU alone fill it together.  Each iteration of muca_batch_run is the paper's
- * Fig. 1 step for every system at once: sweeps of all walkers of all systems in
- * ONE persistent kernel launch over a tile list, then the merge, the
+ * Fig. 1 step for every system at once: sweeps of all walkers of all systems
+ * (side by side, or in one persistent launch: see muca_batch_set_form), then the merge, the
  * accumulated-statistics recursion and the threshold rebuild for all systems
  * (one launch each).  With use_graph != 0 all n_iter iterations are captured
  * once into a CUDA graph (re-captured when n_iter or sweeps change) and
@@ -255,6 +256,16 @@ int muca_get_sweep_counter(muca_ctx *ctx, int64_t *host_out);
 int muca_batch_create(muca_ctx *const *systems, int n, muca_batch **out);
 int muca_batch_run(muca_batch *batch, int n_iter, int64_t sweeps, int use_graph);
 int muca_batch_free(muca_batch *batch);
+/* How a batch runs its sweeps.  form 1 (default): each context's own sweep
+ * kernel in its configured form ("pipeline", "block"), one stream per
+ * context, forked from and joined back into the batch's stream, heaviest
+ * system first, so the launches run side by side (in a graph: as parallel
+ * branches); the merge, recursion and threshold launches stay batched.
+ * form 0: the one persistent launch over a tile list described above (one
+ * warp per 32 walkers, 128 walkers a tile).  Same results either way.
+ * Changing the form drops a captured graph.  Errors: MUCA_ERR_ARG for another
+ * value. */
+int muca_batch_set_form(muca_batch *batch, int form);
 
 /* Diagnostics: evaluate the library's deterministic binary64 exp (fn = 0) or
  * log (fn = 1) -- the functions the weight recursion and the threshold build

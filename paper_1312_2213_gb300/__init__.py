@@ -25,7 +25,7 @@ __all__ = ["Muca", "MucaError", "ISING2D", "POTTS2D", "ISING2D_MUMA", "POLYMER3D
            "muca_get_state", "muca_set_state",
            "muca_get_spins", "muca_get_walker_bins", "muca_get_thresholds", "muca_get_sweep_counter",
            "muca_synchronize", "muca_free", "muca_last_error", "muca_det_math",
-           "muca_iterate_noalloc", "muca_get_coords", "muca_get_drift", "muca_batch_create", "muca_batch_run", "muca_batch_free", "Batch"]
+           "muca_iterate_noalloc", "muca_get_coords", "muca_get_drift", "muca_batch_create", "muca_batch_run", "muca_batch_free", "muca_batch_set_form", "Batch"]
 
 
 def _p(a: np.ndarray):
@@ -187,17 +187,28 @@ def muca_batch_run(b, n_iter: int, sweeps: int, use_graph: bool = True):
     check(load().muca_batch_run(b, n_iter, sweeps, 1 if use_graph else 0), "muca_batch_run")
 
 
+def muca_batch_set_form(b, form: int):
+    check(load().muca_batch_set_form(b, int(form)), "muca_batch_set_form")
+
+
 def muca_batch_free(b):
     check(load().muca_batch_free(b), "muca_batch_free")
 
 
 class Batch:
-    """Several Muca systems advanced together (one persistent sweep launch per iteration;
-    optionally the whole run as one CUDA graph)."""
+    """Several Muca systems advanced together: per iteration every system's own sweep kernel on a
+    stream of its own, side by side (form 1, default), or one persistent sweep launch over all
+    systems (form 0); then batched merge, recursion and thresholds; optionally the whole run as
+    one CUDA graph."""
 
-    def __init__(self, systems):
+    def __init__(self, systems, form: int = 1):
         self.systems = list(systems)
         self.h = muca_batch_create([s.h for s in self.systems])
+        if form != 1:
+            self.set_form(form)
+
+    def set_form(self, form: int):
+        muca_batch_set_form(self.h, form)
 
     def run(self, n_iter: int, sweeps: int, use_graph: bool = True):
         muca_batch_run(self.h, n_iter, sweeps, use_graph)

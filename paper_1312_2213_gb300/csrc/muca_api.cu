@@ -147,6 +147,9 @@ void fill_shape(muca_ctx *c, int system, int L, int q, int p)
     c->pstride = (p + 31) / 32 * 32;
     c->wpw = words_per_walker(system, L);
     c->nblk_max = (p + 31) / 32;  // smallest allowed block is one warp
+    // default walkers per block: 64, or 32 where only that fits the code form (e.g. q = 10 Potts,
+    // L = 48, whose threshold table alone takes 184 KB of shared memory)
+    if (!spin_sweep_tn_fits(system, L, c->B, 64) && spin_sweep_tn_fits(system, L, c->B, 32)) c->block = 32;
 }
 
 // Reachable bins of the periodic L x L lattice (L even): the Ising model has
@@ -286,6 +289,17 @@ SpinSweepArgs sweep_args(const muca_ctx *c, int64_t sweeps, int block)
     a.bin_lo = c->h_rlist.front();
     a.bin_hi = c->h_rlist.back();
     return a;
+}
+
+// The context's sweep in its configured form (code form, producer/consumer or one warp), falling
+// back to the next lower form where one does not fit the system, L, bin count or block.
+cudaError_t launch_system_sweep(const muca_ctx *c, const SpinSweepArgs &a, cudaStream_t s)
+{
+    if (c->pipeline >= 2 && spin_sweep_tn_fits(c->system, c->L, c->B, c->block))
+        return launch_spin_sweep_tn(c->system, c->L, a, c->block, s);
+    if (c->pipeline >= 1 && spin_sweep_pc_fits(c->system, c->L, c->B, c->block))
+        return launch_spin_sweep_pc(c->system, c->L, a, c->block, s);
+    return launch_spin_sweep(c->system, c->L, a, c->block, s);
 }
 
 PolyArgs poly_args(const muca_ctx *c, int64_t sweeps)
@@ -692,13 +706,7 @@ int muca_iterate(muca_ctx *c, int64_t sweeps)
     a.obs = (c->observables && c->system == kIsing) ? c->obs : nullptr;
     a.debug_drop_row = c->debug_drop_row;
     c->debug_drop_row = -1;
-    if (c->pipeline >= 2 && spin_sweep_tn_fits(c->system, c->L, c->B, c->block)) {
-        MUCA_CUDA(launch_spin_sweep_tn(c->system, c->L, a, c->block, c->stream));
-    } else if (c->pipeline >= 1 && spin_sweep_pc_fits(c->system, c->L, c->B, c->block)) {
-        MUCA_CUDA(launch_spin_sweep_pc(c->system, c->L, a, c->block, c->stream));
-    } else {
-        MUCA_CUDA(launch_spin_sweep(c->system, c->L, a, c->block, c->stream));
-    }
+    MUCA_CUDA(launch_system_sweep(c, a, c->stream));
     MUCA_CUDA(launch_advance(c->state, sweeps, c->stream));
     c->started = true;
     c->open = true;
@@ -1110,6 +1118,14 @@ struct muca_batch {
     cudaGraphExec_t exec = nullptr;
     int g_iter = 0;
     int64_t g_sweeps = 0;
+    // form 1: every system's own sweep launch on a stream of its own, forked from and joined
+    // back into the batch stream (captured as parallel graph branches)
+    int form = 0;  // set to 1 (the default) by muca_batch_create
+    std::vector<cudaStream_t> sub;
+    std::vector<cudaEvent_t> ev_join;
+    cudaEvent_t ev_fork = nullptr;
+    std::vector<SpinSweepArgs> h_own;  // form 1: per-system launch arguments
+    std::vector<int> order;            // systems, heaviest first (tile order; form 1 launch order)
 };
 
 namespace {
@@ -1117,7 +1133,18 @@ namespace {
 int batch_enqueue_iteration(muca_batch *b, int64_t sweeps)
 {
     const int n = (int)b->sys.size();
-    MUCA_CUDA(launch_sweep_batch(b->d_sys, b->d_tiles, b->ntiles, b->block, b->smem, b->stream));
+    if (b->form == 1) {
+        MUCA_CUDA(cudaEventRecord(b->ev_fork, b->stream));
+        // heaviest first, so that their blocks take the SMs before the light systems' blocks
+        for (int i : b->order) {
+            MUCA_CUDA(cudaStreamWaitEvent(b->sub[i], b->ev_fork, 0));
+            MUCA_CUDA(launch_system_sweep(b->sys[i], b->h_own[i], b->sub[i]));
+            MUCA_CUDA(cudaEventRecord(b->ev_join[i], b->sub[i]));
+        }
+        for (int i = 0; i < n; ++i) MUCA_CUDA(cudaStreamWaitEvent(b->stream, b->ev_join[i], 0));
+    } else {
+        MUCA_CUDA(launch_sweep_batch(b->d_sys, b->d_tiles, b->ntiles, b->block, b->smem, b->stream));
+    }
     MUCA_CUDA(launch_advance_batch(b->d_states, n, sweeps, b->stream));
     MUCA_CUDA(launch_merge_batch(b->d_upd, n, b->max_bins, b->stream));
     MUCA_CUDA(launch_recursion_batch(b->d_upd, n, b->max_nreach, b->stream));
@@ -1178,6 +1205,7 @@ int muca_batch_create(muca_ctx *const *systems, int n, muca_batch **out)
     }
     for (int i : order)
         for (int w0 = 0; w0 < b->sys[i]->p; w0 += b->block) tiles.push_back(make_int2(i, w0));
+    b->order = order;
     b->ntiles = (int)tiles.size();
     b->h_sys.resize(n);
     const size_t sz_sys = align_up(sizeof(SpinSweepArgs) * n), sz_tiles = align_up(sizeof(int2) * tiles.size()),
@@ -1208,6 +1236,10 @@ int muca_batch_create(muca_ctx *const *systems, int n, muca_batch **out)
         delete b;
         return fail(MUCA_ERR_CUDA, "muca_batch_create: %s", cudaGetErrorString(e));
     }
+    if (int rc = muca_batch_set_form(b, 1)) {  // default: the systems' own kernels side by side
+        muca_batch_free(b);
+        return rc;
+    }
     *out = b;
     return MUCA_OK;
 }
@@ -1222,6 +1254,8 @@ int muca_batch_run(muca_batch *b, int n_iter, int64_t sweeps, int use_graph)
         if (b->sys[i]->open)
             return fail(MUCA_ERR_STATE, "system %d has unmerged sweeps; call muca_merge_and_update first", i);
     for (int i = 0; i < n; ++i) b->h_sys[i] = sweep_args(b->sys[i], sweeps, b->block);
+    b->h_own.resize(n);
+    for (int i = 0; i < n; ++i) b->h_own[i] = sweep_args(b->sys[i], sweeps, b->sys[i]->block);
     // order the batch's own stream after the systems' earlier work
     MUCA_CUDA(cudaEventRecord(b->ev_in, b->ctx_stream));
     MUCA_CUDA(cudaStreamWaitEvent(b->stream, b->ev_in, 0));
@@ -1230,8 +1264,8 @@ int muca_batch_run(muca_batch *b, int n_iter, int64_t sweeps, int use_graph)
     // the flatness ratio may change between runs
     std::vector<UpdateArgs> upd(n);
     for (int i = 0; i < n; ++i) {
-        upd[i] = update_args(b->sys[i]);
-        upd[i].nblocks = (b->sys[i]->p + b->block - 1) / b->block;
+        upd[i] = update_args(b->sys[i]);  // form 1: each system's own block count
+        if (b->form == 0) upd[i].nblocks = (b->sys[i]->p + b->block - 1) / b->block;
     }
     MUCA_CUDA(cudaMemcpyAsync(b->d_upd, upd.data(), sizeof(UpdateArgs) * n, cudaMemcpyHostToDevice, b->stream));
     if (use_graph) {
@@ -1279,11 +1313,45 @@ int muca_batch_free(muca_batch *b)
     cudaError_t e = cudaStreamSynchronize(b->stream);
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->dmem) cudaFree(b->dmem);
+    for (cudaStream_t st : b->sub) {
+        if (cudaStreamSynchronize(st) != cudaSuccess && e == cudaSuccess) e = cudaErrorUnknown;
+        cudaStreamDestroy(st);
+    }
+    for (cudaEvent_t ev : b->ev_join) cudaEventDestroy(ev);
+    if (b->ev_fork) cudaEventDestroy(b->ev_fork);
     cudaStreamDestroy(b->stream);
     cudaEventDestroy(b->ev_in);
     cudaEventDestroy(b->ev_out);
     delete b;
     if (e != cudaSuccess) return fail(MUCA_ERR_CUDA, "muca_batch_free: %s", cudaGetErrorString(e));
+    return MUCA_OK;
+}
+
+int muca_batch_set_form(muca_batch *b, int form)
+{
+    if (!b) return fail(MUCA_ERR_ARG, "batch is NULL");
+    if (form != 0 && form != 1) return fail(MUCA_ERR_ARG, "batch form must be 0 or 1");
+    if (form == 1 && b->sub.empty()) {
+        const int n = (int)b->sys.size();
+        for (int i = 0; i < n; ++i) {
+            cudaStream_t st = nullptr;
+            cudaEvent_t ev = nullptr;
+            if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess)
+                return fail(MUCA_ERR_CUDA, "muca_batch_set_form: cannot create a stream");
+            b->sub.push_back(st);
+            if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess)
+                return fail(MUCA_ERR_CUDA, "muca_batch_set_form: cannot create an event");
+            b->ev_join.push_back(ev);
+        }
+        if (cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming) != cudaSuccess)
+            return fail(MUCA_ERR_CUDA, "muca_batch_set_form: cannot create an event");
+    }
+    if (form != b->form && b->exec) {  // the captured graph belongs to the other form
+        MUCA_CUDA(cudaStreamSynchronize(b->stream));
+        cudaGraphExecDestroy(b->exec);
+        b->exec = nullptr;
+    }
+    b->form = form;
     return MUCA_OK;
 }
 

@@ -26,8 +26,9 @@ def _make():
     return [m.Muca(s, L, q, p, seed, beta=beta) for s, L, q, p, seed, beta in MIX]
 
 
+@pytest.mark.parametrize("form", [0, 1])
 @pytest.mark.parametrize("use_graph", [False, True])
-def test_batch_equals_individual_runs(use_graph):
+def test_batch_equals_individual_runs(use_graph, form):
     n_iter, sweeps = 3, 15
     ref = _make()
     for _ in range(n_iter):
@@ -35,7 +36,7 @@ def test_batch_equals_individual_runs(use_graph):
             c.iterate(sweeps)
             c.merge_and_update()
     sys_ = _make()
-    b = m.Batch(sys_)
+    b = m.Batch(sys_, form=form)
     b.run(n_iter, sweeps, use_graph=use_graph)
     b.run(2, sweeps, use_graph=use_graph)  # second run: graph re-captured for a new n_iter
     for _ in range(2):
@@ -51,9 +52,10 @@ def test_batch_equals_individual_runs(use_graph):
     b.close()
 
 
-def test_batch_graph_replay_matches_oracle():
+@pytest.mark.parametrize("form", [0, 1])
+def test_batch_graph_replay_matches_oracle(form):
     sys_ = _make()
-    b = m.Batch(sys_)
+    b = m.Batch(sys_, form=form)
     for _ in range(2):
         b.run(2, 10, use_graph=True)   # same graph replayed twice
     s, L, q, p, seed, beta = MIX[1]
@@ -76,3 +78,29 @@ def test_batch_rejects_unmerged_and_duplicates():
     assert e.value.code == -5
     sys_[0].merge_and_update()
     b.run(1, 5)
+
+
+def test_batch_form_switch_keeps_results():
+    """Alternating the two forms (the captured graph of one is dropped for the other) gives the
+    same state as individual runs; bad form values are refused."""
+    ref = _make()
+    for _ in range(4):
+        for c in ref:
+            c.iterate(12)
+            c.merge_and_update()
+    sys_ = _make()
+    b = m.Batch(sys_)
+    b.run(1, 12, use_graph=True)
+    b.set_form(1)
+    b.run(1, 12, use_graph=True)
+    b.set_form(0)
+    b.run(1, 12, use_graph=False)
+    b.set_form(1)
+    b.run(1, 12, use_graph=False)
+    with pytest.raises(m.MucaError):
+        b.set_form(2)
+    for r, c in zip(ref, sys_):
+        np.testing.assert_array_equal(r.lnW().view(np.uint64), c.lnW().view(np.uint64))
+        np.testing.assert_array_equal(r.spins(), c.spins())
+        assert r.metrics() == c.metrics()
+    b.close()
