@@ -553,8 +553,10 @@ __device__ __forceinline__ void produce_sweep_potts_tn(uint32_t g, uint32_t wid,
     }
 }
 
-// The consumer runs a rolled loop over the row's byte words (4 sites each) and
-// peels the last word, which holds the last site's right-neighbour term.  The
+// The consumer runs a loop over the row's byte words (4 sites each), unrolled
+// by two (rolled it lost 16-20 % to loop overhead between the words' chains;
+// fully unrolled, L = 48 stalled on instruction fetch), and peels the last
+// word, which holds the last site's right-neighbour term.  The
 // final row above lives in a per-lane shared-memory row sU (bytes), rewritten
 // word by word as the current row completes.
 template <int L, int RD, int RECORD>
@@ -624,7 +626,7 @@ __device__ __forceinline__ void potts_sweep_tc(uint32_t *__restrict__ lat, int p
             accP = acc;
         };
         uint32_t fprev = 0u;
-#pragma unroll 1
+#pragma unroll 2
         for (int j = 0; j < W4 - 1; ++j) {
             const uint2 op = opn, cd = cdn;
             const uint4 u = ru[j * 32];
