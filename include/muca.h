@@ -117,6 +117,13 @@ int muca_init_ex(muca_ctx **out, int system, int L_or_N, int q, int p, uint64_t 
  *                 call returns MUCA_ERR_TIMEOUT.  The context's walker state is
  *                 invalid afterwards (restore a checkpoint with muca_set_state).
  *                 No effect with pipeline = 0 or a row past the call's sweeps.
+ *   "spin_limit"  tries (of mbarrier.try_wait, each suspending the warp for a
+ *                 few microseconds) one row hand-over of the producer/consumer
+ *                 forms makes before it gives up; 0 (default) = 2^17, about a
+ *                 second on GB300.  The environment variable MUCA_SPIN_LIMIT
+ *                 sets it at muca_init.  A limit too small for a healthy run
+ *                 only makes the next synchronising call report
+ *                 MUCA_ERR_TIMEOUT.  Any time.
  *   "model"       polymer, before the first iterate: 0 (default) = the benchmark
  *                 parameters (FENE K = 40, R = 1.5, rest length 0; LJ sigma = 1 cut
  *                 at 2.5 and shifted), 1 = the paper's own parameters of Eq. (7)

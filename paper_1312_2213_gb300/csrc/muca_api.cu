@@ -6,6 +6,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <algorithm>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <new>
@@ -70,6 +71,7 @@ struct muca_ctx {
     int model = 0;     // polymer: 0 benchmark parameters, 1 the paper's (Eq. 7)
     int moves = 0;     // polymer: 0 single-bead shifts, 1 shifts and spherical rotations
     int debug_drop_row = -1;  // test hook for the bounded waits (next spin iterate only)
+    int spin_limit = 0;       // tries of one bounded hand-over wait (0: the kernels' default)
     int recursion = 0;        // weight update: 0 accumulated statistics, 1 plain W/H
     int observables = 0;      // Ising: per-sweep sums of 1, |M|, M^2 per bin
     unsigned long long *obs = nullptr;  // [0, 3B): sums being filled, [3B, 6B): of the last update
@@ -288,6 +290,7 @@ SpinSweepArgs sweep_args(const muca_ctx *c, int64_t sweeps, int block)
     a.tun = c->tun;
     a.bin_lo = c->h_rlist.front();
     a.bin_hi = c->h_rlist.back();
+    a.spin_limit = c->spin_limit;
     return a;
 }
 
@@ -433,6 +436,10 @@ int create(muca_ctx **out, int system, int L, int q, int p, uint64_t seed, void 
     if (!c) return fail(MUCA_ERR_OOM, "host allocation failed");
     fill_shape(c, system, L, q, p);
     c->seed = seed;
+    if (const char *env = std::getenv("MUCA_SPIN_LIMIT")) {  // bound of the hand-over waits
+        const long v = std::strtol(env, nullptr, 10);
+        if (v > 0 && v <= 0x7fffffffL) c->spin_limit = (int)v;
+    }
     const size_t need = plan(c).total;
     if (arena) {
         if (arena_bytes < need || ((uintptr_t)arena % kAlign) != 0) {
@@ -618,6 +625,13 @@ int muca_set_param(muca_ctx *c, const char *key, double v)
         if ((double)b != v || b < 32 || b > kMaxSweepBlock || (b % 32) != 0)
             return fail(MUCA_ERR_ARG, "block must be a multiple of 32 in [32, %d]", kMaxSweepBlock);
         c->block = b;
+        return MUCA_OK;
+    }
+    if (k == "spin_limit") {
+        const long long lim = (long long)v;
+        if ((double)lim != v || lim < 0 || lim > 0x7fffffffLL)
+            return fail(MUCA_ERR_ARG, "spin_limit must be an integer in [0, 2^31)");
+        c->spin_limit = (int)lim;
         return MUCA_OK;
     }
     if (k == "pipeline") {

@@ -316,6 +316,7 @@ __device__ __forceinline__ void sweep_block_tn(const SpinSweepArgs &a, int w0, i
     }
     if (tid == 0)  // per pair: FULL[kRing] (NP producer warps arrive), EMPTY[kRing] (the consumer)
         for (int i = 0; i < ncw * 2 * kRing; ++i) mbar_init(bars + i, ((i / kRing) % 2 == 0) ? 32 * NP : 32);
+    set_block_spin_limit(a.spin_limit);
     __syncthreads();
 
     const int w = w0 + pair * 32 + lane;
@@ -713,6 +714,7 @@ __device__ __forceinline__ void sweep_block_tnp(const SpinSweepArgs &a, int w0, 
     }
     if (tid == 0)  // per pair: FULL[RD] (NP producer warps arrive), EMPTY[RD] (the consumer)
         for (int i = 0; i < ncw * 2 * RD; ++i) mbar_init(bars + i, ((i / RD) % 2 == 0) ? 32 * NP : 32);
+    set_block_spin_limit(a.spin_limit);
     __syncthreads();
 
     const int w = w0 + pair * 32 + lane;

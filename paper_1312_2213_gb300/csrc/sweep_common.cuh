@@ -67,10 +67,26 @@ __device__ __forceinline__ bool mbar_try(unsigned long long *bar, unsigned parit
     return ok != 0;
 }
 
-// Bounded wait; returns false (and leaves the barrier alone) after kSpinLimit tries.
+// The block's bound on one wait, in tries: kSpinLimit unless the launch sets its own
+// (SpinSweepArgs::spin_limit, from the context's "spin_limit" parameter or the
+// MUCA_SPIN_LIMIT environment variable).  Thread 0 sets it before the block's first
+// barrier.
+__device__ __forceinline__ int &block_spin_limit()
+{
+    __shared__ int s_limit;
+    return s_limit;
+}
+
+__device__ __forceinline__ void set_block_spin_limit(int limit)
+{
+    if (threadIdx.x == 0) block_spin_limit() = limit > 0 ? limit : kSpinLimit;
+}
+
+// Bounded wait; returns false (and leaves the barrier alone) after the block's limit.
 __device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity)
 {
-    for (int i = 0; i < kSpinLimit; ++i)
+    const int lim = block_spin_limit();
+    for (int i = 0; i < lim; ++i)
         if (mbar_try(bar, parity)) return true;
     return false;
 }

@@ -288,6 +288,7 @@ __device__ __forceinline__ void sweep_block_pc(const SpinSweepArgs &a, int w0, i
     }
     if (tid == 0)
         for (int i = 0; i < ncw * 2 * kRing; ++i) mbar_init(bars + i, 32);
+    set_block_spin_limit(a.spin_limit);
     __syncthreads();
 
     const int w = w0 + pair * 32 + lane;

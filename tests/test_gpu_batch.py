@@ -104,3 +104,34 @@ def test_batch_form_switch_keeps_results():
         np.testing.assert_array_equal(r.spins(), c.spins())
         assert r.metrics() == c.metrics()
     b.close()
+
+
+def test_side_by_side_batch_with_mixed_forms_and_blocks():
+    """Form 1 runs every system in its own configured form and block: one system per sweep form
+    and several block sizes give the same results as the systems run on their own."""
+    cfg = [(m.ISING2D, 16, 2, 100, 21, None, 0, 64), (m.ISING2D, 16, 2, 100, 22, None, 1, 128),
+           (m.ISING2D, 16, 2, 100, 23, None, 2, 32), (m.POTTS2D, 16, 6, 90, 24, None, 2, 64),
+           (m.ISING2D_MUMA, 8, 2, 70, 25, 0.4407, 1, 64)]
+
+    def make():
+        out = []
+        for s, L, q, p, seed, beta, pipe, blk in cfg:
+            c = m.Muca(s, L, q, p, seed, beta=beta, block=blk)
+            c.set_param("pipeline", pipe)
+            out.append(c)
+        return out
+
+    ref = make()
+    for _ in range(3):
+        for c in ref:
+            c.iterate(25)
+            c.merge_and_update()
+    sys_ = make()
+    b = m.Batch(sys_, form=1)
+    b.run(3, 25, use_graph=True)
+    for r, c in zip(ref, sys_):
+        np.testing.assert_array_equal(r.lnW().view(np.uint64), c.lnW().view(np.uint64))
+        np.testing.assert_array_equal(r.histogram(), c.histogram())
+        np.testing.assert_array_equal(r.spins(), c.spins())
+        assert r.metrics() == c.metrics()
+    b.close()
