@@ -40,6 +40,7 @@ extern "C" {
 #define MUCA_ERR_TIMEOUT (-4)     /* a bounded device wait gave up */
 #define MUCA_ERR_STATE (-5)       /* call not allowed in the context's current state */
 #define MUCA_ERR_RANGE (-6)       /* value outside the supported range */
+#define MUCA_ERR_CHECK (-7)       /* checked build: a device bounds check failed */
 
 /* Systems (paper: Ising paragraph, Potts paragraph, multimagnetic ensemble
  * Eq. 3, bead-spring polymer Eq. 7). */
@@ -117,6 +118,13 @@ int muca_init_ex(muca_ctx **out, int system, int L_or_N, int q, int p, uint64_t 
  *                 call returns MUCA_ERR_TIMEOUT.  The context's walker state is
  *                 invalid afterwards (restore a checkpoint with muca_set_state).
  *                 No effect with pipeline = 0 or a row past the call's sweeps.
+ *   "debug_check" checked build only (libmuca_checked.so, -DMUCA_CHECKED, which
+ *                 bounds-checks every shared-memory table access of the spin
+ *                 sweeps, clamps an index outside the table to its first entry
+ *                 and makes the next synchronising call return MUCA_ERR_CHECK):
+ *                 1 makes every check of the following iterates fail, to test
+ *                 that path (all accesses then read the table's first entry).
+ *                 The regular build refuses the key with MUCA_ERR_ARG.
  *   "spin_limit"  tries (of mbarrier.try_wait, each suspending the warp for a
  *                 few microseconds) one row hand-over of the producer/consumer
  *                 forms makes before it gives up; 0 (default) = 2^17, about a

@@ -55,19 +55,26 @@ PROTOTYPES = {
 }
 
 
+def checked() -> bool:
+    """MUCA_DEBUG=1 selects the checked build (bounds checks on the sweeps' table accesses)."""
+    return os.environ.get("MUCA_DEBUG", "") == "1"
+
+
 def library_path() -> str:
-    return _build.LIB
+    return _build.LIB_CHECKED if checked() else _build.LIB
 
 
 def load(build_if_missing: bool = True):
-    """Load libmuca.so (building it first if it is missing or stale)."""
+    """Load libmuca.so, or libmuca_checked.so under MUCA_DEBUG=1 (building it first if it is
+    missing or stale)."""
     global _lib
     if _lib is None:
+        path = library_path()
         if build_if_missing:
-            _build.build()
-        if not os.path.exists(_build.LIB):
-            raise ImportError("libmuca.so is not built; run __graft_entry__.build()")
-        lib = ctypes.CDLL(_build.LIB)
+            _build.build(checked=checked())
+        if not os.path.exists(path):
+            raise ImportError("%s is not built; run __graft_entry__.build()" % os.path.basename(path))
+        lib = ctypes.CDLL(path)
         for name, (res, args) in PROTOTYPES.items():
             fn = getattr(lib, name)
             fn.restype = res

@@ -72,6 +72,7 @@ struct muca_ctx {
     int moves = 0;     // polymer: 0 single-bead shifts, 1 shifts and spherical rotations
     int debug_drop_row = -1;  // test hook for the bounded waits (next spin iterate only)
     int spin_limit = 0;       // tries of one bounded hand-over wait (0: the kernels' default)
+    int debug_check = 0;      // checked build: every table bounds check of the next iterate fails
     int recursion = 0;        // weight update: 0 accumulated statistics, 1 plain W/H
     int observables = 0;      // Ising: per-sweep sums of 1, |M|, M^2 per bin
     unsigned long long *obs = nullptr;  // [0, 3B): sums being filled, [3B, 6B): of the last update
@@ -291,6 +292,7 @@ SpinSweepArgs sweep_args(const muca_ctx *c, int64_t sweeps, int block)
     a.bin_lo = c->h_rlist.front();
     a.bin_hi = c->h_rlist.back();
     a.spin_limit = c->spin_limit;
+    a.debug_check = c->debug_check;
     return a;
 }
 
@@ -481,6 +483,7 @@ int check_device_flag(muca_ctx *c)
     int err = 0;
     MUCA_CUDA(cudaMemcpyAsync(&err, &c->state->err, sizeof err, cudaMemcpyDeviceToHost, c->stream));
     MUCA_CUDA(cudaStreamSynchronize(c->stream));
+    if (err & 2) return fail(MUCA_ERR_CHECK, "a device bounds check failed (checked build); the last iterations are invalid");
     if (err) return fail(MUCA_ERR_TIMEOUT, "a bounded device wait gave up; the last iterations are invalid");
     return MUCA_OK;
 }
@@ -507,6 +510,68 @@ struct Section {
     void *dev;
     size_t bytes;
 };
+
+// A spin state read from a buffer must be one the sweeps can run: every Potts colour below q,
+// no bits past the last site of a row, and each walker's bin equal to the bin of its lattice
+// (the sweeps move the bin by each accepted move's change, so a bin that disagrees with its
+// lattice could walk off the shared-memory tables).  `lat` is the lattice section, unaligned.
+bool spin_state_consistent(const muca_ctx *c, const char *lat, const char *bins, std::string &why)
+{
+    const int L = c->L, N = c->N, bits = (c->system == kPotts) ? 4 : 1;
+    const int WR = (c->system == kPotts) ? potts_words_per_row(L) : ising_words_per_row(L);
+    std::vector<uint32_t> rows((size_t)L * WR);
+    std::vector<uint8_t> col((size_t)N);  // Potts colours
+    std::vector<uint64_t> r64((size_t)L);  // Ising / MUMA rows (L <= 64 bits)
+    const uint64_t mask = (L == 64) ? ~0ull : ((1ull << L) - 1ull);
+    for (int w = 0; w < c->p; ++w) {
+        for (int k = 0; k < L * WR; ++k)
+            memcpy(&rows[k], lat + ((size_t)k * c->pstride + w) * sizeof(uint32_t), sizeof(uint32_t));
+        for (int y = 0; y < L; ++y)
+            for (int j = 0; j < WR; ++j) {
+                const int used = std::min(32, L * bits - 32 * j);  // bits of sites in word j
+                if (used < 32 && (rows[(size_t)y * WR + j] >> used) != 0u) {
+                    why = "walker " + std::to_string(w) + ": bits past the last site of a row";
+                    return false;
+                }
+            }
+        int want;
+        if (c->system == kPotts) {
+            for (int i = 0; i < N; ++i) {
+                const int y = i / L, x = i - y * L;
+                const uint32_t v = (rows[(size_t)y * WR + (4 * x) / 32] >> ((4 * x) & 31)) & 15u;
+                if (v >= (uint32_t)c->q) {
+                    why = "walker " + std::to_string(w) + ": colour " + std::to_string(v) + " >= q";
+                    return false;
+                }
+                col[i] = (uint8_t)v;
+            }
+            int E = 0;
+            for (int y = 0; y < L; ++y) {
+                const uint8_t *r = &col[(size_t)y * L], *d = &col[(size_t)((y + 1) % L) * L];
+                for (int x = 0; x < L; ++x) E -= (r[x] == r[(x + 1) % L]) + (r[x] == d[x]);
+            }
+            want = E + 2 * N;
+        } else {  // bit 1 = spin -1; a bond is broken where the bits differ
+            int broken = 0, minus = 0;
+            for (int y = 0; y < L; ++y)
+                r64[y] = rows[(size_t)y * WR] | (WR > 1 ? (uint64_t)rows[(size_t)y * WR + 1] << 32 : 0ull);
+            for (int y = 0; y < L; ++y) {
+                const uint64_t r = r64[y], right = ((r >> 1) | (r << (L - 1))) & mask;  // bit x: site x+1
+                broken += __builtin_popcountll(r ^ right) + __builtin_popcountll(r ^ r64[(y + 1) % L]);
+                minus += __builtin_popcountll(r);
+            }
+            want = (c->system == kIsing) ? broken / 2 : N - minus;  // (E + 2N) / 4 with E = 2 broken - 2N
+        }
+        int32_t b;
+        memcpy(&b, bins + (size_t)w * sizeof(int32_t), sizeof b);
+        if (b != want) {
+            why = "walker " + std::to_string(w) + " has bin " + std::to_string(b) + ", its lattice bin " +
+                  std::to_string(want);
+            return false;
+        }
+    }
+    return true;
+}
 
 std::vector<Section> state_sections(const muca_ctx *c)
 {
@@ -626,6 +691,15 @@ int muca_set_param(muca_ctx *c, const char *key, double v)
             return fail(MUCA_ERR_ARG, "block must be a multiple of 32 in [32, %d]", kMaxSweepBlock);
         c->block = b;
         return MUCA_OK;
+    }
+    if (k == "debug_check") {
+#ifdef MUCA_CHECKED
+        if (v != 0.0 && v != 1.0) return fail(MUCA_ERR_ARG, "debug_check must be 0 or 1");
+        c->debug_check = (int)v;
+        return MUCA_OK;
+#else
+        return fail(MUCA_ERR_ARG, "debug_check needs the checked build (MUCA_DEBUG=1)");
+#endif
     }
     if (k == "spin_limit") {
         const long long lim = (long long)v;
@@ -1041,6 +1115,12 @@ int muca_set_state(muca_ctx *c, const void *host_buf, size_t bytes)
                 c->B = oldB;
                 return fail(MUCA_ERR_ARG, "state buffer: walker %d has bin %d", w, b);
             }
+        }
+        std::string why;
+        if (c->system != kPolymer &&
+            !spin_state_consistent(c, (const char *)host_buf + sizeof h, (const char *)bins, why)) {
+            c->B = oldB;
+            return fail(MUCA_ERR_ARG, "state buffer: %s", why.c_str());
         }
     }
     c->record = h.record;

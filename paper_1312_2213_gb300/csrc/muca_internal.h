@@ -49,6 +49,7 @@ struct SpinSweepArgs {
     uint8_t *tun = nullptr;  // [p] tunnelling state per walker (0 none, 1 lowest bin last, 2 highest)
     int bin_lo = 0, bin_hi = 0;  // lowest and highest reachable bins
     int spin_limit = 0;          // tries a bounded hand-over wait makes before it gives up (0: default)
+    int debug_check = 0;         // checked build only: every table bounds check fails (test hook)
 };
 
 // Philox round keys for a seed: round r uses (lo + r*W0, hi + r*W1).

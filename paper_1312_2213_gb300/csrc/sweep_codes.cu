@@ -2,6 +2,7 @@
 // MUMA and Potts).
 #include "muca_device.cuh"
 #include "muca_internal.h"
+#include "muca_checks.cuh"
 #include "sweep_common.cuh"
 
 namespace muca {
@@ -182,9 +183,9 @@ __device__ __forceinline__ void ising_sweep_tc(uint32_t *__restrict__ lat, int p
     // producer's columns are 4 c, so a threshold address is one add and the bin's histogram
     // counter an immediate offset from the (already updated) bin address.
     const int sbase = (int)__cvta_generic_to_shared(sTH);
-    auto th = [](int addr) -> uint32_t {
+    auto th = [sbase](int addr) -> uint32_t {
         uint32_t v;
-        asm("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(addr));
+        asm("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(checked_addr(addr, sbase)));
         return v;
     };
     // bin-row move of an accepted flip in bytes: Ising (c - 2) rows from the column,
@@ -264,7 +265,8 @@ __device__ __forceinline__ void ising_sweep_tc(uint32_t *__restrict__ lat, int p
             const bool acc = uw < T;  // the producer's clamp makes this "always or u < T"
             if (acc) cur[x >> 5] ^= 1u << (x & 31);
             bB = acc ? bB + dR : bB;
-            if (RECORD == 0) asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(bB + 4 * C), "r"(1u) : "memory");
+            if (RECORD == 0)
+                asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(checked_addr(bB + 4 * C, sbase)), "r"(1u) : "memory");
             accP = acc;
         }
 #pragma unroll
@@ -278,7 +280,7 @@ __device__ __forceinline__ void ising_sweep_tc(uint32_t *__restrict__ lat, int p
         ++k;
     }
     bR = (bB - sbase) / 4;
-    if (RECORD == 1) atomicAdd(&sTH[bR + C], 1u);
+    if (RECORD == 1) atomicAdd(&sTH[checked_word(bR + C)], 1u);
     if (SYS == kIsing && obs && !bad) record_observables(obs, bR / RS, L * L, pc);
 }
 
@@ -317,6 +319,7 @@ __device__ __forceinline__ void sweep_block_tn(const SpinSweepArgs &a, int w0, i
     if (tid == 0)  // per pair: FULL[kRing] (NP producer warps arrive), EMPTY[kRing] (the consumer)
         for (int i = 0; i < ncw * 2 * kRing; ++i) mbar_init(bars + i, ((i / kRing) % 2 == 0) ? 32 * NP : 32);
     set_block_spin_limit(a.spin_limit);
+    checks_begin(a.B * RS, a.debug_check);
     __syncthreads();
 
     const int w = w0 + pair * 32 + lane;
@@ -380,6 +383,7 @@ __device__ __forceinline__ void sweep_block_tn(const SpinSweepArgs &a, int w0, i
         if (a.tun) a.tun[w] = (uint8_t)tst;
     }
     flush_metrics(a.metrics, nacc, ev);
+    checks_end(a.state);
 }
 
 template <int SYS, int L>
@@ -577,12 +581,14 @@ __device__ __forceinline__ void potts_sweep_tc(uint32_t *__restrict__ lat, int p
     // As in the Ising consumer: 32-bit shared-window byte addresses (bB = table base + 4 RS bin,
     // codes scaled to 4 c), clamped acceptance words, one compare.
     const int sbase = (int)__cvta_generic_to_shared(sTH);
-    auto th = [](int addr) -> uint32_t {
+    auto th = [sbase](int addr) -> uint32_t {
         uint32_t v;
-        asm("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(addr));
+        asm("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(checked_addr(addr, sbase)));
         return v;
     };
-    auto hist = [](int addr) { asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(addr), "r"(1u) : "memory"); };
+    auto hist = [sbase](int addr) {
+        asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(checked_addr(addr, sbase)), "r"(1u) : "memory");
+    };
     int bB = sbase + bR * 4;
 #pragma unroll 1
     for (int y = 0; y < L; ++y) {
@@ -673,7 +679,7 @@ __device__ __forceinline__ void potts_sweep_tc(uint32_t *__restrict__ lat, int p
     }
     bR = (bB - sbase) / 4;
     nacc >>= 3;
-    if (RECORD == 1) atomicAdd(&sTH[bR + 9], 1u);
+    if (RECORD == 1) atomicAdd(&sTH[checked_word(bR + 9)], 1u);
 }
 
 // Shared memory a consumer warp owns: RD ring rows (acceptance words 16 B,
@@ -715,6 +721,7 @@ __device__ __forceinline__ void sweep_block_tnp(const SpinSweepArgs &a, int w0, 
     if (tid == 0)  // per pair: FULL[RD] (NP producer warps arrive), EMPTY[RD] (the consumer)
         for (int i = 0; i < ncw * 2 * RD; ++i) mbar_init(bars + i, ((i / RD) % 2 == 0) ? 32 * NP : 32);
     set_block_spin_limit(a.spin_limit);
+    checks_begin(a.B * RS, a.debug_check);
     __syncthreads();
 
     const int w = w0 + pair * 32 + lane;
@@ -787,6 +794,7 @@ __device__ __forceinline__ void sweep_block_tnp(const SpinSweepArgs &a, int w0, 
         if (a.tun) a.tun[w] = (uint8_t)tst;
     }
     flush_metrics(a.metrics, nacc, ev);
+    checks_end(a.state);
 }
 
 template <int L, int RD>

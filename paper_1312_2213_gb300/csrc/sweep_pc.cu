@@ -1,6 +1,7 @@
 // sweep_pc.cu -- producer/consumer form of the spin sweep (Ising, MUMA, Potts).
 #include "muca_device.cuh"
 #include "muca_internal.h"
+#include "muca_checks.cuh"
 #include "sweep_common.cuh"
 
 namespace muca {
@@ -74,7 +75,7 @@ __device__ __forceinline__ void ising_sweep_pc(uint32_t *__restrict__ lat, int p
         };
         int c0, c1, d0, d1;
         site(0, c0, c1, d0, d1);
-        uint32_t T0 = sTH[bR + c0], T1 = 0u;
+        uint32_t T0 = sTH[checked_word(bR + c0)], T1 = 0u;
         bool accP = false;
         int dRp = 0;
         uint4 u = make_uint4(0u, 0u, 0u, 0u);
@@ -88,14 +89,14 @@ __device__ __forceinline__ void ising_sweep_pc(uint32_t *__restrict__ lat, int p
             if (x + 1 < L) {
                 int n0, n1c, e0, e1;
                 site(x + 1, n0, n1c, e0, e1);
-                T0 = sTH[bR + n0];
-                T1 = sTH[bR + dR + n1c];
+                T0 = sTH[checked_word(bR + n0)];
+                T1 = sTH[checked_word(bR + dR + n1c)];
                 d0 = e0;
                 d1 = e1;
             }
             const bool acc = (T == kAlways) || (uw < T);
             if (acc) cur[x >> 5] ^= 1u << (x & 31);
-            if (RECORD == 0) atomicAdd(&sTH[(acc ? bR + dR : bR) + C], 1u);
+            if (RECORD == 0) atomicAdd(&sTH[checked_word((acc ? bR + dR : bR) + C)], 1u);
             accP = acc;
             dRp = dR;
         }
@@ -119,7 +120,7 @@ __device__ __forceinline__ void ising_sweep_pc(uint32_t *__restrict__ lat, int p
             dn[j] = (y + 2 < L) ? nxt[j] : first[j];
         }
     }
-    if (RECORD == 1) atomicAdd(&sTH[bR + C], 1u);
+    if (RECORD == 1) atomicAdd(&sTH[checked_word(bR + C)], 1u);
     if (SYS == kIsing && obs && !bad) record_observables(obs, bR / RS, L * L, pc);
 }
 
@@ -181,7 +182,7 @@ __device__ __forceinline__ void potts_sweep_pc(uint32_t *__restrict__ lat, int p
         uint32_t nwc;
         int c0, c1, d0, d1;
         site(0, u.x, 0u, nwc, c0, c1, d0, d1);
-        uint32_t T0 = sTH[bR + c0], T1 = 0u;
+        uint32_t T0 = sTH[checked_word(bR + c0)], T1 = 0u;
         bool accP = false;
         int dRp = 0;
 #pragma unroll
@@ -199,8 +200,8 @@ __device__ __forceinline__ void potts_sweep_pc(uint32_t *__restrict__ lat, int p
                 const uint32_t uprop = ((x + 1) & 1) ? u.z : u_next.x;
                 int n0, n1c, e0, e1;
                 site(x + 1, uprop, nw, nwc, n0, n1c, e0, e1);
-                T0 = sTH[bR + n0];
-                T1 = sTH[bR + dR + n1c];
+                T0 = sTH[checked_word(bR + n0)];
+                T1 = sTH[checked_word(bR + dR + n1c)];
                 d0 = e0;
                 d1 = e1;
             }
@@ -209,7 +210,7 @@ __device__ __forceinline__ void potts_sweep_pc(uint32_t *__restrict__ lat, int p
                 const int wi = (4 * x) >> 5, sh = (4 * x) & 31;
                 cur[wi] = (cur[wi] & ~(15u << sh)) | (nw << sh);
             }
-            if (RECORD == 0) atomicAdd(&sTH[(acc ? bR + dR : bR) + 9], 1u);
+            if (RECORD == 0) atomicAdd(&sTH[checked_word((acc ? bR + dR : bR) + 9)], 1u);
             accP = acc;
             dRp = dR;
         }
@@ -232,7 +233,7 @@ __device__ __forceinline__ void potts_sweep_pc(uint32_t *__restrict__ lat, int p
             dn[j] = (y + 2 < L) ? nxt[j] : first[j];
         }
     }
-    if (RECORD == 1) atomicAdd(&sTH[bR + 9], 1u);
+    if (RECORD == 1) atomicAdd(&sTH[checked_word(bR + 9)], 1u);
 }
 
 // Producer side: the Philox blocks of one sweep, row by row, for the walkers of
@@ -289,6 +290,7 @@ __device__ __forceinline__ void sweep_block_pc(const SpinSweepArgs &a, int w0, i
     if (tid == 0)
         for (int i = 0; i < ncw * 2 * kRing; ++i) mbar_init(bars + i, 32);
     set_block_spin_limit(a.spin_limit);
+    checks_begin(a.B * RS, a.debug_check);
     __syncthreads();
 
     const int w = w0 + pair * 32 + lane;
@@ -356,6 +358,7 @@ __device__ __forceinline__ void sweep_block_pc(const SpinSweepArgs &a, int w0, i
         if (a.tun) a.tun[w] = (uint8_t)tst;
     }
     flush_metrics(a.metrics, nacc, ev);
+    checks_end(a.state);
 }
 
 

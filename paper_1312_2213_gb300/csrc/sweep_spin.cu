@@ -32,6 +32,7 @@
 // with the next row prefetched one row ahead.
 #include "muca_device.cuh"
 #include "muca_internal.h"
+#include "muca_checks.cuh"
 #include "sweep_common.cuh"
 
 namespace muca {
@@ -87,7 +88,7 @@ __device__ __forceinline__ void ising_sweep(uint32_t *__restrict__ lat, int ps, 
         };
         int c0, c1, d0, d1;
         site(0, c0, c1, d0, d1);
-        uint32_t T0 = sTH[bR + c0], T1 = 0u;
+        uint32_t T0 = sTH[checked_word(bR + c0)], T1 = 0u;
         bool accP = false;
         int dRp = 0;
         uint4 u = u_next;
@@ -104,14 +105,14 @@ __device__ __forceinline__ void ising_sweep(uint32_t *__restrict__ lat, int ps, 
             if (x + 1 < L) {
                 int n0, n1c, e0, e1;
                 site(x + 1, n0, n1c, e0, e1);
-                T0 = sTH[bR + n0];
-                T1 = sTH[bR + dR + n1c];
+                T0 = sTH[checked_word(bR + n0)];
+                T1 = sTH[checked_word(bR + dR + n1c)];
                 d0 = e0;
                 d1 = e1;
             }
             const bool acc = (T == kAlways) || (uw < T);
             if (acc) cur[x >> 5] ^= 1u << (x & 31);
-            if (RECORD == 0) atomicAdd(&sTH[(acc ? bR + dR : bR) + C], 1u);
+            if (RECORD == 0) atomicAdd(&sTH[checked_word((acc ? bR + dR : bR) + C)], 1u);
             accP = acc;
             dRp = dR;
         }
@@ -133,7 +134,7 @@ __device__ __forceinline__ void ising_sweep(uint32_t *__restrict__ lat, int ps, 
             dn[j] = (y + 2 < L) ? nxt[j] : first[j];
         }
     }
-    if (RECORD == 1) atomicAdd(&sTH[bR + C], 1u);
+    if (RECORD == 1) atomicAdd(&sTH[checked_word(bR + C)], 1u);
     if (SYS == kIsing && obs) record_observables(obs, bR / RS, L * L, pc);
 }
 
@@ -190,7 +191,7 @@ __device__ __forceinline__ void potts_sweep(uint32_t *__restrict__ lat, int ps, 
         uint32_t nwc;
         int c0, c1, d0, d1;
         site(0, u.x, 0u, nwc, c0, c1, d0, d1);
-        uint32_t T0 = sTH[bR + c0], T1 = 0u;
+        uint32_t T0 = sTH[checked_word(bR + c0)], T1 = 0u;
         bool accP = false;
         int dRp = 0;
 #pragma unroll
@@ -208,8 +209,8 @@ __device__ __forceinline__ void potts_sweep(uint32_t *__restrict__ lat, int ps, 
                 const uint32_t uprop = ((x + 1) & 1) ? u.z : u_next.x;
                 int n0, n1c, e0, e1;
                 site(x + 1, uprop, nw, nwc, n0, n1c, e0, e1);
-                T0 = sTH[bR + n0];
-                T1 = sTH[bR + dR + n1c];
+                T0 = sTH[checked_word(bR + n0)];
+                T1 = sTH[checked_word(bR + dR + n1c)];
                 d0 = e0;
                 d1 = e1;
             }
@@ -218,7 +219,7 @@ __device__ __forceinline__ void potts_sweep(uint32_t *__restrict__ lat, int ps, 
                 const int wi = (4 * x) >> 5, sh = (4 * x) & 31;
                 cur[wi] = (cur[wi] & ~(15u << sh)) | (nw << sh);
             }
-            if (RECORD == 0) atomicAdd(&sTH[(acc ? bR + dR : bR) + 9], 1u);
+            if (RECORD == 0) atomicAdd(&sTH[checked_word((acc ? bR + dR : bR) + 9)], 1u);
             accP = acc;
             dRp = dR;
         }
@@ -239,7 +240,7 @@ __device__ __forceinline__ void potts_sweep(uint32_t *__restrict__ lat, int ps, 
             dn[j] = (y + 2 < L) ? nxt[j] : first[j];
         }
     }
-    if (RECORD == 1) atomicAdd(&sTH[bR + 9], 1u);
+    if (RECORD == 1) atomicAdd(&sTH[checked_word(bR + 9)], 1u);
 }
 
 
@@ -260,6 +261,7 @@ __device__ __forceinline__ void sweep_block(const SpinSweepArgs &a, int w0, int 
         const int b = i / RS, c = i - (i / RS) * RS;
         sTH[i] = (c < C) ? a.T[b * C + c] : 0u;
     }
+    checks_begin(a.B * RS, a.debug_check);
     __syncthreads();
 
     const int w = w0 + tid;
@@ -318,6 +320,7 @@ __device__ __forceinline__ void sweep_block(const SpinSweepArgs &a, int w0, int 
         if (a.tun) a.tun[w] = (uint8_t)tst;
     }
     flush_metrics(a.metrics, nacc, ev);
+    checks_end(a.state);
 }
 
 // One system per launch: block k runs walkers [k*blockDim.x, (k+1)*blockDim.x).

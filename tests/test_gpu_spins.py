@@ -265,3 +265,48 @@ def test_observables_refused_where_not_recorded():
     h = m.Muca(m.ISING2D, 8, 2, 8, 1)
     with pytest.raises(m.MucaError):
         h.observables(0.4)
+
+
+def _state_offsets(g, C):
+    """Byte offsets of the lattice and bin sections in a spin state buffer (header first)."""
+    WR = (4 * g.L + 31) // 32 if g.system == m.POTTS2D else (g.L + 31) // 32
+    pstride = (g.p + 31) // 32 * 32
+    lat_b = g.L * WR * pstride * 4
+    sizes = [lat_b, 4 * g.p] + [8 * g.B] * 6 + [4 * g.B * C, 48 * g.B, 64, g.p]
+    blob = g.get_state()
+    head = blob.nbytes - sum(sizes)
+    return blob, head, head + lat_b, WR, pstride
+
+
+@pytest.mark.parametrize("system,L,q,C", [(m.ISING2D, 24, 2, 5), (m.POTTS2D, 16, 5, 9), (m.ISING2D_MUMA, 16, 2, 10)])
+def test_state_buffer_must_be_consistent(system, L, q, C):
+    """muca_set_state refuses a buffer whose walker bin disagrees with its lattice, a Potts colour
+    >= q, or set bits past a row's last site (the sweeps would move such a bin off the tables);
+    the untouched buffer is accepted."""
+    g = m.Muca(system, L, q, 40, 3, beta=0.4407 if system == m.ISING2D_MUMA else None)
+    g.iterate(20)
+    g.merge_and_update()
+    blob, head, bins_off, WR, pstride = _state_offsets(g, C)
+    c = m.Muca(system, L, q, 40, 3, beta=0.4407 if system == m.ISING2D_MUMA else None)
+    c.set_state(blob)  # consistent
+    np.testing.assert_array_equal(c.spins(), g.spins())
+
+    bad = blob.copy()
+    bins = bad[bins_off:bins_off + 4 * 40].view(np.int32)
+    bins[7] += 1 if bins[7] + 1 < g.B else -1  # a bin that is not its lattice's
+    with pytest.raises(m.MucaError) as e:
+        c.set_state(bad)
+    assert e.value.code == -1 and "bin" in str(e.value)
+
+    bad = blob.copy()
+    lat = bad[head:bins_off].view(np.uint32)
+    if system == m.POTTS2D:
+        lat[0 * pstride + 5] = (lat[0 * pstride + 5] & ~np.uint32(0xF)) | np.uint32(q)  # colour q at site 0
+    else:
+        lat[0 * pstride + 5] |= np.uint32(1 << (L % 32 if L % 32 else 31))  # past the row (L = 24) or a site
+    with pytest.raises(m.MucaError):
+        c.set_state(bad)
+    c.set_state(blob)
+    c.iterate(5)
+    g.iterate(5)
+    np.testing.assert_array_equal(c.spins(), g.spins())
