@@ -83,10 +83,12 @@ __device__ __forceinline__ void set_block_spin_limit(int limit)
 }
 
 // Bounded wait; returns false (and leaves the barrier alone) after the block's limit.
+// The limit is read only when the first try fails, off the hand-over's fast path.
 __device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity)
 {
+    if (mbar_try(bar, parity)) return true;
     const int lim = block_spin_limit();
-    for (int i = 0; i < lim; ++i)
+    for (int i = 1; i < lim; ++i)
         if (mbar_try(bar, parity)) return true;
     return false;
 }
