@@ -23,6 +23,30 @@ def main():
         for j, o in enumerate(om):
             f.write("%d %d\n" % (4 * j - 2 * N, o))
 
+    # 16 x 16: thermodynamics from Kaufman's closed form (oracle/exact.py), the derivatives of ln Z
+    # by central differences at 60 digits (step 1e-12 / 1e-10, truncation ~1e-20):
+    # <E> = -d lnZ / d beta, C = beta^2 d^2 lnZ / d beta^2.
+    import mpmath
+
+    from oracle import exact
+
+    L, N = 16, 256
+    with mpmath.workdps(60):
+        with open(os.path.join(HERE, "ising_L16_kaufman.txt"), "w") as f:
+            f.write("# Exact thermodynamics of the 16x16 periodic Ising model (J = 1), from Kaufman's\n")
+            f.write("# closed form of Z (Phys. Rev. 76, 1232 (1949)) as evaluated by oracle/exact.py;\n")
+            f.write("# <E> = -d lnZ/d beta and C = beta^2 d^2 lnZ/d beta^2 by central differences at 60 digits.\n")
+            f.write("# columns: beta  lnZ  <E>/N  C/N\n")
+            for beta in ("0.2", "0.3", "0.4", "0.4406867935097715", "0.5", "0.6"):
+                b = mpmath.mpf(beta)
+                lz = lambda t: exact.kaufman_lnZ(L, L, t)  # noqa: E731
+                lnZ = lz(b)
+                h1, h2 = mpmath.mpf("1e-12"), mpmath.mpf("1e-10")
+                d1 = (lz(b + h1) - lz(b - h1)) / (2 * h1)
+                d2 = (lz(b + h2) - 2 * lnZ + lz(b - h2)) / (h2 * h2)
+                f.write("%s %s %s %s\n" % (beta, mpmath.nstr(lnZ, 20), mpmath.nstr(-d1 / N, 20),
+                                            mpmath.nstr(b * b * d2 / N, 20)))
+
 
 if __name__ == "__main__":
     main()

@@ -1,0 +1,45 @@
+"""The whole GPU path against exact physics at a size no enumeration reaches: eight independent
+multicanonical runs of the 16x16 Ising model (512 walkers each, batched) iterate to a flat
+histogram, refine with eight longer iterations, and reweight (Eq. 2) to six temperatures.  The
+mean over the runs of <E>/N, C/N and ln Z must agree with Kaufman's exact finite-lattice values
+(tests/golden/ising_L16_kaufman.txt, written by tests/golden/make_golden.py from oracle/exact.py)
+within four standard errors of that mean.  The seeds are fixed, so the run is reproducible."""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import paper_1312_2213_gb300 as m
+
+pytestmark = pytest.mark.gpu
+GOLD = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "ising_L16_kaufman.txt")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def test_ising_L16_thermodynamics_match_kaufman():
+    gold = [tuple(float(x) for x in line.split()) for line in open(GOLD) if not line.startswith("#")]
+    N = 256
+    systems = [m.Muca(m.ISING2D, 16, 2, 512, s) for s in range(101, 109)]
+    b = m.Batch(systems)
+    for it in range(400):
+        b.run(1, 20, use_graph=False)
+        flat = [s.flatness() for s in systems]
+        if all(f[0] > 0 and f[0] >= 0.5 * f[1] for f in flat):
+            break
+    else:
+        pytest.fail("no flat histogram within 400 iterations")
+    b.run(8, 500, use_graph=False)
+    for beta, lnZ, e, c in gold:
+        outs = np.array([s.reweight(beta)[0] for s in systems])  # {<E>, <E^2>, C/N, ln Z}
+        for name, est, exact in (("E/N", outs[:, 0] / N, e), ("C/N", outs[:, 2], c), ("lnZ", outs[:, 3], lnZ)):
+            mean, err = est.mean(), est.std(ddof=1) / math.sqrt(len(est))
+            assert abs(mean - exact) < 4 * err, (beta, name, mean, exact, err)
+    b.close()
