@@ -43,3 +43,29 @@ def test_ising_L16_thermodynamics_match_kaufman():
             mean, err = est.mean(), est.std(ddof=1) / math.sqrt(len(est))
             assert abs(mean - exact) < 4 * err, (beta, name, mean, exact, err)
     b.close()
+
+
+def test_potts_q2_L16_maps_onto_kaufman():
+    """q = 2 Potts is Ising with E_Potts = -N + E_Ising / 2: at beta_Potts = 2 beta the exact values
+    are <E>/N = -1 + <E_Ising>/(2N), the same C/N, and ln Z = 2 beta N + ln Z_Ising.  The Potts
+    code path (nibble lattices, its own producers and consumer) against them."""
+    gold = [tuple(float(x) for x in line.split()) for line in open(GOLD) if not line.startswith("#")]
+    N = 256
+    systems = [m.Muca(m.POTTS2D, 16, 2, 512, s) for s in range(201, 209)]
+    b = m.Batch(systems)
+    for it in range(400):
+        b.run(1, 20, use_graph=False)
+        flat = [s.flatness() for s in systems]
+        if all(f[0] > 0 and f[0] >= 0.5 * f[1] for f in flat):
+            break
+    else:
+        pytest.fail("no flat histogram within 400 iterations")
+    b.run(8, 500, use_graph=False)
+    for beta, lnZ, e, c in gold:
+        bp = 2 * beta
+        outs = np.array([s.reweight(bp)[0] for s in systems])
+        for name, est, exact in (("E/N", outs[:, 0] / N, -1.0 + e / 2), ("C/N", outs[:, 2], c),
+                                 ("lnZ", outs[:, 3], bp * N + lnZ)):
+            mean, err = est.mean(), est.std(ddof=1) / math.sqrt(len(est))
+            assert abs(mean - exact) < 4 * err, (beta, name, mean, exact, err)
+    b.close()
