@@ -69,3 +69,46 @@ def test_potts_q2_L16_maps_onto_kaufman():
             mean, err = est.mean(), est.std(ddof=1) / math.sqrt(len(est))
             assert abs(mean - exact) < 4 * err, (beta, name, mean, exact, err)
     b.close()
+
+
+def _to_flat(systems, batch=None, sweeps=20, max_iter=400):
+    for it in range(max_iter):
+        if batch is not None:
+            batch.run(1, sweeps, use_graph=False)
+        else:
+            for c in systems:
+                c.iterate(sweeps)
+                c.merge_and_update()
+        flat = [s.flatness() for s in systems]
+        if all(f[0] > 0 and f[0] >= 0.5 * f[1] for f in flat):
+            return
+    pytest.fail("no flat histogram within %d iterations" % max_iter)
+
+
+def test_multimagnetic_and_energy_observables_agree():
+    """Two independent routes to the canonical magnetisation of the 16x16 Ising model at
+    beta = 0.4: the multimagnetic run (weights in M at fixed beta, Eq. 3, reweighted over its own
+    M histogram) and MUCA in E with per-bin |M| and M^2 sums (Eq. 2).  Eight seeds each; the means
+    of <|M|>/N, <M^2>/N^2 and chi/N agree within four combined standard errors."""
+    beta = 0.4
+    mm = [m.Muca(m.ISING2D_MUMA, 16, 2, 512, s, beta=beta) for s in range(301, 309)]
+    b = m.Batch(mm)
+    _to_flat(mm, b)
+    b.run(8, 500, use_graph=False)
+    b.close()
+    a = np.array([c.reweight(beta)[0][:3] for c in mm])
+    me = []
+    for s in range(401, 409):
+        c = m.Muca(m.ISING2D, 16, 2, 512, s)
+        c.set_param("observables", 1)
+        me.append(c)
+    _to_flat(me)
+    for _ in range(8):
+        for c in me:
+            c.iterate(500)
+            c.merge_and_update()
+    o = np.array([c.observables(beta)[0] for c in me])
+    for k, name in enumerate(("<|M|>/N", "<M^2>/N^2", "chi/N")):
+        ma, mo = a[:, k].mean(), o[:, k].mean()
+        ea, eo = a[:, k].std(ddof=1) / math.sqrt(len(a)), o[:, k].std(ddof=1) / math.sqrt(len(o))
+        assert abs(ma - mo) < 4 * math.hypot(ea, eo), (name, ma, ea, mo, eo)
