@@ -54,6 +54,7 @@ int fail(int code, const char *fmt, ...)
     } while (0)
 
 constexpr size_t kAlign = 256;
+constexpr size_t kMaxSmem = 227u * 1024u;  // dynamic shared memory a block can have
 size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
 struct Layout {
@@ -113,7 +114,7 @@ bool valid_config(int system, int L, int q, int p, std::string &why)
     if (system != kIsing && system != kPotts && system != kMuma) { why = "unknown system"; return false; }
     if (system == kPotts && (q < 2 || q > 16)) { why = "Potts q must be in [2, 16]"; return false; }
     if (!spin_sweep_supported(system, L)) {
-        why = "lattice size not supported (L in {4,8,12,16,24,32,48,64}; Potts L <= 48)";
+        why = "lattice size not supported (L in {4,8,12,16,24,32,48,64})";
         return false;
     }
     return true;
@@ -1220,6 +1221,7 @@ struct muca_batch {
     cudaEvent_t ev_fork = nullptr;
     std::vector<SpinSweepArgs> h_own;  // form 1: per-system launch arguments
     std::vector<int> order;            // systems, heaviest first (tile order; form 1 launch order)
+    bool tiles_fit = true;             // every system's table fits the form-0 kernel's shared memory
 };
 
 namespace {
@@ -1289,7 +1291,9 @@ int muca_batch_create(muca_ctx *const *systems, int n, muca_batch **out)
     std::vector<DevState *> states(n);
     for (int i = 0; i < n; ++i) {
         muca_ctx *c = b->sys[i];
-        b->smem = std::max(b->smem, spin_sweep_smem_bytes(c->system, c->B));
+        const size_t sm = spin_sweep_smem_bytes(c->system, c->B);
+        if (sm <= kMaxSmem) b->smem = std::max(b->smem, sm);
+        else b->tiles_fit = false;  // e.g. q-Potts at L = 64: only form 1 runs it
         b->max_bins = std::max(b->max_bins, c->B);
         b->max_nreach = std::max(b->max_nreach, c->nreach);
         b->max_cells = std::max(b->max_cells, c->B * c->C);
@@ -1320,7 +1324,7 @@ int muca_batch_create(muca_ctx *const *systems, int n, muca_batch **out)
     e = cudaMemcpy(b->d_tiles, tiles.data(), sizeof(int2) * tiles.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(b->d_upd, upd.data(), sizeof(UpdateArgs) * n, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(b->d_states, states.data(), sizeof(DevState *) * n, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = prepare_sweep_batch(b->smem);
+    if (e == cudaSuccess && b->tiles_fit) e = prepare_sweep_batch(b->smem);
     if (e == cudaSuccess) e = prepare_recursion_batch(b->max_nreach);
     if (e != cudaSuccess) {
         cudaFree(b->dmem);
@@ -1425,6 +1429,8 @@ int muca_batch_set_form(muca_batch *b, int form)
 {
     if (!b) return fail(MUCA_ERR_ARG, "batch is NULL");
     if (form != 0 && form != 1) return fail(MUCA_ERR_ARG, "batch form must be 0 or 1");
+    if (form == 0 && !b->tiles_fit)
+        return fail(MUCA_ERR_ARG, "batch form 0 needs every system's table in shared memory (not q-Potts at L = 64)");
     if (form == 1 && b->sub.empty()) {
         const int n = (int)b->sys.size();
         for (int i = 0; i < n; ++i) {

@@ -64,6 +64,21 @@ __device__ __forceinline__ int checked_addr(int addr, int base)
     return addr;
 }
 
+// An index into an array of n entries other than the table (checked build: the
+// histogram counters of the global-table Potts form).
+__device__ __forceinline__ int checked_index(int i, int n)
+{
+#ifdef MUCA_CHECKED
+    if ((unsigned)i >= (unsigned)n) {
+        block_check_flag() = 1;
+        return 0;
+    }
+#else
+    (void)n;
+#endif
+    return i;
+}
+
 // After the block's last barrier.
 __device__ __forceinline__ void checks_end(const DevState *state)
 {

@@ -142,13 +142,26 @@ __device__ __forceinline__ void ising_sweep(uint32_t *__restrict__ lat, int ps, 
 // state different from the old one, new = (old + 1 + mulhi(u, q-1)) mod q.
 // dE = n_eq(old) - n_eq(new) in [-4, 4]; column dE+4; bin E+2N moves by dE.
 // The "left neighbour changed" candidate uses the left site's proposed colour.
-template <int L, int RECORD>
+// GT (a table too large for shared memory: q-Potts at L = 64, 8193 x 9 words):
+// the thresholds are read from the global [B][9] table gT (L2-resident), sTH holds
+// only the B histogram counters and bR is the bin itself.
+template <int L, int RECORD, bool GT = false>
 __device__ __forceinline__ void potts_sweep(uint32_t *__restrict__ lat, int ps, int &bR,
                                             uint32_t *__restrict__ sTH, uint32_t g, uint32_t wid,
-                                            const uint32_t (&rk)[20], uint32_t q, unsigned &nacc)
+                                            const uint32_t (&rk)[20], uint32_t q, unsigned &nacc,
+                                            const uint32_t *__restrict__ gT = nullptr, int nbins = 0)
 {
     constexpr int WR = potts_words_per_row(L);
-    constexpr int RS = 10;
+    constexpr int RS = GT ? 1 : 10;
+    auto tload = [&](int row, int c) -> uint32_t {
+        return GT ? __ldg(gT + checked_word(row * 9 + c)) : sTH[checked_word(row + c)];
+    };
+    auto hist = [&](int row) {
+        if (GT)
+            atomicAdd(&sTH[checked_index(row, nbins)], 1u);
+        else
+            atomicAdd(&sTH[checked_word(row + 9)], 1u);
+    };
     uint32_t up[WR], cur[WR], dn[WR], first[WR], nxt[WR], old[WR];
 #pragma unroll
     for (int j = 0; j < WR; ++j) {
@@ -191,7 +204,7 @@ __device__ __forceinline__ void potts_sweep(uint32_t *__restrict__ lat, int ps, 
         uint32_t nwc;
         int c0, c1, d0, d1;
         site(0, u.x, 0u, nwc, c0, c1, d0, d1);
-        uint32_t T0 = sTH[checked_word(bR + c0)], T1 = 0u;
+        uint32_t T0 = tload(bR, c0), T1 = 0u;
         bool accP = false;
         int dRp = 0;
 #pragma unroll
@@ -209,8 +222,8 @@ __device__ __forceinline__ void potts_sweep(uint32_t *__restrict__ lat, int ps, 
                 const uint32_t uprop = ((x + 1) & 1) ? u.z : u_next.x;
                 int n0, n1c, e0, e1;
                 site(x + 1, uprop, nw, nwc, n0, n1c, e0, e1);
-                T0 = sTH[checked_word(bR + n0)];
-                T1 = sTH[checked_word(bR + dR + n1c)];
+                T0 = tload(bR, n0);
+                T1 = tload(bR + dR, n1c);
                 d0 = e0;
                 d1 = e1;
             }
@@ -219,7 +232,7 @@ __device__ __forceinline__ void potts_sweep(uint32_t *__restrict__ lat, int ps, 
                 const int wi = (4 * x) >> 5, sh = (4 * x) & 31;
                 cur[wi] = (cur[wi] & ~(15u << sh)) | (nw << sh);
             }
-            if (RECORD == 0) atomicAdd(&sTH[checked_word((acc ? bR + dR : bR) + 9)], 1u);
+            if (RECORD == 0) hist(acc ? bR + dR : bR);
             accP = acc;
             dRp = dR;
         }
@@ -240,7 +253,7 @@ __device__ __forceinline__ void potts_sweep(uint32_t *__restrict__ lat, int ps, 
             dn[j] = (y + 2 < L) ? nxt[j] : first[j];
         }
     }
-    if (RECORD == 1) atomicAdd(&sTH[checked_word(bR + 9)], 1u);
+    if (RECORD == 1) hist(bR);
 }
 
 
@@ -323,6 +336,69 @@ __device__ __forceinline__ void sweep_block(const SpinSweepArgs &a, int w0, int 
     checks_end(a.state);
 }
 
+// q-Potts lattices whose threshold table does not fit in shared memory (L = 64: 8193
+// bins x 9 columns, 295 KB): one warp per 32 walkers, the thresholds read from the
+// global table (it stays in L2), only the B histogram counters in shared memory.
+template <int L>
+__device__ __forceinline__ void sweep_block_potts_gt(const SpinSweepArgs &a, int w0, int slot, uint32_t *smem)
+{
+    uint32_t *sH = smem;
+    const int tid = threadIdx.x;
+    for (int i = tid; i < a.B; i += blockDim.x) sH[i] = 0u;
+    checks_begin(a.B * 9, a.debug_check);
+    __syncthreads();
+
+    const int w = w0 + tid;
+    const bool active = w < a.p;
+    const uint32_t wid = (uint32_t)(w + a.walker_offset);
+    const uint32_t g0 = (uint32_t)a.state->sweep_counter;
+    uint32_t *lat = a.lattice + (active ? w : 0);
+    int bin = active ? a.bin[w] : 0;
+    unsigned long long *Hb = a.Hpart + (size_t)slot * a.B;
+    int tst = (active && a.tun) ? a.tun[w] : 0;
+    unsigned ev = 0;
+    unsigned long long nacc = 0;
+
+    for (int64_t s0 = 0; s0 < a.sweeps; s0 += a.flush_every) {
+        const int64_t s1 = (a.sweeps < s0 + a.flush_every) ? a.sweeps : s0 + a.flush_every;
+        if (active) {
+#pragma unroll 1
+            for (int64_t sw = s0; sw < s1; ++sw) {
+                const uint32_t g = g0 + (uint32_t)sw;
+                unsigned na = 0;
+                if (a.record == 0)
+                    potts_sweep<L, 0, true>(lat, a.pstride, bin, sH, g, wid, a.rk, (uint32_t)a.q, na, a.T, a.B);
+                else
+                    potts_sweep<L, 1, true>(lat, a.pstride, bin, sH, g, wid, a.rk, (uint32_t)a.q, na, a.T, a.B);
+                nacc += na;
+                tunnel_step(bin, a.bin_lo, a.bin_hi, tst, ev);
+            }
+        }
+        __syncthreads();
+        for (int b = tid; b < a.B; b += blockDim.x) {
+            const uint32_t c = sH[b];
+            if (c) {
+                Hb[b] += c;
+                sH[b] = 0u;
+            }
+        }
+        __syncthreads();
+    }
+    if (active) {
+        a.bin[w] = bin;
+        if (a.tun) a.tun[w] = (uint8_t)tst;
+    }
+    flush_metrics(a.metrics, nacc, ev);
+    checks_end(a.state);
+}
+
+template <int L>
+__global__ void __launch_bounds__(kMaxSweepBlock) k_sweep_potts_gt(const SpinSweepArgs a)
+{
+    extern __shared__ __align__(16) uint32_t smem[];
+    sweep_block_potts_gt<L>(a, blockIdx.x * blockDim.x, blockIdx.x, smem);
+}
+
 // One system per launch: block k runs walkers [k*blockDim.x, (k+1)*blockDim.x).
 template <int SYS, int L>
 __global__ void __launch_bounds__(kMaxSweepBlock) k_sweep_spin(const SpinSweepArgs a)
@@ -374,10 +450,14 @@ cudaError_t prepare_sweep_batch(size_t smem)
 
 size_t spin_sweep_smem_bytes(int system, int B) { return (size_t)B * (num_cols(system) + 1) * sizeof(uint32_t); }
 
+// The global-table Potts form (L = 64).
+static bool potts_gt(int system, int L) { return system == kPotts && L == 64; }
+
 bool spin_sweep_supported(int system, int L)
 {
     if (system != kIsing && system != kPotts && system != kMuma) return false;
     if (!sweep_L_supported(L)) return false;
+    if (potts_gt(system, L)) return true;
     const int N = L * L;
     const int B = (system == kPotts) ? 2 * N + 1 : N + 1;
     return spin_sweep_smem_bytes(system, B) <= 227u * 1024u;
@@ -415,6 +495,13 @@ static cudaError_t launch_sys(int L, const SpinSweepArgs &a, int block, cudaStre
 cudaError_t launch_spin_sweep(int system, int L, const SpinSweepArgs &a, int block, cudaStream_t s)
 {
     if (!spin_sweep_supported(system, L)) return cudaErrorInvalidValue;
+    if (potts_gt(system, L)) {
+        const size_t smem = (size_t)a.B * sizeof(uint32_t);
+        cudaError_t e = cudaFuncSetAttribute(k_sweep_potts_gt<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        k_sweep_potts_gt<64><<<(a.p + block - 1) / block, block, smem, s>>>(a);
+        return cudaGetLastError();
+    }
     switch (system) {
     case kIsing: return launch_sys<kIsing>(L, a, block, s);
     case kMuma: return launch_sys<kMuma>(L, a, block, s);

@@ -310,3 +310,30 @@ def test_state_buffer_must_be_consistent(system, L, q, C):
     c.iterate(5)
     g.iterate(5)
     np.testing.assert_array_equal(c.spins(), g.spins())
+
+
+@pytest.mark.parametrize("record", [0, 1])
+def test_potts_L64_global_table_bit_exact(record):
+    """q-Potts at L = 64 (8193 bins x 9 columns, too large for shared memory) runs the one-warp
+    form with the thresholds read from the global table: bit-exact against the oracle."""
+    run_pair(m.POTTS2D, 64, 10, 40, 17, 3, 10, record=record, nthreads=NT)
+
+
+def test_potts_L64_in_a_batch():
+    """Side by side (form 1) a batch runs it; the persistent tile form refuses it."""
+    cfg = [(m.POTTS2D, 64, 10, 40, 3), (m.ISING2D, 16, 2, 64, 4)]
+    ref = [m.Muca(s, L, q, p, seed) for s, L, q, p, seed in cfg]
+    for _ in range(2):
+        for c in ref:
+            c.iterate(8)
+            c.merge_and_update()
+    sys_ = [m.Muca(s, L, q, p, seed) for s, L, q, p, seed in cfg]
+    b = m.Batch(sys_)
+    with pytest.raises(m.MucaError):
+        b.set_form(0)
+    b.run(2, 8, use_graph=True)
+    for r, c in zip(ref, sys_):
+        np.testing.assert_array_equal(r.lnW().view(np.uint64), c.lnW().view(np.uint64))
+        np.testing.assert_array_equal(r.spins(), c.spins())
+        assert r.metrics() == c.metrics()
+    b.close()
