@@ -261,13 +261,6 @@ void orc_poly_set_model(void *h, int model)
     }
 }
 
-static uint32_t poly_word(const orc_poly *P, uint32_t c0, uint32_t c1, uint32_t w, uint32_t tag, int k)
-{
-    uint32_t ctr[4] = {c0, c1, w, tag}, key[2] = {(uint32_t)(P->seed & 0xffffffffu), (uint32_t)(P->seed >> 32)}, out[4];
-    orc_philox4x32_10(ctr, key, out);
-    return out[k];
-}
-
 void orc_poly_init(void *h)
 {
     orc_poly *P = (orc_poly *)h;
