@@ -45,7 +45,7 @@ INSTR_PER_ATTEMPT = 30
 # k_sweep_spin_tn build (dram__bytes_read.sum + dram__bytes_write.sum; mean of the Ising and MUMA
 # launches: 1.24 MB and 2.19 MB read, nothing written).  It is the walker state and does not grow
 # with the sweep count.  Set to None whenever the kernel changes until it is measured again.
-TRAFFIC_PER_LAUNCH = 1.71e6
+TRAFFIC_PER_LAUNCH = None
 METRIC = "MUCA move attempts/s (Ising L=32 p=8192: MUCA in E + MUMA in M)"
 UNIT = "attempts/s"
 L2_FLUSH_BYTES = 256 << 20

@@ -195,7 +195,10 @@ __device__ __forceinline__ void ising_sweep_tc(uint32_t *__restrict__ lat, int p
     uint32_t up[WR], cur[WR], old[WR];
 #pragma unroll
     for (int j = 0; j < WR; ++j) up[j] = lat[((L - 1) * WR + j) * ps];
-#pragma unroll 1
+    // two rows an iteration from L = 32 up (2-4 % there; L = 16 rows are short enough that the
+    // larger body costs more than the loop overhead it saves)
+    constexpr int kRowUnroll = (L >= 32) ? 2 : 1;
+#pragma unroll kRowUnroll
     for (int y = 0; y < L; ++y) {
         const int slot = k % kRing;
         if (!bad && !mbar_wait(&full[slot], (unsigned)((k / kRing) & 1))) bad = true;
