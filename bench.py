@@ -43,9 +43,9 @@ N = L * L
 INSTR_PER_ATTEMPT = 30
 # DRAM bytes (read + write) per launch of the timed sweep kernel, from one ncu capture of the current
 # k_sweep_spin_tn build (dram__bytes_read.sum + dram__bytes_write.sum; mean of the Ising and MUMA
-# launches: 1.24 MB and 2.19 MB read, nothing written).  It is the walker state and does not grow
+# launches: 1.25 MB and 2.17 MB read, nothing written).  It is the walker state and does not grow
 # with the sweep count.  Set to None whenever the kernel changes until it is measured again.
-TRAFFIC_PER_LAUNCH = None
+TRAFFIC_PER_LAUNCH = 1.71e6
 METRIC = "MUCA move attempts/s (Ising L=32 p=8192: MUCA in E + MUMA in M)"
 UNIT = "attempts/s"
 L2_FLUSH_BYTES = 256 << 20
