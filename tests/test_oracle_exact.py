@@ -85,3 +85,24 @@ def test_ising_EM_bruteforce_equals_tm_and_marginals(orc):
     assert [sum(row) for row in tm6] == orc.tm_ising(6)
     for row in tm6:
         assert row == row[::-1]                # Omega(E, M) = Omega(E, -M)
+
+
+def test_ising_L16_kaufman_golden_file():
+    """tests/golden/ising_L16_kaufman.txt (used by the GPU physics test) is what its generator
+    computes from Kaufman's closed form: ln Z at every beta, and <E>/N, C/N by central differences,
+    re-derived here at beta = 0.4 with a different step."""
+    import os
+
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "ising_L16_kaufman.txt")
+    rows = [[mpmath.mpf(x) for x in line.split()] for line in open(path) if not line.startswith("#")]
+    assert len(rows) == 6
+    for beta, lnZ, _, _ in rows:
+        assert abs(ex.kaufman_lnZ(16, 16, beta) - lnZ) < mpmath.mpf(10) ** -15 * abs(lnZ)
+    beta, _, e, c = next(r for r in rows if abs(r[0] - mpmath.mpf("0.4")) < 1e-12)
+    with mpmath.workdps(60):
+        h = mpmath.mpf("1e-9")
+        f = lambda t: ex.kaufman_lnZ(16, 16, t)  # noqa: E731
+        d1 = (f(beta + h) - f(beta - h)) / (2 * h)
+        d2 = (f(beta + h) - 2 * f(beta) + f(beta - h)) / (h * h)
+    assert abs(-d1 / 256 - e) < 1e-12
+    assert abs(beta * beta * d2 / 256 - c) < 1e-8
