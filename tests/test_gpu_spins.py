@@ -337,3 +337,11 @@ def test_potts_L64_in_a_batch():
         np.testing.assert_array_equal(r.spins(), c.spins())
         assert r.metrics() == c.metrics()
     b.close()
+
+
+@pytest.mark.parametrize("system,q", [(m.ISING2D, 2), (m.POTTS2D, 8), (m.ISING2D_MUMA, 2)])
+def test_full_size_bit_exact_with_nontrivial_weights(system, q):
+    """Benchmark size and launch configuration (L = 32, p = 8192, code form, 64 walkers a block):
+    four short iterations, so that the later ones run on weights the earlier histograms set
+    (thresholds below "always"), compared with the oracle over all walkers bit for bit."""
+    run_pair(system, 32, q, 8192, 23, 4, 20, beta=0.4407 if system == m.ISING2D_MUMA else 0.0, nthreads=NT)
