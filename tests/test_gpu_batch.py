@@ -135,3 +135,22 @@ def test_side_by_side_batch_with_mixed_forms_and_blocks():
         np.testing.assert_array_equal(r.spins(), c.spins())
         assert r.metrics() == c.metrics()
     b.close()
+
+
+def test_full_size_mix_bit_exact_against_the_oracle():
+    """The batched mix at its benchmark size (Ising L = 16..64 and q = 10 Potts L = 16..48,
+    2048 walkers each, side by side in one graph): three short iterations, every system bit-exact
+    against its own oracle run."""
+    mix = [(m.ISING2D, L, 2, 2048, 500 + i) for i, L in enumerate((16, 24, 32, 48, 64))] + \
+          [(m.POTTS2D, L, 10, 2048, 600 + i) for i, L in enumerate((16, 24, 32, 48))]
+    sys_ = [m.Muca(s, L, q, p, seed) for s, L, q, p, seed in mix]
+    b = m.Batch(sys_)
+    b.run(3, 4, use_graph=True)
+    for (s, L, q, p, seed), c in zip(mix, sys_):
+        o = oracle.Run(s, L, q, p, seed)
+        o.init()
+        for _ in range(3):
+            o.iterate(4, 16)
+            o.update()
+        compare_state(c, o, "mix system %d L=%d" % (s, L))
+    b.close()
