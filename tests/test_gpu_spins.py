@@ -234,6 +234,10 @@ def test_errors_are_reported_not_raised_in_c():
 def test_p_equals_one_and_tiny_lattice():
     run_pair(m.ISING2D, 4, 2, 1, seed=8, iters=3, sweeps=200, nthreads=1)
     run_pair(m.POTTS2D, 4, 16, 1, seed=8, iters=3, sweeps=200, nthreads=1)
+    run_pair(m.ISING2D_MUMA, 4, 2, 1, seed=8, iters=3, sweeps=200, beta=0.4407, nthreads=1)
+    # one walker in a 32-lane consumer warp of the code form (31 inactive lanes)
+    run_pair(m.ISING2D, 8, 2, 1, seed=9, iters=3, sweeps=100, nthreads=1, pipeline=2)
+    run_pair(m.POTTS2D, 8, 5, 1, seed=9, iters=3, sweeps=100, nthreads=1, pipeline=2)
 
 
 @pytest.mark.parametrize("pipeline,L,p", [(0, 8, 64), (1, 16, 70), (2, 16, 70), (2, 32, 100)])
