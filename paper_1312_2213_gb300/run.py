@@ -54,17 +54,16 @@ def make_system(spec: dict, flat_ratio: float = 0.5) -> Muca:
     return c
 
 
-def _flat(c) -> bool:
+def _flat(c, ratio: float) -> bool:
     mn, mean, _ = c.flatness()
-    return bool(mn > 0 and mn >= c._flat_ratio * mean)
+    return bool(mn > 0 and mn >= ratio * mean)
 
 
 def run(cfg: dict, log=None, out=sys.stdout) -> dict:
     specs = cfg["systems"] if "systems" in cfg else [cfg]
     ratio = cfg.get("flat_ratio", 0.5)
     systems = [make_system(s, ratio) for s in specs]
-    for c, s in zip(systems, specs):
-        c._flat_ratio = s.get("flat_ratio", ratio)
+    ratios = [s.get("flat_ratio", ratio) for s in specs]
     iters, sweeps = int(cfg.get("iterations", 10)), int(cfg.get("sweeps", 1000))
     stop = bool(cfg.get("stop_when_flat", False))
     spins_only = all(c.system != POLYMER3D for c in systems)
@@ -87,13 +86,13 @@ def run(cfg: dict, log=None, out=sys.stdout) -> dict:
             if log is not None:
                 for c in systems:
                     log.log(c, seconds=dt / len(systems))
-            if stop and all(_flat(c) for c in systems):
+            if stop and all(_flat(c, r) for c, r in zip(systems, ratios)):
                 break
         result = {"iterations": done, "systems": []}
-        for c, s in zip(systems, specs):
+        for c, s, ratio_c in zip(systems, specs, ratios):
             mn, mean, mx = (float(x) for x in c.flatness())
             r = {"system": s["system"], ("N" if c.system == POLYMER3D else "L"): c.L, "p": c.p,
-                 "flat": _flat(c), "h_min": mn, "h_mean": mean, "h_max": mx, "reweight": {}}
+                 "flat": _flat(c, ratio_c), "h_min": mn, "h_mean": mean, "h_max": mx, "reweight": {}}
             for beta in cfg.get("reweight_betas", []):
                 vals, _ = c.reweight(float(beta))
                 r["reweight"][str(beta)] = [float(v) for v in vals]
