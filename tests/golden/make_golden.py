@@ -23,17 +23,22 @@ def main():
         for j, o in enumerate(om):
             f.write("%d %d\n" % (4 * j - 2 * N, o))
 
-    # 16 x 16: thermodynamics from Kaufman's closed form (oracle/exact.py), the derivatives of ln Z
+    # 16 x 16 and 32 x 32: thermodynamics from Kaufman's closed form (oracle/exact.py), the derivatives of ln Z
     # by central differences at 60 digits (step 1e-12 / 1e-10, truncation ~1e-20):
     # <E> = -d lnZ / d beta, C = beta^2 d^2 lnZ / d beta^2.
     import mpmath
 
     from oracle import exact
 
-    L, N = 16, 256
+    for L in (16, 32):
+        _kaufman_table(L, mpmath, exact)
+
+
+def _kaufman_table(L, mpmath, exact):
+    N = L * L
     with mpmath.workdps(60):
-        with open(os.path.join(HERE, "ising_L16_kaufman.txt"), "w") as f:
-            f.write("# Exact thermodynamics of the 16x16 periodic Ising model (J = 1), from Kaufman's\n")
+        with open(os.path.join(HERE, "ising_L%d_kaufman.txt" % L), "w") as f:
+            f.write("# Exact thermodynamics of the %dx%d periodic Ising model (J = 1), from Kaufman's\n" % (L, L))
             f.write("# closed form of Z (Phys. Rev. 76, 1232 (1949)) as evaluated by oracle/exact.py;\n")
             f.write("# <E> = -d lnZ/d beta and C = beta^2 d^2 lnZ/d beta^2 by central differences at 60 digits.\n")
             f.write("# columns: beta  lnZ  <E>/N  C/N\n")
