@@ -52,11 +52,12 @@ __device__ __forceinline__ uint4 clamp_words(uint4 u)
     return u;
 }
 
-// Producer warps per consumer warp in the code forms.  One Philox4x32-10 block
-// costs a scheduler about 90 cycles of integer-multiply throughput and a single
-// warp reaches about 134 cycles a block, so one producer cannot keep up with its
-// consumer; the row's site groups are split over NP producers (on other
-// schedulers), which arrive together on the row's FULL barrier.
+// Producer warps per consumer warp in the Ising/MUMA code form (the Potts form
+// has kPottsProducers).  One Philox4x32-10 block costs a scheduler about 90
+// cycles of integer-multiply throughput and a single warp reaches about 134
+// cycles a block, so one producer cannot keep up with its consumer; the row's
+// site groups are split over the producers (on other schedulers), which arrive
+// together on the row's FULL barrier.
 constexpr int kCodeProducers = 2;
 
 template <int WR>
