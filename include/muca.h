@@ -89,11 +89,13 @@ int muca_init_ex(muca_ctx **out, int system, int L_or_N, int q, int p, uint64_t 
  *                 code form; the code form runs for 32 or 64);
  *                 polymer: threads per block (default 256).  Before the first
  *                 iterate.
- *   "pipeline"    spins: 2 (default) pairs every warp of walkers with a
- *                 producer warp that computes their random numbers and, for
- *                 Ising and MUMA, each site's neighbour code into a
- *                 shared-memory ring; 1 does the same with random numbers
- *                 only; 0 runs one warp per 32 walkers.  A form that does not
+ *   "pipeline"    spins: 2 (default) pairs every warp of walkers with
+ *                 producer warps (two; three for Potts) that compute their
+ *                 random numbers and each site's neighbour code (Potts: also
+ *                 the proposal) into a shared-memory ring; 1 does the same
+ *                 with random numbers only, one producer warp; 0 runs one
+ *                 warp per 32 walkers (q-Potts at L = 64 always: its table
+ *                 is read from global memory).  A form that does not
  *                 fit the system, L, bin count or block falls back to the next
  *                 lower one.  Ring hand-overs are bounded waits; a wait that
  *                 gives up makes the next synchronising call return
