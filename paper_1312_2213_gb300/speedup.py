@@ -82,12 +82,21 @@ def study(system: int, L: int, q: int, p_values, n_seeds: int, max_iter: int, ra
         if log:
             log(row)
     base = next((r for r in rows if r["p"] == 1 and r["converged"]), None)
+    # without p = 1 (a single chain can take too long), S* relative to the smallest converged p:
+    # p0 S*_p / S*_p0 = p0 [N_iter M]_p0 / [N_iter M]_p, which equals S*_p where S*_p0 = p0
+    ref = next((r for r in sorted(rows, key=lambda r: r["p"]) if r["converged"]), None)
     for r in rows:
         if base and r["converged"]:
             r["S_star"] = base["n_iter_mean"] * base["sweeps_per_iteration"] / (
                 r["n_iter_mean"] * r["sweeps_per_iteration"])
         else:
             r["S_star"] = math.nan
+        if ref and r["converged"]:
+            r["S_star_rel"] = ref["p"] * ref["n_iter_mean"] * ref["sweeps_per_iteration"] / (
+                r["n_iter_mean"] * r["sweeps_per_iteration"])
+            r["S_star_rel_to_p"] = ref["p"]
+        else:
+            r["S_star_rel"] = math.nan
     return rows
 
 

@@ -31,3 +31,16 @@ def test_unconverged_seeds_are_left_out(monkeypatch):
                         lambda system, L, q, p, seeds, M, max_iter, ratio, beta: [10, None, 14])
     rows = speedup.study(m.ISING2D, 8, 2, [1], 3, 100)
     assert rows[0]["converged"] == 2 and rows[0]["n_iter_mean"] == 12.0
+
+
+def test_s_star_relative_to_the_smallest_p(monkeypatch):
+    """Without p = 1 the study reports p0 S*_p / S*_p0 against the smallest converged p0."""
+    fake = {16: [20, 22], 64: [None, None], 256: [30, 30]}
+    monkeypatch.setattr(speedup, "iterations_to_flat",
+                        lambda system, L, q, p, seeds, M, max_iter, ratio, beta: fake[p])
+    rows = speedup.study(m.ISING2D, 32, 2, [16, 64, 256], 2, 100)
+    by_p = {r["p"]: r for r in rows}
+    assert by_p[16]["S_star_rel"] == 16.0 and by_p[16]["S_star_rel_to_p"] == 16
+    assert math.isnan(by_p[64]["S_star_rel"]) and math.isnan(by_p[16]["S_star"])
+    want = 16 * 21 * speedup.m_opt(m.ISING2D, 32, 16) / (30 * speedup.m_opt(m.ISING2D, 32, 256))
+    assert math.isclose(by_p[256]["S_star_rel"], want)
