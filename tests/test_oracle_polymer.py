@@ -84,6 +84,22 @@ def test_fene_dimer_density_of_states(orc):
     le = np.log(omega[seen])
     off = np.median(le - lo)
     assert np.max(np.abs(lo + off - le)) < 0.15
+    # Eq. 2 at bin centres: the oracle's reweighting equals the formula written out on its own
+    # estimate ln H - ln W, and, from the exact binned Omega, <E> within the estimate's spread
+    centres = np.array(edges[:-1]) + 0.05
+    for beta in (0.5, 1.0):
+        out, _ = P.reweight(beta)
+        la = lo - beta * centres[seen]
+        w = np.exp(la - la.max())
+        e1 = float((w * centres[seen]).sum() / w.sum())
+        e2 = float((w * centres[seen] ** 2).sum() / w.sum())
+        assert abs(out[0] - e1) < 1e-9 * max(1.0, abs(e1))
+        assert abs(out[1] - e2) < 1e-9 * max(1.0, abs(e2))
+        assert abs(out[2] - beta * beta * (e2 - e1 * e1) / 2) < 1e-9 * max(1.0, out[2])
+        lx = le - beta * centres[seen]
+        wx = np.exp(lx - lx.max())
+        ex_e = float((wx * centres[seen]).sum() / wx.sum())
+        assert abs(out[0] - ex_e) < 0.02 * ex_e, (beta, out[0], ex_e)
 
 
 def test_paper_model_pair_potentials(orc):
