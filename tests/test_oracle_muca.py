@@ -401,3 +401,19 @@ def test_observables_at_low_temperature_from_a_muca_run(orc):
     got = r.reweight_observables(0.6)
     m1, _ = _canonical_m_moments(orc, 4, 0.6)
     assert abs(got[0] - m1) < 0.03 * m1
+
+
+def test_flatness_is_min_over_mean_on_reachable_bins(orc):
+    """Reading 9 written out: {min, mean, max} of the last merged histogram over the reachable
+    bins, and flat iff every reachable bin is visited and min >= ratio * mean."""
+    r = orc.Run(1, 6, 3, 16, 4)
+    r.init()
+    for it in range(6):
+        r.iterate(300, 4)
+        r.update()
+        H = r.histogram()[r.reachable()].astype(float)
+        for ratio in (0.2, 0.5, 0.8):
+            flat, st = r.is_flat(ratio)
+            assert st[0] == H.min() and st[2] == H.max()
+            assert abs(st[1] - H.mean()) <= 1e-12 * H.mean()
+            assert flat == bool(H.min() > 0 and H.min() >= ratio * H.mean())
