@@ -349,3 +349,21 @@ def test_full_size_bit_exact_with_nontrivial_weights(system, q):
     four short iterations, so that the later ones run on weights the earlier histograms set
     (thresholds below "always"), compared with the oracle over all walkers bit for bit."""
     run_pair(system, 32, q, 8192, 23, 4, 20, beta=0.4407 if system == m.ISING2D_MUMA else 0.0, nthreads=NT)
+
+
+@pytest.mark.parametrize("system,L,q", [(m.ISING2D, 8, 2), (m.POTTS2D, 8, 4), (m.ISING2D_MUMA, 8, 2)])
+def test_flatness_matches_oracle(system, L, q):
+    """The device's flatness statistic (min, mean, max over the reachable bins) and its flat
+    decision equal the oracle's after every iteration."""
+    beta = 0.4407 if system == m.ISING2D_MUMA else 0.0
+    g = m.Muca(system, L, q, 48, 6, beta=beta if system == m.ISING2D_MUMA else None)
+    o = oracle.Run(system, L, q, 48, 6, beta=beta)
+    o.init()
+    for _ in range(8):
+        g.iterate(200)
+        flat_g = g.merge_and_update(want_flat=True)
+        o.iterate(200, NT)
+        o.update()
+        flat_o, st = o.is_flat(0.5)
+        np.testing.assert_array_equal(g.flatness(), st)
+        assert flat_g == flat_o
