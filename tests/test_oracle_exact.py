@@ -87,22 +87,23 @@ def test_ising_EM_bruteforce_equals_tm_and_marginals(orc):
         assert row == row[::-1]                # Omega(E, M) = Omega(E, -M)
 
 
-def test_ising_L16_kaufman_golden_file():
-    """tests/golden/ising_L16_kaufman.txt (used by the GPU physics test) is what its generator
-    computes from Kaufman's closed form: ln Z at every beta, and <E>/N, C/N by central differences,
-    re-derived here at beta = 0.4 with a different step."""
+@pytest.mark.parametrize("L", [16, 32])
+def test_ising_kaufman_golden_files(L):
+    """tests/golden/ising_L{16,32}_kaufman.txt (the GPU physics test, the configuration-2 run) are
+    what their generator computes from Kaufman's closed form: ln Z at every beta, and <E>/N, C/N
+    by central differences, re-derived here at beta = 0.4 with a different step."""
     import os
 
-    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "ising_L16_kaufman.txt")
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "ising_L%d_kaufman.txt" % L)
     rows = [[mpmath.mpf(x) for x in line.split()] for line in open(path) if not line.startswith("#")]
     assert len(rows) == 6
     for beta, lnZ, _, _ in rows:
-        assert abs(ex.kaufman_lnZ(16, 16, beta) - lnZ) < mpmath.mpf(10) ** -15 * abs(lnZ)
+        assert abs(ex.kaufman_lnZ(L, L, beta) - lnZ) < mpmath.mpf(10) ** -15 * abs(lnZ)
     beta, _, e, c = next(r for r in rows if abs(r[0] - mpmath.mpf("0.4")) < 1e-12)
     with mpmath.workdps(60):
         h = mpmath.mpf("1e-9")
-        f = lambda t: ex.kaufman_lnZ(16, 16, t)  # noqa: E731
+        f = lambda t: ex.kaufman_lnZ(L, L, t)  # noqa: E731
         d1 = (f(beta + h) - f(beta - h)) / (2 * h)
         d2 = (f(beta + h) - 2 * f(beta) + f(beta - h)) / (h * h)
-    assert abs(-d1 / 256 - e) < 1e-12
-    assert abs(beta * beta * d2 / 256 - c) < 1e-8
+    assert abs(-d1 / (L * L) - e) < 1e-12
+    assert abs(beta * beta * d2 / (L * L) - c) < 1e-8
