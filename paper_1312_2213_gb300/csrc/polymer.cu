@@ -238,11 +238,23 @@ __device__ bool poly_rotation(const long long *Xg, int N, int i, uint32_t g, uin
     return true;
 }
 
+// Shared-memory floats of one walker's float-pair shadows (6 N), padded so that
+// consecutive walkers of a warp start G banks apart: the G lanes of walker g read
+// bead j = lane + G k, so with 32/G walkers a warp every pair-loop load touches 32
+// distinct banks (unpadded, 6 N = 0 mod 32 for N = 32, 64, 128 and the walkers of
+// a warp collided pairwise).  A multiple of 4 floats, so that the uint4 Philox
+// blocks that follow all slots stay 16-byte aligned for any walker count.
+__host__ __device__ inline int poly_slot_floats(int N, int G)
+{
+    const int r = (6 * N) & 31;
+    return 6 * N + (G < 32 ? ((G - r) & 31) : ((4 - r) & 3));
+}
+
 // Sweeps: G lanes per walker, 32/G walkers a warp, all on the same bead i.  A
 // walker's float-pair shadows and this sweep's Philox blocks live in shared
-// memory (40 N bytes, 56 N with rotations); its int64 master coordinates stay in
-// global memory (read at the sweep start and for the moved bead, written on
-// acceptance).  The two
+// memory (40 N bytes, 56 N with rotations, plus the padding above); its int64
+// master coordinates stay in global memory (read at the sweep start and for the
+// moved bead, written on acceptance).  The two
 // bonds of bead i (FENE) are taken by lanes 0 and 1 of the group, the other
 // partners (LJ, |i - j| >= 2) by lanes j mod G, so no lane runs both branches.
 template <int G, int RECORD>
@@ -252,11 +264,11 @@ __global__ void __launch_bounds__(kMaxSweepBlock) k_sweep_polymer(const PolyArgs
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, wpb = blockDim.x >> 5, N = a.N;
     const int gi = lane / G, li = lane % G;
-    const int spb = wpb * W, slot = wib * W + gi;
-    float *xs = (float *)smem + (size_t)slot * 6 * N;
+    const int spb = wpb * W, slot = wib * W + gi, sst = poly_slot_floats(N, G);
+    float *xs = (float *)smem + (size_t)slot * sst;
     float *xl = xs + 3 * N;
-    uint4 *su = (uint4 *)(smem + (size_t)spb * 6 * N * sizeof(float)) + (size_t)slot * N;
-    uint4 *sm = (uint4 *)(smem + (size_t)spb * N * (6 * sizeof(float) + sizeof(uint4))) + (size_t)slot * N;  // moves
+    uint4 *su = (uint4 *)(smem + (size_t)spb * sst * sizeof(float)) + (size_t)slot * N;
+    uint4 *sm = su + (size_t)spb * N;  // moves
     const int w0 = (blockIdx.x * wpb + wib) * W;
     if (w0 >= a.p) return;  // whole warps only; no block-wide barrier follows
     const int w = w0 + gi;
@@ -451,7 +463,8 @@ template <int G>
 static cudaError_t launch_g(const PolyArgs &a, int block, cudaStream_t s)
 {
     const int wpb = block / 32, spb = wpb * (32 / G);
-    const size_t smem = (size_t)spb * a.N * (6 * sizeof(float) + (a.moves ? 2 : 1) * sizeof(uint4));
+    const size_t smem = (size_t)spb * ((size_t)poly_slot_floats(a.N, G) * sizeof(float) +
+                                       (size_t)a.N * (a.moves ? 2 : 1) * sizeof(uint4));
     const int nblk = (a.p + spb - 1) / spb;
     cudaError_t e;
     if (a.record == 0) {

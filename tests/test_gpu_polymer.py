@@ -74,15 +74,17 @@ def test_first_iteration_trajectories_identical():
     assert int(g.histogram().sum()) == int(o.histogram().sum()) == p * S * N
 
 
-@pytest.mark.parametrize("lanes,p", [(0, 64), (8, 61), (16, 63), (32, 64)])
-def test_first_iteration_histogram_in_pilot_window(lanes, p):
+@pytest.mark.parametrize("lanes,p,block", [(0, 64, None), (8, 61, None), (16, 63, None), (32, 64, None),
+                                           (32, 37, 96), (16, 29, 32), (8, 45, 160)])
+def test_first_iteration_histogram_in_pilot_window(lanes, p, block):
     """In the pilot window (walk-in, then ln W = 0): walkers without a near-tie or bin-edge event
     in the oracle are bit-identical, and the histograms differ only through bin-edge events.  Every
     lane grouping (8, 16, 32 lanes a walker), with walker counts that leave the last warp partly
-    empty."""
+    empty, and blocks with an odd warp count (odd N: the per-walker shared-memory slots must keep
+    the Philox blocks behind them 16-byte aligned)."""
     N, S = 13, 40
     lo, hi = WINDOWS[str(N)]["e_lo"], WINDOWS[str(N)]["e_hi"]
-    g = m.Muca(m.POLYMER3D, N, 0, p, 5, window=(lo, hi))
+    g = m.Muca(m.POLYMER3D, N, 0, p, 5, window=(lo, hi), block=block)
     g.set_param("lanes", lanes)
     o = oracle.PolyRun(N, p, 5, lo, hi)
     o.init()
