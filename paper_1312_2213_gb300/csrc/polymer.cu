@@ -238,23 +238,24 @@ __device__ bool poly_rotation(const long long *Xg, int N, int i, uint32_t g, uin
     return true;
 }
 
-// Shared-memory floats of one walker's float-pair shadows (6 N), padded so that
-// consecutive walkers of a warp start G banks apart: the G lanes of walker g read
-// bead j = lane + G k, so with 32/G walkers a warp every pair-loop load touches 32
-// distinct banks (unpadded, 6 N = 0 mod 32 for N = 32, 64, 128 and the walkers of
-// a warp collided pairwise).  A multiple of 4 floats, so that the uint4 Philox
-// blocks that follow all slots stay 16-byte aligned for any walker count.
-__host__ __device__ inline int poly_slot_floats(int N, int G)
+// Shared-memory floats of one walker's float-pair shadows: 6 N, rounded up to a
+// multiple of 4 for one walker a warp (G = 32), so that the uint4 Philox blocks
+// behind all slots start 16-byte aligned for any warp count and odd N (with 2 or
+// 4 walkers a warp the slot count is even and 6 N always suffices).  Padding the
+// slots so that the walkers of a warp read disjoint banks (6 N = 0 mod 32 puts
+// them on the same banks for N = 32, 64, 128) was measured on GB300: within 1 %
+// at N = 64 and 128, 2-5 % slower at N = 32 and 13, so it is not done.
+template <int G>
+__host__ __device__ inline int poly_slot_floats(int N)
 {
-    const int r = (6 * N) & 31;
-    return 6 * N + (G < 32 ? ((G - r) & 31) : ((4 - r) & 3));
+    return G == 32 ? (6 * N + 3) & ~3 : 6 * N;
 }
 
 // Sweeps: G lanes per walker, 32/G walkers a warp, all on the same bead i.  A
 // walker's float-pair shadows and this sweep's Philox blocks live in shared
-// memory (40 N bytes, 56 N with rotations, plus the padding above); its int64
-// master coordinates stay in global memory (read at the sweep start and for the
-// moved bead, written on acceptance).  The two
+// memory (40 N bytes, 56 N with rotations); its int64 master coordinates stay in
+// global memory (read at the sweep start and for the moved bead, written on
+// acceptance).  The two
 // bonds of bead i (FENE) are taken by lanes 0 and 1 of the group, the other
 // partners (LJ, |i - j| >= 2) by lanes j mod G, so no lane runs both branches.
 template <int G, int RECORD>
@@ -264,7 +265,7 @@ __global__ void __launch_bounds__(kMaxSweepBlock) k_sweep_polymer(const PolyArgs
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, wpb = blockDim.x >> 5, N = a.N;
     const int gi = lane / G, li = lane % G;
-    const int spb = wpb * W, slot = wib * W + gi, sst = poly_slot_floats(N, G);
+    const int spb = wpb * W, slot = wib * W + gi, sst = poly_slot_floats<G>(N);
     float *xs = (float *)smem + (size_t)slot * sst;
     float *xl = xs + 3 * N;
     uint4 *su = (uint4 *)(smem + (size_t)spb * sst * sizeof(float)) + (size_t)slot * N;
@@ -463,7 +464,7 @@ template <int G>
 static cudaError_t launch_g(const PolyArgs &a, int block, cudaStream_t s)
 {
     const int wpb = block / 32, spb = wpb * (32 / G);
-    const size_t smem = (size_t)spb * ((size_t)poly_slot_floats(a.N, G) * sizeof(float) +
+    const size_t smem = (size_t)spb * ((size_t)poly_slot_floats<G>(a.N) * sizeof(float) +
                                        (size_t)a.N * (a.moves ? 2 : 1) * sizeof(uint4));
     const int nblk = (a.p + spb - 1) / spb;
     cudaError_t e;
