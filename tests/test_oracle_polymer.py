@@ -1,6 +1,7 @@
 """Pins for the polymer oracle (Eq. 7 reading): pair potentials against their defining
 properties, exact energy bookkeeping, exact dyadic moves, and multicanonical sampling of the
-FENE dimer against its closed-form binned density of states."""
+FENE dimer against its closed-form binned density of states and of the FENE + LJ trimer against
+its density of states by quadrature."""
 import math
 
 import numpy as np
@@ -101,6 +102,39 @@ def test_fene_dimer_density_of_states(orc):
         ex_e = float((wx * centres[seen]).sum() / wx.sum())
         assert abs(out[0] - ex_e) < 0.02 * ex_e, (beta, out[0], ex_e)
 
+
+
+def test_fene_lj_trimer_density_of_states(orc):
+    """N = 3: two FENE bonds and the Lennard-Jones pair (0, 2), the smallest chain in which every
+    term of Eq. (7) acts and a middle bead moves two bonds and the pair at once.  The oracle's
+    multicanonical estimate ln H - ln W over a window from just above the lowest energy (~10.62)
+    against the binned density of states by quadrature (inner integral in closed form).  A wrong
+    sign of the LJ shift, a cutoff of 2 or 3 instead of 2.5, K = 41 or R = 1.49 each move some bin
+    by more than the tolerance; the estimate's own deviation is ~0.01 rms."""
+    e_lo, e_hi = 10.7, 18.7
+    P = orc.PolyRun(3, 64, 13, e_lo, e_hi)
+    P.init()
+    for _ in range(14):
+        P.iterate(12000, 8)
+        P.update()
+    B = P.B
+    edges = [e_lo + 0.1 * b for b in range(B + 1)]
+    omega = np.array(ex.fene_lj_trimer_omega(edges, 40.0, 1.5, RC))
+    assert omega.max() / omega.min() > 50
+    H = P.histogram().astype(float)
+    assert np.all(H > 0)
+    lo = np.log(H) - P.lnW_sampled()
+    le = np.log(omega)
+    d = lo + np.median(le - lo) - le
+    assert np.max(np.abs(d)) < 0.05 and np.sqrt(np.mean(d * d)) < 0.02
+    # Eq. 2 at bin centres against the same sums over the exact binned Omega
+    centres = np.array(edges[:-1]) + 0.05
+    for beta in (0.5, 2.0):
+        out, _ = P.reweight(beta)
+        lx = le - beta * centres
+        wx = np.exp(lx - lx.max())
+        ex_e = float((wx * centres).sum() / wx.sum())
+        assert abs(out[0] - ex_e) < 0.005 * ex_e, (beta, out[0], ex_e)
 
 def test_paper_model_pair_potentials(orc):
     """Model 1 (Eq. 7 with K = 40, r0 = 0.7, r_max = 1): LJ zero at sigma = 2^(-1/6) r0 and
