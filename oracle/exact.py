@@ -12,9 +12,11 @@
   on pairs |i-j| >= 2 in Eq. (7)).
 * ``fene_lj_trimer_omega``: binned density of states of three beads, two FENE
   bonds and the Lennard-Jones pair (0, 2), by a quadrature whose innermost
-  integral is done in closed form.
+  integral is done in closed form (both parameter sets of Eq. (7)).
 """
 from __future__ import annotations
+
+import math
 
 import mpmath
 import numpy as np
@@ -93,45 +95,64 @@ def fene_shifted_dimer_omega(e_edges, K: float, R: float, r0: float, dps: int = 
         return [float(vol(b) - vol(a)) for a, b in zip(e_edges[:-1], e_edges[1:])]
 
 
-def fene_lj_trimer_omega(e_edges, K: float, R: float, rc: float, n: int = 800):
-    """Relative binned density of states of the N = 3 chain of Eq. (7) as read for the benchmark
-    configuration: FENE bonds V_F(r) = -(K/2) R^2 ln(1 - (r/R)^2) (r < R) on (0, 1) and (1, 2), and
-    the Lennard-Jones pair (0, 2), V_LJ(r) = 4 (r^-12 - r^-6) - 4 (rc^-12 - rc^-6) for r < rc, else 0.
+def fene_lj_trimer_omega(e_edges, K: float, R: float, rc, n: int = 400, r0: float = 0.0,
+                         sigma: float = 1.0):
+    """Relative binned density of states of the N = 3 chain of Eq. (7): FENE bonds
+    V_F(r) = -(K/2) R^2 ln(1 - ((r - r0)/R)^2) (|r - r0| < R) on (0, 1) and (1, 2), and the
+    Lennard-Jones pair (0, 2), V_LJ(s) = 4 ((sigma/s)^12 - (sigma/s)^6) - V_c for s < rc, else 0,
+    with V_c the unshifted value at rc (truncated and shifted; rc = None: no cutoff, V_c = 0).
+    The benchmark configuration's reading is r0 = 0, R = 1.5, sigma = 1, rc = 2.5; the paper's own
+    set is r0 = 0.7, R = 0.3, sigma = 2^(-1/6) r0, no cutoff.
 
     With bead 1 at the origin the bond vectors a = x0 - x1 and b = x2 - x1 are independent and
-    uniform in the ball of radius R, and the (0, 2) distance is s = |a - b|.  In spherical
+    uniform in the shell |r - r0| < R, and the (0, 2) distance is s = |a - b|.  In spherical
     coordinates d^3a d^3b = 8 pi^2 r_a^2 r_b^2 dr_a dr_b dc, c the cosine of the angle between a and
     b, and s^2 = r_a^2 + r_b^2 - 2 r_a r_b c turns dc into s ds / (r_a r_b).  So the volume with
     energy below E is
 
-        C(E) = 8 pi^2 int_0^R int_0^R r_a r_b m(r_a, r_b) dr_a dr_b,
+        C(E) = 8 pi^2 int int r_a r_b m(r_a, r_b) dr_a dr_b,
         m = int over s in [|r_a - r_b|, r_a + r_b] with V_LJ(s) < t of s ds,  t = E - V_F(r_a) - V_F(r_b).
 
-    {s : V_LJ(s) < t} is an interval: with x = s^-6, 4 (x^2 - x) = t + 4 (rc^-12 - rc^-6) has the
-    roots x = (1 +- sqrt(1 + t + 4 (rc^-12 - rc^-6))) / 2; the larger gives the inner end, the
-    smaller the outer one for t <= 0 (V_LJ = 0 beyond rc, so for t > 0 the interval is unbounded),
-    and the set is empty below the well's bottom.  m is then (hi^2 - lo^2)/2 exactly; the outer
-    double integral is a midpoint rule on n x n points (the integrand is continuous and piecewise
-    smooth; n = 800 agrees with n = 3200 to ~1e-5 of C).  A bin [E_a, E_b) holds C(E_b) - C(E_a).
+    {s : V_LJ(s) < t} is an interval: with x = (sigma/s)^6, 4 (x^2 - x) = t + V_c has the roots
+    x = (1 +- sqrt(1 + t + V_c)) / 2; the larger gives the inner end, the smaller the outer one
+    for t <= 0 (for t > 0 the interval is unbounded: V_LJ < 0 up to rc and 0 beyond), and the set
+    is empty below the well's bottom.  m is then (hi^2 - lo^2)/2 exactly; the outer double integral
+    is a midpoint rule in w = sqrt(V_F) for each bond, n points on each side of r0 (the integrand
+    is continuous and piecewise smooth).  A bin [E_a, E_b) holds C(E_b) - C(E_a).
     """
-    vrc = 4.0 * (rc ** -12 - rc ** -6)
-    h = R / n
-    r = (np.arange(n) + 0.5) * h
-    ra, rb = np.meshgrid(r, r, indexing="ij")
-    iu = ra >= rb                        # the integrand is symmetric in (r_a, r_b)
-    ra, rb = ra[iu], rb[iu]
-    wgt = np.where(ra > rb, 2.0, 1.0) * ra * rb * h * h * 8.0 * np.pi ** 2
-    vf = -(K * R * R / 2.0) * (np.log1p(-(ra / R) ** 2) + np.log1p(-(rb / R) ** 2))
+    vc = 0.0 if rc is None else 4.0 * ((sigma / rc) ** 12 - (sigma / rc) ** 6)
+    if not (r0 == 0.0 or r0 >= R):
+        raise ValueError("the bond shell must not reach r = 0 unless r0 = 0")
+    # One bond: nodes uniform in w = sqrt(V_F) (equal energy resolution up to the top of the window;
+    # dr/dw stays finite at w = 0), on both sides of r0 when r0 > 0.  Bonds above
+    # E_max - min V_LJ contribute to no bin.
+    KR2 = K * R * R
+    w_max = math.sqrt(max(e_edges[-1], 0.0) + 1.0 + abs(vc))
+    dw = w_max / n
+    w = (np.arange(n) + 0.5) * dw
+    v = w * w
+    q = np.exp(-2.0 * v / KR2)
+    sv = np.sqrt(-np.expm1(-2.0 * v / KR2))
+    drdw = 2.0 * w * R * q / (KR2 * sv) * dw
+    r = np.concatenate([r0 + R * sv, r0 - R * sv]) if r0 > 0.0 else R * sv
+    dr = np.concatenate([drdw, drdw]) if r0 > 0.0 else drdw
+    vb = np.concatenate([v, v]) if r0 > 0.0 else v
+    ia, ib = np.triu_indices(r.size)     # the integrand is symmetric in (r_a, r_b)
+    ra, rb = r[ia], r[ib]
+    wgt = np.where(ia != ib, 2.0, 1.0) * ra * rb * dr[ia] * dr[ib] * 8.0 * np.pi ** 2
+    vf = vb[ia] + vb[ib]
+    ra, rb = np.maximum(ra, rb), np.minimum(ra, rb)
     s_lo, s_hi = ra - rb, ra + rb
 
     def cum(E):
         t = E - vf
-        disc = 1.0 + t + vrc
+        disc = 1.0 + t + vc
         ok = disc > 0.0
         sq = np.sqrt(np.where(ok, disc, 0.0))
-        inner = ((1.0 + sq) / 2.0) ** (-1.0 / 6.0)
+        inner = sigma * ((1.0 + sq) / 2.0) ** (-1.0 / 6.0)
         xm = (1.0 - sq) / 2.0
-        outer = np.where(t > 0.0, np.inf, np.where(xm > 0.0, np.maximum(xm, 1e-300) ** (-1.0 / 6.0), np.inf))
+        outer = np.where(t > 0.0, np.inf,
+                         np.where(xm > 0.0, sigma * np.maximum(xm, 1e-300) ** (-1.0 / 6.0), np.inf))
         lo = np.maximum(s_lo, inner)
         hi = np.minimum(s_hi, outer)
         m = np.where(ok & (hi > lo), (hi * hi - lo * lo) / 2.0, 0.0)
@@ -139,4 +160,3 @@ def fene_lj_trimer_omega(e_edges, K: float, R: float, rc: float, n: int = 800):
 
     c = [cum(float(e)) for e in e_edges]
     return [b - a for a, b in zip(c[:-1], c[1:])]
-

@@ -104,23 +104,35 @@ def test_fene_dimer_density_of_states(orc):
 
 
 
-def test_fene_lj_trimer_density_of_states(orc):
+@pytest.mark.parametrize("model", [0, 1])
+def test_fene_lj_trimer_density_of_states(orc, model):
     """N = 3: two FENE bonds and the Lennard-Jones pair (0, 2), the smallest chain in which every
     term of Eq. (7) acts and a middle bead moves two bonds and the pair at once.  The oracle's
-    multicanonical estimate ln H - ln W over a window from just above the lowest energy (~10.62)
-    against the binned density of states by quadrature (inner integral in closed form).  A wrong
-    sign of the LJ shift, a cutoff of 2 or 3 instead of 2.5, K = 41 or R = 1.49 each move some bin
-    by more than the tolerance; the estimate's own deviation is ~0.01 rms."""
-    e_lo, e_hi = 10.7, 18.7
-    P = orc.PolyRun(3, 64, 13, e_lo, e_hi)
+    multicanonical estimate ln H - ln W over a window from just above the lowest energy against
+    the binned density of states by quadrature (inner integral in closed form), in the
+    configuration's reading (model 0, lowest energy ~10.62) and with the paper's parameters
+    (model 1, lowest energy -1: an equilateral triangle of side r0).  Mistakes this fails on:
+    model 0, a wrong sign of the LJ shift (0.27 in some bin), a cutoff of 2 or 3, K = 41, R = 1.49;
+    model 1, sigma = r0 (0.28), a cutoff at 2.5 sigma, R = 0.29.  The estimate's own deviation is
+    ~0.01 rms."""
+    if model == 0:
+        e_lo, e_hi, sweeps, final = 10.7, 18.7, 12000, 0
+        omega_args = dict(K=40.0, R=1.5, rc=RC)
+    else:
+        e_lo, e_hi, sweeps, final = -0.9, 7.1, 6000, 30000
+        omega_args = dict(K=40.0, R=0.3, rc=None, r0=0.7, sigma=2.0 ** (-1.0 / 6.0) * 0.7)
+    P = orc.PolyRun(3, 64, 13, e_lo, e_hi, model=model)
     P.init()
     for _ in range(14):
-        P.iterate(12000, 8)
+        P.iterate(sweeps, 8)
+        P.update()
+    if final:   # one long iteration on the converged weights (the thin top shells, as for N = 2)
+        P.iterate(final, 8)
         P.update()
     B = P.B
     edges = [e_lo + 0.1 * b for b in range(B + 1)]
-    omega = np.array(ex.fene_lj_trimer_omega(edges, 40.0, 1.5, RC))
-    assert omega.max() / omega.min() > 50
+    omega = np.array(ex.fene_lj_trimer_omega(edges, **omega_args))
+    assert omega.max() / omega.min() > 10
     H = P.histogram().astype(float)
     assert np.all(H > 0)
     lo = np.log(H) - P.lnW_sampled()
@@ -134,7 +146,8 @@ def test_fene_lj_trimer_density_of_states(orc):
         lx = le - beta * centres
         wx = np.exp(lx - lx.max())
         ex_e = float((wx * centres).sum() / wx.sum())
-        assert abs(out[0] - ex_e) < 0.005 * ex_e, (beta, out[0], ex_e)
+        assert abs(out[0] - ex_e) < 0.005 * max(1.0, abs(ex_e)), (beta, out[0], ex_e)
+
 
 def test_paper_model_pair_potentials(orc):
     """Model 1 (Eq. 7 with K = 40, r0 = 0.7, r_max = 1): LJ zero at sigma = 2^(-1/6) r0 and
