@@ -23,6 +23,17 @@ def main():
         for j, o in enumerate(om):
             f.write("%d %d\n" % (4 * j - 2 * N, o))
 
+    # 4 x 4 q = 8 Potts (the benchmark's q; the proposal draws from q - 1 = 7 colours)
+    L, q, N = 4, 8, 16
+    om = oracle.tm_potts(L, q)
+    with open(os.path.join(HERE, "potts_q8_L4_omega.txt"), "w") as f:
+        f.write("# Exact density of states Omega(E) of the 4x4 periodic q = 8 Potts model (J = 1),\n")
+        f.write("# H = -J sum_<ij> delta(s_i, s_j) (Potts paragraph of the paper), by the oracle's transfer\n")
+        f.write("# matrix, which tests/test_oracle_exact.py pins to brute force (q = 3) and to counting.\n")
+        f.write("# columns: E  Omega(E)\n")
+        for j, o in enumerate(om):
+            f.write("%d %d\n" % (j - 2 * N, o))
+
     # 16 x 16 and 32 x 32: thermodynamics from Kaufman's closed form (oracle/exact.py), the derivatives of ln Z
     # by central differences at 60 digits (step 1e-12 / 1e-10, truncation ~1e-20):
     # <E> = -d lnZ / d beta, C = beta^2 d^2 lnZ / d beta^2.

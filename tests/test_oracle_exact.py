@@ -1,5 +1,7 @@
 """Pins for the exact tools: brute force == transfer matrix == Kaufman's closed form,
 plus the textbook invariants of Omega(E).  These tools in turn pin the MUCA oracle."""
+import os
+
 import mpmath
 import numpy as np
 import pytest
@@ -64,6 +66,8 @@ def test_potts_invariants_and_reachable(orc, q, L):
     assert sum(om) == q ** N
     assert om[0] == q                          # E = -2N: all spins equal
     assert om[4] == (q * (q - 1) * N if q > 2 else 2 * N)  # one site differs from its 4 neighbours
+    assert om[6] == q * (q - 1) * 2 * N                # a domino of one new colour (6 broken bonds)
+    assert om[7] == q * (q - 1) * (q - 2) * 2 * N      # a domino of two new colours (7)
     r = orc.Run(orc.POTTS, L, q, 1, 1)
     np.testing.assert_array_equal(r.reachable(), np.array(om) > 0)
 
@@ -107,3 +111,22 @@ def test_ising_kaufman_golden_files(L):
         d2 = (f(beta + h) - 2 * f(beta) + f(beta - h)) / (h * h)
     assert abs(-d1 / (L * L) - e) < 1e-12
     assert abs(beta * beta * d2 / (L * L) - c) < 1e-8
+
+
+def test_potts_q8_L4_golden_file(orc):
+    """The stored 4x4 q = 8 Omega (written by tests/golden/make_golden.py from the oracle's transfer
+    matrix): q^N states in all, the low-lying counts by hand (one site: q(q-1)N; a domino of one
+    or two new colours: 2N q(q-1), 2N q(q-1)(q-2)) and the unreachable bins of the rule."""
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "potts_q8_L4_omega.txt")
+    rows = [l.split() for l in open(path) if l.strip() and not l.startswith("#")]
+    E = [int(r[0]) for r in rows]
+    om = [int(r[1]) for r in rows]
+    q, N = 8, 16
+    assert E == list(range(-2 * N, 1))
+    assert sum(om) == q ** N
+    assert om[0] == q and om[4] == q * (q - 1) * N
+    assert om[6] == 2 * N * q * (q - 1) and om[7] == 2 * N * q * (q - 1) * (q - 2)
+    assert [b for b in range(2 * N + 1) if om[b] == 0] == [1, 2, 3, 5]
+    r = orc.Run(orc.POTTS, 4, q, 1, 1)
+    np.testing.assert_array_equal(r.reachable(), np.array(om) > 0)
+

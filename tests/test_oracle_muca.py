@@ -1,6 +1,7 @@
 """Pins for the oracle's MUCA / multimagnetic chains, merge, recursion, thresholds and
 reweighting (Eq. 1-3, Fig. 1 scheme), against exact results and invariants."""
 import math
+import os
 
 import mpmath
 import numpy as np
@@ -336,6 +337,36 @@ def test_muca_potts_q3_L6_converges(orc):
     lo += le[0] - lo[0]
     assert np.max(np.abs(lo - le)) < 0.25
 
+
+
+def _golden_omega(name):
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", name)
+    return np.array([float(l.split()[1]) for l in open(path) if l.strip() and not l.startswith("#")])
+
+
+def test_muca_potts_q8_L4_is_unbiased_over_16_seeds(orc):
+    """q = 8 (the benchmark's q; proposals draw one of q - 1 = 7 colours, not a power of two) on
+    the 4x4 torus: ln H - ln W against the exact Omega (golden file), which spans 28 units of
+    ln Omega over 29 reachable bins.  Every seed within 0.2 in every bin; the 16-seed mean within
+    4 standard errors + 0.005 per bin."""
+    om = _golden_omega("potts_q8_L4_omega.txt")
+    devs = []
+    for seed in range(1, 17):
+        r = orc.Run(orc.POTTS, 4, 8, 64, seed)
+        r.init()
+        for _ in range(12):
+            r.iterate(4000, NT)
+            r.update()
+        reach = r.reachable()
+        np.testing.assert_array_equal(reach, om > 0)
+        lo = np.log(r.histogram()[reach].astype(float)) - r.lnW_sampled()[reach]
+        le = np.log(om[reach])
+        devs.append(lo + (le[0] - lo[0]) - le)
+    d = np.array(devs)[:, 1:]
+    assert np.abs(d).max() < 0.2
+    mean = d.mean(axis=0)
+    se = d.std(axis=0, ddof=1) / np.sqrt(d.shape[0])
+    assert np.all(np.abs(mean) < 4.0 * se + 0.005), np.max(np.abs(mean) / se)
 
 def test_multimagnetic_converges_to_exact_P_of_M(orc):
     """MUMA at beta = 0.4407, L = 6: ln W(M) -> -ln P_beta(M) + const, with
