@@ -394,6 +394,30 @@ def test_multimagnetic_converges_to_exact_P_of_M(orc):
     assert out[0] == pytest.approx((P * absM).sum() / N, rel=0.02)
 
 
+
+def test_multimagnetic_is_unbiased_over_16_seeds(orc):
+    """The multimagnetic workload above from 16 seeds: every seed within 0.15 of -ln P_beta(M) in
+    every bin, and the 16-seed mean within 4 standard errors + 0.005 per bin."""
+    beta, L, N = 0.4407, 6, 36
+    em = orc.tm_ising_EM(L)
+    with mpmath.workdps(40):
+        lnPM = np.array([float(mpmath.log(mpmath.fsum(mpmath.mpf(em[j][m]) * mpmath.exp(-beta * (4 * j - 2 * N))
+                                                      for j in range(N + 1)))) for m in range(N + 1)])
+    devs = []
+    for seed in range(1, 17):
+        r = orc.Run(2, L, 2, 64, seed, beta=beta)
+        r.init()
+        for _ in range(10):
+            r.iterate(3000, NT)
+            r.update()
+        lo = np.log(r.histogram().astype(float)) - r.lnW_sampled()
+        devs.append(lo + (lnPM[0] - lo[0]) - lnPM)
+    d = np.array(devs)[:, 1:]
+    assert np.abs(d).max() < 0.15
+    mean = d.mean(axis=0)
+    se = d.std(axis=0, ddof=1) / np.sqrt(d.shape[0])
+    assert np.all(np.abs(mean) < 4.0 * se + 0.005), np.max(np.abs(mean) / se)
+
 def _canonical_m_moments(orc, L, beta):
     """Exact <|M|>/N and <M^2>/N^2 at beta from the brute-force Omega(E, M)."""
     om = orc.bruteforce_ising_EM(L).astype(float)
