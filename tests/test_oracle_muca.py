@@ -324,6 +324,34 @@ def test_muca_ising_L8_is_unbiased_over_16_seeds(orc):
     assert np.all(np.abs(mean) < 4.0 * se + 0.005), np.max(np.abs(mean) / se)
     assert se.max() < 0.02
 
+
+def test_statistical_speedup_is_at_least_linear_for_ising_L8(orc):
+    """Eq. 6 on the oracle: 16 seeds per p start from ln W = 0 with M(p) = round(5.7 L^2.51 / p)
+    sweeps a walker per iteration (Eq. 4, the paper's Ising fit) and stop at their first flat merged
+    histogram; S*_p = [N_iter M]_1 / [N_iter M]_p.  The paper finds S*_p close to p for the 2D Ising
+    model up to p = 64 (Fig. 3); at L = 8 the oracle's S*_p is at least 0.9 p."""
+    L = 8
+
+    def m_opt(p):
+        return max(1, int(round(5.7 * L ** 2.51 / p)))
+
+    cost = {}
+    for p in (1, 4, 16, 64):
+        n = []
+        for k in range(16):
+            r = orc.Run(0, L, 2, p, 1000 + 7919 * k + p)
+            r.init()
+            for it in range(1, 501):
+                r.iterate(m_opt(p), NT)
+                r.update()
+                if r.is_flat(0.5)[0]:
+                    n.append(it)
+                    break
+        assert len(n) == 16, p
+        cost[p] = float(np.mean(n)) * m_opt(p)
+    for p in (4, 16, 64):
+        assert cost[1] / cost[p] >= 0.9 * p, (p, cost[1] / cost[p])
+
 def test_muca_potts_q3_L6_converges(orc):
     om = np.array([float(x) for x in orc.tm_potts(6, 3)])
     r = orc.Run(1, 6, 3, 64, 2)
