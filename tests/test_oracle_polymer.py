@@ -104,8 +104,8 @@ def test_fene_dimer_density_of_states(orc):
 
 
 
-@pytest.mark.parametrize("model", [0, 1])
-def test_fene_lj_trimer_density_of_states(orc, model):
+@pytest.mark.parametrize("model,moves", [(0, 0), (1, 0), (0, 1), (1, 1)])
+def test_fene_lj_trimer_density_of_states(orc, model, moves):
     """N = 3: two FENE bonds and the Lennard-Jones pair (0, 2), the smallest chain in which every
     term of Eq. (7) acts and a middle bead moves two bonds and the pair at once.  The oracle's
     multicanonical estimate ln H - ln W over a window from just above the lowest energy against
@@ -114,14 +114,16 @@ def test_fene_lj_trimer_density_of_states(orc, model):
     (model 1, lowest energy -1: an equilateral triangle of side r0).  Mistakes this fails on:
     model 0, a wrong sign of the LJ shift (0.27 in some bin), a cutoff of 2 or 3, K = 41, R = 1.49;
     model 1, sigma = r0 (0.28), a cutoff at 2.5 sigma, R = 0.29.  The estimate's own deviation is
-    ~0.01 rms."""
+    ~0.01 rms.  With spherical rotations in the move set (moves = 1) the same Omega must come out:
+    rotating an end bead about its neighbour changes only the LJ pair, the middle bead one bond
+    and the pair."""
     if model == 0:
         e_lo, e_hi, sweeps, final = 10.7, 18.7, 12000, 0
         omega_args = dict(K=40.0, R=1.5, rc=RC)
     else:
         e_lo, e_hi, sweeps, final = -0.9, 7.1, 6000, 30000
         omega_args = dict(K=40.0, R=0.3, rc=None, r0=0.7, sigma=2.0 ** (-1.0 / 6.0) * 0.7)
-    P = orc.PolyRun(3, 64, 13, e_lo, e_hi, model=model)
+    P = orc.PolyRun(3, 64, 13, e_lo, e_hi, model=model, moves=moves)
     P.init()
     for _ in range(14):
         P.iterate(sweeps, 8)
