@@ -281,6 +281,32 @@ def test_reweight_exact_omega(orc):
         assert np.exp(lnP[np.isfinite(lnP)]).sum() == pytest.approx(1.0, rel=1e-12)
 
 
+
+def test_reweight_exact_potts_q8_omega(orc):
+    """Eq. (2) for the Potts model on an exact histogram (H = the golden 4x4 q = 8 Omega, W = 1):
+    <E>, <E^2>, C_V per site and ln Z (ground state normalised to q states) equal direct summation
+    at 50 digits, across the first-order transition (beta_c = ln(1 + sqrt 8) = 1.342)."""
+    om = _golden_omega("potts_q8_L4_omega.txt")
+    r = orc.Run(orc.POTTS, 4, 8, 1, 1)
+    r.init()
+    r.set_open_histogram(om.astype(np.uint64))
+    r.update()
+    N = 16
+    Es = [b - 2 * N for b in range(2 * N + 1)]
+    for beta in (0.5, 1.342, 2.5):
+        out, lnP = r.reweight(beta)
+        with mpmath.workdps(50):
+            b = mpmath.mpf(beta)
+            w = [mpmath.mpf(int(o)) * mpmath.exp(-b * E) for o, E in zip(om, Es)]
+            Z = mpmath.fsum(w)
+            e1 = mpmath.fsum(wi * E for wi, E in zip(w, Es)) / Z
+            e2 = mpmath.fsum(wi * E * E for wi, E in zip(w, Es)) / Z
+        assert out[0] == pytest.approx(float(e1), rel=1e-12)
+        assert out[1] == pytest.approx(float(e2), rel=1e-12)
+        assert out[2] == pytest.approx(float(b * b * (e2 - e1 * e1) / N), rel=1e-9)
+        assert out[3] == pytest.approx(float(mpmath.log(Z)), rel=1e-12)
+        assert np.exp(lnP[np.isfinite(lnP)]).sum() == pytest.approx(1.0, rel=1e-12)
+
 def test_muca_converges_to_exact_ising_L8(orc):
     """The config-1 workload (L = 8, p = 64, 10 iterations of 1e4 sweeps): flat histogram and
     ln Omega_hat = ln H - ln W within 0.15 of Beale's exact Omega in every reachable bin."""
