@@ -307,6 +307,35 @@ def test_reweight_exact_potts_q8_omega(orc):
         assert out[3] == pytest.approx(float(mpmath.log(Z)), rel=1e-12)
         assert np.exp(lnP[np.isfinite(lnP)]).sum() == pytest.approx(1.0, rel=1e-12)
 
+
+def test_reweight_exact_multimagnetic_histogram(orc):
+    """MUMA reweighting (reading of Eq. 2 over M at the run's own beta) on an exact histogram:
+    H(M) = P_beta(M) (from the exact Omega(E, M) of 6x6, scaled to 1e15 and rounded) and W = 1 give
+    <|M|>/N, <M^2>/N^2, the susceptibility beta N (<M^2>/N^2 - <|M|>^2/N^2) and
+    ln P(M = 0) - ln P(M = N) of direct summation."""
+    beta, L, N = 0.4407, 6, 36
+    em = orc.tm_ising_EM(L)
+    with mpmath.workdps(50):
+        P = [mpmath.fsum(mpmath.mpf(em[j][m]) * mpmath.exp(-mpmath.mpf(beta) * (4 * j - 2 * N))
+                         for j in range(N + 1)) for m in range(N + 1)]
+        top = max(P)
+        H = [int(mpmath.nint(mpmath.mpf(10) ** 15 * x / top)) for x in P]
+        Hm = [mpmath.mpf(h) for h in H]
+        Z = mpmath.fsum(Hm)
+        absM = [abs(2 * m - N) for m in range(N + 1)]
+        a1 = mpmath.fsum(h * a for h, a in zip(Hm, absM)) / Z / N
+        a2 = mpmath.fsum(h * a * a for h, a in zip(Hm, absM)) / Z / N ** 2
+        barrier = mpmath.log(Hm[N // 2]) - mpmath.log(Hm[N])
+    r = orc.Run(2, L, 2, 1, 1, beta=beta)
+    r.init()
+    r.set_open_histogram(np.array(H, dtype=np.uint64))
+    r.update()
+    out, _ = r.reweight(beta)
+    assert out[0] == pytest.approx(float(a1), rel=1e-12)
+    assert out[1] == pytest.approx(float(a2), rel=1e-12)
+    assert out[2] == pytest.approx(float(beta * N * (a2 - a1 * a1)), rel=1e-9)
+    assert out[3] == pytest.approx(float(barrier), rel=1e-12)
+
 def test_muca_converges_to_exact_ising_L8(orc):
     """The config-1 workload (L = 8, p = 64, 10 iterations of 1e4 sweeps): flat histogram and
     ln Omega_hat = ln H - ln W within 0.15 of Beale's exact Omega in every reachable bin."""
