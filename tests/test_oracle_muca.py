@@ -93,14 +93,22 @@ def test_merge_is_partition_independent(orc):
     np.testing.assert_array_equal(a.spins(), b.spins())
 
 
-def test_recursion_ideal_histogram_gives_minus_ln_omega(orc):
+@pytest.mark.parametrize("case", ["ising_L8", "potts_q8_L4"])
+def test_recursion_ideal_histogram_gives_minus_ln_omega(orc, case):
     """Feeding H = Omega (sampled with W = 1) returns ln W = -ln Omega + const; a second
-    histogram proportional to Omega*W is flat and leaves ln W unchanged."""
-    om = np.array([float(x) for x in orc.tm_ising(8)])
-    r = orc.Run(0, 8, 2, 1, 1)
+    histogram proportional to Omega*W is flat and leaves ln W unchanged.  Ising L = 8 has one
+    unreachable bin between reachable neighbours, 4x4 q = 8 Potts the gaps {1, 2, 3} and {5}."""
+    if case == "ising_L8":
+        om_int = orc.tm_ising(8)
+        r = orc.Run(0, 8, 2, 1, 1)
+    else:
+        om_int = [int(x) for x in _golden_omega("potts_q8_L4_omega.txt")]
+        r = orc.Run(orc.POTTS, 4, 8, 1, 1)
+    om = np.array([float(x) for x in om_int])
     r.init()
     reach = r.reachable()
-    r.set_open_histogram(np.array(orc.tm_ising(8), dtype=np.uint64))
+    np.testing.assert_array_equal(reach, om > 0)
+    r.set_open_histogram(np.array(om_int, dtype=np.uint64))
     r.update()
     lnW = r.lnW()
     target = -np.log(om[reach])
