@@ -118,7 +118,10 @@ def fene_lj_trimer_omega(e_edges, K: float, R: float, rc, n: int = 400, r0: floa
     for t <= 0 (for t > 0 the interval is unbounded: V_LJ < 0 up to rc and 0 beyond), and the set
     is empty below the well's bottom.  m is then (hi^2 - lo^2)/2 exactly; the outer double integral
     is a midpoint rule in w = sqrt(V_F) for each bond, n points on each side of r0 (the integrand
-    is continuous and piecewise smooth).  A bin [E_a, E_b) holds C(E_b) - C(E_a).
+    is continuous and piecewise smooth), up to the top edge; the node spacing grows with that edge,
+    so it suits windows of a few tens of energy units (n = 400 agrees with n = 1600 to ~4e-3 in
+    the bins of the configuration's N = 3 window, ~1e-3 in the paper model's).  A bin [E_a, E_b)
+    holds C(E_b) - C(E_a).
     """
     vc = 0.0 if rc is None else 4.0 * ((sigma / rc) ** 12 - (sigma / rc) ** 6)
     if not (r0 == 0.0 or r0 >= R):

@@ -130,3 +130,42 @@ def test_potts_q8_L4_golden_file(orc):
     r = orc.Run(orc.POTTS, 4, q, 1, 1)
     np.testing.assert_array_equal(r.reachable(), np.array(om) > 0)
 
+
+
+@pytest.mark.parametrize("model", [0, 1])
+def test_trimer_quadrature_matches_direct_sampling(model):
+    """The N = 3 quadrature (oracle/exact.py) against the definition sampled directly: 4e6 pairs of
+    bond vectors drawn uniformly in the bond ball (model 0) or shell (model 1), their energy
+    V_F(a) + V_F(b) + V_LJ(|a - b|) binned.  Every bin of the window within 4.5 standard
+    deviations of the quadrature's share of the bond-pair volume, chi^2 per bin below 1.5."""
+    K = 40.0
+    if model == 0:
+        R, r0, lo = 1.5, 0.0, 10.7
+        kw = dict(K=K, R=R, rc=2.5)
+    else:
+        R, r0, lo = 0.3, 0.7, -0.9
+        kw = dict(K=K, R=R, rc=None, r0=r0, sigma=2.0 ** (-1.0 / 6.0) * r0)
+    edges = [lo + 0.1 * k for k in range(81)]
+    r_in, r_out = max(r0 - R, 0.0), r0 + R
+    vol = 4.0 * np.pi / 3.0 * (r_out ** 3 - r_in ** 3)
+    rng = np.random.default_rng(5)
+    n = 4_000_000
+
+    def bonds():
+        r = (r_in ** 3 + rng.random(n) * (r_out ** 3 - r_in ** 3)) ** (1.0 / 3.0)
+        v = rng.normal(size=(n, 3))
+        return r, v * (r / np.linalg.norm(v, axis=1))[:, None]
+
+    ra, a = bonds()
+    rb, b = bonds()
+    vf = -(K * R * R / 2.0) * (np.log1p(-((ra - r0) / R) ** 2) + np.log1p(-((rb - r0) / R) ** 2))
+    s = np.linalg.norm(a - b, axis=1)
+    if model == 0:
+        vl = np.where(s < 2.5, 4.0 * (s ** -12 - s ** -6) - 4.0 * (2.5 ** -12 - 2.5 ** -6), 0.0)
+    else:
+        sg = 2.0 ** (-1.0 / 6.0) * r0
+        vl = 4.0 * ((sg / s) ** 12 - (sg / s) ** 6)
+    h, _ = np.histogram(vf + vl, bins=np.array(edges))
+    expect = np.array(ex.fene_lj_trimer_omega(edges, **kw)) / vol ** 2 * n
+    z = (h - expect) / np.sqrt(expect)
+    assert np.abs(z).max() < 4.5 and np.mean(z * z) < 1.5, (np.abs(z).max(), np.mean(z * z))
