@@ -66,6 +66,36 @@ def test_moves_are_exact_and_energy_tracks(orc):
     assert int(P.histogram().sum()) <= 8 * 200 * 13
 
 
+
+def test_walk_in_never_moves_away_and_records_inside_only(orc):
+    """Thermalisation reading: random-walk chains start far above the N = 13 pilot window; outside
+    it a move is accepted only if it does not increase the distance to the window, and only attempts
+    made inside count.  Sweep by sweep: no walker's distance grows, a walker inside stays inside,
+    and the iteration's histogram holds between N x (walkers inside at its start) and N x (walkers
+    inside at its end) counts.  All 16 chains are in within 200 sweeps."""
+    lo, hi, N, p = 33.3, 87.3, 13, 16
+    P = orc.PolyRun(N, p, 3, lo, hi)
+    P.init()
+
+    def dist():
+        E = P.energy()
+        return np.maximum(np.maximum(E - hi, lo - E), 0.0)
+
+    d = dist()
+    assert np.all(d > 200.0)
+    for _ in range(200):
+        P.iterate(1, 4)
+        P.update()
+        d2 = dist()
+        assert np.all(d2 <= d + 1e-9)
+        assert np.all(d2[d == 0.0] == 0.0)
+        n_in0, n_in1 = int((d == 0.0).sum()), int((d2 == 0.0).sum())
+        assert N * n_in0 <= int(P.histogram().sum()) <= N * n_in1
+        d = d2
+        if np.all(d == 0.0):
+            break
+    assert np.all(d == 0.0)
+
 def test_fene_dimer_density_of_states(orc):
     """N = 2: the energy is the FENE energy of the bond vector, uniform in the ball r < R, so the
     binned density of states is (4 pi/3)(r(E_b)^3 - r(E_a)^3) with r(E) = R sqrt(1 - exp(-2E/(K R^2)))."""
