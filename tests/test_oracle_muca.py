@@ -68,6 +68,24 @@ def test_first_sweep_accepts_everything(orc):
     np.testing.assert_array_equal(r.spins(), -s0)
 
 
+
+@pytest.mark.parametrize("q", [3, 8, 16])
+def test_first_potts_sweep_applies_a_uniform_proposal_at_every_site(orc, q):
+    """Potts proposal reading: with ln W = 0 every proposal is accepted, so after one sweep each
+    site has moved by (new - old) mod q = 1 + mulhi(u, q - 1), never 0 and uniform over the q - 1
+    other colours (chi^2 over 32768 sites below its 0.1 % point)."""
+    r = orc.Run(orc.POTTS, 8, q, 512, 7)
+    r.init()
+    s0 = r.spins().astype(np.int64)
+    r.iterate(1, NT)
+    d = (r.spins().astype(np.int64) - s0) % q
+    assert d.min() >= 1
+    counts = np.bincount(d.ravel(), minlength=q)[1:]
+    expect = d.size / (q - 1)
+    chi2 = float(((counts - expect) ** 2 / expect).sum())
+    chi2_999 = {1: 10.83, 6: 22.46, 14: 36.12}[q - 2]   # 0.1 % points, q - 2 degrees of freedom
+    assert chi2 < chi2_999, (q, chi2)
+
 @pytest.mark.parametrize("record", [0, 1])
 def test_histogram_totals(orc, record):
     r = orc.Run(0, 8, 2, 32, 4, record=record)
