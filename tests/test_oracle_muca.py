@@ -194,16 +194,24 @@ def test_plain_and_accumulated_updates_agree_on_the_first_update(orc):
     np.testing.assert_allclose(out[0], out[1], rtol=0, atol=1e-10)
 
 
-def test_plain_update_reaches_the_fixed_point_of_an_ideal_histogram(orc):
+@pytest.mark.parametrize("case", ["ising_L4", "potts_q8_L4"])
+def test_plain_update_reaches_the_fixed_point_of_an_ideal_histogram(orc, case):
     """If the histogram is exactly Omega(E) W(E) (ideal sampling), one plain update gives
     ln W = -ln Omega + const: the sign and the bookkeeping of the rule (exact Omega of the
-    4x4 Ising lattice by brute force)."""
-    r = orc.Run(0, 4, 2, 1, 1, recursion=1)
+    4x4 Ising lattice by brute force; of 4x4 q = 8 Potts from the golden file, whose unreachable
+    bins sit between reachable ones)."""
+    if case == "ising_L4":
+        r = orc.Run(0, 4, 2, 1, 1, recursion=1)
+        omega = orc.bruteforce_ising(4).astype(float)
+        scale = 1000.0
+    else:
+        r = orc.Run(orc.POTTS, 4, 8, 1, 1, recursion=1)
+        omega = _golden_omega("potts_q8_L4_omega.txt")
+        scale = 1.0
     r.init()
-    omega = orc.bruteforce_ising(4).astype(float)
     reach = r.reachable()
     H = np.zeros(r.B, dtype=np.uint64)
-    H[reach] = (omega[reach] * 1000).astype(np.uint64)  # W = 1 initially
+    H[reach] = (omega[reach] * scale).astype(np.uint64)  # W = 1 initially
     r.set_open_histogram(H)
     r.update()
     idx = np.nonzero(reach)[0]
