@@ -169,3 +169,31 @@ def test_trimer_quadrature_matches_direct_sampling(model):
     expect = np.array(ex.fene_lj_trimer_omega(edges, **kw)) / vol ** 2 * n
     z = (h - expect) / np.sqrt(expect)
     assert np.abs(z).max() < 4.5 and np.mean(z * z) < 1.5, (np.abs(z).max(), np.mean(z * z))
+
+
+def test_oracle_muca_reproduces_kaufman_thermodynamics_L16(orc):
+    """The whole oracle loop at 16x16 (beyond any enumeration here): 8 seeds of 64 walkers, 20
+    iterations of 2000 sweeps, then Eq. 2 at the golden file's betas (Kaufman's closed form).
+    <E>/N, C/N and ln Z (normalised at the ground state) each within 4 standard errors of the
+    8-seed mean, plus 1e-4 of the value."""
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "ising_L16_kaufman.txt")
+    gold = [[float(x) for x in l.split()] for l in open(path) if l.strip() and not l.startswith("#")]
+    N = 256
+    vals = []
+    for seed in range(1, 9):
+        r = orc.Run(0, 16, 2, 64, seed)
+        r.init()
+        for _ in range(20):
+            r.iterate(2000, 8)
+            r.update()
+        row = []
+        for beta, _, _, _ in gold:
+            out, _ = r.reweight(beta)
+            row.append((out[0] / N, out[2], out[3]))
+        vals.append(row)
+    v = np.array(vals)                     # seeds x betas x (E/N, C/N, lnZ)
+    mean = v.mean(axis=0)
+    err = v.std(axis=0, ddof=1) / np.sqrt(v.shape[0])
+    exact = np.array([[e, c, lz] for _, lz, e, c in gold])
+    assert np.all(np.abs(mean - exact) < 4.0 * err + 1e-4 * np.abs(exact)), np.max(np.abs(mean - exact) / err)
+
