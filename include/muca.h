@@ -61,7 +61,8 @@ const char *muca_last_error(void);
  * (Fig. 1: "initialized in p independent realizations with the same weight
  * function").  L_or_N is the lattice side L (spins) or the bead count N
  * (polymer); q is the number of Potts states (ignored otherwise).
- * Spins: L in {4, 8, 12, 16, 24, 32, 48, 64}; Potts 2 <= q <= 16, L <= 48.
+ * Spins: L in {4, 8, 12, 16, 24, 32, 48, 64}; Potts 2 <= q <= 16 (at L = 64
+ * the Potts threshold table is read from global memory, see "pipeline").
  * Polymer: 2 <= N <= 128 beads; the walkers start as random walks of unit
  * bonds and walk into the energy window before anything is recorded.
  * The walkers' initial states are drawn from the counter-based generator
@@ -134,6 +135,13 @@ int muca_init_ex(muca_ctx **out, int system, int L_or_N, int q, int p, uint64_t 
  *                 sets it at muca_init.  A limit too small for a healthy run
  *                 only makes the next synchronising call report
  *                 MUCA_ERR_TIMEOUT.  Any time.
+ *   "flush_every" lattice systems: at most this many sweeps between two flushes
+ *                 of a thread block's shared-memory uint32 histogram counters
+ *                 to its uint64 slot; 0 (default) = the largest count that
+ *                 cannot overflow a counter (floor((2^32 - 1) / (block * N)),
+ *                 or / block with "record" = 1).  Results do not depend on it;
+ *                 a small value makes short runs cross the flush between
+ *                 chunks of sweeps (tests).  Any time.
  *   "model"       polymer, before the first iterate: 0 (default) = the benchmark
  *                 parameters (FENE K = 40, R = 1.5, rest length 0; LJ sigma = 1 cut
  *                 at 2.5 and shifted), 1 = the paper's own parameters of Eq. (7)
@@ -235,8 +243,9 @@ int muca_get_observables(muca_ctx *ctx, double beta, double host_out[3], uint64_
  * {accepted moves of the last closed iteration, its tunnelling events,
  * accepted moves of all closed iterations, their tunnelling events, sweeps of
  * the last closed iteration, closed iterations}; acceptance rate = out[0] /
- * (p N out[4]).  A sharded context counts its own walkers.  Synchronises the
- * context's stream. */
+ * (p N out[4]).  A sharded context counts its own walkers.  Sweeps run by
+ * muca_iterate_noalloc count toward the next closed iteration like any other.
+ * Synchronises the context's stream. */
 int muca_get_metrics(muca_ctx *ctx, uint64_t host_out[6]);
 
 /* Checkpoint: the complete state (walkers, weights, recursion state, counters).
@@ -297,7 +306,14 @@ int muca_det_math(int fn, const double *host_in, double *host_out, int64_t n);
  * (like muca_iterate) and writes the merged histogram of exactly these sweeps to
  * the caller's DEVICE buffer dev_H_out (B uint64, overwritten; the context's own
  * open histogram and H are not touched, the weights are not updated).  Walkers,
- * bins and the sweep counter advance as with muca_iterate.
+ * bins and the sweep counter advance as with muca_iterate, and the sweeps run
+ * in the context's configured form ("pipeline", "block"), so they are as fast
+ * as muca_iterate's; a bounded hand-over wait that gives up shows as
+ * MUCA_ERR_TIMEOUT at the next synchronising call (muca_synchronize).  The
+ * accepted moves and tunnelling events of these sweeps are added to the
+ * context's open metrics counters (muca_get_metrics reports them with the next
+ * closed iteration, whose sweep count includes these sweeps); observables are
+ * not recorded.
  * Scratch: the per-block partial histograms live in one static device array of
  * 2^19 uint64 slots (4 MiB) that every GPU loading the library holds until the
  * process exits; a call needs ceil(p/block) * B slots and returns MUCA_ERR_RANGE

@@ -75,6 +75,7 @@ struct muca_ctx {
     int spin_limit = 0;       // tries of one bounded hand-over wait (0: the kernels' default)
     int debug_check = 0;      // checked build: every table bounds check of the next iterate fails
     int recursion = 0;        // weight update: 0 accumulated statistics, 1 plain W/H
+    int flush_cap = 0;        // spins: most sweeps between histogram flushes (0: the counters' own bound)
     int observables = 0;      // Ising: per-sweep sums of 1, |M|, M^2 per bin
     unsigned long long *obs = nullptr;  // [0, 3B): sums being filled, [3B, 6B): of the last update
     unsigned long long *metrics = nullptr;  // kMetricWords counters, see UpdateArgs::metrics
@@ -284,6 +285,7 @@ SpinSweepArgs sweep_args(const muca_ctx *c, int64_t sweeps, int block)
     const unsigned long long per_sweep = (unsigned long long)block * (c->record == 0 ? (unsigned)c->N : 1u);
     unsigned long long fe = 0xFFFFFFFFull / per_sweep;
     if (fe < 1) fe = 1;
+    if (c->flush_cap > 0 && fe > (unsigned long long)c->flush_cap) fe = (unsigned long long)c->flush_cap;
     if (fe > (unsigned long long)sweeps) fe = (unsigned long long)sweeps;
     a.flush_every = (int)(fe > 0x7fffffffull ? 0x7fffffffull : fe);
     fill_round_keys(a, c->seed);
@@ -709,6 +711,13 @@ int muca_set_param(muca_ctx *c, const char *key, double v)
         if ((double)lim != v || lim < 0 || lim > 0x7fffffffLL)
             return fail(MUCA_ERR_ARG, "spin_limit must be an integer in [0, 2^31)");
         c->spin_limit = (int)lim;
+        return MUCA_OK;
+    }
+    if (k == "flush_every") {
+        if (c->system == kPolymer) return fail(MUCA_ERR_ARG, "flush_every applies to lattice systems only");
+        const long long n = (long long)v;
+        if ((double)n != v || n < 0 || n > 0x7fffffffLL) return fail(MUCA_ERR_ARG, "flush_every must be an integer >= 0");
+        c->flush_cap = (int)n;
         return MUCA_OK;
     }
     if (k == "pipeline") {
@@ -1520,7 +1529,9 @@ extern "C" int muca_iterate_noalloc(muca_ctx *c, int64_t sweeps, uint64_t *dev_H
     MUCA_CUDA(cudaMemsetAsync(scratch, 0, need * sizeof(unsigned long long), c->stream));
     SpinSweepArgs a = sweep_args(c, sweeps, c->block);
     a.Hpart = scratch;
-    MUCA_CUDA(launch_spin_sweep(c->system, c->L, a, c->block, c->stream));
+    // the context's configured sweep form, as muca_iterate runs it: every form writes its block
+    // histograms to slots 0 .. ceil(p / block) - 1 of a.Hpart
+    MUCA_CUDA(launch_system_sweep(c, a, c->stream));
     MUCA_CUDA(launch_advance(c->state, sweeps, c->stream));
     UpdateArgs u = update_args(c);
     u.Hpart = scratch;

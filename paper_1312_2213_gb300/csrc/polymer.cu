@@ -3,11 +3,12 @@
 // K = 40, R = 1.5, Lennard-Jones 12-6 between beads |i-j| >= 2 with eps = sigma
 // = 1, cut at 2.5 and shifted; single-bead moves in a cube of side 0.3).
 //
-// One warp per walker.  The beads are visited in order; for bead i every lane
+// G lanes of a warp per walker (G = 8, 16 or 32; 32/G walkers share a warp).
+// The beads are visited in order; for bead i every lane of the walker's group
 // evaluates the old and the new pair energies with its partner beads
-// j = lane, lane + 32, ... in FP32 and keeps a compensated (Kahan) sum; the lane
+// j = lane, lane + G, ... in FP32 and keeps a compensated (Kahan) sum; the lane
 // sums are converted to 64-bit fixed point (2^-32 energy units) and added with
-// an exact integer warp reduction.  Nothing on the hot path uses FP64, whose
+// an exact integer reduction over the group.  Nothing on the hot path uses FP64, whose
 // rate on GB300 is a small fraction of FP32.
 //
 // Exactness: master coordinates are int64 on a 2^-44 grid and a move adds

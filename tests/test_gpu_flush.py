@@ -1,0 +1,113 @@
+"""The flush of the sweeps' shared-memory histogram counters between chunks of sweeps.
+
+A thread block counts its walkers' bins in uint32 shared-memory counters and adds them to its
+uint64 slot every ``flush_every`` sweeps, so no counter can overflow.  The automatic chunk
+(floor((2^32 - 1) / (block * N)) sweeps, 65535 at L = 32) is longer than any test run, so these
+tests cap it with the "flush_every" parameter: a 10-sweep iterate with flush_every = 3 crosses
+three flushes inside the launch before the final one, in every sweep form.  Histograms,
+lattices, bins, thresholds and ln W must stay bit-identical to the oracle, which has no
+chunks at all (the paper's merge is a plain sum of the walkers' histograms)."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_1312_2213_gb300 as m
+from gpu_util import compare_state
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+CASES = [(m.ISING2D, 16, 2, 0.0), (m.ISING2D_MUMA, 16, 2, 0.4407), (m.POTTS2D, 16, 8, 0.0)]
+
+
+@pytest.mark.parametrize("pipeline", [2, 1, 0])
+@pytest.mark.parametrize("record", [0, 1])
+@pytest.mark.parametrize("system,L,q,beta", CASES)
+def test_flush_between_chunks_bit_exact(system, L, q, beta, pipeline, record):
+    p, S = 100, 10
+    g = m.Muca(system, L, q, p, 13, beta=beta if system == m.ISING2D_MUMA else None, record=record)
+    g.set_param("pipeline", pipeline)
+    g.set_param("flush_every", 3)
+    o = oracle.Run(system, L, q, p, 13, beta=beta, record=record)
+    o.init()
+    for it in range(3):
+        g.iterate(S)
+        g.merge_and_update()
+        o.iterate(S, 8)
+        o.update()
+        compare_state(g, o, "after iteration %d (pipeline %d)" % (it, pipeline))
+
+
+@pytest.mark.parametrize("cap", [1, 2, 7])
+def test_flush_cap_does_not_change_results(cap):
+    """The chunk length is invisible: cap 1, 2, 7 and the automatic chunk give identical
+    histograms on the default (code) form with 64-walker blocks."""
+    runs = []
+    for c in (0, cap):
+        g = m.Muca(m.ISING2D, 32, 2, 130, 5)
+        g.set_param("flush_every", c)
+        g.iterate(9)
+        g.merge_and_update()
+        runs.append((g.histogram(), g.spins(), g.bins()))
+    for a, b in zip(*runs):
+        np.testing.assert_array_equal(a, b)
+
+
+def test_flush_in_potts_global_table_form():
+    """q-Potts at L = 64 (threshold table in global memory, histogram in shared memory)."""
+    p, S = 40, 5
+    g = m.Muca(m.POTTS2D, 64, 10, p, 3)
+    g.set_param("flush_every", 2)
+    o = oracle.Run(m.POTTS2D, 64, 10, p, 3)
+    o.init()
+    for it in range(2):
+        g.iterate(S)
+        g.merge_and_update()
+        o.iterate(S, 8)
+        o.update()
+        compare_state(g, o, "after iteration %d" % it)
+
+
+@pytest.mark.parametrize("form", [0, 1])
+@pytest.mark.parametrize("use_graph", [False, True])
+def test_flush_in_batches(form, use_graph):
+    """Both batch forms (the persistent tile launch and the systems' own kernels side by side),
+    plain and captured in a graph."""
+    spec = [(m.ISING2D, 16, 2, 70), (m.POTTS2D, 8, 10, 50), (m.ISING2D_MUMA, 12, 2, 40)]
+    gs, os_ = [], []
+    for k, (system, L, q, p) in enumerate(spec):
+        beta = 0.4407 if system == m.ISING2D_MUMA else 0.0
+        g = m.Muca(system, L, q, p, 40 + k, beta=beta if system == m.ISING2D_MUMA else None)
+        g.set_param("flush_every", 2)
+        gs.append(g)
+        o = oracle.Run(system, L, q, p, 40 + k, beta=beta)
+        o.init()
+        os_.append(o)
+    b = m.Batch(gs, form=form)
+    b.run(3, 5, use_graph=use_graph)
+    for g in gs:
+        g.synchronize()
+    for g, o in zip(gs, os_):
+        for _ in range(3):
+            o.iterate(5, 8)
+            o.update()
+        compare_state(g, o, "after a batch of 3 iterations (form %d)" % form)
+    b.close()
+
+
+def test_flush_every_argument_checks():
+    g = m.Muca(m.ISING2D, 8, 2, 32, 1)
+    for bad in (-1, 0.5):
+        with pytest.raises(m.MucaError):
+            g.set_param("flush_every", bad)
+    pol = m.Muca(m.POLYMER3D, 13, 0, 8, 1)
+    with pytest.raises(m.MucaError):
+        pol.set_param("flush_every", 2)

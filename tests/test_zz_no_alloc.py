@@ -21,11 +21,12 @@ def _gpu():
 
 
 @pytest.mark.parametrize("system,L,q,p", [(m.ISING2D, 32, 2, 1000), (m.POTTS2D, 16, 10, 300),
-                                          (m.ISING2D_MUMA, 16, 2, 257)])
+                                          (m.ISING2D_MUMA, 16, 2, 257), (m.POTTS2D, 64, 8, 40)])
 def test_noalloc_matches_allocating_path_on_two_calls(system, L, q, p):
+    """Also q-Potts at L = 64, whose sweep reads its threshold table from global memory."""
     import torch
 
-    S = 150
+    S = 150 if L < 64 else 4
     beta = 0.4407 if system == m.ISING2D_MUMA else None
     ref1 = m.Muca(system, L, q, p, 77, beta=beta)   # one iterate, then merge
     ref2 = m.Muca(system, L, q, p, 77, beta=beta)   # two iterates, then one merge
@@ -52,6 +53,31 @@ def test_noalloc_matches_allocating_path_on_two_calls(system, L, q, p):
     np.testing.assert_array_equal(nal.bins(), ref2.bins())
     assert nal.sweep_counter() == 2 * S
     assert int(h2.sum()) == p * S * L * L
+    # the no-alloc sweeps count toward the next closed iteration's metrics, like any sweeps
+    nal.merge_and_update()
+    mn, mr = nal.metrics(), ref2.metrics()
+    assert mn["sweeps"] == mr["sweeps"] == 2 * S
+    assert mn["accepted"] == mr["accepted"] > 0
+    assert mn["tunnelling_events"] == mr["tunnelling_events"]
+
+
+def test_noalloc_records_no_observables():
+    """Observable sums are recorded by muca_iterate only: an iteration made of no-alloc sweeps
+    closes with empty sums."""
+    import torch
+
+    g = m.Muca(m.ISING2D, 16, 2, 64, 9)
+    g.set_param("observables", 1)
+    g.iterate(20)
+    g.merge_and_update()
+    _, sums = g.observables(0.4)
+    assert int(sums[:, 0].sum()) == 64 * 20
+    dH = torch.zeros(g.B, dtype=torch.int64, device="cuda")
+    m.muca_iterate_noalloc(g.h, 20, dH.data_ptr())
+    g.merge_and_update()
+    _, sums = g.observables(0.4)
+    assert int(sums.sum()) == 0
+    assert int(dH.sum()) == 64 * 20 * 256
 
 
 def test_noalloc_rejects_sizes_beyond_the_static_array():
