@@ -120,6 +120,21 @@ def _bind_polymer(L):
     L.orc_poly_energy.restype = c.c_double
     L.orc_poly_pair.argtypes = [c.c_double, c.c_int, c.c_int]
     L.orc_poly_pair.restype = c.c_double
+    L.orc_poly_get_first_events.argtypes = [c.c_void_p, c.c_void_p]
+    L.orc_poly_get_delta.argtypes = [c.c_void_p, c.c_void_p]
+    L.orc_poly_get_drift.argtypes = [c.c_void_p]
+    L.orc_poly_get_drift.restype = c.c_double
+    L.orc_poly_set_trace.argtypes = [c.c_void_p, c.c_void_p]
+    L.orc_poly_set_tau.argtypes = [c.c_void_p, c.c_double]
+    L.orc_poly_set_perturbation.argtypes = [c.c_void_p, c.c_double, c.c_uint64]
+    L.orc_poly_set_lnW.argtypes = [c.c_void_p, c.c_void_p]
+    L.orc_poly_pair_scale.argtypes = [c.c_double, c.c_int, c.c_int]
+    L.orc_poly_pair_scale.restype = c.c_double
+
+
+# One record of the oracle's polymer trace (orc_poly_trace_rec).
+POLY_TRACE_DTYPE = np.dtype([("dE", "<f8"), ("scale", "<f8"), ("E", "<f8"), ("delta", "<f8"), ("bin_new", "<i4"),
+                             ("bin_after", "<i4"), ("flags", "<i4"), ("pad", "<i4")])
 
 
 def _ptr(a: np.ndarray):
@@ -350,6 +365,38 @@ class PolyRun:
     def refresh_energy(self) -> float:
         return self._lib.orc_poly_refresh_energy(self.h)
 
+    def drift(self) -> float:
+        """Largest change of a running energy at the refresh after a call, since init."""
+        return self._lib.orc_poly_get_drift(self.h)
+
+    def first_events(self) -> np.ndarray:
+        """Per walker, the attempt index (sweep * N + bead) of the first event of the last call,
+        N * sweeps if only its closing refresh was one, -1 if none."""
+        return self._get("orc_poly_get_first_events", self.p, np.int64)
+
+    def delta(self) -> np.ndarray:
+        """Per walker, the bound on the energy difference of an FP32 implementation."""
+        return self._get("orc_poly_get_delta", self.p, np.float64)
+
+    def set_perturbation(self, perturb: float, seed: int = 99):
+        """Plant an error of up to perturb * sigma in every pair term (tests of the event rule)."""
+        self._lib.orc_poly_set_perturbation(self.h, perturb, seed)
+
+    def set_lnW(self, lnW):
+        lnW = np.ascontiguousarray(lnW, dtype=np.float64)
+        assert lnW.shape == (self.B,)
+        self._lib.orc_poly_set_lnW(self.h, _ptr(lnW))
+
+    def iterate_traced(self, sweeps: int, nthreads: int = 1) -> np.ndarray:
+        """Run `sweeps` sweeps and return the record of every attempt, shape (p, sweeps, N)."""
+        t = np.zeros(self.p * sweeps * self.N, dtype=POLY_TRACE_DTYPE)
+        self._lib.orc_poly_set_trace(self.h, t.ctypes.data_as(ctypes.c_void_p))
+        try:
+            self.iterate(sweeps, nthreads)
+        finally:
+            self._lib.orc_poly_set_trace(self.h, None)
+        return t.reshape(self.p, sweeps, self.N)
+
     def _get(self, name, n, dtype):
         a = np.zeros(n, dtype=dtype)
         getattr(self._lib, name)(self.h, _ptr(a))
@@ -396,3 +443,8 @@ def poly_energy(X: np.ndarray, model: int = 0) -> float:
 
 def poly_pair(r: float, sep: int, model: int = 0) -> float:
     return lib().orc_poly_pair(float(r), int(sep), int(model))
+
+
+def poly_pair_scale(r: float, sep: int, model: int = 0) -> float:
+    """First-order error scale |v(r)| + |r v'(r)| of a pair term."""
+    return lib().orc_poly_pair_scale(float(r), int(sep), int(model))

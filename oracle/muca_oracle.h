@@ -118,6 +118,22 @@ void orc_poly_reweight(void *h, double beta, double out[4], double *lnP /* nulla
 void orc_poly_get_walker_events(void *h, int64_t *out /* p*2 */);
 void orc_poly_get_metrics(void *h, uint64_t out[5]); /* as orc_get_metrics; ends: bins 0 and B-1 */
 double orc_poly_energy(int N, const double *X, int model); /* model 0 benchmark, 1 paper */
+/* One attempt of the polymer trace: energy change (NaN if a bond broke or a
+ * rotation found no point), its error scale S, the energy after the decision
+ * and the bound delta after it, bins of the proposed and of the kept energy,
+ * flags (1 accepted, 2 broken, 4 event, 8 started inside the window). */
+typedef struct {
+    double dE, scale, E, delta;
+    int32_t bin_new, bin_after, flags, pad;
+} orc_poly_trace_rec;
+void orc_poly_get_first_events(void *h, int64_t *out /* p */);
+double orc_poly_get_drift(void *h);
+void orc_poly_get_delta(void *h, double *out /* p */);
+void orc_poly_set_trace(void *h, orc_poly_trace_rec *buf);
+void orc_poly_set_tau(void *h, double tau);
+void orc_poly_set_perturbation(void *h, double perturb, uint64_t seed); /* tests of the event rule */
+void orc_poly_set_lnW(void *h, const double *lnW);
+double orc_poly_pair_scale(double r, int sep, int model);
 double orc_poly_pair(double r, int sep, int model);
 
 #ifdef __cplusplus

@@ -44,6 +44,35 @@
  * words of blocks (64 i + t, sweep, walker, tag 4), two pairs a block, at most
  * 64 pairs (none accepted: the move is rejected).  Every step is a correctly
  * rounded binary64 operation, and the offset is rounded to the grid.
+ *
+ * Energy refresh: after each call that runs sweeps, every walker's energy is
+ * recomputed from scratch (the largest change is kept as the drift), so a
+ * running sum carries its rounding only within one call.
+ *
+ * Events (trajectory parity with an implementation whose pair terms are FP32):
+ * the oracle's decisions are exact functions of binary64 energies, so an
+ * implementation that evaluates the pair terms in lower precision can decide
+ * differently only where a decision is within its error of a boundary.  Its
+ * error is bounded per pair term by tau * sigma(r), with the first-order error
+ * scale sigma(r) = |v(r)| + |r v'(r)| (rounding of the value plus the error of
+ * the separation carried through the potential), tau = 1e-6 by default (the
+ * tolerance of the energy change, relative to the size of its terms).  Per
+ * walker the oracle keeps delta, a bound on |E_impl - E|: tau * sum over all
+ * pairs of sigma at the start and after each refresh, plus tau * S + rho for
+ * every accepted move (S = sum of sigma over the move's old and new pair
+ * terms, rho = 32 * 2^-32 for the rounding of a fixed-point energy change
+ * summed over at most 32 lanes).  An attempt is an event when
+ *   - its acceptance test is a near tie, |u_3 2^-32 - p_acc| < 1e-6;
+ *   - its new energy lies within delta + tau * S + rho of a bin edge of the
+ *     window (edges 0 .. B), so the new bin may differ;
+ *   - outside the window, the two distances to the window differ by less than
+ *     2 delta + tau * S + rho (the walk-in decision may differ);
+ *   - a bond of the move is within 1e-5 (relative) of breaking, or the move's
+ *     terms are so large (S > 2^21) that a lower-precision sum may overflow;
+ * and the refresh at the end of a call is an event when the refreshed energy
+ * lies within the new delta of a bin edge.  The oracle records each walker's
+ * first event of a call (attempt index sweep * N + bead, N * sweeps for the
+ * refresh) and, on request, a trace of every attempt.
  */
 #include <math.h>
 #include <pthread.h>
@@ -83,7 +112,23 @@ typedef struct {
     uint8_t *tun;
     uint64_t m_last[2], m_total[2];
     int64_t sweeps_last, sweep_at_update;
+    /* events: tolerance per unit of error scale, per-walker energy bounds, first event of the
+     * last call, largest refresh change; optional per-attempt trace of the next call */
+    double tau;
+    double *delta;
+    int64_t *first;
+    double *drift;
+    orc_poly_trace_rec *trace;
+    /* planted error for the tests of the event rule: every pair term of a move and
+     * of a from-scratch energy is changed by perturb * sigma * xi, xi in [-1, 1)
+     * from a Philox word (tag 7, key perturb_seed); 0 = off */
+    double perturb;
+    uint64_t perturb_seed;
 } orc_poly;
+
+#define POLY_TAG_PERTURB 7u
+
+#define POLY_RHO (32.0 * 0x1p-32)
 
 static double poly_lj(double r2)
 {
@@ -141,6 +186,65 @@ static double poly_dist2(const double *a, const double *b)
     return dx * dx + dy * dy + dz * dz;
 }
 
+/* First-order error scale sigma(r) = |v(r)| + |r v'(r)| of a pair term at squared
+ * distance r2 (0 for an LJ pair beyond the cutoff, +inf for a broken bond). */
+static double poly_pair_scale(const orc_poly *P, double r2, int sep)
+{
+    if (sep == 1) {
+        const double c = 0.5 * P->K * P->R * P->R;
+        if (P->model == 1) {
+            const double r = sqrt(r2), y = (r - P->r0) / P->R, g = 1.0 - y * y;
+            if (!(g > 0.0)) return INFINITY;
+            return c * (fabs(log(g)) + 2.0 * fabs(y) * r / (P->R * g));
+        }
+        const double x = r2 / (P->R * P->R), g = 1.0 - x;
+        if (!(g > 0.0)) return INFINITY;
+        return c * (fabs(log(g)) + 2.0 * x / g);
+    }
+    if (P->model == 1) {
+        const double s2 = P->sigma2 / r2, s6 = s2 * s2 * s2;
+        return 4.0 * (13.0 * s6 * s6 + 7.0 * s6);
+    }
+    if (r2 >= POLY_RC * POLY_RC) return 0.0;
+    const double i2 = 1.0 / r2, i6 = i2 * i2 * i2;
+    const double irc2 = 1.0 / (POLY_RC * POLY_RC), irc6 = irc2 * irc2 * irc2;
+    return 4.0 * (13.0 * i6 * i6 + 7.0 * i6) + 4.0 * fabs(irc6 * irc6 - irc6);
+}
+
+/* Planted error of a pair term (tests of the event rule only): perturb * sigma * xi with
+ * xi = u 2^-31 - 1 from the Philox word of counter (c0, c1, c2, tag 7). */
+static double poly_perturbation(const orc_poly *P, double sigma, uint32_t c0, uint32_t c1, uint32_t c2)
+{
+    if (P->perturb == 0.0 || !(sigma < INFINITY)) return 0.0;
+    uint32_t key[2] = {(uint32_t)(P->perturb_seed & 0xffffffffu), (uint32_t)(P->perturb_seed >> 32)};
+    uint32_t ctr[4] = {c0, c1, c2, POLY_TAG_PERTURB}, u[4];
+    orc_philox4x32_10(ctr, key, u);
+    return P->perturb * sigma * ((double)u[0] * 0x1p-31 - 1.0);
+}
+
+/* Sum of sigma over all pairs of a configuration. */
+static double poly_scale_all(const orc_poly *P, const double *X)
+{
+    double S = 0.0;
+    for (int i = 0; i < P->N; ++i)
+        for (int j = i + 1; j < P->N; ++j) S += poly_pair_scale(P, poly_dist2(X + 3 * i, X + 3 * j), j - i);
+    return S;
+}
+
+/* Is E within m of a bin edge of the window (e_lo + k / 10, k = 0 .. B)? */
+static int poly_near_edge(const orc_poly *P, double E, double m)
+{
+    const double t = (E - P->e_lo) * 10.0, k = nearbyint(t);
+    return k >= 0.0 && k <= (double)P->B && fabs(t - k) < 10.0 * m;
+}
+
+/* A bond of squared length r2 within 1e-5 (relative) of breaking. */
+static int poly_bond_near_break(const orc_poly *P, double r2)
+{
+    if (P->model == 1) return fabs(fabs(sqrt(r2) - P->r0) / P->R - 1.0) < 1e-5;
+    return fabs(r2 / (P->R * P->R) - 1.0) < 1e-5;
+}
+
 /* Energy of one configuration from scratch, pairs i < j in order. */
 double orc_poly_energy(int N, const double *X, int model)
 {
@@ -155,6 +259,21 @@ static double poly_energy_P(const orc_poly *P, const double *X)
     double E = 0.0;
     for (int i = 0; i < P->N; ++i)
         for (int j = i + 1; j < P->N; ++j) E += poly_pair2(P, poly_dist2(X + 3 * i, X + 3 * j), j - i);
+    return E;
+}
+
+/* The same with the planted error of the tests of the event rule (tag word 2^31 + pair index,
+ * sweep counter g, walker w). */
+static double poly_energy_perturbed(const orc_poly *P, const double *X, uint32_t g, int w)
+{
+    double E = poly_energy_P(P, X);
+    if (P->perturb == 0.0) return E;
+    for (int i = 0; i < P->N; ++i)
+        for (int j = i + 1; j < P->N; ++j) {
+            const double r2 = poly_dist2(X + 3 * i, X + 3 * j);
+            E += poly_perturbation(P, poly_pair_scale(P, r2, j - i), 0x80000000u + (uint32_t)(i * P->N + j), g,
+                                   (uint32_t)w);
+        }
     return E;
 }
 
@@ -194,6 +313,11 @@ void *orc_poly_create(int N, int p, uint64_t seed, double e_lo, double e_hi, dou
     P->acc_w = (uint64_t *)calloc((size_t)p, sizeof(uint64_t));
     P->ev_w = (uint64_t *)calloc((size_t)p, sizeof(uint64_t));
     P->tun = (uint8_t *)calloc((size_t)p, 1);
+    P->tau = 1e-6;
+    P->delta = (double *)calloc((size_t)p, sizeof(double));
+    P->first = (int64_t *)calloc((size_t)p, sizeof(int64_t));
+    P->drift = (double *)calloc((size_t)p, sizeof(double));
+    for (int w = 0; w < p; ++w) P->first[w] = -1;
     return P;
 }
 
@@ -204,6 +328,7 @@ void orc_poly_free(void *h)
     free(P->X); free(P->E); free(P->lnW); free(P->lnW_sampled); free(P->G); free(P->lnR);
     free(P->H_open); free(P->H_last); free(P->events);
     free(P->acc_w); free(P->ev_w); free(P->tun);
+    free(P->delta); free(P->first); free(P->drift);
     free(P);
 }
 
@@ -296,7 +421,10 @@ void orc_poly_init(void *h)
             }
             for (int a = 0; a < 3; ++a) X[3 * k + a] = cand[a];
         }
-        P->E[w] = poly_energy_P(P, X);
+        P->E[w] = poly_energy_perturbed(P, X, 0u, w);
+        P->delta[w] = P->tau * poly_scale_all(P, X) + POLY_RHO;
+        P->first[w] = -1;
+        P->drift[w] = 0.0;
     }
     for (int b = 0; b < P->B; ++b) {
         P->lnW[b] = P->lnW_sampled[b] = P->G[b] = P->lnR[b] = 0.0;
@@ -324,6 +452,8 @@ static void poly_walker_sweeps(orc_poly *P, int w, int64_t g0, int64_t sweeps, u
     double *X = P->X + (size_t)w * N * 3;
     double E = P->E[w];
     int64_t *ev = P->events + 2 * (size_t)w;
+    const int muca = P->beta <= 0.0;
+    int64_t first = -1; /* first event of this call (attempt index) */
     uint32_t key[2] = {(uint32_t)(P->seed & 0xffffffffu), (uint32_t)(P->seed >> 32)};
     for (int64_t sw = 0; sw < sweeps; ++sw) {
         uint32_t g = (uint32_t)(g0 + sw);
@@ -331,7 +461,7 @@ static void poly_walker_sweeps(orc_poly *P, int w, int64_t g0, int64_t sweeps, u
             uint32_t ctr[4] = {(uint32_t)i, g, (uint32_t)w, POLY_TAG_SWEEP}, u[4];
             orc_philox4x32_10(ctr, key, u);
             double xn[3] = {X[3 * i], X[3 * i + 1], X[3 * i + 2]};
-            int rotation = 0, broken = 0;
+            int rotation = 0, broken = 0, event = 0;
             if (P->moves == 1) {
                 uint32_t mc[4] = {(uint32_t)i, g, (uint32_t)w, POLY_TAG_MOVE}, mw[4];
                 orc_philox4x32_10(mc, key, mw);
@@ -341,24 +471,42 @@ static void poly_walker_sweeps(orc_poly *P, int w, int64_t g0, int64_t sweeps, u
             if (!rotation)
                 for (int a = 0; a < 3; ++a)
                     xn[a] = X[3 * i + a] + (double)((int64_t)u[a] - 2147483648LL) * POLY_STEP_Q * POLY_GRID;
-            double dE = 0.0;
+            /* energy change and its error scale S (old and new pair terms) */
+            double dE = 0.0, S = 0.0;
             for (int j = 0; j < N; ++j) {
                 if (j == i) continue;
                 int sep = abs(i - j);
-                double vn = poly_pair2(P, poly_dist2(xn, X + 3 * j), sep);
-                double vo = poly_pair2(P, poly_dist2(X + 3 * i, X + 3 * j), sep);
+                double r2n = poly_dist2(xn, X + 3 * j), r2o = poly_dist2(X + 3 * i, X + 3 * j);
+                double vn = poly_pair2(P, r2n, sep);
+                double vo = poly_pair2(P, r2o, sep);
                 if (isinf(vn)) broken = 1;
+                if (sep == 1 && poly_bond_near_break(P, r2n)) event = 1;
+                const double so = poly_pair_scale(P, r2o, sep), sn = isinf(vn) ? 0.0 : poly_pair_scale(P, r2n, sep);
+                S += so + sn;
+                if (P->perturb != 0.0 && !isinf(vn)) {
+                    const uint32_t pj = (uint32_t)(2 * (i * N + j));
+                    vo += poly_perturbation(P, so, pj, g, (uint32_t)w);
+                    vn += poly_perturbation(P, sn, pj + 1u, g, (uint32_t)w);
+                }
                 dE += vn - vo;
             }
             int accept = 0;
             double En = E + dE;
+            const int b = muca ? poly_bin(P, E) : 0, inside = muca && b >= 0 && b < P->B;
+            const double m = P->delta[w] + P->tau * S + POLY_RHO;
+            if (muca && !broken && S > 0x1p21) event = 1;
             if (!broken) {
-                if (P->beta > 0.0) {
+                if (!muca) {
                     double d = -P->beta * dE;
                     accept = d >= 0.0 || (double)u[3] < floor(ldexp(orc_det_exp(d), 32));
                 } else {
-                    int b = poly_bin(P, E), bn = poly_bin(P, En);
-                    if (b >= 0 && b < P->B) {
+                    int bn = poly_bin(P, En);
+                    if (poly_near_edge(P, En, m)) {
+                        /* the new energy is within the implementation's error of a bin edge */
+                        event = 1;
+                        ev[1] += 1;
+                    }
+                    if (inside) {
                         if (bn >= 0 && bn < P->B) {
                             double d = P->lnW[bn] - P->lnW[b];
                             if (d >= 0.0) {
@@ -366,38 +514,52 @@ static void poly_walker_sweeps(orc_poly *P, int w, int64_t g0, int64_t sweeps, u
                             } else {
                                 double pa = orc_det_exp(d);
                                 accept = (double)u[3] < floor(ldexp(pa, 32));
-                                if (fabs((double)u[3] * 0x1p-32 - pa) < 1e-6) ev[0] += 1;
+                                if (fabs((double)u[3] * 0x1p-32 - pa) < 1e-6) {
+                                    event = 1;
+                                    ev[0] += 1;
+                                }
                             }
-                            /* a bin edge within 1e-4 of the new energy: an FP32 implementation of
-                             * the pair terms may bin this state differently */
-                            double edge = (En - P->e_lo) * 10.0;
-                            if (fabs(edge - nearbyint(edge)) < 1e-3) ev[1] += 1;
                         }
                     } else {
-                        accept = poly_window_dist(P, En) <= poly_window_dist(P, E);
+                        double dn = poly_window_dist(P, En), dd = poly_window_dist(P, E);
+                        accept = dn <= dd;
+                        if (fabs(dn - dd) < P->delta[w] + m) event = 1;
                     }
                 }
             }
+            if (event && first < 0) first = sw * N + i;
             if (accept) {
                 for (int a = 0; a < 3; ++a) X[3 * i + a] = xn[a];
                 E = En;
                 P->acc_w[w] += 1;
+                if (muca) P->delta[w] += P->tau * S + POLY_RHO;
             }
-            if (P->record == 0 && P->beta <= 0.0) {
-                int b = poly_bin(P, E);
-                if (b >= 0 && b < P->B) hist[b] += 1;
+            if (P->trace) {
+                orc_poly_trace_rec *t = P->trace + ((size_t)w * (size_t)sweeps + (size_t)sw) * (size_t)N + i;
+                t->dE = broken ? NAN : dE;
+                t->scale = S;
+                t->E = E;
+                t->delta = P->delta[w];
+                t->bin_new = muca ? poly_bin(P, En) : 0;
+                t->bin_after = muca ? poly_bin(P, E) : 0;
+                t->flags = (accept ? 1 : 0) | (broken ? 2 : 0) | (event ? 4 : 0) | (inside ? 8 : 0);
+                t->pad = 0;
+            }
+            if (P->record == 0 && muca) {
+                int bb = poly_bin(P, E);
+                if (bb >= 0 && bb < P->B) hist[bb] += 1;
             }
         }
-        if (P->record == 1 && P->beta <= 0.0) {
-            int b = poly_bin(P, E);
-            if (b >= 0 && b < P->B) hist[b] += 1;
+        if (P->record == 1 && muca) {
+            int bb = poly_bin(P, E);
+            if (bb >= 0 && bb < P->B) hist[bb] += 1;
         }
         {
-            const int b = poly_bin(P, E);
-            if (b == 0) {
+            const int bb = poly_bin(P, E);
+            if (bb == 0) {
                 if (P->tun[w] == 2) P->ev_w[w] += 1;
                 P->tun[w] = 1;
-            } else if (b == P->B - 1) {
+            } else if (bb == P->B - 1) {
                 if (P->tun[w] == 1) P->ev_w[w] += 1;
                 P->tun[w] = 2;
             }
@@ -407,7 +569,16 @@ static void poly_walker_sweeps(orc_poly *P, int w, int64_t g0, int64_t sweeps, u
     double c[3] = {X[0], X[1], X[2]};
     for (int j = 0; j < N; ++j)
         for (int a = 0; a < 3; ++a) X[3 * j + a] -= c[a];
+    /* refresh the running energy from scratch; the new bound is that of a from-scratch sum */
+    if (sweeps > 0) {
+        const double e = poly_energy_perturbed(P, X, (uint32_t)(g0 + sweeps), w);
+        if (fabs(e - E) > P->drift[w]) P->drift[w] = fabs(e - E);
+        E = e;
+        P->delta[w] = P->tau * poly_scale_all(P, X) + POLY_RHO;
+        if (muca && first < 0 && poly_near_edge(P, E, P->delta[w])) first = sweeps * N;
+    }
     P->E[w] = E;
+    P->first[w] = first;
 }
 
 typedef struct {
@@ -604,4 +775,67 @@ void orc_poly_get_walker_events(void *h, int64_t *out)
 {
     orc_poly *P = (orc_poly *)h;
     memcpy(out, P->events, sizeof(int64_t) * 2 * (size_t)P->p);
+}
+
+/* First event of each walker in the last call that ran sweeps (attempt index
+ * sweep * N + bead within the call, sweeps * N for the refresh, -1 none). */
+void orc_poly_get_first_events(void *h, int64_t *out)
+{
+    orc_poly *P = (orc_poly *)h;
+    memcpy(out, P->first, sizeof(int64_t) * (size_t)P->p);
+}
+
+/* Largest change of a running energy at a refresh since init. */
+double orc_poly_get_drift(void *h)
+{
+    orc_poly *P = (orc_poly *)h;
+    double d = 0.0;
+    for (int w = 0; w < P->p; ++w)
+        if (P->drift[w] > d) d = P->drift[w];
+    return d;
+}
+
+/* Per-walker energy bounds delta (see the header). */
+void orc_poly_get_delta(void *h, double *out)
+{
+    orc_poly *P = (orc_poly *)h;
+    memcpy(out, P->delta, sizeof(double) * (size_t)P->p);
+}
+
+/* Trace of every attempt of the next calls (p * sweeps * N records, walker-major,
+ * then sweep, then bead), or NULL to stop tracing. */
+void orc_poly_set_trace(void *h, orc_poly_trace_rec *buf) { ((orc_poly *)h)->trace = buf; }
+
+/* Tolerance of the pair terms per unit of error scale (default 1e-6); before init. */
+void orc_poly_set_tau(void *h, double tau) { ((orc_poly *)h)->tau = tau; }
+
+/* Planted error of the pair terms (tests of the event rule only), see orc_poly. */
+void orc_poly_set_perturbation(void *h, double perturb, uint64_t seed)
+{
+    orc_poly *P = (orc_poly *)h;
+    P->perturb = perturb;
+    P->perturb_seed = seed;
+}
+
+/* Replace ln W (B doubles), e.g. to give two runs the same weights. */
+void orc_poly_set_lnW(void *h, const double *lnW)
+{
+    orc_poly *P = (orc_poly *)h;
+    memcpy(P->lnW, lnW, sizeof(double) * (size_t)P->B);
+}
+
+/* First-order error scale sigma(r) = |v| + |r v'| of a pair term (see the header). */
+double orc_poly_pair_scale(double r, int sep, int model)
+{
+    orc_poly P;
+    memset(&P, 0, sizeof P);
+    P.K = 40.0;
+    P.R = 1.5;
+    P.model = model;
+    if (model == 1) {
+        P.R = POLY_PAPER_R;
+        P.r0 = POLY_PAPER_R0;
+        P.sigma2 = poly_paper_sigma2();
+    }
+    return poly_pair_scale(&P, r * r, sep);
 }
