@@ -200,6 +200,35 @@ int muca_merge_and_update(muca_ctx *ctx, int *is_flat);
 int muca_merge_open(muca_ctx *ctx, uint64_t *dev_H_out);
 int muca_update_with(muca_ctx *ctx, const uint64_t *dev_H, int *is_flat);
 
+/* Replace the current weights ln W^(n) with host_lnW (B doubles; unreachable
+ * bins are set to -inf whatever the buffer holds; reachable bins must be
+ * finite) and rebuild what the sweeps read from them (thresholds, or the
+ * polymer's fixed-point table).  Use: a production run at fixed weights, e.g.
+ * converged weights of an earlier run (the paper's last step: simulate with the
+ * final W and reweight, Eq. 2).  The accumulated statistics of the recursion
+ * are not touched, so the next muca_merge_and_update computes W^(n+1) from
+ * them as before; the histogram it merges is reweighted with the weights set
+ * here.  Synchronous.  Errors: MUCA_ERR_ARG on a wrong length or a non-finite
+ * reachable bin. */
+int muca_set_lnW(muca_ctx *ctx, const double *host_lnW, int nbins);
+
+/* Polymer parity inspection (no counterpart in the paper): the next
+ * muca_iterate of this context writes one 32-byte record per attempt of every
+ * walker into the caller's DEVICE buffer dev_records (16-byte aligned; index
+ * (walker * sweeps + sweep) * N + bead, sweep counted within that call):
+ *   int64 dq     energy change of the attempt in units of 2^-32 (0 if a lane
+ *                sum was too large),
+ *   int64 E      the walker's energy after the decision (2^-32 units),
+ *   int32 bn     bin of the proposed energy (-1 below, B above the window),
+ *   int32 b      bin after the decision,
+ *   int32 flags  1 accepted, 2 a bond broke (or a rotation found no point),
+ *                4 a lane sum too large (move rejected),
+ *   int32 pad.
+ * n_records is the buffer's capacity; that iterate returns MUCA_ERR_ARG if it
+ * makes more than n_records attempts.  Only that one iterate records.  Errors:
+ * MUCA_ERR_ARG for a spin context, a NULL or misaligned buffer. */
+int muca_poly_trace(muca_ctx *ctx, void *dev_records, int64_t n_records);
+
 /* Number of histogram bins B of the context. */
 int muca_num_bins(const muca_ctx *ctx, int *nbins);
 

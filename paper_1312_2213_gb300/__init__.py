@@ -25,7 +25,7 @@ __all__ = ["Muca", "MucaError", "ISING2D", "POTTS2D", "ISING2D_MUMA", "POLYMER3D
            "muca_get_state", "muca_set_state",
            "muca_get_spins", "muca_get_walker_bins", "muca_get_thresholds", "muca_get_sweep_counter",
            "muca_synchronize", "muca_free", "muca_last_error", "muca_det_math",
-           "muca_iterate_noalloc", "muca_get_coords", "muca_get_drift", "muca_batch_create", "muca_batch_run", "muca_batch_free", "muca_batch_set_form", "Batch"]
+           "muca_iterate_noalloc", "muca_set_lnW", "muca_poly_trace", "POLY_TRACE_DTYPE", "muca_get_coords", "muca_get_drift", "muca_batch_create", "muca_batch_run", "muca_batch_free", "muca_batch_set_form", "Batch"]
 
 
 def _p(a: np.ndarray):
@@ -81,6 +81,20 @@ def muca_num_bins(h) -> int:
     n = ctypes.c_int()
     check(load().muca_num_bins(h, ctypes.byref(n)), "muca_num_bins")
     return n.value
+
+
+def muca_set_lnW(h, lnW: np.ndarray):
+    lnW = np.ascontiguousarray(lnW, dtype=np.float64)
+    check(load().muca_set_lnW(h, _p(lnW), lnW.size), "muca_set_lnW")
+
+
+def muca_poly_trace(h, dev_ptr: int, n_records: int):
+    check(load().muca_poly_trace(h, ctypes.c_void_p(dev_ptr), int(n_records)), "muca_poly_trace")
+
+
+# One record of muca_poly_trace (32 bytes).
+POLY_TRACE_DTYPE = np.dtype([("dq", "<i8"), ("E", "<i8"), ("bn", "<i4"), ("b", "<i4"), ("flags", "<i4"),
+                             ("pad", "<i4")])
 
 
 def muca_get_lnW(h, out: np.ndarray):
@@ -297,6 +311,21 @@ class Muca:
 
     def merge_and_update(self, want_flat: bool = False):
         return muca_merge_and_update(self.h, want_flat)
+
+    def set_lnW(self, lnW: np.ndarray):
+        muca_set_lnW(self.h, lnW)
+
+    def iterate_traced(self, sweeps: int) -> np.ndarray:
+        """Polymer: run `sweeps` sweeps and return the record of every attempt, shape
+        (p, sweeps, N), dtype POLY_TRACE_DTYPE (muca_poly_trace)."""
+        import torch
+
+        n = self.p * sweeps * self.N
+        buf = torch.empty(n * POLY_TRACE_DTYPE.itemsize, dtype=torch.uint8, device="cuda")
+        muca_poly_trace(self.h, buf.data_ptr(), n)
+        muca_iterate(self.h, sweeps)
+        muca_synchronize(self.h)
+        return buf.cpu().numpy().view(POLY_TRACE_DTYPE).reshape(self.p, sweeps, self.N)
 
     def lnW(self) -> np.ndarray:
         a = np.zeros(self.B, dtype=np.float64)

@@ -27,6 +27,8 @@ PROTOTYPES = {
     "muca_iterate": (c_int, [c_vp, c_i64]),
     "muca_merge_and_update": (c_int, [c_vp, P(c_int)]),
     "muca_num_bins": (c_int, [c_vp, P(c_int)]),
+    "muca_set_lnW": (c_int, [c_vp, c_vp, c_int]),
+    "muca_poly_trace": (c_int, [c_vp, c_vp, c_i64]),
     "muca_get_lnW": (c_int, [c_vp, c_vp, c_int]),
     "muca_get_lnW_sampled": (c_int, [c_vp, c_vp, c_int]),
     "muca_get_histogram": (c_int, [c_vp, c_vp, c_int]),

@@ -76,6 +76,8 @@ struct muca_ctx {
     int debug_check = 0;      // checked build: every table bounds check of the next iterate fails
     int recursion = 0;        // weight update: 0 accumulated statistics, 1 plain W/H
     int flush_cap = 0;        // spins: most sweeps between histogram flushes (0: the counters' own bound)
+    PolyTraceRec *trace = nullptr;  // polymer: attempt records of the next iterate (device), or null
+    int64_t trace_n = 0;            // records the trace buffer holds
     int observables = 0;      // Ising: per-sweep sums of 1, |M|, M^2 per bin
     unsigned long long *obs = nullptr;  // [0, 3B): sums being filled, [3B, 6B): of the last update
     unsigned long long *metrics = nullptr;  // kMetricWords counters, see UpdateArgs::metrics
@@ -794,6 +796,14 @@ int muca_iterate(muca_ctx *c, int64_t sweeps)
     if (c->system == kPolymer) {
         if (sweeps > 0x7fffffffLL / c->N) return fail(MUCA_ERR_RANGE, "too many sweeps in one call");
         PolyArgs pa = poly_args(c, sweeps);
+        if (c->trace) {  // one-shot: this iterate only
+            const int64_t need = (int64_t)c->p * sweeps * c->N;
+            pa.trace = c->trace;
+            c->trace = nullptr;
+            if (c->trace_n < need)
+                return fail(MUCA_ERR_ARG, "trace buffer holds %lld records; this iterate makes %lld",
+                            (long long)c->trace_n, (long long)need);
+        }
         MUCA_CUDA(launch_poly_sweep(pa, c->block, c->stream));
         MUCA_CUDA(launch_advance(c->state, sweeps, c->stream));
         // refresh the running energies from scratch; the largest change is recorded
@@ -876,6 +886,40 @@ int muca_update_with(muca_ctx *c, const uint64_t *dev_H, int *is_flat)
         if (int rc = d2h(c, &f, &c->state->flat, sizeof(int))) return rc;
         *is_flat = f;
     }
+    return MUCA_OK;
+}
+
+int muca_set_lnW(muca_ctx *c, const double *host_lnW, int nbins)
+{
+    if (int rc = check_ctx(c)) return rc;
+    if (!host_lnW || nbins != c->B) return fail(MUCA_ERR_ARG, "need a host buffer of %d doubles", c->B);
+    std::vector<double> v(host_lnW, host_lnW + c->B);
+    for (int b = 0; b < c->B; ++b) {
+        if (!c->h_reach[b]) {
+            v[b] = -INFINITY;  // unreachable bins keep ln W = -inf
+        } else if (!(std::fabs(v[b]) <= 1e300)) {
+            return fail(MUCA_ERR_ARG, "ln W of reachable bin %d is not finite", b);
+        }
+    }
+    MUCA_CUDA(cudaMemcpyAsync(c->lnW, v.data(), sizeof(double) * c->B, cudaMemcpyHostToDevice, c->stream));
+    if (c->system == kPolymer) {
+        MUCA_CUDA(launch_poly_lnwq(c->lnW, c->lnWq, c->B, c->stream));
+    } else {
+        UpdateArgs a = update_args(c);
+        MUCA_CUDA(launch_thresholds(a, c->stream));
+    }
+    MUCA_CUDA(cudaStreamSynchronize(c->stream));  // the host buffer may go away after the call
+    return MUCA_OK;
+}
+
+int muca_poly_trace(muca_ctx *c, void *dev_records, int64_t n_records)
+{
+    if (int rc = check_ctx(c)) return rc;
+    if (c->system != kPolymer) return fail(MUCA_ERR_ARG, "muca_poly_trace: polymer contexts only");
+    if (!dev_records || n_records < 1) return fail(MUCA_ERR_ARG, "muca_poly_trace: need a device buffer");
+    if (((uintptr_t)dev_records % 16) != 0) return fail(MUCA_ERR_ARG, "muca_poly_trace: buffer not 16-byte aligned");
+    c->trace = (PolyTraceRec *)dev_records;
+    c->trace_n = n_records;
     return MUCA_OK;
 }
 

@@ -101,6 +101,15 @@ constexpr int kPolyMaxBins = 12288;  // the recursion stages 2 doubles a bin in 
 constexpr int kPolyMaxN = 128;
 constexpr long long kPolyStepQ = 1229;  // displacement grid units per unit of (u - 2^31)
 
+// One attempt of a polymer sweep, recorded for parity checks (muca_poly_trace):
+// the energy change and the energy after the decision (2^-32 units), the bin of
+// the proposed energy and the bin after the decision, flags 1 accepted, 2 a bond
+// broke (or a rotation found no point), 4 a lane sum too large (rejected).
+struct PolyTraceRec {
+    long long dq, E;
+    int32_t bn, b, flags, pad;
+};
+
 struct PolyArgs {
     long long *X;
     long long *E;
@@ -121,6 +130,7 @@ struct PolyArgs {
     uint32_t rk[20];
     unsigned long long *metrics = nullptr;  // open counters {accepted moves, tunnelling events}
     uint8_t *tun = nullptr;                 // [p] tunnelling state per walker
+    PolyTraceRec *trace = nullptr;          // [p][sweeps][N] attempt records, or null
 };
 bool polymer_supported(int N);
 cudaError_t launch_poly_init(const PolyArgs &a, cudaStream_t s);

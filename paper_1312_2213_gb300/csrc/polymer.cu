@@ -387,6 +387,16 @@ __global__ void __launch_bounds__(kMaxSweepBlock) k_sweep_polymer(const PolyArgs
                     acc = dnew <= dold;
                 }
             }
+            if (a.trace && li == 0 && active) {  // parity inspection only
+                PolyTraceRec r;
+                r.dq = q;
+                r.E = acc ? En : E;
+                r.bn = bn;
+                r.b = acc ? bn : b;
+                r.flags = (acc ? 1 : 0) | (broken ? 2 : 0) | (huge ? 4 : 0);
+                r.pad = 0;
+                a.trace[((size_t)w * (size_t)a.sweeps + (size_t)sw) * (size_t)N + i] = r;
+            }
             if (acc) {
                 if (li == 0) {
                     if (active) {

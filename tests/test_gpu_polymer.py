@@ -1,8 +1,9 @@
 """GPU polymer path (8, 16 or 32 lanes per walker, FP32 pair terms, exact fixed-point sums) against the
-FP64 oracle.  Coordinates live on a 2^-44 grid on both sides, so trajectories that make the same
-accept/reject decisions are bit-identical; decisions can differ only at near-ties of the
-acceptance test or when an energy lies within the FP32 error of a bin edge, which the oracle
-counts.  Tolerance for energies: 1e-6 of the sum of |pair energies| (FP32 pair terms)."""
+FP64 oracle: initial chains, the all-accepting first iteration, the FENE dimer's closed form,
+reweighting, checkpoints and the paper's parameter set.  Trajectory parity attempt by attempt and
+the density of states against the oracle are in test_gpu_polymer_parity.py.  Coordinates live on a
+2^-44 grid on both sides, so trajectories that make the same accept/reject decisions are
+bit-identical.  Tolerance for energies: 1e-6 of the sum of |pair energies| (FP32 pair terms)."""
 import json
 import os
 
@@ -72,54 +73,6 @@ def test_first_iteration_trajectories_identical():
     for w in range(p):
         assert abs(ge[w] - oe[w]) <= 1e-6 * energy_scale(gX[w]) + 1e-9
     assert int(g.histogram().sum()) == int(o.histogram().sum()) == p * S * N
-
-
-@pytest.mark.parametrize("lanes,p,block", [(0, 64, None), (8, 61, None), (16, 63, None), (32, 64, None),
-                                           (32, 37, 96), (16, 29, 32), (8, 45, 160)])
-def test_first_iteration_histogram_in_pilot_window(lanes, p, block):
-    """In the pilot window (walk-in, then ln W = 0): walkers without a near-tie or bin-edge event
-    in the oracle are bit-identical, and the histograms differ only through bin-edge events.  Every
-    lane grouping (8, 16, 32 lanes a walker), with walker counts that leave the last warp partly
-    empty, and blocks with an odd warp count (odd N: the per-walker shared-memory slots must keep
-    the Philox blocks behind them 16-byte aligned)."""
-    N, S = 13, 40
-    lo, hi = WINDOWS[str(N)]["e_lo"], WINDOWS[str(N)]["e_hi"]
-    g = m.Muca(m.POLYMER3D, N, 0, p, 5, window=(lo, hi), block=block)
-    g.set_param("lanes", lanes)
-    o = oracle.PolyRun(N, p, 5, lo, hi)
-    o.init()
-    g.iterate(S)
-    g.merge_and_update()
-    o.iterate(S, 8)
-    o.update()
-    clean = o.walker_events().sum(axis=1) == 0
-    same = np.all(g.coords() == o.coords(), axis=(1, 2))
-    assert clean.mean() > 0.6 and np.all(same[clean])
-    assert g.drift() < 1e-3
-    edge_events = int(o.counters()[1])
-    dH = np.abs(g.histogram().astype(np.int64) - o.histogram().astype(np.int64)).sum()
-    assert dH <= 4 * edge_events + 8 + 2 * S * N * int((~same).sum())
-
-
-@pytest.mark.parametrize("N", [13, 64])
-def test_multicanonical_iterations_agree_with_oracle(N):
-    """Real multicanonical iterations in the pilot window (walk-in first): walkers whose oracle
-    trajectory had no near-tie or bin-edge event stay bit-identical for the first iteration; the
-    weights of later iterations then agree within the statistical noise of the histograms."""
-    p, S = 64, 40 if N == 13 else 10
-    lo, hi = WINDOWS[str(N)]["e_lo"], WINDOWS[str(N)]["e_hi"]
-    g = m.Muca(m.POLYMER3D, N, 0, p, 9, window=(lo, hi))
-    o = oracle.PolyRun(N, p, 9, lo, hi)
-    o.init()
-    g.iterate(S)
-    g.merge_and_update()
-    o.iterate(S, 8)
-    o.update()
-    clean = o.walker_events().sum(axis=1) == 0
-    same = np.all(g.coords() == o.coords(), axis=(1, 2))
-    assert clean.mean() > 0.6
-    assert np.all(same[clean])
-    assert g.drift() < 1e-3
 
 
 def test_fene_dimer_matches_closed_form():
@@ -209,29 +162,6 @@ def test_paper_model_init_bit_exact(N):
         assert abs(ge[w] - oe[w]) <= 1e-6 * energy_scale(o.coords()[w], 1) + 1e-9
 
 
-def test_paper_model_first_iteration_in_pilot_window():
-    """Model 1, N = 40, in its pilot window (walk-in, then ln W = 0): walkers without a near-tie or
-    bin-edge event in the oracle are bit-identical; the energy refresh drift stays small."""
-    N, p, S = 40, 48, 12
-    lo, hi = PAPER_WINDOWS[str(N)]["e_lo"], PAPER_WINDOWS[str(N)]["e_hi"]
-    g = m.Muca(m.POLYMER3D, N, 0, p, 29, window=(lo, hi))
-    g.set_param("model", 1)
-    o = oracle.PolyRun(N, p, 29, lo, hi, model=1)
-    o.init()
-    g.iterate(S)
-    g.merge_and_update()
-    o.iterate(S, 8)
-    o.update()
-    clean = o.walker_events().sum(axis=1) == 0
-    same = np.all(g.coords() == o.coords(), axis=(1, 2))
-    assert clean.mean() > 0.5 and np.all(same[clean])
-    assert g.drift() < 1e-3
-    ge, oe = g.energies(), o.energy()
-    X = o.coords()
-    for w in np.nonzero(clean)[0][:8]:
-        assert abs(ge[w] - oe[w]) <= 1e-6 * energy_scale(X[w], 1) + 1e-9
-
-
 def test_paper_model_state_round_trip():
     """The model travels with the checkpoint."""
     g = m.Muca(m.POLYMER3D, 40, 0, 8, 3, window=(PAPER_WINDOWS["40"]["e_lo"], PAPER_WINDOWS["40"]["e_hi"]))
@@ -245,25 +175,3 @@ def test_paper_model_state_round_trip():
     g.iterate(2)
     h.iterate(2)
     np.testing.assert_array_equal(g.coords(), h.coords())
-
-
-@pytest.mark.parametrize("model,N", [(0, 13), (1, 40)])
-def test_rotation_moves_first_iteration_bit_exact(model, N):
-    """Move set 1 (shifts and spherical rotations, binary64 rotations rounded to the grid): walkers
-    without a near-tie or bin-edge event in the oracle follow bit-identical trajectories."""
-    p, S = 48, 12
-    W = PAPER_WINDOWS if model == 1 else WINDOWS
-    lo, hi = W[str(N)]["e_lo"], W[str(N)]["e_hi"]
-    g = m.Muca(m.POLYMER3D, N, 0, p, 31, window=(lo, hi))
-    g.set_param("model", model)
-    g.set_param("moves", 1)
-    o = oracle.PolyRun(N, p, 31, lo, hi, model=model, moves=1)
-    o.init()
-    g.iterate(S)
-    g.merge_and_update()
-    o.iterate(S, 8)
-    o.update()
-    clean = o.walker_events().sum(axis=1) == 0
-    same = np.all(g.coords() == o.coords(), axis=(1, 2))
-    assert clean.mean() > 0.5 and np.all(same[clean])
-    assert g.drift() < 1e-3 * max(1.0, N / 13)
