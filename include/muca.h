@@ -154,8 +154,11 @@ int muca_init_ex(muca_ctx **out, int system, int L_or_N, int q, int p, uint64_t 
  *                 rotation puts the bead on a uniform point of the sphere about a
  *                 bonded neighbour, keeping that bond's length, computed in
  *                 correctly rounded binary64 and rounded to the coordinate grid).
- *   "lanes"       polymer: lanes of a warp per walker in the sweep, 8, 16 or 32
- *                 (32/lanes walkers share a warp); 0 (default) means 16.  The pair terms are
+ *   "lanes"       polymer: lanes of a warp per walker in the sweep, 1, 2, 4, 8, 16 or
+ *                 32 (32/lanes walkers share a warp; with 1 lane a walker's lane takes
+ *                 both bonds of the moved bead); 0 (default) means 16.  A grouping whose
+ *                 warp does not fit a block's shared memory falls back to the next larger
+ *                 one, and the block shrinks to the warps that fit.  The pair terms are
  *                 FP32 and their grouping over lanes changes their rounding, so
  *                 runs with different values agree within the FP32 tolerance,
  *                 not bit for bit.  Any time.

@@ -765,7 +765,8 @@ int muca_set_param(muca_ctx *c, const char *key, double v)
     }
     if (k == "lanes") {
         if (c->system != kPolymer) return fail(MUCA_ERR_ARG, "lanes applies to the polymer only");
-        if (v != 0.0 && v != 8.0 && v != 16.0 && v != 32.0) return fail(MUCA_ERR_ARG, "lanes must be 0, 8, 16 or 32");
+        if (v != 0.0 && v != 1.0 && v != 2.0 && v != 4.0 && v != 8.0 && v != 16.0 && v != 32.0)
+            return fail(MUCA_ERR_ARG, "lanes must be 0, 1, 2, 4, 8, 16 or 32");
         c->lanes = (int)v;
         return MUCA_OK;
     }

@@ -136,7 +136,7 @@ bool polymer_supported(int N);
 cudaError_t launch_poly_init(const PolyArgs &a, cudaStream_t s);
 cudaError_t launch_poly_energy(const PolyArgs &a, int track_drift, cudaStream_t s);
 cudaError_t launch_poly_sweep(const PolyArgs &a, int block, cudaStream_t s);
-int poly_lanes(int N, int requested);
+int poly_lanes(const PolyArgs &a, int requested);
 cudaError_t launch_poly_lnwq(const double *lnW, long long *lnWq, int B, cudaStream_t s);
 cudaError_t launch_poly_unpack(const PolyArgs &a, double *coords, double *energies, cudaStream_t s);
 

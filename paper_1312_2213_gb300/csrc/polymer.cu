@@ -331,19 +331,26 @@ __global__ void __launch_bounds__(kMaxSweepBlock) k_sweep_polymer(const PolyArgs
                     }
                 }
             }
-            {
-                const int jb = (li == 0) ? i - 1 : i + 1;
-                if (li < 2 && jb >= 0 && jb < N) {
+            // the bonds (i-1, i) and (i, i+1): lanes 0 and 1 of the group, or the walker's only lane
+            // for both when G = 1
+#pragma unroll
+            for (int t = 0; t < (G == 1 ? 2 : 1); ++t) {
+                const int jb = (G == 1 ? t == 0 : li == 0) ? i - 1 : i + 1;
+                if ((G == 1 || li < 2) && jb >= 0 && jb < N) {
                     const float xj = xs[jb], yj = xs[N + jb], zj = xs[2 * N + jb];
                     const float ljx = xl[jb], ljy = xl[N + jb], ljz = xl[2 * N + jb];
                     const float ax = (xo - xj) + (lxo - ljx), ay = (yo - yj) + (lyo - ljy), az = (zo - zj) + (lzo - ljz);
                     const float bx = (xn - xj) + (lxn - ljx), by = (yn - yj) + (lyn - ljy), bz = (zn - zj) + (lzn - ljz);
                     const float r2o = ax * ax + ay * ay + az * az;
                     const float r2n = bx * bx + by * by + bz * bz;
-                    broken = broken || !fene_intact(r2n, a);
+                    const bool brk = !fene_intact(r2n, a);
+                    broken = broken || brk;
                     const float vo = fene_energy(r2o, a);
-                    const float vn = broken ? vo : fene_energy(r2n, a);
-                    s = vn - vo;
+                    const float vn = brk ? vo : fene_energy(r2n, a);
+                    const float y = (vn - vo) - c;  // compensated, as the pair terms below
+                    const float tt = s + y;
+                    c = (tt - s) - y;
+                    s = tt;
                 }
             }
 #pragma unroll 2
@@ -471,12 +478,27 @@ cudaError_t launch_poly_energy(const PolyArgs &a, int track_drift, cudaStream_t 
     return cudaGetLastError();
 }
 
+// Shared memory of one warp of the sweep: 32/G walkers' float-pair shadows and Philox blocks.
+template <int G>
+static size_t poly_warp_smem(const PolyArgs &a)
+{
+    return (size_t)(32 / G) * ((size_t)poly_slot_floats<G>(a.N) * sizeof(float) +
+                               (size_t)a.N * (a.moves ? 2 : 1) * sizeof(uint4));
+}
+
+constexpr size_t kPolySmemMax = 227u * 1024u;
+
 template <int G>
 static cudaError_t launch_g(const PolyArgs &a, int block, cudaStream_t s)
 {
-    const int wpb = block / 32, spb = wpb * (32 / G);
-    const size_t smem = (size_t)spb * ((size_t)poly_slot_floats<G>(a.N) * sizeof(float) +
-                                       (size_t)a.N * (a.moves ? 2 : 1) * sizeof(uint4));
+    // as many warps of the requested block as fit the shared memory of one block
+    int wpb = block / 32;
+    const size_t per_warp = poly_warp_smem<G>(a);
+    if ((size_t)wpb * per_warp > kPolySmemMax) wpb = (int)(kPolySmemMax / per_warp);
+    if (wpb < 1) return cudaErrorInvalidValue;
+    block = 32 * wpb;
+    const int spb = wpb * (32 / G);
+    const size_t smem = (size_t)wpb * per_warp;
     const int nblk = (a.p + spb - 1) / spb;
     cudaError_t e;
     if (a.record == 0) {
@@ -492,20 +514,35 @@ static cudaError_t launch_g(const PolyArgs &a, int block, cudaStream_t s)
 }
 
 // Lanes per walker: the fixed cost of an attempt (group reductions, the bin and
-// weight lookups, the decision) is shared by 32/G walkers, the pair terms are
-// spread over G lanes.  Measured on GB300 (4096 walkers, 256-thread blocks), 16
-// lanes is the fastest or within 3% of it for N = 13, 32, 64 and 128.
-int poly_lanes(int N, int requested)
+// weight lookups, the decision) is shared by the 32/G walkers of a warp, the pair
+// terms are spread over G lanes.  A request for a grouping whose warp does not fit
+// the shared memory of a block falls back to the next larger G.  Measured on GB300
+// with 4096 walkers (pilot windows), 16 lanes is the fastest at N = 13, 32, 64 and
+// 128: fewer lanes share the fixed cost among more walkers but leave 4096 G / 32
+// warps to hide latency (G = 4: 2.1e9 against 3.0e9 attempts/s at N = 13; G = 1:
+// 1.1e9), so 16 stays the default.
+template <int G>
+static bool poly_fits(const PolyArgs &a)
 {
-    (void)N;
-    if (requested == 8 || requested == 16 || requested == 32) return requested;
-    return 16;
+    return poly_warp_smem<G>(a) <= kPolySmemMax;
+}
+
+int poly_lanes(const PolyArgs &a, int requested)
+{
+    int g = (requested == 1 || requested == 2 || requested == 4 || requested == 8 || requested == 16 ||
+             requested == 32) ? requested : 16;
+    if (g == 1 && !poly_fits<1>(a)) g = 2;
+    if (g == 2 && !poly_fits<2>(a)) g = 4;
+    return g;
 }
 
 cudaError_t launch_poly_sweep(const PolyArgs &a, int block, cudaStream_t s)
 {
     if (!polymer_supported(a.N)) return cudaErrorInvalidValue;
-    switch (poly_lanes(a.N, a.lanes)) {
+    switch (poly_lanes(a, a.lanes)) {
+    case 1: return launch_g<1>(a, block, s);
+    case 2: return launch_g<2>(a, block, s);
+    case 4: return launch_g<4>(a, block, s);
     case 8: return launch_g<8>(a, block, s);
     case 16: return launch_g<16>(a, block, s);
     default: return launch_g<32>(a, block, s);
