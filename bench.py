@@ -18,6 +18,11 @@ proposed single-spin update, accepted or not), whole job.
                 persistent launch per iteration, and against the whole loop as one CUDA graph.
   polymer       the bead-spring polymer, N in {13,32,64,128}, p = 4096, in its pilot windows.
 
+With N > 1 GPUs (torchrun) each system's walkers are split over the ranks (8192 a rank, weak
+scaling) and every iteration ends with one all-reduce of the B-bin histogram per system (the
+paper's Fig. 1 exchange, NCCL on device buffers) before the identical recursion on every rank;
+`--mode replicas` runs an independent system pair per rank instead.
+
 `--impl reference` times the CPU oracle itself as the reference arm.
 """
 from __future__ import annotations
@@ -65,7 +70,41 @@ def parse():
     ap.add_argument("--no-extras", action="store_true", help="skip the batched-mix, Potts and polymer measurements")
     ap.add_argument("--workload", default="all", choices=["all", "mix", "polymer", "potts"],
                     help="mix / polymer / potts: run only that measurement (for profiling)")
+    ap.add_argument("--mode", default="shard", choices=["shard", "replicas"],
+                    help="N > 1: 'shard' runs each system's walkers split over the ranks with one histogram "
+                         "all-reduce per iteration (Fig. 1); 'replicas' runs an independent system pair per rank")
     return ap.parse_args()
+
+
+def make_sharded_systems(m, rank: int, world: int, stream=None, p_per_rank: int = P, ctx_factory=None,
+                         device: str = "cuda"):
+    """The workload split over `world` ranks with weak scaling: each system has p_per_rank walkers
+    per rank (p_per_rank * world in all, one seed per system), rank r holding walkers
+    [r p_per_rank, (r + 1) p_per_rank).  After every iteration's sweeps the ranks add their open
+    histograms with one all-reduce of B uint64 per system and run the same recursion."""
+    from paper_1312_2213_gb300.shard import ShardedMuca
+
+    p_all = p_per_rank * world
+    return [ShardedMuca(m.ISING2D if m else 0, L, 2, p_all, 1, ctx_factory=ctx_factory, device=device, stream=stream),
+            ShardedMuca(m.ISING2D_MUMA if m else 2, L, 2, p_all, 1001, ctx_factory=ctx_factory, device=device,
+                        beta=BETA_MUMA, stream=stream)]
+
+
+def sharded_step(systems, sweeps: int, kevents=None, stream=None):
+    """One step of the sharded workload: every system's sweeps on this rank's walkers, then the
+    exchange and the update (kernel events around the sweeps if kevents is given)."""
+    for s in systems:
+        if kevents is not None:
+            import torch
+
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            s.iterate(sweeps)
+            b.record(stream)
+            kevents.append((a, b))
+        else:
+            s.iterate(sweeps)
+        s.merge_and_update()
 
 
 MIX = [(0, L, 2) for L in (16, 24, 32, 48, 64)] + [(1, L, 10) for L in (16, 24, 32, 48)]
@@ -298,25 +337,22 @@ def run_ours(args):
         dist.init_process_group("nccl")
     m.load()
     stream = torch.cuda.Stream()
-    seed = 1 + 7919 * rank
-    systems = [m.Muca(m.ISING2D, L, 2, P, seed, stream=stream),
-               m.Muca(m.ISING2D_MUMA, L, 2, P, seed + 1000, beta=BETA_MUMA, stream=stream)]
+    sharded = world > 1 and args.mode == "shard"
+    if sharded:
+        systems = make_sharded_systems(m, rank, world, stream=stream)
+        ctxs = [s.ctx for s in systems]
+    else:
+        seed = 1 + 7919 * rank
+        systems = [m.Muca(m.ISING2D, L, 2, P, seed, stream=stream),
+                   m.Muca(m.ISING2D_MUMA, L, 2, P, seed + 1000, beta=BETA_MUMA, stream=stream)]
+        ctxs = systems
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
     sweeps = args.sweeps
     step_attempts = len(systems) * P * sweeps * N
     launches_per_step = len(systems) * 5  # sweep, counter advance, merge, recursion, thresholds
 
     def step(kevents=None):
-        for s in systems:
-            if kevents is not None:
-                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                a.record(stream)
-                s.iterate(sweeps)
-                b.record(stream)
-                kevents.append((a, b))
-            else:
-                s.iterate(sweeps)
-            s.merge_and_update()
+        sharded_step(systems, sweeps, kevents, stream)
 
     with torch.cuda.stream(stream):
         for _ in range(args.warmup):
@@ -349,7 +385,7 @@ def run_ours(args):
 
     # end to end through the C ABI: state in from pinned host memory, state out, every step
     bufs = []
-    for s in systems:
+    for s in ctxs:
         n = m.muca_get_state(s.h, None)
         t = torch.empty(n, dtype=torch.uint8, pin_memory=True)
         buf = t.numpy()
@@ -359,11 +395,11 @@ def run_ours(args):
     torch.cuda.synchronize()
     h0 = time.perf_counter()
     for _ in range(e2e_steps):
-        for s, (_, buf) in zip(systems, bufs):
-            m.muca_set_state(s.h, buf)
+        for s, c, (_, buf) in zip(systems, ctxs, bufs):
+            m.muca_set_state(c.h, buf)
             s.iterate(sweeps)
             s.merge_and_update()
-            m.muca_get_state(s.h, buf)
+            m.muca_get_state(c.h, buf)
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - h0
     state_bytes = sum(b.nbytes for _, b in bufs)
@@ -394,7 +430,8 @@ def run_ours(args):
                        "sweeps_per_step": sweeps, "beta_muma": BETA_MUMA,
                        "l2": "flushed between steps (256 MiB write on the stream)",
                        "parallelism": "walkers (one chain per thread)" if world == 1 else
-                       "independent replicas, one per GPU"},
+                       ("walkers of each system sharded over %d GPUs (%d a GPU), one histogram all-reduce "
+                        "per system per iteration" % (world, P) if sharded else "independent replicas, one per GPU")},
             "e2e": e2e, "gpu_launches": launches_per_step * args.steps, "roofline": roofline,
             "clocks": ck}
     if not args.no_extras:

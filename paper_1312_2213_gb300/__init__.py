@@ -312,6 +312,16 @@ class Muca:
     def merge_and_update(self, want_flat: bool = False):
         return muca_merge_and_update(self.h, want_flat)
 
+    def merge_open(self, dev_buf):
+        """Sum the open histogram into a device tensor of B int64 and clear it (sharded runs);
+        returns when the buffer holds the sum."""
+        muca_merge_open(self.h, dev_buf.data_ptr())
+        muca_synchronize(self.h)
+
+    def update_with(self, dev_buf, want_flat: bool = False):
+        """Close the iteration with a summed histogram held in a device tensor (sharded runs)."""
+        return muca_update_with(self.h, dev_buf.data_ptr(), want_flat)
+
     def set_lnW(self, lnW: np.ndarray):
         muca_set_lnW(self.h, lnW)
 

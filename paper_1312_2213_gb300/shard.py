@@ -18,7 +18,7 @@ from __future__ import annotations
 import torch
 import torch.distributed as dist
 
-from . import Muca, muca_merge_open, muca_update_with
+from . import Muca
 
 
 def shard_range(p: int, rank: int, world: int) -> tuple[int, int]:
@@ -27,15 +27,21 @@ def shard_range(p: int, rank: int, world: int) -> tuple[int, int]:
 
 
 class ShardedMuca:
-    def __init__(self, system: int, L: int, q: int, p: int, seed: int, group=None, **kw):
+    """One rank's shard of a system.  `ctx_factory` builds the rank's context (default: a Muca
+    context on the current CUDA device); anything with the same iterate / merge_open / update_with
+    / metrics methods works, which lets the exchange itself be tested without a GPU."""
+
+    def __init__(self, system: int, L: int, q: int, p: int, seed: int, group=None, ctx_factory=None,
+                 device: str = "cuda", **kw):
         self.group = group
         rank, world = dist.get_rank(group), dist.get_world_size(group)
         self.w0, self.w1 = shard_range(p, rank, world)
         if self.w1 <= self.w0:
             raise ValueError("more ranks than walkers")
-        self.ctx = Muca(system, L, q, self.w1 - self.w0, seed, walker_offset=self.w0, **kw)
+        self.ctx = (ctx_factory or Muca)(system, L, q, self.w1 - self.w0, seed, walker_offset=self.w0, **kw)
         self.B = self.ctx.B
-        self.buf = torch.zeros(self.B, dtype=torch.int64, device="cuda")
+        self.device = device
+        self.buf = torch.zeros(self.B, dtype=torch.int64, device=device)
 
     def set_group(self, group):
         """Continue in another process group (e.g. the survivors after a rank failed)."""
@@ -46,16 +52,16 @@ class ShardedMuca:
 
     def merge_and_update(self, want_flat: bool = False):
         """Sum the open histograms of all ranks and close the iteration on this rank."""
-        muca_merge_open(self.ctx.h, self.buf.data_ptr())
-        self.ctx.synchronize()  # the buffer is read by torch below
-        if dist.get_backend(self.group) == "nccl":
+        self.ctx.merge_open(self.buf)
+        if dist.get_backend(self.group) == "nccl" or self.buf.device.type == "cpu":
             dist.all_reduce(self.buf, group=self.group)
         else:
             host = self.buf.cpu()
             dist.all_reduce(host, group=self.group)
             self.buf.copy_(host)
-        torch.cuda.synchronize()
-        return muca_update_with(self.ctx.h, self.buf.data_ptr(), want_flat)
+        if self.buf.device.type == "cuda":
+            torch.cuda.synchronize()
+        return self.ctx.update_with(self.buf, want_flat)
 
     def metrics(self) -> dict:
         """The last closed iteration's metrics summed over the ranks of the group (each rank
@@ -64,7 +70,7 @@ class ShardedMuca:
         keys = ("accepted", "tunnelling_events", "accepted_total", "tunnelling_events_total")
         t = torch.tensor([d[k] for k in keys] + [self.w1 - self.w0], dtype=torch.int64)
         if dist.get_backend(self.group) == "nccl":
-            t = t.cuda()
+            t = t.to(self.device)
         dist.all_reduce(t, group=self.group)
         t = t.cpu()
         out = dict(d)

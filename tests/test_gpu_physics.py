@@ -112,3 +112,24 @@ def test_multimagnetic_and_energy_observables_agree():
         ma, mo = a[:, k].mean(), o[:, k].mean()
         ea, eo = a[:, k].std(ddof=1) / math.sqrt(len(a)), o[:, k].std(ddof=1) / math.sqrt(len(o))
         assert abs(ma - mo) < 4 * math.hypot(ea, eo), (name, ma, ea, mo, eo)
+
+
+def test_potts_q8_L4_density_of_states_matches_the_golden_omega():
+    """8-state Potts on the 4x4 torus through the CUDA path: ln H - ln W after 12 iterations of
+    4000 sweeps (1024 walkers) against the exact Omega(E) (tests/golden/potts_q8_L4_omega.txt,
+    written from the transfer matrix), which spans 28 units of ln Omega over 29 reachable bins; the
+    unreachable bins (1, 2, 3, 5 broken bonds) must stay unvisited.  Every bin within 0.05."""
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "potts_q8_L4_omega.txt")
+    om = np.array([float(l.split()[1]) for l in open(path) if l.strip() and not l.startswith("#")])
+    g = m.Muca(m.POTTS2D, 4, 8, 1024, 17)
+    for _ in range(12):
+        g.iterate(4000)
+        g.merge_and_update()
+    H = g.histogram()
+    reach = om > 0
+    assert np.all(H[~reach] == 0) and np.all(H[reach] > 0)
+    lo = np.log(H[reach].astype(float)) - g.lnW_sampled()[reach]
+    le = np.log(om[reach])
+    d = lo + (le[0] - lo[0]) - le
+    d -= d.mean()
+    assert np.abs(d).max() < 0.05, np.abs(d).max()
