@@ -1197,8 +1197,11 @@ int muca_set_state(muca_ctx *c, const void *host_buf, size_t bytes)
     const int slots = (c->system == kPolymer) ? 1 : c->nblk_max;
     MUCA_CUDA(cudaMemsetAsync(c->Hpart, 0, sizeof(unsigned long long) * (size_t)slots * c->B, c->stream));
     const char *p = (const char *)host_buf + sizeof h;
+    bool open_counts = false;  // the buffer carries sweeps not merged yet
     for (const Section &sec : state_sections(c)) {
         void *dst = sec.dev ? sec.dev : (void *)c->Hpart;  // open histogram -> slot 0
+        if (!sec.dev)
+            for (size_t i = 0; i < sec.bytes && !open_counts; ++i) open_counts = p[i] != 0;
         cudaError_t e = cudaMemcpyAsync(dst, p, sec.bytes, cudaMemcpyHostToDevice, c->stream);
         if (e != cudaSuccess) return fail(MUCA_ERR_CUDA, "muca_set_state: %s", cudaGetErrorString(e));
         p += sec.bytes;
@@ -1206,7 +1209,7 @@ int muca_set_state(muca_ctx *c, const void *host_buf, size_t bytes)
     MUCA_CUDA(cudaMemcpyAsync(c->state, &h.dev, sizeof h.dev, cudaMemcpyHostToDevice, c->stream));
     MUCA_CUDA(cudaStreamSynchronize(c->stream));
     c->started = true;
-    c->open = true;
+    c->open = open_counts;
     return MUCA_OK;
 }
 

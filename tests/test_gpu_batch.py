@@ -154,3 +154,23 @@ def test_full_size_mix_bit_exact_against_the_oracle():
             o.update()
         compare_state(c, o, "mix system %d L=%d" % (s, L))
     b.close()
+
+
+def test_batch_runs_after_restoring_a_merged_checkpoint():
+    """A checkpoint taken after a merge carries no unmerged counts, so a batch may run right after
+    it is restored; one taken between an iterate and its merge still makes the batch refuse."""
+    a = m.Muca(m.ISING2D, 16, 2, 64, 3)
+    a.iterate(5)
+    a.merge_and_update()
+    merged = a.get_state()
+    a.iterate(5)
+    unmerged = a.get_state()
+    c = m.Muca(m.ISING2D, 16, 2, 64, 3)
+    c.set_state(merged)
+    b = m.Batch([c])
+    b.run(1, 5, use_graph=False)
+    c.set_state(unmerged)
+    with pytest.raises(m.MucaError) as e:
+        b.run(1, 5, use_graph=False)
+    assert e.value.code == -5
+    b.close()
