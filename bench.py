@@ -46,6 +46,11 @@ N = L * L
 # (10 rounds x 4 ops / 4 = 10), neighbour bits and count 8, table column and address 2,
 # threshold load 1, integer compare 2, flip/select 3, bin update 2, histogram atomic 1, loop 1.
 INSTR_PER_ATTEMPT = 30
+# Cycles an attempt of one walker's chain in this design's sweep with its scheduler to itself
+# (one consumer warp an SM, p = 4096 in 32-walker blocks, measured on GB300 at 2.07 GHz): the
+# bound p f / CHAIN_CYCLES on attempts/s of one system, against which the kernel's rate is also
+# reported (the issue-peak fraction counts all schedulers, which a chain per walker cannot fill).
+CHAIN_CYCLES = 42.9
 # DRAM bytes (read + write) per launch of the timed sweep kernel, from one ncu capture of the current
 # k_sweep_spin_tn build (dram__bytes_read.sum + dram__bytes_write.sum; mean of the Ising and MUMA
 # launches: 1.25 MB and 2.17 MB read, nothing written).  It is the walker state and does not grow
@@ -423,6 +428,11 @@ def run_ours(args):
                 "kernel": "k_sweep_spin_tn (code form; Ising L=32 MUCA and MUMA)", "kernel_ms": sweep_ms,
                 "peak_basis": "%d SMs x 4 schedulers x 32 lanes x %.0f MHz (median sampled SM clock)" % (sms, f_mhz),
                 "instr_per_attempt": INSTR_PER_ATTEMPT}
+    chain_rate = P * f_mhz * 1e6 / CHAIN_CYCLES
+    kernel_rate = P * sweeps * N / (sweep_ms / 1e3)
+    roofline["chain_bound"] = {"cycles_per_attempt": CHAIN_CYCLES, "attempts_per_s": chain_rate,
+                               "achieved_attempts_per_s": kernel_rate, "frac": kernel_rate / chain_rate,
+                               "basis": "p x f_SM / cycles of one walker's chain with its scheduler to itself"}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u32", "data": "synthetic",
