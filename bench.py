@@ -47,10 +47,11 @@ N = L * L
 # threshold load 1, integer compare 2, flip/select 3, bin update 2, histogram atomic 1, loop 1.
 INSTR_PER_ATTEMPT = 30
 # Cycles an attempt of one walker's chain in this design's sweep with its scheduler to itself
-# (one consumer warp an SM, p = 4096 in 32-walker blocks, measured on GB300 at 2.07 GHz): the
-# bound p f / CHAIN_CYCLES on attempts/s of one system, against which the kernel's rate is also
-# reported (the issue-peak fraction counts all schedulers, which a chain per walker cannot fill).
-CHAIN_CYCLES = 42.9
+# (one consumer warp an SM, p = 4096 in 32-walker blocks, measured on GB300 at 2.07 GHz): Ising
+# 42.9, multimagnetic 49.1, averaged over the step's two systems.  p f / CHAIN_CYCLES bounds the
+# attempts/s of the sweep kernel, and its rate is reported against it as well (the issue-peak
+# fraction counts all schedulers, which one chain per walker cannot fill at p = 8192).
+CHAIN_CYCLES = (42.9 + 49.1) / 2
 # DRAM bytes (read + write) per launch of the timed sweep kernel, from one ncu capture of the current
 # k_sweep_spin_tn build (dram__bytes_read.sum + dram__bytes_write.sum; mean of the Ising and MUMA
 # launches: 1.25 MB and 2.17 MB read, nothing written).  It is the walker state and does not grow
