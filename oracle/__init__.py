@@ -397,6 +397,22 @@ class PolyRun:
             self._lib.orc_poly_set_trace(self.h, None)
         return t.reshape(self.p, sweeps, self.N)
 
+    def iterate_range_traced(self, sweeps: int, w0: int, w1: int, nthreads: int = 1) -> np.ndarray:
+        """Run `sweeps` sweeps of walkers [w0, w1) (the sweep counter does not advance: call
+        advance() once for all ranges) and return their records, shape (w1 - w0, sweeps, N)."""
+        t = np.zeros((w1 - w0) * sweeps * self.N, dtype=POLY_TRACE_DTYPE)
+        self._lib.orc_poly_set_trace(self.h, t.ctypes.data_as(ctypes.c_void_p))
+        try:
+            self.iterate_range(sweeps, w0, w1, nthreads)
+        finally:
+            self._lib.orc_poly_set_trace(self.h, None)
+        return t.reshape(w1 - w0, sweeps, self.N)
+
+    def walker_energies(self, idx) -> tuple:
+        """(energies, bounds delta) of the given walkers."""
+        idx = np.asarray(idx)
+        return self.energy()[idx], self.delta()[idx]
+
     def _get(self, name, n, dtype):
         a = np.zeros(n, dtype=dtype)
         getattr(self._lib, name)(self.h, _ptr(a))

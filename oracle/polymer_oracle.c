@@ -119,6 +119,7 @@ typedef struct {
     int64_t *first;
     double *drift;
     orc_poly_trace_rec *trace;
+    int trace_w0; /* walker whose records start the trace buffer (ranged calls) */
     /* planted error for the tests of the event rule: every pair term of a move and
      * of a from-scratch energy is changed by perturb * sigma * xi, xi in [-1, 1)
      * from a Philox word (tag 7, key perturb_seed); 0 = off */
@@ -535,7 +536,8 @@ static void poly_walker_sweeps(orc_poly *P, int w, int64_t g0, int64_t sweeps, u
                 if (muca) P->delta[w] += P->tau * S + POLY_RHO;
             }
             if (P->trace) {
-                orc_poly_trace_rec *t = P->trace + ((size_t)w * (size_t)sweeps + (size_t)sw) * (size_t)N + i;
+                orc_poly_trace_rec *t =
+                    P->trace + ((size_t)(w - P->trace_w0) * (size_t)sweeps + (size_t)sw) * (size_t)N + i;
                 t->dE = broken ? NAN : dE;
                 t->scale = S;
                 t->E = E;
@@ -601,6 +603,7 @@ void orc_poly_iterate_range(void *h, int64_t sweeps, int w0, int w1, int nthread
     if (w0 < 0) w0 = 0;
     if (w1 > P->p) w1 = P->p;
     if (w1 <= w0 || sweeps <= 0) return;
+    P->trace_w0 = w0; /* a trace of this call holds walkers w0 .. w1-1 */
     int nw = w1 - w0;
     if (nthreads < 1) nthreads = 1;
     if (nthreads > nw) nthreads = nw;
@@ -802,8 +805,9 @@ void orc_poly_get_delta(void *h, double *out)
     memcpy(out, P->delta, sizeof(double) * (size_t)P->p);
 }
 
-/* Trace of every attempt of the next calls (p * sweeps * N records, walker-major,
- * then sweep, then bead), or NULL to stop tracing. */
+/* Trace of every attempt of the next calls ((w1 - w0) * sweeps * N records for a
+ * call over walkers [w0, w1), walker-major, then sweep, then bead), or NULL to
+ * stop tracing. */
 void orc_poly_set_trace(void *h, orc_poly_trace_rec *buf) { ((orc_poly *)h)->trace = buf; }
 
 /* Tolerance of the pair terms per unit of error scale (default 1e-6); before init. */

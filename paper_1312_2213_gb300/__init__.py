@@ -325,9 +325,10 @@ class Muca:
     def set_lnW(self, lnW: np.ndarray):
         muca_set_lnW(self.h, lnW)
 
-    def iterate_traced(self, sweeps: int) -> np.ndarray:
+    def iterate_traced(self, sweeps: int, walkers=None) -> np.ndarray:
         """Polymer: run `sweeps` sweeps and return the record of every attempt, shape
-        (p, sweeps, N), dtype POLY_TRACE_DTYPE (muca_poly_trace)."""
+        (p, sweeps, N), dtype POLY_TRACE_DTYPE (muca_poly_trace); with `walkers` (indices) only
+        their records are copied back, shape (len(walkers), sweeps, N)."""
         import torch
 
         n = self.p * sweeps * self.N
@@ -335,7 +336,11 @@ class Muca:
         muca_poly_trace(self.h, buf.data_ptr(), n)
         muca_iterate(self.h, sweeps)
         muca_synchronize(self.h)
-        return buf.cpu().numpy().view(POLY_TRACE_DTYPE).reshape(self.p, sweeps, self.N)
+        rows = buf.view(self.p, -1)
+        if walkers is not None:
+            rows = rows[torch.as_tensor(np.asarray(walkers), device="cuda")]
+        k = rows.shape[0]
+        return rows.cpu().numpy().reshape(-1).view(POLY_TRACE_DTYPE).reshape(k, sweeps, self.N)
 
     def lnW(self) -> np.ndarray:
         a = np.zeros(self.B, dtype=np.float64)

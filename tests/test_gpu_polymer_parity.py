@@ -65,6 +65,13 @@ def _pair(N, p, seed, model, moves, lanes=0, block=None, window=None):
 
 def compare_call(tg, to, g, o, lo, alive, stats, what):
     """Compare one call's traces walker by walker (see the module docstring); updates `alive`."""
+    compare_arrays(tg, to, g.coords(), o.coords(), g.bins(), o.bins(), o.energy(), o.delta(), lo, alive, stats,
+                   what)
+
+
+def compare_arrays(tg, to, Xg, Xo, bins_g, bins_o, E_end, d_end, lo, alive, stats, what):
+    """compare_call on arrays: traces (walkers, sweeps, N), end coordinates and bins of both sides,
+    the oracle's refreshed energies and bounds, all for the same walkers in the same order."""
     p = tg.shape[0]
     flat = lambda a: a.reshape(p, -1)
     acc_g, acc_o = flat(tg["flags"]) & 1, flat(to["flags"]) & 1
@@ -75,8 +82,6 @@ def compare_call(tg, to, g, o, lo, alive, stats, what):
     dq, dE, sc = flat(tg["dq"]) * Q, flat(to["dE"]), flat(to["scale"])
     Eg, Eo, dl = flat(tg["E"]) * Q, flat(to["E"]), flat(to["delta"])
     gbad = (flat(tg["flags"]) & 6) != 0
-    Xg, Xo, bins_g, bins_o = g.coords(), o.coords(), g.bins(), o.bins()
-    E_end, d_end = o.energy(), o.delta()
     for w in np.nonzero(alive)[0]:
         n = first[w] if first[w] >= 0 else dis.shape[1]
         ok = np.isfinite(dE[w, :n]) & ~gbad[w, :n]
@@ -238,3 +243,38 @@ def test_trimer_density_of_states_by_quadrature(model, moves):
     d = lo_ + np.median(le - lo_) - le
     print("\nmodel %d moves %d: max |d| %.4f rms %.4f" % (model, moves, np.abs(d).max(), np.sqrt((d * d).mean())))
     assert np.max(np.abs(d)) < 0.05 and np.sqrt(np.mean(d * d)) < 0.02
+
+
+
+@pytest.mark.parametrize("N,calls", [(13, [100, 20]), (128, [80, 4])])
+def test_full_size_sampled_walkers_in_the_bench_configuration(N, calls):
+    """The bench's configuration (p = 4096, 256-thread blocks, 16 lanes a walker, pilot window): the
+    GPU runs all walkers with tracing; the oracle runs only 24 walkers spread over the launch (the
+    first and last, block and warp edges, odd positions), one at a time.  Each sampled walker agrees
+    up to its first disagreement, which must be an oracle-flagged event, as in the cases above.  The
+    second call runs under non-trivial weights: the oracle's update from the sampled walkers'
+    histogram, given to the GPU."""
+    p = 4096
+    lo, hi = WINDOWS[0][str(N)]["e_lo"], WINDOWS[0][str(N)]["e_hi"]
+    g = m.Muca(m.POLYMER3D, N, 0, p, 5, window=(lo, hi))
+    o = oracle.PolyRun(N, p, 5, lo, hi)
+    o.init()
+    sample = np.array([0, 1, 15, 16, 17, 31, 32, 33, 511, 512, 1000, 1023, 1024, 2047, 2048, 2049, 2500,
+                       3071, 3072, 3583, 4000, 4093, 4094, 4095])
+    np.testing.assert_array_equal(g.coords()[sample], o.coords()[sample])
+    alive = np.ones(sample.size, dtype=bool)
+    stats = {"ratio": [], "energy": [], "compared": 0, "attempts": 0, "diverged": 0}
+    for k, S in enumerate(calls):
+        tg = g.iterate_traced(S, walkers=sample)
+        to = np.concatenate([o.iterate_range_traced(S, int(w), int(w) + 1) for w in sample])
+        o.advance(S)
+        compare_arrays(tg, to, g.coords()[sample], o.coords()[sample], g.bins()[sample], o.bins()[sample],
+                       o.energy()[sample], o.delta()[sample], lo, alive, stats, "call %d" % k)
+        g.merge_and_update()
+        o.update()
+        g.set_lnW(o.lnW())
+    r = np.concatenate(stats["ratio"])
+    print("\nfull size N=%d: %d of %d sampled attempts compared, %d walkers diverged at events; "
+          "|dE_gpu - dE_oracle| / S max %.3g" % (N, stats["compared"], stats["attempts"], stats["diverged"], r.max()))
+    assert stats["compared"] > 0.5 * stats["attempts"]
+    assert r.max() <= TAU
