@@ -6,9 +6,10 @@
 // G lanes of a warp per walker (G = 8, 16 or 32; 32/G walkers share a warp).
 // The beads are visited in order; for bead i every lane of the walker's group
 // evaluates the old and the new pair energies with its partner beads
-// j = lane, lane + G, ... in FP32 and keeps a compensated (Kahan) sum; the lane
-// sums are converted to 64-bit fixed point (2^-32 energy units) and added with
-// an exact integer reduction over the group.  Nothing on the hot path uses FP64, whose
+// j = lane, lane + G, ... in FP32 and keeps a compensated (Kahan) sum (the old
+// bond energies come from a per-walker cache, updated on acceptance); the lane
+// sums are added in FP32 over the group and the total is converted once to 64-bit
+// fixed point (2^-32 energy units).  Nothing on the hot path uses FP64, whose
 // rate on GB300 is a small fraction of FP32.
 //
 // Exactness: master coordinates are int64 on a 2^-44 grid and a move adds
@@ -23,8 +24,9 @@
 // energy is an exact sum of the fixed-point energy changes; it is refreshed from
 // scratch after every iterate call, and the largest difference is recorded.
 // Acceptance inside the window: d = ln W(b') - ln W(b) from a fixed-point table,
-// accept iff d >= 0 or u < 2^32 exp(d) (FP32 exp); outside the window a move is
-// accepted iff it does not increase the distance to the window (walk-in).
+// accept iff d >= 0 or ln(u 2^-32) < d (the FP32 logarithm of each bead's
+// acceptance word is taken once a sweep); outside the window a move is accepted
+// iff it does not increase the distance to the window (walk-in).
 #include "muca_device.cuh"
 #include "muca_internal.h"
 
@@ -187,14 +189,6 @@ __global__ void k_poly_energy(const PolyArgs a, int track)
 }
 
 template <int G>
-__device__ __forceinline__ long long group_sum_ll(long long q)  // exact sum over the G lanes of a walker
-{
-#pragma unroll
-    for (int off = G / 2; off; off >>= 1) q += __shfl_xor_sync(0xffffffffu, q, off);
-    return q;
-}
-
-template <int G>
 __device__ __forceinline__ bool group_any(bool p, int gi)
 {
     const unsigned bal = __ballot_sync(0xffffffffu, p);
@@ -239,17 +233,16 @@ __device__ bool poly_rotation(const long long *Xg, int N, int i, uint32_t g, uin
     return true;
 }
 
-// Shared-memory floats of one walker's float-pair shadows: 6 N, rounded up to a
-// multiple of 4 for one walker a warp (G = 32), so that the uint4 Philox blocks
-// behind all slots start 16-byte aligned for any warp count and odd N (with 2 or
-// 4 walkers a warp the slot count is even and 6 N always suffices).  Padding the
-// slots so that the walkers of a warp read disjoint banks (6 N = 0 mod 32 puts
-// them on the same banks for N = 32, 64, 128) was measured on GB300: within 1 %
-// at N = 64 and 128, 2-5 % slower at N = 32 and 13, so it is not done.
+// Shared-memory floats of one walker's slot: the float-pair shadows (6 N) and the
+// energies of its N - 1 bonds, rounded up to a multiple of 4 so that the uint4
+// Philox blocks behind all slots start 16-byte aligned for any walker count and
+// odd N.  (Padding the slots so that the walkers of a warp read disjoint banks was
+// measured on GB300 with the 6 N layout: within 1 % at N = 64 and 128, 2-5 %
+// slower at N = 32 and 13, so it is not done.)
 template <int G>
 __host__ __device__ inline int poly_slot_floats(int N)
 {
-    return G == 32 ? (6 * N + 3) & ~3 : 6 * N;
+    return (7 * N + 3) & ~3;  // hi[3N], lo[3N], bond energies[N]; a multiple of 4 floats
 }
 
 // Sweeps: G lanes per walker, 32/G walkers a warp, all on the same bead i.  A
@@ -269,6 +262,7 @@ __global__ void __launch_bounds__(kMaxSweepBlock) k_sweep_polymer(const PolyArgs
     const int spb = wpb * W, slot = wib * W + gi, sst = poly_slot_floats<G>(N);
     float *xs = (float *)smem + (size_t)slot * sst;
     float *xl = xs + 3 * N;
+    float *eb = xs + 6 * N;  // eb[j]: FP32 energy of bond (j, j+1) at the current shadows
     uint4 *su = (uint4 *)(smem + (size_t)spb * sst * sizeof(float)) + (size_t)slot * N;
     uint4 *sm = su + (size_t)spb * N;  // moves
     const int w0 = (blockIdx.x * wpb + wib) * W;
@@ -294,8 +288,19 @@ __global__ void __launch_bounds__(kMaxSweepBlock) k_sweep_polymer(const PolyArgs
             grid_to_ff(Xg[j] - A0, xs[j], xl[j]);
             grid_to_ff(Xg[N + j] - A1, xs[N + j], xl[N + j]);
             grid_to_ff(Xg[2 * N + j] - A2, xs[2 * N + j], xl[2 * N + j]);
-            su[j] = philox4x32_10_rk(make_uint4((uint32_t)j, g, wid, kTagSweep), a.rk);
+            uint4 r = philox4x32_10_rk(make_uint4((uint32_t)j, g, wid, kTagSweep), a.rk);
+            // the acceptance test u 2^-32 < exp(d) is taken as ln(u 2^-32) < d: the logarithm
+            // (FP32, -inf for u = 0) is taken here, once a bead and sweep, off the serial path
+            r.w = __float_as_uint(logf((float)r.w * 0x1p-32f));
+            su[j] = r;
             if (a.moves) sm[j] = philox4x32_10_rk(make_uint4((uint32_t)j, g, wid, kTagPolyMove), a.rk);
+        }
+        __syncwarp();
+        for (int j = li; j + 1 < N; j += G) {
+            const float dx = (xs[j] - xs[j + 1]) + (xl[j] - xl[j + 1]);
+            const float dy = (xs[N + j] - xs[N + j + 1]) + (xl[N + j] - xl[N + j + 1]);
+            const float dz = (xs[2 * N + j] - xs[2 * N + j + 1]) + (xl[2 * N + j] - xl[2 * N + j + 1]);
+            eb[j] = fene_energy(dx * dx + dy * dy + dz * dz, a);
         }
         __syncwarp();
 #pragma unroll 1
@@ -332,21 +337,22 @@ __global__ void __launch_bounds__(kMaxSweepBlock) k_sweep_polymer(const PolyArgs
                 }
             }
             // the bonds (i-1, i) and (i, i+1): lanes 0 and 1 of the group, or the walker's only lane
-            // for both when G = 1
+            // for both when G = 1; the old energies come from the bond cache, the new ones are
+            // kept to update it if the move is accepted
+            float vnb[2] = {0.0f, 0.0f};
 #pragma unroll
             for (int t = 0; t < (G == 1 ? 2 : 1); ++t) {
                 const int jb = (G == 1 ? t == 0 : li == 0) ? i - 1 : i + 1;
                 if ((G == 1 || li < 2) && jb >= 0 && jb < N) {
                     const float xj = xs[jb], yj = xs[N + jb], zj = xs[2 * N + jb];
                     const float ljx = xl[jb], ljy = xl[N + jb], ljz = xl[2 * N + jb];
-                    const float ax = (xo - xj) + (lxo - ljx), ay = (yo - yj) + (lyo - ljy), az = (zo - zj) + (lzo - ljz);
                     const float bx = (xn - xj) + (lxn - ljx), by = (yn - yj) + (lyn - ljy), bz = (zn - zj) + (lzn - ljz);
-                    const float r2o = ax * ax + ay * ay + az * az;
                     const float r2n = bx * bx + by * by + bz * bz;
                     const bool brk = !fene_intact(r2n, a);
                     broken = broken || brk;
-                    const float vo = fene_energy(r2o, a);
+                    const float vo = eb[jb < i ? jb : i];
                     const float vn = brk ? vo : fene_energy(r2n, a);
+                    vnb[t] = vn;
                     const float y = (vn - vo) - c;  // compensated, as the pair terms below
                     const float tt = s + y;
                     c = (tt - s) - y;
@@ -372,8 +378,13 @@ __global__ void __launch_bounds__(kMaxSweepBlock) k_sweep_polymer(const PolyArgs
             broken = group_any<G>(broken, gi);
             // |lane sum| >= 2^22 only for overlapping beads: such a move is rejected
             const bool huge = group_any<G>(!(fabsf(s) < 4194304.0f), gi);
-            long long q = huge ? 0 : (f2ll_exact(s * 0x1p32f) - f2ll_exact(c * 0x1p32f));
-            q = group_sum_ll<G>(q);
+            // the lanes' compensated sums added in FP32 by a butterfly: every lane adds the same
+            // two operands at every step (a + b = b + a exactly), so all lanes of the group end
+            // with the same sum, converted once to 2^-32 fixed point
+            float lane_sum = s - c;
+#pragma unroll
+            for (int off = G / 2; off; off >>= 1) lane_sum += __shfl_xor_sync(0xffffffffu, lane_sum, off);
+            const long long q = huge ? 0 : f2ll_exact(lane_sum * 0x1p32f);
             const long long En = E + q;
             const int bn = poly_bin(En, a);
             bool acc = false;
@@ -381,12 +392,8 @@ __global__ void __launch_bounds__(kMaxSweepBlock) k_sweep_polymer(const PolyArgs
                 if (b >= 0 && b < a.B) {
                     if (bn >= 0 && bn < a.B) {
                         const long long dq = __ldg(a.lnWq + bn) - __ldg(a.lnWq + b);
-                        if (dq >= 0) {
-                            acc = true;
-                        } else {
-                            const float thr = expf(q32_to_float(dq)) * 4294967296.0f;
-                            acc = (float)u.w < thr;
-                        }
+                        // accept iff d >= 0 or ln(u 2^-32) < d (the logarithm is in u.w)
+                        acc = dq >= 0 || __uint_as_float(u.w) < q32_to_float(dq);
                     }
                 } else {
                     const long long dold = (b < 0) ? a.elo_q - E : E - a.ehi_q;
@@ -405,6 +412,13 @@ __global__ void __launch_bounds__(kMaxSweepBlock) k_sweep_polymer(const PolyArgs
                 a.trace[((size_t)w * (size_t)a.sweeps + (size_t)sw) * (size_t)N + i] = r;
             }
             if (acc) {
+                if (G == 1) {
+                    if (i > 0) eb[i - 1] = vnb[0];
+                    if (i + 1 < N) eb[i] = vnb[1];
+                } else if (li < 2) {
+                    const int jb = li == 0 ? i - 1 : i + 1;
+                    if (jb >= 0 && jb < N) eb[jb < i ? jb : i] = vnb[0];
+                }
                 if (li == 0) {
                     if (active) {
                         Xg[i] = n0;
