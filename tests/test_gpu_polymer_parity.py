@@ -278,3 +278,38 @@ def test_full_size_sampled_walkers_in_the_bench_configuration(N, calls):
           "|dE_gpu - dE_oracle| / S max %.3g" % (N, stats["compared"], stats["attempts"], stats["diverged"], r.max()))
     assert stats["compared"] > 0.5 * stats["attempts"]
     assert r.max() <= TAU
+
+
+@pytest.mark.parametrize("N,p,window,calls,floor", [
+    (2, 64, (0.0, 12.0), [60, 30, 30], 0.5),           # the dimer: one bond, no Lennard-Jones pair
+    (3, 61, (10.7, 18.7), [60, 30, 30], 0.5),          # the trimer window just above the ground state
+    # the largest window, 12288 bins: every energy of the random-walk start lies inside, so the
+    # chains stay stretched (E ~ 300, bonds near breaking, where the FENE terms' FP32 error is
+    # largest) and events, hence divergences, come sooner; a smaller share is compared
+    (13, 40, (33.3, 33.3 + 1228.8), [100, 20], 0.1),
+])
+def test_trajectories_degenerate_chains_and_the_largest_window(N, p, window, calls, floor):
+    """Same rule as above at the edges: every walker agrees up to its first disagreement, which
+    must be a flagged event."""
+    g, o, lo = _pair(N, p, 3, 0, 0, window=window)
+    assert g.B == o.B and (N != 13 or g.B == 12288)
+    alive = np.ones(p, dtype=bool)
+    stats = {"ratio": [], "energy": [], "compared": 0, "attempts": 0, "diverged": 0}
+    for k, S in enumerate(calls):
+        tg = g.iterate_traced(S)
+        to = o.iterate_traced(S, NT)
+        compare_call(tg, to, g, o, lo, alive, stats, "call %d" % k)
+        g.merge_and_update()
+        o.update()
+        g.set_lnW(o.lnW())
+    assert stats["compared"] > floor * stats["attempts"]
+    r = np.concatenate(stats["ratio"])
+    assert r.max() <= TAU
+
+
+def test_window_beyond_the_largest_is_refused():
+    g = m.Muca(m.POLYMER3D, 13, 0, 8, 1, window=(33.3, 33.3 + 1228.8))   # 12288 bins: accepted
+    assert g.B == 12288
+    with pytest.raises(m.MucaError) as e:
+        g.set_param("e_hi", 33.3 + 1228.9)                               # 12289 bins
+    assert e.value.code == -6
