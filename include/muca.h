@@ -62,7 +62,7 @@ const char *muca_last_error(void);
  * function").  L_or_N is the lattice side L (spins) or the bead count N
  * (polymer); q is the number of Potts states (ignored otherwise).
  * Spins: L in {4, 8, 12, 16, 24, 32, 48, 64}; Potts 2 <= q <= 16 (at L = 64
- * the Potts threshold table is read from global memory, see "pipeline").
+ * the Potts threshold table is split, see "pipeline").
  * Polymer: 2 <= N <= 128 beads; the walkers start as random walks of unit
  * bonds and walk into the energy window before anything is recorded.
  * The walkers' initial states are drawn from the counter-based generator
@@ -95,8 +95,11 @@ int muca_init_ex(muca_ctx **out, int system, int L_or_N, int q, int p, uint64_t 
  *                 random numbers and each site's neighbour code (Potts: also
  *                 the proposal) into a shared-memory ring; 1 does the same
  *                 with random numbers only, one producer warp; 0 runs one
- *                 warp per 32 walkers (q-Potts at L = 64 always: its table
- *                 is read from global memory).  A form that does not
+ *                 warp per 32 walkers.  q-Potts at L = 64: the code form keeps
+ *                 the upper 16 bits of its 295 KB threshold table in shared
+ *                 memory (32 walkers a block) and decides equal upper halves
+ *                 on the full words; 0 reads the full table from global
+ *                 memory.  A form that does not
  *                 fit the system, L, bin count or block falls back to the next
  *                 lower one.  Ring hand-overs are bounded waits; a wait that
  *                 gives up makes the next synchronising call return

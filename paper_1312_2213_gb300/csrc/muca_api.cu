@@ -157,8 +157,9 @@ void fill_shape(muca_ctx *c, int system, int L, int q, int p)
     // default walkers per block: 64, or 32 where only that fits the code form (e.g. q = 10 Potts,
     // L = 48, whose threshold table alone takes 184 KB of shared memory)
     if (!spin_sweep_tn_fits(system, L, c->B, 64) && spin_sweep_tn_fits(system, L, c->B, 32)) c->block = 32;
-    // the global-table Potts form (L = 64) hides more of its L2 latency with four warps a block
-    if (system == kPotts && L == 64) c->block = 128;
+    // without the code form, the global-table Potts form (L = 64) hides more of its L2 latency
+    // with four warps a block
+    if (system == kPotts && L == 64 && !spin_sweep_tn_fits(system, L, c->B, 32)) c->block = 128;
 }
 
 // Reachable bins of the periodic L x L lattice (L even): the Ising model has

@@ -456,13 +456,21 @@ __host__ __device__ constexpr int potts_part_begin(int WR, int part)
 // Philox blocks each); its old and down rows rotate through registers so that
 // word i is always element 0.  (A fully unrolled row was several times larger
 // than the instruction cache serves without fetch stalls.)
+// The split table (L = 64, see potts_split_full): the acceptance words travel as their
+// upper 16 bits, two to a 32-bit word (uint2 per 4 sites instead of uint4).
+template <int L>
+struct PottsSplit {
+    static constexpr bool on = L > 48;
+};
+
 template <int L, int RD, int PART>
 __device__ __forceinline__ void produce_sweep_potts_tn(uint32_t g, uint32_t wid, const uint32_t (&rk)[20],
                                                        const uint32_t *__restrict__ lat, int ps, uint32_t q,
-                                                       uint4 *ring_u, uint2 *ring_c, uint2 *ring_op,
+                                                       void *ring_u, uint2 *ring_c, uint2 *ring_op,
                                                        unsigned long long *full, unsigned long long *empty, int &k,
                                                        bool &bad, int drop_k)
 {
+    constexpr bool SPLIT = PottsSplit<L>::on;
     static_assert(L % 8 == 0, "whole nibble words a row");
     constexpr int WR = L / 8;
     constexpr size_t S = (size_t)(L / 4) * 32;
@@ -484,7 +492,8 @@ __device__ __forceinline__ void produce_sweep_potts_tn(uint32_t g, uint32_t wid,
 #pragma unroll
             for (int j = 0; j < WR; ++j) nn[j] = lat[(y2 * WR + j) * ps];
         }
-        uint4 *wu = ring_u + slot * S;
+        uint4 *wu = (uint4 *)ring_u + slot * S;
+        uint2 *wu16 = (uint2 *)ring_u + slot * S;
         uint2 *wc = ring_c + slot * S;
         uint2 *wop = ring_op + slot * S;
         // this producer's nibble words [i0, i1); the arrays are rotated so that word i0 is element 0
@@ -517,7 +526,10 @@ __device__ __forceinline__ void produce_sweep_potts_tn(uint32_t g, uint32_t wid,
                 const uint32_t base = (uint32_t)(y * (L / 2) + 2 * j);
                 const uint4 r0 = philox4x32_10_rk(make_uint4(base, g, wid, kTagSweep), rk);
                 const uint4 r1 = philox4x32_10_rk(make_uint4(base + 1u, g, wid, kTagSweep), rk);
-                wu[j * 32] = clamp_words(make_uint4(r0.y, r0.w, r1.y, r1.w));
+                if (SPLIT)  // upper halves only: no clamp (a tie is decided on the full words)
+                    wu16[j * 32] = make_uint2((r0.y >> 16) | (r0.w & 0xFFFF0000u), (r1.y >> 16) | (r1.w & 0xFFFF0000u));
+                else
+                    wu[j * 32] = clamp_words(make_uint4(r0.y, r0.w, r1.y, r1.w));
                 const uint32_t up4[4] = {r0.x, r0.z, r1.x, r1.z};
                 uint32_t pb = 0u;
 #pragma unroll
@@ -568,26 +580,61 @@ __device__ __forceinline__ void produce_sweep_potts_tn(uint32_t g, uint32_t wid,
 // word, which holds the last site's right-neighbour term.  The
 // final row above lives in a per-lane shared-memory row sU (bytes), rewritten
 // word by word as the current row completes.
+// The full acceptance test behind the split table: the walker's acceptance word
+// recomputed from its Philox block (block `blk` of the sweep, word y for even
+// sites and w for odd ones) against the full threshold T[bin][col] in global
+// memory.  Only lanes whose upper halves tie (probability 2^-16) call it.
+__device__ __noinline__ bool potts_split_full(const uint32_t *__restrict__ Tg, int bin, int col, uint32_t blk,
+                                              uint32_t g, uint32_t wid, uint32_t key0, uint32_t key1, int odd)
+{
+    const uint4 r = philox4x32_10(make_uint4(blk, g, wid, kTagSweep), key0, key1);
+    const uint32_t u = odd ? r.w : r.y;
+    const uint32_t T = Tg[bin * 9 + col];
+    return T == kAlways || u < T;
+}
+
+// Row layout of the Potts tables: 10 words a bin (9 thresholds, the counter), or at
+// L = 64 the split row of 6 words (9 upper halves of the thresholds, a pad halfword,
+// the counter in word 5).  Codes are scaled to byte offsets into a row (4 c, or 2 c
+// for halfword entries), and a bin move of (c - 4) rows is (cs - 4 CSC) MS bytes.
+template <int L>
+struct PottsRow {
+    static constexpr bool split = PottsSplit<L>::on;
+    static constexpr int RSW = split ? 6 : 10;  // words a row
+    static constexpr int HW = split ? 5 : 9;    // counter word
+    static constexpr int CSC = split ? 2 : 4;   // code scale
+    static constexpr int C4 = 4 * CSC;          // scaled code of dE = 0
+    static constexpr int MS = 4 * RSW / CSC;    // bytes a row per unit of scaled code
+};
+
 template <int L, int RD, int RECORD>
 __device__ __forceinline__ void potts_sweep_tc(uint32_t *__restrict__ lat, int ps, int &bR,
-                                               uint32_t *__restrict__ sTH, const uint4 *__restrict__ ring_u,
+                                               uint32_t *__restrict__ sTH, const void *__restrict__ ring_u_,
                                                const uint2 *__restrict__ ring_c, const uint2 *__restrict__ ring_op,
                                                uint32_t *__restrict__ sU, unsigned long long *full,
-                                               unsigned long long *empty, int &k, bool &bad, unsigned &nacc)
+                                               unsigned long long *empty, int &k, bool &bad, unsigned &nacc,
+                                               uint32_t g, uint32_t wid, uint32_t key0, uint32_t key1,
+                                               const uint32_t *__restrict__ Tg)
 {
     static_assert(L % 8 == 0, "whole nibble words a row");
+    using R = PottsRow<L>;
+    constexpr bool SPLIT = R::split;
     constexpr int WR = L / 8;
     constexpr int W4 = L / 4;
-    constexpr int RS = 10;
     constexpr size_t S = (size_t)W4 * 32;
+    const uint4 *ring_u = (const uint4 *)ring_u_;
+    const uint2 *ring_u16 = (const uint2 *)ring_u_;
     // byte i of a packed word (selector bytes 4 pick zeros)
     auto byte_of = [](uint32_t w, int i) -> int { return (int)__byte_perm(w, 0u, 0x4440u | (uint32_t)i); };
-    // As in the Ising consumer: 32-bit shared-window byte addresses (bB = table base + 4 RS bin,
-    // codes scaled to 4 c), clamped acceptance words, one compare.
+    // As in the Ising consumer: 32-bit shared-window byte addresses (bB = table base + 4 RSW bin,
+    // codes scaled to CSC c), clamped acceptance words, one compare (split: upper halves).
     const int sbase = (int)__cvta_generic_to_shared(sTH);
     auto th = [sbase](int addr) -> uint32_t {
         uint32_t v;
-        asm("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(checked_addr(addr, sbase)));
+        if (SPLIT)
+            asm("ld.shared.u16 %0, [%1];" : "=r"(v) : "r"(checked_addr(addr, sbase)));
+        else
+            asm("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(checked_addr(addr, sbase)));
         return v;
     };
     auto hist = [sbase](int addr) {
@@ -604,50 +651,69 @@ __device__ __forceinline__ void potts_sweep_tc(uint32_t *__restrict__ lat, int p
             continue;
         }
         const uint4 *ru = ring_u + slot * S;
+        const uint2 *ru16 = ring_u16 + slot * S;
         const uint2 *rc = ring_c + slot * S;
         const uint2 *rop = ring_op + slot * S;
+        // the acceptance words of byte word j (split: their upper halves)
+        auto words = [&](int j) -> uint4 {
+            if (SPLIT) {
+                const uint2 h = ru16[j * 32];
+                return make_uint4(h.x & 0xFFFFu, h.x >> 16, h.y & 0xFFFFu, h.y >> 16);
+            }
+            return ru[j * 32];
+        };
         // code bytes of word j with the up neighbour's term added (bytes stay in [0, 8]),
-        // scaled to byte offsets 4 c
+        // scaled to byte offsets CSC c
         auto codes = [&](int j, uint2 op, uint32_t ubw) -> uint2 {
             uint2 c = rc[j * 32];
             const uint32_t np = ne_bytes(ubw, op.y), no = ne_bytes(ubw, op.x);
-            c.x = (c.x + np - no) << 2;
-            c.y = (c.y + np - no) << 2;
+            c.x = (c.x + np - no) << (SPLIT ? 1 : 2);
+            c.y = (c.y + np - no) << (SPLIT ? 1 : 2);
             return c;
         };
         uint2 opn = rop[0];
         uint2 cdn = codes(0, opn, sU[0]);
         const int c00 = byte_of(cdn.x, 0);
         uint32_t T0 = th(bB + c00), T1 = 0u;
-        int d0 = (c00 - 16) * RS, d1 = 0;  // bin-row move (c - 4) rows, in bytes
+        int d0 = (c00 - R::C4) * R::MS, d1 = 0;  // bin-row move (c - 4) rows, in bytes
+        int nP0 = c00, nP1 = 0;                   // scaled columns of T0 / T1 (split: for a tie)
         bool accP = false;
-        // decide the current site (threshold T0 or T1 by the previous decision) and
+        // decide the current site x (threshold T0 or T1 by the previous decision) and
         // load both candidates of the next site, whose code bytes are n0 / n1
-        auto site = [&](uint32_t uw, int n0, int n1, uint32_t &am, int i) {
+        auto site = [&](uint32_t uw, int n0, int n1, uint32_t &am, int i, int x) {
             const int dR = accP ? d1 : d0;
             const uint32_t T = accP ? T1 : T0;
+            const int cP = accP ? nP1 : nP0;
             T0 = th(bB + n0);
             T1 = th(bB + dR + n1);
-            d0 = (n0 - 16) * RS;
-            d1 = (n1 - 16) * RS;
-            const bool acc = uw < T;  // the producer's clamp makes this "always or u < T"
+            d0 = (n0 - R::C4) * R::MS;
+            d1 = (n1 - R::C4) * R::MS;
+            nP0 = n0;
+            nP1 = n1;
+            bool acc = uw < T;  // the producer's clamp makes this "always or u < T"
+            if (SPLIT) {        // upper halves equal: the full words decide (rare)
+                if (uw == T)
+                    acc = potts_split_full(Tg, (bB - sbase) / (4 * R::RSW), cP / R::CSC,
+                                           (uint32_t)(y * (L / 2) + x / 2), g, wid, key0, key1, x & 1);
+            }
+            (void)cP;
             if (acc) am |= 0xffu << (8 * i);
             bB = acc ? bB + dR : bB;
-            if (RECORD == 0) hist(bB + 4 * 9);
+            if (RECORD == 0) hist(bB + 4 * R::HW);
             accP = acc;
         };
         uint32_t fprev = 0u;
 #pragma unroll 2
         for (int j = 0; j < W4 - 1; ++j) {
             const uint2 op = opn, cd = cdn;
-            const uint4 u = ru[j * 32];
+            const uint4 u = words(j);
             opn = rop[(j + 1) * 32];
             cdn = codes(j + 1, opn, sU[(j + 1) * 32]);
             uint32_t am = 0u;
-            site(u.x, byte_of(cd.x, 1), byte_of(cd.y, 1), am, 0);
-            site(u.y, byte_of(cd.x, 2), byte_of(cd.y, 2), am, 1);
-            site(u.z, byte_of(cd.x, 3), byte_of(cd.y, 3), am, 2);
-            site(u.w, byte_of(cdn.x, 0), byte_of(cdn.y, 0), am, 3);
+            site(u.x, byte_of(cd.x, 1), byte_of(cd.y, 1), am, 0, 4 * j);
+            site(u.y, byte_of(cd.x, 2), byte_of(cd.y, 2), am, 1, 4 * j + 1);
+            site(u.z, byte_of(cd.x, 3), byte_of(cd.y, 3), am, 2, 4 * j + 2);
+            site(u.w, byte_of(cdn.x, 0), byte_of(cdn.y, 0), am, 3, 4 * j + 3);
             nacc += (unsigned)__popc(am);  // 0xff per accepted site: 8 x accepted (divided at the end)
             const uint32_t f = op.x ^ ((op.x ^ op.y) & am);
             sU[j * 32] = f;
@@ -657,21 +723,26 @@ __device__ __forceinline__ void potts_sweep_tc(uint32_t *__restrict__ lat, int p
         {
             constexpr int j = W4 - 1;
             const uint2 op = opn, cd = cdn;
-            const uint4 u = ru[j * 32];
+            const uint4 u = words(j);
             uint32_t am = 0u;
-            site(u.x, byte_of(cd.x, 1), byte_of(cd.y, 1), am, 0);
-            site(u.y, byte_of(cd.x, 2), byte_of(cd.y, 2), am, 1);
+            site(u.x, byte_of(cd.x, 1), byte_of(cd.y, 1), am, 0, 4 * j);
+            site(u.y, byte_of(cd.x, 2), byte_of(cd.y, 2), am, 1, 4 * j + 1);
             // the last site's right neighbour is site 0 of this row, final by now (word 0 is in sU)
             const uint32_t f0 = sU[0] & 0xffu;
             const int t = (int)(f0 != (op.y >> 24)) - (int)(f0 != (op.x >> 24));
-            site(u.z, byte_of(cd.x, 3) + 4 * t, byte_of(cd.y, 3) + 4 * t, am, 2);
+            site(u.z, byte_of(cd.x, 3) + R::CSC * t, byte_of(cd.y, 3) + R::CSC * t, am, 2, 4 * j + 2);
             // the last site: decision only
             const int dR = accP ? d1 : d0;
             const uint32_t T = accP ? T1 : T0;
-            const bool acc = u.w < T;
+            bool acc = u.w < T;
+            if (SPLIT) {
+                if (u.w == T)
+                    acc = potts_split_full(Tg, (bB - sbase) / (4 * R::RSW), (accP ? nP1 : nP0) / R::CSC,
+                                           (uint32_t)(y * (L / 2) + (L - 1) / 2), g, wid, key0, key1, 1);
+            }
             if (acc) am |= 0xff000000u;
             bB = acc ? bB + dR : bB;
-            if (RECORD == 0) hist(bB + 4 * 9);
+            if (RECORD == 0) hist(bB + 4 * R::HW);
             accP = acc;
             nacc += (unsigned)__popc(am);
             const uint32_t f = op.x ^ ((op.x ^ op.y) & am);
@@ -683,21 +754,30 @@ __device__ __forceinline__ void potts_sweep_tc(uint32_t *__restrict__ lat, int p
     }
     bR = (bB - sbase) / 4;
     nacc >>= 3;
-    if (RECORD == 1) atomicAdd(&sTH[checked_word(bR + 9)], 1u);
+    if (RECORD == 1) atomicAdd(&sTH[checked_word(bR + R::HW)], 1u);
 }
 
-// Shared memory a consumer warp owns: RD ring rows (acceptance words 16 B,
-// codes 8 B, old/proposed bytes 8 B, per group of 4 sites and lane) and its up row.
+// Shared memory a consumer warp owns: RD ring rows (acceptance words 16 B, or their
+// upper halves 8 B at L = 64, codes 8 B, old/proposed bytes 8 B, per group of 4 sites
+// and lane) and its up row.
 __host__ __device__ constexpr size_t tnp_warp_bytes(int L, int RD)
 {
-    return (size_t)RD * (size_t)(L / 4) * 32 * (16 + 8 + 8) + (size_t)(L / 4) * 32 * 4;
+    return (size_t)RD * (size_t)(L / 4) * 32 * ((L > 48 ? 8 : 16) + 8 + 8) + (size_t)(L / 4) * 32 * 4;
+}
+
+// Bytes of the Potts threshold + counter table: 10 words a bin, or the split rows of
+// 6 words at L = 64.
+__host__ __device__ constexpr size_t tnp_table_bytes(int L, int B)
+{
+    return ((size_t)B * (L > 48 ? 24 : 40) + 15) / 16 * 16;
 }
 
 template <int L, int RD>
 __device__ __forceinline__ void sweep_block_tnp(const SpinSweepArgs &a, int w0, int slot_id, uint32_t *smem)
 {
+    using R = PottsRow<L>;
     constexpr int C = 9;
-    constexpr int RS = C + 1;
+    constexpr int RS = R::RSW;  // words a table row
     constexpr size_t S = (size_t)(L / 4) * 32;
     constexpr int NP = kPottsProducers;
     const int ncw = blockDim.x / (32 * kCodeWarpsPerWalkerWarp);
@@ -708,19 +788,28 @@ __device__ __forceinline__ void sweep_block_tnp(const SpinSweepArgs &a, int w0, 
     const int pair = role.pair, part = role.part;
     const int drop_k = (blockIdx.x == 0 && producer && pair == 0 && part == 0) ? a.debug_drop_row : -1;
     uint32_t *sTH = smem;
-    const size_t th_bytes = ((size_t)a.B * RS * 4 + 15) / 16 * 16;
+    const size_t th_bytes = tnp_table_bytes(L, a.B);
+    constexpr size_t UB = R::split ? 8 : 16;  // ring bytes of a group's acceptance words
     char *rbase = (char *)smem + th_bytes + (size_t)pair * tnp_warp_bytes(L, RD);
-    uint4 *ring_u = (uint4 *)rbase + lane;
-    uint2 *ring_c = (uint2 *)(rbase + (size_t)RD * S * 16) + lane;
-    uint2 *ring_op = (uint2 *)(rbase + (size_t)RD * S * 24) + lane;
-    uint32_t *sU = (uint32_t *)(rbase + (size_t)RD * S * 32) + lane;
+    void *ring_u = R::split ? (void *)((uint2 *)rbase + lane) : (void *)((uint4 *)rbase + lane);
+    uint2 *ring_c = (uint2 *)(rbase + (size_t)RD * S * UB) + lane;
+    uint2 *ring_op = (uint2 *)(rbase + (size_t)RD * S * (UB + 8)) + lane;
+    uint32_t *sU = (uint32_t *)(rbase + (size_t)RD * S * (UB + 16)) + lane;
     unsigned long long *bars = (unsigned long long *)((char *)smem + th_bytes + (size_t)ncw * tnp_warp_bytes(L, RD));
     unsigned long long *full = bars + (size_t)pair * 2 * RD, *empty = full + RD;
 
     const int tid = threadIdx.x;
-    for (int i = tid; i < a.B * RS; i += blockDim.x) {
-        const int b = i / RS, c = i - (i / RS) * RS;
-        sTH[i] = (c < C) ? a.T[b * C + c] : 0u;
+    if (R::split) {  // halfword rows: 9 upper halves, a pad, the counter's two halves
+        uint16_t *h = (uint16_t *)smem;
+        for (int i = tid; i < a.B * 12; i += blockDim.x) {
+            const int b = i / 12, c = i - (i / 12) * 12;
+            h[i] = (c < C) ? (uint16_t)(a.T[b * C + c] >> 16) : (uint16_t)0;
+        }
+    } else {
+        for (int i = tid; i < a.B * RS; i += blockDim.x) {
+            const int b = i / RS, c = i - (i / RS) * RS;
+            sTH[i] = (c < C) ? a.T[b * C + c] : 0u;
+        }
     }
     if (tid == 0)  // per pair: FULL[RD] (NP producer warps arrive), EMPTY[RD] (the consumer)
         for (int i = 0; i < ncw * 2 * RD; ++i) mbar_init(bars + i, ((i / RD) % 2 == 0) ? 32 * NP : 32);
@@ -766,10 +855,10 @@ __device__ __forceinline__ void sweep_block_tnp(const SpinSweepArgs &a, int w0, 
                 unsigned na = 0;
                 if (a.record == 0)
                     potts_sweep_tc<L, RD, 0>(lat, a.pstride, bR, sTH, ring_u, ring_c, ring_op, sU, full, empty, k, bad,
-                                             na);
+                                             na, g, wid, a.key0, a.key1, a.T);
                 else
                     potts_sweep_tc<L, RD, 1>(lat, a.pstride, bR, sTH, ring_u, ring_c, ring_op, sU, full, empty, k, bad,
-                                             na);
+                                             na, g, wid, a.key0, a.key1, a.T);
                 nacc += na;
                 tunnel_step(bR, r_lo, r_hi, tst, ev);
             } else if (consumer) {
@@ -784,10 +873,10 @@ __device__ __forceinline__ void sweep_block_tnp(const SpinSweepArgs &a, int w0, 
         }
         __syncthreads();
         for (int b = tid; b < a.B; b += blockDim.x) {
-            const uint32_t c = sTH[b * RS + C];
+            const uint32_t c = sTH[b * RS + R::HW];
             if (c) {
                 Hb[b] += c;
-                sTH[b * RS + C] = 0u;
+                sTH[b * RS + R::HW] = 0u;
             }
         }
         __syncthreads();
@@ -811,14 +900,14 @@ __global__ void __launch_bounds__(kMaxSweepBlock, 1) k_sweep_potts_tn(const Spin
 static size_t potts_tn_smem_bytes(int L, int RD, int B, int walkers_per_block)
 {
     const int ncw = walkers_per_block / 32;
-    return ((size_t)B * 10 * 4 + 15) / 16 * 16 + (size_t)ncw * tnp_warp_bytes(L, RD) +
+    return tnp_table_bytes(L, B) + (size_t)ncw * tnp_warp_bytes(L, RD) +
            (size_t)ncw * 2 * RD * sizeof(unsigned long long);
 }
 
 // Deepest ring (4 or 2 rows) whose block fits in shared memory; 0 if none does.
 static int potts_tn_depth(int L, int B, int walkers_per_block)
 {
-    if (L < 8 || L > 48 || L % 8 != 0 || !sweep_L_supported(L)) return 0;
+    if (L < 8 || L > 64 || L % 8 != 0 || !sweep_L_supported(L)) return 0;
     if (potts_tn_smem_bytes(L, 4, B, walkers_per_block) <= 227u * 1024u) return 4;
     if (potts_tn_smem_bytes(L, 2, B, walkers_per_block) <= 227u * 1024u) return 2;
     return 0;
@@ -881,6 +970,9 @@ static cudaError_t launch_potts_tn_rd(int L, const SpinSweepArgs &a, int block, 
     case 24: return launch_one_tnp<24, RD>(a, block, s);
     case 32: return launch_one_tnp<32, RD>(a, block, s);
     case 48: return launch_one_tnp<48, RD>(a, block, s);
+    case 64:  // the split table: only the two-row ring fits (32 walkers a block)
+        if constexpr (RD == 2) return launch_one_tnp<64, 2>(a, block, s);
+        return cudaErrorInvalidValue;
     default: return cudaErrorInvalidValue;
     }
 }

@@ -61,10 +61,13 @@ def test_flush_cap_does_not_change_results(cap):
         np.testing.assert_array_equal(a, b)
 
 
-def test_flush_in_potts_global_table_form():
-    """q-Potts at L = 64 (threshold table in global memory, histogram in shared memory)."""
+@pytest.mark.parametrize("pipeline", [2, 0])
+def test_flush_in_potts_L64_forms(pipeline):
+    """q-Potts at L = 64: the code form with the split table (upper halves and counters in shared
+    memory) and the one-warp form with the table in global memory."""
     p, S = 40, 5
     g = m.Muca(m.POTTS2D, 64, 10, p, 3)
+    g.set_param("pipeline", pipeline)
     g.set_param("flush_every", 2)
     o = oracle.Run(m.POTTS2D, 64, 10, p, 3)
     o.init()

@@ -317,10 +317,21 @@ def test_state_buffer_must_be_consistent(system, L, q, C):
 
 
 @pytest.mark.parametrize("record", [0, 1])
-def test_potts_L64_global_table_bit_exact(record):
-    """q-Potts at L = 64 (8193 bins x 9 columns, too large for shared memory) runs the one-warp
-    form with the thresholds read from the global table: bit-exact against the oracle."""
-    run_pair(m.POTTS2D, 64, 10, 40, 17, 3, 10, record=record, nthreads=NT)
+@pytest.mark.parametrize("pipeline", [2, 0])
+def test_potts_L64_bit_exact(record, pipeline):
+    """q-Potts at L = 64: 8193 bins x 9 columns of 32-bit thresholds (295 KB) do not fit a block's
+    shared memory.  The code form (pipeline 2) keeps their upper 16 bits there and decides a tie of
+    the upper halves of u and T on the full words (u recomputed from its Philox block, T read from
+    the global table); the one-warp form (pipeline 0) reads the full table from global memory.
+    Bit-exact against the oracle over 64 walkers x 3 x 10 sweeps = 7.9e6 attempts, in which about
+    120 upper-half ties occur (40 of them in the first iteration, where every threshold is
+    'always' and the fast compare alone would reject)."""
+    run_pair(m.POTTS2D, 64, 10, 64, 17, 3, 10, record=record, nthreads=NT, pipeline=pipeline)
+
+
+def test_potts_L64_q2_split_table():
+    """q = 2 at L = 64 in the code form: the odd bins are unreachable (threshold 0 into them)."""
+    run_pair(m.POTTS2D, 64, 2, 40, 5, 2, 8, nthreads=NT)
 
 
 def test_potts_L64_in_a_batch():
