@@ -74,7 +74,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sweeps", type=int, default=400, help="sweeps per system in the CPU sample")
     ap.add_argument("--no-extras", action="store_true", help="skip the batched-mix, Potts and polymer measurements")
-    ap.add_argument("--workload", default="all", choices=["all", "mix", "polymer", "potts"],
+    ap.add_argument("--workload", default="all", choices=["all", "mix", "polymer", "potts", "potts64"],
                     help="mix / polymer / potts: run only that measurement (for profiling)")
     ap.add_argument("--mode", default="shard", choices=["shard", "replicas"],
                     help="N > 1: 'shard' runs each system's walkers split over the ranks with one histogram "
@@ -201,6 +201,16 @@ def run_potts(m, torch, L=32, q=8, p=8192, sweeps=2000):
     g.close()
     att = p * sweeps * L * L
     return {"L": L, "q": q, "walkers": p, "sweeps": sweeps, "attempts_per_s": att / t, "kernel_ms": t * 1e3}
+
+
+def run_potts64(m, torch, q=10, sweeps=150):
+    """q-Potts at L = 64 (the paper's Fig. 4 lattice; the code form with the split threshold table):
+    p = 4864 (one 32-walker block an SM) and p = 8192 (two waves of blocks)."""
+    out = {"L": 64, "q": q, "sweeps": sweeps, "form": "code form, split threshold table"}
+    for p in (4864, 8192):
+        r = run_potts(m, torch, L=64, q=q, p=p, sweeps=sweeps)
+        out["p%d" % p] = {"attempts_per_s": r["attempts_per_s"], "kernel_ms": r["kernel_ms"]}
+    return out
 
 
 def run_polymer(m, torch, p=4096, budget_attempts=2.0e8):
@@ -448,6 +458,7 @@ def run_ours(args):
     if not args.no_extras:
         line["batched_mix"] = run_mix(m, torch)
         line["potts_q8_L32"] = run_potts(m, torch)
+        line["potts_q10_L64"] = run_potts64(m, torch)
         line["polymer"] = run_polymer(m, torch)
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_sample(args.cpu_sweeps, 5)
@@ -466,7 +477,8 @@ def main():
         import paper_1312_2213_gb300 as m
 
         m.load()
-        res = {"mix": run_mix, "polymer": run_polymer, "potts": run_potts}[args.workload](m, torch)
+        res = {"mix": run_mix, "polymer": run_polymer, "potts": run_potts,
+               "potts64": run_potts64}[args.workload](m, torch)
         print(json.dumps({"workload": args.workload, **res}), flush=True)
     else:
         run_ours(args)
