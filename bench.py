@@ -204,10 +204,10 @@ def run_potts(m, torch, L=32, q=8, p=8192, sweeps=2000):
 
 
 def run_potts64(m, torch, q=10, sweeps=150):
-    """q-Potts at L = 64 (the paper's Fig. 4 lattice; the code form with the split threshold table):
-    p = 4864 (one 32-walker block an SM) and p = 8192 (two waves of blocks)."""
+    """q-Potts at L = 64 (the paper's Fig. 4 lattice; the code form with the split threshold table,
+    64 walkers a block): p = 8192 and p = 9728 (one block on each of the 152 SMs)."""
     out = {"L": 64, "q": q, "sweeps": sweeps, "form": "code form, split threshold table"}
-    for p in (4864, 8192):
+    for p in (8192, 9728):
         r = run_potts(m, torch, L=64, q=q, p=p, sweeps=sweeps)
         out["p%d" % p] = {"attempts_per_s": r["attempts_per_s"], "kernel_ms": r["kernel_ms"]}
     return out

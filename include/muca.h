@@ -97,9 +97,9 @@ int muca_init_ex(muca_ctx **out, int system, int L_or_N, int q, int p, uint64_t 
  *                 with random numbers only, one producer warp; 0 runs one
  *                 warp per 32 walkers.  q-Potts at L = 64: the code form keeps
  *                 the upper 16 bits of its 295 KB threshold table in shared
- *                 memory (32 walkers a block) and decides equal upper halves
- *                 on the full words; 0 reads the full table from global
- *                 memory.  A form that does not
+ *                 memory beside 16-bit visit counters (64 walkers a block)
+ *                 and decides equal upper halves on the full words; 0 reads
+ *                 the full table from global memory.  A form that does not
  *                 fit the system, L, bin count or block falls back to the next
  *                 lower one.  Ring hand-overs are bounded waits; a wait that
  *                 gives up makes the next synchronising call return

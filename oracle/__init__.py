@@ -60,6 +60,7 @@ def lib():
                 getattr(L, name).argtypes = [ctypes.c_void_p]
                 getattr(L, name).restype = ctypes.c_int
             L.orc_set_recursion.argtypes = [ctypes.c_void_p, ctypes.c_int]
+            L.orc_set_lnW.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
             L.orc_set_observables.argtypes = [ctypes.c_void_p, ctypes.c_int]
             L.orc_get_observables.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
             L.orc_reweight_obs.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
@@ -194,6 +195,12 @@ class Run:
 
     def update(self):
         self._lib.orc_update(self.h)
+
+    def set_lnW(self, lnW):
+        """Run on at fixed weights: ln W of the reachable bins, -inf elsewhere; thresholds rebuilt."""
+        w = np.ascontiguousarray(lnW, dtype=np.float64)
+        assert w.shape == (self.B,)
+        self._lib.orc_set_lnW(self.h, _ptr(w))
 
     def observable_sums(self) -> np.ndarray:
         """Per-bin sums (samples, |M|, M^2) of the last update, shape (B, 3)."""

@@ -532,6 +532,11 @@ void orc_set_open_histogram(orc_run *r, const uint64_t *H) { memcpy(r->H_open, H
 void orc_get_open_histogram(const orc_run *r, uint64_t *out) { memcpy(out, r->H_open, sizeof(uint64_t) * r->B); }
 
 void orc_set_recursion(orc_run *r, int mode) { r->recursion = mode; }
+void orc_set_lnW(orc_run *r, const double *lnW)
+{
+    for (int b = 0; b < r->B; ++b) r->lnW[b] = r->reach[b] ? lnW[b] : -INFINITY;
+    orc_build_thresholds(r);
+}
 void orc_set_observables(orc_run *r, int on) { r->observables = on; }
 void orc_get_observables(const orc_run *r, uint64_t *out) { memcpy(out, r->O_last, sizeof(uint64_t) * 3 * r->B); }
 

@@ -55,6 +55,9 @@ void orc_update(orc_run *r);
 /* Select the weight update: 0 = accumulated statistics (R5, default),
  * 1 = the plain W/H rule (R5'). */
 void orc_set_recursion(orc_run *r, int mode);
+/* Fixed weights (a production run at given ln W, Eq. 1): ln W of the reachable bins
+ * from lnW[B], -inf elsewhere, then the thresholds (a6). */
+void orc_set_lnW(orc_run *r, const double *lnW);
 /* Observables (Ising, reading R9): per-sweep sums of 1, |M|, M^2 per bin. */
 void orc_set_observables(orc_run *r, int on);
 void orc_get_observables(const orc_run *r, uint64_t *out); /* 3*B, last update */

@@ -37,6 +37,20 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1
     return c;
 }
 
+// Same function as a rolled loop: small code for a rarely taken path.
+__device__ __forceinline__ uint4 philox4x32_10_rolled(uint4 c, uint32_t k0, uint32_t k1)
+{
+#pragma unroll 1
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t hi0 = __umulhi(kPhiloxM0, c.x), lo0 = kPhiloxM0 * c.x;
+        const uint32_t hi1 = __umulhi(kPhiloxM1, c.z), lo1 = kPhiloxM1 * c.z;
+        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+        k0 += kPhiloxW0;
+        k1 += kPhiloxW1;
+    }
+    return c;
+}
+
 // Same function with the ten round keys precomputed (rk[2r], rk[2r+1] = key of round r);
 // when rk lives in the kernel parameters each round reads its key straight from the
 // constant bank.

@@ -463,14 +463,57 @@ struct PottsSplit {
     static constexpr bool on = L > 48;
 };
 
+// The 16-bit stand-ins of the split table.  A threshold T keeps 0xFFFF only for "always"
+// and min(T >> 16, 0xFFFE) otherwise; a random word u travels as min(u >> 16, 0xFFFE).  Then
+// the upper halves decide exactly wherever they differ (u < T when the half of u is the
+// smaller, u >= T when it is the larger, u < T whenever T is "always"), and only equal
+// halves -- never with T "always" -- need the full words.
+__host__ __device__ __forceinline__ uint16_t split_hi(uint32_t T)
+{
+    return T == kAlways ? (uint16_t)0xFFFFu : (uint16_t)((T >> 16) < 0xFFFEu ? (T >> 16) : 0xFFFEu);
+}
+
+// The split table's 16-bit counters, emptied into the block's 64-bit slot: every bin's
+// count is taken and cleared with one atomic AND while the consumers keep counting.
+// Producer part 1 of every consumer warp scans all bins after every F-th row it hands
+// over.  Having produced row k it knows its consumer has finished row k - RD, so the
+// consumer counts at most F + RD rows between two scans, and F + RD <= 2^16 / (32 L x
+// consumer warps) keeps every counter below 2^16.  Words are read eight at a time so the
+// loads overlap; the AND runs only where a count is not zero.
+template <int RS>
+__device__ __forceinline__ void split_scan(const uint32_t *sTH, unsigned long long *Hb, int B, int lane)
+{
+    const int sbase = (int)__cvta_generic_to_shared(sTH);
+    for (int b0 = lane; b0 < B; b0 += 8 * 32) {
+        uint32_t w[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const int b = b0 + 32 * i;
+            w[i] = 0u;
+            if (b < B)
+                asm volatile("ld.shared.u32 %0, [%1];" : "=r"(w[i]) : "r"(checked_addr(sbase + 4 * (b * RS + RS - 1), sbase)));
+        }
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const int b = b0 + 32 * i;
+            if (w[i] >> 16) {
+                const uint32_t old = atomicAnd(const_cast<uint32_t *>(&sTH[b * RS + RS - 1]), 0xFFFFu);
+                atomicAdd(&Hb[b], (unsigned long long)(old >> 16));
+            }
+        }
+    }
+}
+
 template <int L, int RD, int PART>
 __device__ __forceinline__ void produce_sweep_potts_tn(uint32_t g, uint32_t wid, const uint32_t (&rk)[20],
                                                        const uint32_t *__restrict__ lat, int ps, uint32_t q,
                                                        void *ring_u, uint2 *ring_c, uint2 *ring_op,
                                                        unsigned long long *full, unsigned long long *empty, int &k,
-                                                       bool &bad, int drop_k)
+                                                       bool &bad, int drop_k, const uint32_t *sTH, unsigned long long *Hb,
+                                                       int B, int F, int &since)
 {
     constexpr bool SPLIT = PottsSplit<L>::on;
+    constexpr int RSW = SPLIT ? 5 : 10;
     static_assert(L % 8 == 0, "whole nibble words a row");
     constexpr int WR = L / 8;
     constexpr size_t S = (size_t)(L / 4) * 32;
@@ -526,8 +569,9 @@ __device__ __forceinline__ void produce_sweep_potts_tn(uint32_t g, uint32_t wid,
                 const uint32_t base = (uint32_t)(y * (L / 2) + 2 * j);
                 const uint4 r0 = philox4x32_10_rk(make_uint4(base, g, wid, kTagSweep), rk);
                 const uint4 r1 = philox4x32_10_rk(make_uint4(base + 1u, g, wid, kTagSweep), rk);
-                if (SPLIT)  // upper halves only: no clamp (a tie is decided on the full words)
-                    wu16[j * 32] = make_uint2((r0.y >> 16) | (r0.w & 0xFFFF0000u), (r1.y >> 16) | (r1.w & 0xFFFF0000u));
+                if (SPLIT)  // upper halves, clamped to 0xFFFE (split_hi)
+                    wu16[j * 32] = make_uint2(__vminu2((r0.y >> 16) | (r0.w & 0xFFFF0000u), 0xFFFEFFFEu),
+                                              __vminu2((r1.y >> 16) | (r1.w & 0xFFFF0000u), 0xFFFEFFFEu));
                 else
                     wu[j * 32] = clamp_words(make_uint4(r0.y, r0.w, r1.y, r1.w));
                 const uint32_t up4[4] = {r0.x, r0.z, r1.x, r1.z};
@@ -566,6 +610,10 @@ __device__ __forceinline__ void produce_sweep_potts_tn(uint32_t g, uint32_t wid,
         }
         if (k != drop_k) mbar_arrive(&full[slot]);
         ++k;
+        if (SPLIT && PART == 1 && ++since == F) {  // empty the 16-bit counters (split_scan)
+            since = 0;
+            split_scan<RSW>(sTH, Hb, B, (int)(threadIdx.x & 31));
+        }
 #pragma unroll
         for (int j = 0; j < WR; ++j) {
             o[j] = d[j];
@@ -574,39 +622,127 @@ __device__ __forceinline__ void produce_sweep_potts_tn(uint32_t g, uint32_t wid,
     }
 }
 
-// The consumer runs a loop over the row's byte words (4 sites each), unrolled
-// by two (rolled it lost 16-20 % to loop overhead between the words' chains;
-// fully unrolled, L = 48 stalled on instruction fetch), and peels the last
-// word, which holds the last site's right-neighbour term.  The
-// final row above lives in a per-lane shared-memory row sU (bytes), rewritten
-// word by word as the current row completes.
 // The full acceptance test behind the split table: the walker's acceptance word
 // recomputed from its Philox block (block `blk` of the sweep, word y for even
 // sites and w for odd ones) against the full threshold T[bin][col] in global
-// memory.  Only lanes whose upper halves tie (probability 2^-16) call it.
-__device__ __noinline__ bool potts_split_full(const uint32_t *__restrict__ Tg, int bin, int col, uint32_t blk,
-                                              uint32_t g, uint32_t wid, uint32_t key0, uint32_t key1, int odd)
+// memory.  Only the row redo (potts_redo_row) calls it, for sites whose upper halves tie.
+__device__ __forceinline__ bool potts_split_full(const uint32_t *__restrict__ Tg, int bin, int col, uint32_t blk,
+                                                uint32_t g, uint32_t wid, uint32_t key0, uint32_t key1, int odd)
 {
-    const uint4 r = philox4x32_10(make_uint4(blk, g, wid, kTagSweep), key0, key1);
+    const uint4 r = philox4x32_10_rolled(make_uint4(blk, g, wid, kTagSweep), key0, key1);
     const uint32_t u = odd ? r.w : r.y;
     const uint32_t T = Tg[bin * 9 + col];
     return T == kAlways || u < T;
 }
 
 // Row layout of the Potts tables: 10 words a bin (9 thresholds, the counter), or at
-// L = 64 the split row of 6 words (9 upper halves of the thresholds, a pad halfword,
-// the counter in word 5).  Codes are scaled to byte offsets into a row (4 c, or 2 c
-// for halfword entries), and a bin move of (c - 4) rows is (cs - 4 CSC) MS bytes.
+// L = 64 the split row of 5 words: the 9 upper halves of the thresholds and a 16-bit
+// counter, the high half of word 4 (whose low half is column 8).  A visit adds 2^16 to
+// word 4, so column 8 never changes; a producer warp empties the 16-bit counters every
+// few rows (split_scan) before they can wrap.  Codes are scaled to byte offsets into a
+// row (4 c, or 2 c for halfword entries), and a bin move of (c - 4) rows is
+// (cs - 4 CSC) MS bytes.
 template <int L>
 struct PottsRow {
     static constexpr bool split = PottsSplit<L>::on;
-    static constexpr int RSW = split ? 6 : 10;  // words a row
-    static constexpr int HW = split ? 5 : 9;    // counter word
-    static constexpr int CSC = split ? 2 : 4;   // code scale
-    static constexpr int C4 = 4 * CSC;          // scaled code of dE = 0
-    static constexpr int MS = 4 * RSW / CSC;    // bytes a row per unit of scaled code
+    static constexpr int RSW = split ? 5 : 10;             // words a row
+    static constexpr int HW = split ? 4 : 9;               // counter word
+    static constexpr uint32_t ONE = split ? 0x10000u : 1u;  // one visit
+    static constexpr int CSH = split ? 16 : 0;             // counter shift in its word
+    static constexpr int CSC = split ? 2 : 4;              // code scale
+    static constexpr int C4 = 4 * CSC;                     // scaled code of dE = 0
+    static constexpr int MS = 4 * RSW / CSC;               // bytes a row per unit of scaled code
 };
 
+// The row redo behind the split table.  The consumer's pass decides every site on the
+// 16-bit stand-ins alone (split_hi), a tie (probability 2^-16 where the threshold is not
+// "always") counting as a rejection, and only notes that the row had one.  A lane whose row had a tie then replays the row from its start
+// along two trajectories at once: the pass's own (its visits are taken back out of the
+// block's 64-bit histogram slot) and the exact one, on which a tie is decided on the full
+// words (potts_split_full) and whose visits are added to the slot.  The exact trajectory
+// rewrites the row (lattice and up row), the bin and the acceptance count, before the
+// ring slot is released.  Up to the first tie the two trajectories coincide.
+template <int L>
+__device__ __forceinline__ void potts_redo_row(uint32_t *__restrict__ lat, int ps, int y, int sbase, int b0, int &bB,
+                                            const uint2 *__restrict__ ru16, const uint2 *__restrict__ rc,
+                                            const uint2 *__restrict__ rop, const uint32_t *__restrict__ uOld,
+                                            uint32_t *__restrict__ uNew, unsigned long long *Hb, int record,
+                                            unsigned &nacc, uint32_t g, uint32_t wid, uint32_t key0, uint32_t key1,
+                                            const uint32_t *__restrict__ Tg)
+{
+    using R = PottsRow<L>;
+    constexpr int W4 = L / 4, WR = L / 8;
+    auto th = [sbase](int addr) -> uint32_t {
+        uint32_t v;
+        asm volatile("ld.shared.u16 %0, [%1];" : "=r"(v) : "r"(checked_addr(addr, sbase)));
+        return v;
+    };
+    int bw = b0, br = b0;    // byte addresses of the bins: the pass's trajectory, the exact one
+    bool pw = false, pr = false;  // the left neighbour's decision on each
+    uint32_t f0w = 0u, f0r = 0u, fprev = 0u;
+    unsigned naw = 0u, nar = 0u;
+#pragma unroll 1
+    for (int j = 0; j < W4; ++j) {
+        const uint2 op = rop[j * 32];
+        const uint32_t ubw = uOld[j * 32];
+        const uint32_t np = ne_bytes(ubw, op.y), no = ne_bytes(ubw, op.x);
+        const uint32_t cx = (rc[j * 32].x + np - no) << 1, cy = (rc[j * 32].y + np - no) << 1;
+        const uint2 h = ru16[j * 32];
+        uint32_t amw = 0u, amr = 0u;
+#pragma unroll 1
+        for (int i = 0; i < 4; ++i) {
+            const int x = 4 * j + i;
+            const uint32_t uw = ((i < 2 ? h.x : h.y) >> (16 * (i & 1))) & 0xFFFFu;
+            int cw = (int)(((pw ? cy : cx) >> (8 * i)) & 0xffu);
+            int cr = (int)(((pr ? cy : cx) >> (8 * i)) & 0xffu);
+            if (x == L - 1) {  // right neighbour: site 0 of this row, final on each trajectory
+                cw += R::CSC * ((int)(f0w != (op.y >> 24)) - (int)(f0w != (op.x >> 24)));
+                cr += R::CSC * ((int)(f0r != (op.y >> 24)) - (int)(f0r != (op.x >> 24)));
+            }
+            const bool aw = uw < th(bw + cw);
+            const uint32_t Tr = th(br + cr);
+            bool ar = uw < Tr;
+            if (uw == Tr)
+                ar = potts_split_full(Tg, (br - sbase) / (4 * R::RSW), cr / R::CSC, (uint32_t)(y * (L / 2) + x / 2), g,
+                                      wid, key0, key1, x & 1);
+            if (aw) {
+                bw += (cw - R::C4) * R::MS;
+                amw |= 0xffu << (8 * i);
+            }
+            if (ar) {
+                br += (cr - R::C4) * R::MS;
+                amr |= 0xffu << (8 * i);
+            }
+            if (record == 0) {
+                atomicAdd(&Hb[(bw - sbase) / (4 * R::RSW)], ~0ull);  // minus one: the pass counted it
+                atomicAdd(&Hb[(br - sbase) / (4 * R::RSW)], 1ull);
+            }
+            pw = aw;
+            pr = ar;
+        }
+        naw += (unsigned)__popc(amw);
+        nar += (unsigned)__popc(amr);
+        const uint32_t fr = op.x ^ ((op.x ^ op.y) & amr);
+        if (j == 0) {
+            f0r = fr & 0xffu;
+            f0w = (op.x ^ ((op.x ^ op.y) & amw)) & 0xffu;
+        }
+        uNew[j * 32] = fr;
+        if (j & 1) lat[(y * WR + (j >> 1)) * ps] = bytes_to_nibs(fprev, fr);
+        fprev = fr;
+    }
+    bB = br;
+    nacc += nar - naw;  // modulo 2^32, like the count itself
+}
+
+// The consumer runs a loop over the row's byte words (4 sites each), unrolled
+// by two (rolled it lost 16-20 % to loop overhead between the words' chains;
+// fully unrolled, L = 48 stalled on instruction fetch), and peels the last
+// word, which holds the last site's right-neighbour term.  The final row above
+// lives in a per-lane shared-memory row (bytes).  With the split table there are
+// two such rows, read and written in turn (the row being decided reads one and
+// writes the other), so that a redo still has the row above; otherwise one row
+// is rewritten word by word as the current row completes.
 template <int L, int RD, int RECORD>
 __device__ __forceinline__ void potts_sweep_tc(uint32_t *__restrict__ lat, int ps, int &bR,
                                                uint32_t *__restrict__ sTH, const void *__restrict__ ring_u_,
@@ -614,7 +750,7 @@ __device__ __forceinline__ void potts_sweep_tc(uint32_t *__restrict__ lat, int p
                                                uint32_t *__restrict__ sU, unsigned long long *full,
                                                unsigned long long *empty, int &k, bool &bad, unsigned &nacc,
                                                uint32_t g, uint32_t wid, uint32_t key0, uint32_t key1,
-                                               const uint32_t *__restrict__ Tg)
+                                               const uint32_t *__restrict__ Tg, unsigned long long *Hb)
 {
     static_assert(L % 8 == 0, "whole nibble words a row");
     using R = PottsRow<L>;
@@ -622,6 +758,7 @@ __device__ __forceinline__ void potts_sweep_tc(uint32_t *__restrict__ lat, int p
     constexpr int WR = L / 8;
     constexpr int W4 = L / 4;
     constexpr size_t S = (size_t)W4 * 32;
+    static_assert(!SPLIT || L % 2 == 0, "the up rows alternate: row L - 1 must leave its values in the first");
     const uint4 *ring_u = (const uint4 *)ring_u_;
     const uint2 *ring_u16 = (const uint2 *)ring_u_;
     // byte i of a packed word (selector bytes 4 pick zeros)
@@ -638,7 +775,7 @@ __device__ __forceinline__ void potts_sweep_tc(uint32_t *__restrict__ lat, int p
         return v;
     };
     auto hist = [sbase](int addr) {
-        asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(checked_addr(addr, sbase)), "r"(1u) : "memory");
+        asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(checked_addr(addr, sbase)), "r"(R::ONE) : "memory");
     };
     int bB = sbase + bR * 4;
 #pragma unroll 1
@@ -654,6 +791,10 @@ __device__ __forceinline__ void potts_sweep_tc(uint32_t *__restrict__ lat, int p
         const uint2 *ru16 = ring_u16 + slot * S;
         const uint2 *rc = ring_c + slot * S;
         const uint2 *rop = ring_op + slot * S;
+        const uint32_t *uOld = (SPLIT && (y & 1)) ? sU + S : sU;  // the row above
+        uint32_t *uNew = (SPLIT && !(y & 1)) ? sU + S : sU;       // this row, as it is decided
+        const int b0 = bB;
+        bool tie = false;
         // the acceptance words of byte word j (split: their upper halves)
         auto words = [&](int j) -> uint4 {
             if (SPLIT) {
@@ -672,31 +813,22 @@ __device__ __forceinline__ void potts_sweep_tc(uint32_t *__restrict__ lat, int p
             return c;
         };
         uint2 opn = rop[0];
-        uint2 cdn = codes(0, opn, sU[0]);
+        uint2 cdn = codes(0, opn, uOld[0]);
         const int c00 = byte_of(cdn.x, 0);
         uint32_t T0 = th(bB + c00), T1 = 0u;
         int d0 = (c00 - R::C4) * R::MS, d1 = 0;  // bin-row move (c - 4) rows, in bytes
-        int nP0 = c00, nP1 = 0;                   // scaled columns of T0 / T1 (split: for a tie)
         bool accP = false;
-        // decide the current site x (threshold T0 or T1 by the previous decision) and
+        // decide the current site (threshold T0 or T1 by the previous decision) and
         // load both candidates of the next site, whose code bytes are n0 / n1
-        auto site = [&](uint32_t uw, int n0, int n1, uint32_t &am, int i, int x) {
+        auto site = [&](uint32_t uw, int n0, int n1, uint32_t &am, int i) {
             const int dR = accP ? d1 : d0;
             const uint32_t T = accP ? T1 : T0;
-            const int cP = accP ? nP1 : nP0;
             T0 = th(bB + n0);
             T1 = th(bB + dR + n1);
             d0 = (n0 - R::C4) * R::MS;
             d1 = (n1 - R::C4) * R::MS;
-            nP0 = n0;
-            nP1 = n1;
-            bool acc = uw < T;  // the producer's clamp makes this "always or u < T"
-            if (SPLIT) {        // upper halves equal: the full words decide (rare)
-                if (uw == T)
-                    acc = potts_split_full(Tg, (bB - sbase) / (4 * R::RSW), cP / R::CSC,
-                                           (uint32_t)(y * (L / 2) + x / 2), g, wid, key0, key1, x & 1);
-            }
-            (void)cP;
+            const bool acc = uw < T;  // the producer's clamp makes this "always or u < T"
+            if (SPLIT) tie |= uw == T;  // upper halves equal: the row is redone (potts_redo_row)
             if (acc) am |= 0xffu << (8 * i);
             bB = acc ? bB + dR : bB;
             if (RECORD == 0) hist(bB + 4 * R::HW);
@@ -708,15 +840,15 @@ __device__ __forceinline__ void potts_sweep_tc(uint32_t *__restrict__ lat, int p
             const uint2 op = opn, cd = cdn;
             const uint4 u = words(j);
             opn = rop[(j + 1) * 32];
-            cdn = codes(j + 1, opn, sU[(j + 1) * 32]);
+            cdn = codes(j + 1, opn, uOld[(j + 1) * 32]);
             uint32_t am = 0u;
-            site(u.x, byte_of(cd.x, 1), byte_of(cd.y, 1), am, 0, 4 * j);
-            site(u.y, byte_of(cd.x, 2), byte_of(cd.y, 2), am, 1, 4 * j + 1);
-            site(u.z, byte_of(cd.x, 3), byte_of(cd.y, 3), am, 2, 4 * j + 2);
-            site(u.w, byte_of(cdn.x, 0), byte_of(cdn.y, 0), am, 3, 4 * j + 3);
+            site(u.x, byte_of(cd.x, 1), byte_of(cd.y, 1), am, 0);
+            site(u.y, byte_of(cd.x, 2), byte_of(cd.y, 2), am, 1);
+            site(u.z, byte_of(cd.x, 3), byte_of(cd.y, 3), am, 2);
+            site(u.w, byte_of(cdn.x, 0), byte_of(cdn.y, 0), am, 3);
             nacc += (unsigned)__popc(am);  // 0xff per accepted site: 8 x accepted (divided at the end)
             const uint32_t f = op.x ^ ((op.x ^ op.y) & am);
-            sU[j * 32] = f;
+            uNew[j * 32] = f;
             if (j & 1) lat[(y * WR + (j >> 1)) * ps] = bytes_to_nibs(fprev, f);
             fprev = f;
         }
@@ -725,51 +857,49 @@ __device__ __forceinline__ void potts_sweep_tc(uint32_t *__restrict__ lat, int p
             const uint2 op = opn, cd = cdn;
             const uint4 u = words(j);
             uint32_t am = 0u;
-            site(u.x, byte_of(cd.x, 1), byte_of(cd.y, 1), am, 0, 4 * j);
-            site(u.y, byte_of(cd.x, 2), byte_of(cd.y, 2), am, 1, 4 * j + 1);
-            // the last site's right neighbour is site 0 of this row, final by now (word 0 is in sU)
-            const uint32_t f0 = sU[0] & 0xffu;
+            site(u.x, byte_of(cd.x, 1), byte_of(cd.y, 1), am, 0);
+            site(u.y, byte_of(cd.x, 2), byte_of(cd.y, 2), am, 1);
+            // the last site's right neighbour is site 0 of this row, final by now (word 0 is written)
+            const uint32_t f0 = uNew[0] & 0xffu;
             const int t = (int)(f0 != (op.y >> 24)) - (int)(f0 != (op.x >> 24));
-            site(u.z, byte_of(cd.x, 3) + R::CSC * t, byte_of(cd.y, 3) + R::CSC * t, am, 2, 4 * j + 2);
+            site(u.z, byte_of(cd.x, 3) + R::CSC * t, byte_of(cd.y, 3) + R::CSC * t, am, 2);
             // the last site: decision only
             const int dR = accP ? d1 : d0;
             const uint32_t T = accP ? T1 : T0;
-            bool acc = u.w < T;
-            if (SPLIT) {
-                if (u.w == T)
-                    acc = potts_split_full(Tg, (bB - sbase) / (4 * R::RSW), (accP ? nP1 : nP0) / R::CSC,
-                                           (uint32_t)(y * (L / 2) + (L - 1) / 2), g, wid, key0, key1, 1);
-            }
+            const bool acc = u.w < T;
+            if (SPLIT) tie |= u.w == T;
             if (acc) am |= 0xff000000u;
             bB = acc ? bB + dR : bB;
             if (RECORD == 0) hist(bB + 4 * R::HW);
-            accP = acc;
             nacc += (unsigned)__popc(am);
             const uint32_t f = op.x ^ ((op.x ^ op.y) & am);
-            sU[j * 32] = f;
+            uNew[j * 32] = f;
             lat[(y * WR + WR - 1) * ps] = bytes_to_nibs(fprev, f);
         }
+        if (SPLIT && tie)
+            potts_redo_row<L>(lat, ps, y, sbase, b0, bB, ru16, rc, rop, uOld, uNew, Hb, RECORD, nacc, g, wid, key0,
+                              key1, Tg);
         mbar_arrive(&empty[slot]);  // after the row is stored: the producer reads it later
         ++k;
     }
     bR = (bB - sbase) / 4;
     nacc >>= 3;
-    if (RECORD == 1) atomicAdd(&sTH[checked_word(bR + R::HW)], 1u);
+    if (RECORD == 1) atomicAdd(&sTH[checked_word(bR + R::HW)], R::ONE);
 }
 
 // Shared memory a consumer warp owns: RD ring rows (acceptance words 16 B, or their
 // upper halves 8 B at L = 64, codes 8 B, old/proposed bytes 8 B, per group of 4 sites
-// and lane) and its up row.
+// and lane) and its up row (two at L = 64).
 __host__ __device__ constexpr size_t tnp_warp_bytes(int L, int RD)
 {
-    return (size_t)RD * (size_t)(L / 4) * 32 * ((L > 48 ? 8 : 16) + 8 + 8) + (size_t)(L / 4) * 32 * 4;
+    return (size_t)RD * (size_t)(L / 4) * 32 * ((L > 48 ? 8 : 16) + 8 + 8) + (size_t)(L > 48 ? 2 : 1) * (L / 4) * 32 * 4;
 }
 
 // Bytes of the Potts threshold + counter table: 10 words a bin, or the split rows of
-// 6 words at L = 64.
+// 5 words at L = 64.
 __host__ __device__ constexpr size_t tnp_table_bytes(int L, int B)
 {
-    return ((size_t)B * (L > 48 ? 24 : 40) + 15) / 16 * 16;
+    return ((size_t)B * (L > 48 ? 20 : 40) + 15) / 16 * 16;
 }
 
 template <int L, int RD>
@@ -799,11 +929,11 @@ __device__ __forceinline__ void sweep_block_tnp(const SpinSweepArgs &a, int w0, 
     unsigned long long *full = bars + (size_t)pair * 2 * RD, *empty = full + RD;
 
     const int tid = threadIdx.x;
-    if (R::split) {  // halfword rows: 9 upper halves, a pad, the counter's two halves
+    if (R::split) {  // halfword rows: 9 upper halves (split_hi), the 16-bit counter
         uint16_t *h = (uint16_t *)smem;
-        for (int i = tid; i < a.B * 12; i += blockDim.x) {
-            const int b = i / 12, c = i - (i / 12) * 12;
-            h[i] = (c < C) ? (uint16_t)(a.T[b * C + c] >> 16) : (uint16_t)0;
+        for (int i = tid; i < a.B * 10; i += blockDim.x) {
+            const int b = i / 10, c = i - (i / 10) * 10;
+            h[i] = (c < C) ? split_hi(a.T[b * C + c]) : (uint16_t)0;
         }
     } else {
         for (int i = tid; i < a.B * RS; i += blockDim.x) {
@@ -830,6 +960,9 @@ __device__ __forceinline__ void sweep_block_tnp(const SpinSweepArgs &a, int w0, 
     int tst = (consumer && active && a.tun) ? a.tun[w] : 0;
     unsigned ev = 0;
     unsigned long long nacc = 0;
+    // rows between two scans of the split table's 16-bit counters (split_scan)
+    const int F = R::split ? 65535 / (ncw * 32 * L) - RD : 0;
+    int since = 0;
     if (consumer && active) {  // the row above row 0: row L-1 as the previous launch left it
         constexpr int WR = L / 8;
 #pragma unroll
@@ -844,21 +977,21 @@ __device__ __forceinline__ void sweep_block_tnp(const SpinSweepArgs &a, int w0, 
             if (producer) {
                 if (part == 0)
                     produce_sweep_potts_tn<L, RD, 0>(g, wid, a.rk, lat, a.pstride, (uint32_t)a.q, ring_u, ring_c,
-                                                     ring_op, full, empty, k, bad, drop_k);
+                                                     ring_op, full, empty, k, bad, drop_k, sTH, Hb, a.B, F, since);
                 else if (part == 1)
                     produce_sweep_potts_tn<L, RD, 1>(g, wid, a.rk, lat, a.pstride, (uint32_t)a.q, ring_u, ring_c,
-                                                     ring_op, full, empty, k, bad, -1);
+                                                     ring_op, full, empty, k, bad, -1, sTH, Hb, a.B, F, since);
                 else
                     produce_sweep_potts_tn<L, RD, 2>(g, wid, a.rk, lat, a.pstride, (uint32_t)a.q, ring_u, ring_c,
-                                                     ring_op, full, empty, k, bad, -1);
+                                                     ring_op, full, empty, k, bad, -1, sTH, Hb, a.B, F, since);
             } else if (consumer && active) {
                 unsigned na = 0;
                 if (a.record == 0)
                     potts_sweep_tc<L, RD, 0>(lat, a.pstride, bR, sTH, ring_u, ring_c, ring_op, sU, full, empty, k, bad,
-                                             na, g, wid, a.key0, a.key1, a.T);
+                                             na, g, wid, a.key0, a.key1, a.T, Hb);
                 else
                     potts_sweep_tc<L, RD, 1>(lat, a.pstride, bR, sTH, ring_u, ring_c, ring_op, sU, full, empty, k, bad,
-                                             na, g, wid, a.key0, a.key1, a.T);
+                                             na, g, wid, a.key0, a.key1, a.T, Hb);
                 nacc += na;
                 tunnel_step(bR, r_lo, r_hi, tst, ev);
             } else if (consumer) {
@@ -873,10 +1006,10 @@ __device__ __forceinline__ void sweep_block_tnp(const SpinSweepArgs &a, int w0, 
         }
         __syncthreads();
         for (int b = tid; b < a.B; b += blockDim.x) {
-            const uint32_t c = sTH[b * RS + R::HW];
+            const uint32_t c = sTH[b * RS + R::HW] >> R::CSH;
             if (c) {
                 Hb[b] += c;
-                sTH[b * RS + R::HW] = 0u;
+                sTH[b * RS + R::HW] -= c << R::CSH;
             }
         }
         __syncthreads();
@@ -891,7 +1024,9 @@ __device__ __forceinline__ void sweep_block_tnp(const SpinSweepArgs &a, int w0, 
 }
 
 template <int L, int RD>
-__global__ void __launch_bounds__(kMaxSweepBlock, 1) k_sweep_potts_tn(const SpinSweepArgs a)
+// At most 64 walkers (256 threads) a block: the L = 48 and 64 forms need more than the 128
+// registers a thread that 512-thread blocks would leave.
+__global__ void __launch_bounds__(kCodeWarpsPerWalkerWarp * 64, 1) k_sweep_potts_tn(const SpinSweepArgs a)
 {
     extern __shared__ __align__(16) uint32_t smem[];
     sweep_block_tnp<L, RD>(a, blockIdx.x * (blockDim.x / kCodeWarpsPerWalkerWarp), blockIdx.x, smem);
@@ -908,7 +1043,9 @@ static size_t potts_tn_smem_bytes(int L, int RD, int B, int walkers_per_block)
 static int potts_tn_depth(int L, int B, int walkers_per_block)
 {
     if (L < 8 || L > 64 || L % 8 != 0 || !sweep_L_supported(L)) return 0;
-    if (potts_tn_smem_bytes(L, 4, B, walkers_per_block) <= 227u * 1024u) return 4;
+    // L = 64 (the split table) is built with the two-row ring only: the four-row one fits
+    // 32-walker blocks but not the default 64
+    if (L < 64 && potts_tn_smem_bytes(L, 4, B, walkers_per_block) <= 227u * 1024u) return 4;
     if (potts_tn_smem_bytes(L, 2, B, walkers_per_block) <= 227u * 1024u) return 2;
     return 0;
 }
@@ -970,7 +1107,7 @@ static cudaError_t launch_potts_tn_rd(int L, const SpinSweepArgs &a, int block, 
     case 24: return launch_one_tnp<24, RD>(a, block, s);
     case 32: return launch_one_tnp<32, RD>(a, block, s);
     case 48: return launch_one_tnp<48, RD>(a, block, s);
-    case 64:  // the split table: only the two-row ring fits (32 walkers a block)
+    case 64:  // the split table: only the two-row ring fits
         if constexpr (RD == 2) return launch_one_tnp<64, 2>(a, block, s);
         return cudaErrorInvalidValue;
     default: return cudaErrorInvalidValue;

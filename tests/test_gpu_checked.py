@@ -53,7 +53,8 @@ def _child():
     for system, L, q, pipeline, block in [(m.ISING2D, 16, 2, 2, 64), (m.ISING2D_MUMA, 16, 2, 2, 32),
                                           (m.POTTS2D, 16, 6, 2, 64), (m.ISING2D, 16, 2, 1, 64),
                                           (m.POTTS2D, 16, 6, 1, 64), (m.ISING2D, 16, 2, 0, 64),
-                                          (m.POTTS2D, 8, 3, 0, 32), (m.POTTS2D, 64, 10, 2, 32)]:
+                                          (m.POTTS2D, 8, 3, 0, 32), (m.POTTS2D, 64, 10, 2, 32),
+                                          (m.POTTS2D, 64, 10, 2, 64)]:
         beta = 0.4407 if system == m.ISING2D_MUMA else 0.0
         g = m.Muca(system, L, q, 70, 5, beta=beta if system == m.ISING2D_MUMA else None, block=block)
         g.set_param("pipeline", pipeline)

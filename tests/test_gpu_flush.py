@@ -63,8 +63,8 @@ def test_flush_cap_does_not_change_results(cap):
 
 @pytest.mark.parametrize("pipeline", [2, 0])
 def test_flush_in_potts_L64_forms(pipeline):
-    """q-Potts at L = 64: the code form with the split table (upper halves and counters in shared
-    memory) and the one-warp form with the table in global memory."""
+    """q-Potts at L = 64: the code form with the split table (upper halves and 16-bit counters in
+    shared memory) and the one-warp form with the table in global memory."""
     p, S = 40, 5
     g = m.Muca(m.POTTS2D, 64, 10, p, 3)
     g.set_param("pipeline", pipeline)
@@ -77,6 +77,38 @@ def test_flush_in_potts_L64_forms(pipeline):
         o.iterate(S, 8)
         o.update()
         compare_state(g, o, "after iteration %d" % it)
+
+
+@pytest.mark.parametrize("block,record", [(64, 0), (32, 0), (64, 1)])
+def test_split_counters_with_every_walker_in_one_bin(block, record):
+    """q-Potts at L = 64 in the code form counts visits in 16-bit counters beside the thresholds'
+    upper halves, which the consumer warps empty every F rows (F = 15 with two consumer warps a
+    block, 31 with one).  Fixed weights ln W = -30 |b - b0| around the walkers' median initial bin
+    b0 send every walker to b0 within the first sweep and keep it there: a move away from b0 has
+    threshold 0, so only moves that keep the energy are accepted.  The counter of b0 then takes
+    64 x 4096 = 2.6e5 visits a sweep, four times its range, and up to 61440 (63488) between two
+    scans.  Histogram, lattices, bins and the next ln W stay bit-identical to the oracle at the
+    same weights."""
+    p, S, q = 64, 6, 10
+    g = m.Muca(m.POTTS2D, 64, q, p, 21, record=record, block=block)
+    o = oracle.Run(m.POTTS2D, 64, q, p, 21, record=record)
+    o.init()
+    b0 = int(np.median(o.bins()))
+    lnW = -30.0 * np.abs(np.arange(g.B) - b0)
+    g.set_lnW(lnW)
+    o.set_lnW(lnW)
+    for it in range(2):
+        g.iterate(S)
+        g.merge_and_update()
+        o.iterate(S, 8)
+        o.update()
+        compare_state(g, o, "after iteration %d" % it)
+        g.set_lnW(lnW)
+        o.set_lnW(lnW)
+    H = g.histogram()
+    assert int(H.sum()) == p * S * (64 * 64 if record == 0 else 1)
+    assert (g.bins() == b0).mean() > 0.9
+    assert H[b0] > 0.9 * H.sum()
 
 
 @pytest.mark.parametrize("form", [0, 1])

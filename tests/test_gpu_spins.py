@@ -320,12 +320,13 @@ def test_state_buffer_must_be_consistent(system, L, q, C):
 @pytest.mark.parametrize("pipeline", [2, 0])
 def test_potts_L64_bit_exact(record, pipeline):
     """q-Potts at L = 64: 8193 bins x 9 columns of 32-bit thresholds (295 KB) do not fit a block's
-    shared memory.  The code form (pipeline 2) keeps their upper 16 bits there and decides a tie of
-    the upper halves of u and T on the full words (u recomputed from its Philox block, T read from
-    the global table); the one-warp form (pipeline 0) reads the full table from global memory.
-    Bit-exact against the oracle over 64 walkers x 3 x 10 sweeps = 7.9e6 attempts, in which about
-    120 upper-half ties occur (40 of them in the first iteration, where every threshold is
-    'always' and the fast compare alone would reject)."""
+    shared memory.  The code form (pipeline 2) keeps 16-bit stand-ins of their upper halves there,
+    decides on those and redoes a walker's row exactly when one of its sites had equal halves (u
+    recomputed from its Philox block, T read from the global table); the one-warp form
+    (pipeline 0) reads the full table from global memory.  Bit-exact against the oracle over 64
+    walkers x 3 x 10 sweeps = 7.9e6 attempts; in the second and third iterations, where the
+    thresholds are no longer all 'always', a few tens of sites tie (2^-16 an attempt), and about
+    half of them the full words accept where the halves alone would have rejected."""
     run_pair(m.POTTS2D, 64, 10, 64, 17, 3, 10, record=record, nthreads=NT, pipeline=pipeline)
 
 

@@ -23,7 +23,8 @@ def _gpu():
 @pytest.mark.parametrize("system,L,q,p", [(m.ISING2D, 32, 2, 1000), (m.POTTS2D, 16, 10, 300),
                                           (m.ISING2D_MUMA, 16, 2, 257), (m.POTTS2D, 64, 8, 40)])
 def test_noalloc_matches_allocating_path_on_two_calls(system, L, q, p):
-    """Also q-Potts at L = 64, whose sweep reads its threshold table from global memory."""
+    """Also q-Potts at L = 64, whose code form keeps only the thresholds' upper halves in shared
+    memory."""
     import torch
 
     S = 150 if L < 64 else 4
