@@ -87,7 +87,8 @@ int muca_init_ex(muca_ctx **out, int system, int L_or_N, int q, int p, uint64_t 
  *   "flat_ratio"  flatness criterion min H / mean H (default 0.5); any time.
  *   "block"       spins: walkers per thread block of the sweep kernel (32..512,
  *                 multiple of 32; default 64, or 32 where only that fits the
- *                 code form; the code form runs for 32 or 64);
+ *                 code form, and 32 for q-Potts when p <= 32 x the SM count;
+ *                 the code form runs for 32 or 64);
  *                 polymer: threads per block (default 256).  Before the first
  *                 iterate.
  *   "pipeline"    spins: 2 (default) pairs every warp of walkers with

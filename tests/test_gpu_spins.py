@@ -103,8 +103,10 @@ def test_record_per_sweep(pipeline):
              pipeline=pipeline)
 
 
-@pytest.mark.parametrize("block", [32, 96, 256, 512])
+@pytest.mark.parametrize("block", [32, 64, 96, 256, 512])
 def test_block_size_does_not_change_results(block):
+    """Explicit walkers per block (the default for q-Potts at p = 300 is 32: every block has an
+    SM to itself); 64 is the code form's two-consumer block."""
     run_pair(m.POTTS2D, 16, 8, 300, seed=7, iters=2, sweeps=20, block=block, nthreads=NT)
 
 
