@@ -3,7 +3,8 @@
 // K = 40, R = 1.5, Lennard-Jones 12-6 between beads |i-j| >= 2 with eps = sigma
 // = 1, cut at 2.5 and shifted; single-bead moves in a cube of side 0.3).
 //
-// G lanes of a warp per walker (G = 8, 16 or 32; 32/G walkers share a warp).
+// G lanes of a warp per walker (G = 1, 2, 4, 8, 16 or 32; 32/G walkers share a
+// warp).
 // The beads are visited in order; for bead i every lane of the walker's group
 // evaluates the old and the new pair energies with its partner beads
 // j = lane, lane + G, ... in FP32 and keeps a compensated (Kahan) sum (the old
@@ -26,7 +27,10 @@
 // Acceptance inside the window: d = ln W(b') - ln W(b) from a fixed-point table,
 // accept iff d >= 0 or ln(u 2^-32) < d (the FP32 logarithm of each bead's
 // acceptance word is taken once a sweep); outside the window a move is accepted
-// iff it does not increase the distance to the window (walk-in).
+// iff it does not increase the distance to the window (walk-in).  Visits are
+// counted in the block's 32-bit shared-memory counters and added to the 64-bit
+// histogram after every chunk of sweeps, so that walkers crowding one bin (right
+// after they walk in, say) do not queue on one global counter.
 #include "muca_device.cuh"
 #include "muca_internal.h"
 
@@ -97,6 +101,13 @@ __device__ __forceinline__ int poly_bin(long long E, const PolyArgs &a)
 {
     const long long b = ((E - a.elo_q) * 10) >> 32;
     return b < -1 ? -1 : (b > (long long)a.B ? a.B : (int)b);
+}
+
+// n visits of a bin: a shared-memory reduction without a returned value, so nothing
+// waits for it.
+__device__ __forceinline__ void count_visits(unsigned *h, unsigned n)
+{
+    asm volatile("red.shared.add.u32 [%0], %1;" ::"r"((unsigned)__cvta_generic_to_shared(h)), "r"(n) : "memory");
 }
 
 // Random-walk initial chain (thread per walker): bead k = bead k-1 + unit vector
@@ -265,11 +276,15 @@ __global__ void __launch_bounds__(kMaxSweepBlock) k_sweep_polymer(const PolyArgs
     float *eb = xs + 6 * N;  // eb[j]: FP32 energy of bond (j, j+1) at the current shadows
     uint4 *su = (uint4 *)(smem + (size_t)spb * sst * sizeof(float)) + (size_t)slot * N;
     uint4 *sm = su + (size_t)spb * N;  // moves
+    // the block's histogram counters, after all slots and Philox blocks
+    unsigned *hs = (unsigned *)(smem + (size_t)spb * sst * sizeof(float) +
+                                (size_t)spb * N * (a.moves ? 2 : 1) * sizeof(uint4));
     const int w0 = (blockIdx.x * wpb + wib) * W;
-    if (w0 >= a.p) return;  // whole warps only; no block-wide barrier follows
+    const bool wactive = w0 < a.p;  // a warp past the last walker only joins the block's flushes
     const int w = w0 + gi;
     const bool active = w < a.p;
-    const int wr = active ? w : w0;  // a group past the last walker shadows the warp's first one, read-only
+    // a group past the last walker shadows the warp's first one, read-only
+    const int wr = active ? w : (wactive ? w0 : 0);
     const uint32_t wid = (uint32_t)(wr + a.walker_offset);
     long long *Xg = a.X + (size_t)wr * 3 * N;
     long long E = a.E[wr];
@@ -281,7 +296,13 @@ __global__ void __launch_bounds__(kMaxSweepBlock) k_sweep_polymer(const PolyArgs
     unsigned ev = 0;
     int tst = (active && a.tun) ? a.tun[w] : 0;
     constexpr float kStep = (float)kPolyStepQ * 0x1p-44f;
-    for (int64_t sw = 0; sw < a.sweeps; ++sw) {
+    for (int i = threadIdx.x; i < a.B; i += blockDim.x) hs[i] = 0u;
+    __syncthreads();
+    // sweeps in chunks whose counts fit the 32-bit counters (spb N a sweep at most)
+    const int64_t fe = (int64_t)(0xFFFFFFFFu / (unsigned)(spb * N));
+    for (int64_t s0 = 0; s0 < a.sweeps; s0 += fe) {
+    const int64_t s1 = (a.sweeps - s0 < fe) ? a.sweeps : s0 + fe;
+    for (int64_t sw = s0; wactive && sw < s1; ++sw) {
         const uint32_t g = g0 + (uint32_t)sw;
         const long long A0 = Xg[0], A1 = Xg[N], A2 = Xg[2 * N];
         for (int j = li; j < N; j += G) {
@@ -437,12 +458,23 @@ __global__ void __launch_bounds__(kMaxSweepBlock) k_sweep_polymer(const PolyArgs
                 ++nacc;
             }
             __syncwarp();
-            if (RECORD == 0 && li == 0 && active && b >= 0 && b < a.B) atomicAdd(a.H + b, 1ull);
+            if (RECORD == 0 && li == 0 && active && b >= 0 && b < a.B) count_visits(&hs[b], 1u);
         }
-        if (RECORD == 1 && li == 0 && active && b >= 0 && b < a.B) atomicAdd(a.H + b, 1ull);
+        if (RECORD == 1 && li == 0 && active && b >= 0 && b < a.B) count_visits(&hs[b], 1u);
         tunnel_step(b, 0, a.B - 1, tst, ev);
         __syncwarp();
     }
+    __syncthreads();  // the chunk's counts into the histogram
+    for (int i = threadIdx.x; i < a.B; i += blockDim.x) {
+        const unsigned c = hs[i];
+        if (c) {
+            atomicAdd(a.H + i, (unsigned long long)c);
+            hs[i] = 0u;
+        }
+    }
+    __syncthreads();
+    }
+    if (!wactive) return;  // (no block-wide operation follows)
     const bool lead = li == 0 && active;
     flush_metrics(a.metrics, lead ? nacc : 0ull, lead ? ev : 0u);
     if (lead && a.tun) a.tun[w] = (uint8_t)tst;
@@ -502,17 +534,24 @@ static size_t poly_warp_smem(const PolyArgs &a)
 
 constexpr size_t kPolySmemMax = 227u * 1024u;
 
+// The block's 32-bit histogram counters (one per bin), after the warps' shared memory.
+static size_t poly_hist_smem(const PolyArgs &a)
+{
+    return ((size_t)a.B * sizeof(unsigned) + 15) / 16 * 16;
+}
+
 template <int G>
 static cudaError_t launch_g(const PolyArgs &a, int block, cudaStream_t s)
 {
     // as many warps of the requested block as fit the shared memory of one block
     int wpb = block / 32;
-    const size_t per_warp = poly_warp_smem<G>(a);
-    if ((size_t)wpb * per_warp > kPolySmemMax) wpb = (int)(kPolySmemMax / per_warp);
+    const size_t per_warp = poly_warp_smem<G>(a), hist = poly_hist_smem(a);
+    if (hist + (size_t)wpb * per_warp > kPolySmemMax)
+        wpb = hist < kPolySmemMax ? (int)((kPolySmemMax - hist) / per_warp) : 0;
     if (wpb < 1) return cudaErrorInvalidValue;
     block = 32 * wpb;
     const int spb = wpb * (32 / G);
-    const size_t smem = (size_t)wpb * per_warp;
+    const size_t smem = (size_t)wpb * per_warp + hist;
     const int nblk = (a.p + spb - 1) / spb;
     cudaError_t e;
     if (a.record == 0) {
@@ -538,7 +577,7 @@ static cudaError_t launch_g(const PolyArgs &a, int block, cudaStream_t s)
 template <int G>
 static bool poly_fits(const PolyArgs &a)
 {
-    return poly_warp_smem<G>(a) <= kPolySmemMax;
+    return poly_warp_smem<G>(a) + poly_hist_smem(a) <= kPolySmemMax;
 }
 
 int poly_lanes(const PolyArgs &a, int requested)
