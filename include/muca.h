@@ -139,11 +139,12 @@ int muca_init_ex(muca_ctx **out, int system, int L_or_N, int q, int p, uint64_t 
  *                 sets it at muca_init.  A limit too small for a healthy run
  *                 only makes the next synchronising call report
  *                 MUCA_ERR_TIMEOUT.  Any time.
- *   "flush_every" lattice systems: at most this many sweeps between two flushes
- *                 of a thread block's shared-memory uint32 histogram counters
- *                 to its uint64 slot; 0 (default) = the largest count that
- *                 cannot overflow a counter (floor((2^32 - 1) / (block * N)),
- *                 or / block with "record" = 1).  Results do not depend on it;
+ *   "flush_every" at most this many sweeps between two flushes of a thread
+ *                 block's shared-memory uint32 histogram counters to its
+ *                 uint64 slot (the polymer: to the uint64 histogram); 0
+ *                 (default) = the largest count that cannot overflow a
+ *                 counter (floor((2^32 - 1) / (block walkers * N)), or
+ *                 / block with "record" = 1).  Results do not depend on it;
  *                 a small value makes short runs cross the flush between
  *                 chunks of sweeps (tests).  Any time.
  *   "model"       polymer, before the first iterate: 0 (default) = the benchmark

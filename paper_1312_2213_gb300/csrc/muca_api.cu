@@ -330,6 +330,7 @@ PolyArgs poly_args(const muca_ctx *c, int64_t sweeps)
     a.record = c->record;
     a.walker_offset = c->walker_offset;
     a.lanes = c->lanes;
+    a.flush_every = c->flush_cap;
     a.elo_q = llrint(c->e_lo * 4294967296.0);                      // e_lo * 2^32
     a.ehi_q = a.elo_q + ((long long)c->B * 4294967296LL + 9) / 10;  // first energy with bin >= B
     a.model = c->model;
@@ -726,7 +727,6 @@ int muca_set_param(muca_ctx *c, const char *key, double v)
         return MUCA_OK;
     }
     if (k == "flush_every") {
-        if (c->system == kPolymer) return fail(MUCA_ERR_ARG, "flush_every applies to lattice systems only");
         const long long n = (long long)v;
         if ((double)n != v || n < 0 || n > 0x7fffffffLL) return fail(MUCA_ERR_ARG, "flush_every must be an integer >= 0");
         c->flush_cap = (int)n;

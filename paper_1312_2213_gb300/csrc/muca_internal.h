@@ -131,6 +131,7 @@ struct PolyArgs {
     unsigned long long *metrics = nullptr;  // open counters {accepted moves, tunnelling events}
     uint8_t *tun = nullptr;                 // [p] tunnelling state per walker
     PolyTraceRec *trace = nullptr;          // [p][sweeps][N] attempt records, or null
+    int flush_every = 0;  // most sweeps between flushes of the block's counters (0: their own bound)
 };
 bool polymer_supported(int N);
 cudaError_t launch_poly_init(const PolyArgs &a, cudaStream_t s);

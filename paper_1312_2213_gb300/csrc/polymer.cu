@@ -299,7 +299,8 @@ __global__ void __launch_bounds__(kMaxSweepBlock) k_sweep_polymer(const PolyArgs
     for (int i = threadIdx.x; i < a.B; i += blockDim.x) hs[i] = 0u;
     __syncthreads();
     // sweeps in chunks whose counts fit the 32-bit counters (spb N a sweep at most)
-    const int64_t fe = (int64_t)(0xFFFFFFFFu / (unsigned)(spb * N));
+    int64_t fe = (int64_t)(0xFFFFFFFFu / (unsigned)(spb * N));
+    if (a.flush_every > 0 && a.flush_every < fe) fe = a.flush_every;
     for (int64_t s0 = 0; s0 < a.sweeps; s0 += fe) {
     const int64_t s1 = (a.sweeps - s0 < fe) ? a.sweeps : s0 + fe;
     for (int64_t sw = s0; wactive && sw < s1; ++sw) {
