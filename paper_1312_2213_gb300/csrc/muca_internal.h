@@ -132,6 +132,8 @@ struct PolyArgs {
     uint8_t *tun = nullptr;                 // [p] tunnelling state per walker
     PolyTraceRec *trace = nullptr;          // [p][sweeps][N] attempt records, or null
     int flush_every = 0;  // most sweeps between flushes of the block's counters (0: their own bound)
+    int64_t sweep_base = 0;    // this launch's first sweep within the iterate (launch_poly_sweep chunks)
+    int64_t trace_sweeps = 0;  // sweeps of the traced iterate
 };
 bool polymer_supported(int N);
 cudaError_t launch_poly_init(const PolyArgs &a, cudaStream_t s);

@@ -28,9 +28,10 @@
 // accept iff d >= 0 or ln(u 2^-32) < d (the FP32 logarithm of each bead's
 // acceptance word is taken once a sweep); outside the window a move is accepted
 // iff it does not increase the distance to the window (walk-in).  Visits are
-// counted in the block's 32-bit shared-memory counters and added to the 64-bit
-// histogram after every chunk of sweeps, so that walkers crowding one bin (right
-// after they walk in, say) do not queue on one global counter.
+// counted in the block's 32-bit shared-memory counters, which the block's last
+// warp to finish adds to the 64-bit histogram (an iterate longer than they can
+// hold runs as several launches), so that walkers crowding one bin (right after
+// they walk in, say) do not queue on one global counter.
 #include "muca_device.cuh"
 #include "muca_internal.h"
 
@@ -276,34 +277,30 @@ __global__ void __launch_bounds__(kMaxSweepBlock) k_sweep_polymer(const PolyArgs
     float *eb = xs + 6 * N;  // eb[j]: FP32 energy of bond (j, j+1) at the current shadows
     uint4 *su = (uint4 *)(smem + (size_t)spb * sst * sizeof(float)) + (size_t)slot * N;
     uint4 *sm = su + (size_t)spb * N;  // moves
-    // the block's histogram counters, after all slots and Philox blocks
+    // the block's histogram counters and its count of finished warps, after all slots and
+    // Philox blocks
     unsigned *hs = (unsigned *)(smem + (size_t)spb * sst * sizeof(float) +
                                 (size_t)spb * N * (a.moves ? 2 : 1) * sizeof(uint4));
+    unsigned *done = hs + a.B;
+    for (int i = threadIdx.x; i <= a.B; i += blockDim.x) hs[i] = 0u;
+    __syncthreads();
     const int w0 = (blockIdx.x * wpb + wib) * W;
-    const bool wactive = w0 < a.p;  // a warp past the last walker only joins the block's flushes
+    if (w0 >= a.p) return;  // whole warps only; no block-wide barrier follows
     const int w = w0 + gi;
     const bool active = w < a.p;
-    // a group past the last walker shadows the warp's first one, read-only
-    const int wr = active ? w : (wactive ? w0 : 0);
+    const int wr = active ? w : w0;  // a group past the last walker shadows the warp's first one, read-only
     const uint32_t wid = (uint32_t)(wr + a.walker_offset);
     long long *Xg = a.X + (size_t)wr * 3 * N;
     long long E = a.E[wr];
     int b = poly_bin(E, a);
-    const uint32_t g0 = (uint32_t)a.state->sweep_counter;
+    const uint32_t g0 = (uint32_t)(a.state->sweep_counter + a.sweep_base);
     const int npl = (N + G - 1) / G;
     // metrics: accepted moves and tunnelling between bins 0 and B-1 (group-uniform values)
     unsigned long long nacc = 0;
     unsigned ev = 0;
     int tst = (active && a.tun) ? a.tun[w] : 0;
     constexpr float kStep = (float)kPolyStepQ * 0x1p-44f;
-    for (int i = threadIdx.x; i < a.B; i += blockDim.x) hs[i] = 0u;
-    __syncthreads();
-    // sweeps in chunks whose counts fit the 32-bit counters (spb N a sweep at most)
-    int64_t fe = (int64_t)(0xFFFFFFFFu / (unsigned)(spb * N));
-    if (a.flush_every > 0 && a.flush_every < fe) fe = a.flush_every;
-    for (int64_t s0 = 0; s0 < a.sweeps; s0 += fe) {
-    const int64_t s1 = (a.sweeps - s0 < fe) ? a.sweeps : s0 + fe;
-    for (int64_t sw = s0; wactive && sw < s1; ++sw) {
+    for (int64_t sw = 0; sw < a.sweeps; ++sw) {
         const uint32_t g = g0 + (uint32_t)sw;
         const long long A0 = Xg[0], A1 = Xg[N], A2 = Xg[2 * N];
         for (int j = li; j < N; j += G) {
@@ -431,7 +428,7 @@ __global__ void __launch_bounds__(kMaxSweepBlock) k_sweep_polymer(const PolyArgs
                 r.b = acc ? bn : b;
                 r.flags = (acc ? 1 : 0) | (broken ? 2 : 0) | (huge ? 4 : 0);
                 r.pad = 0;
-                a.trace[((size_t)w * (size_t)a.sweeps + (size_t)sw) * (size_t)N + i] = r;
+                a.trace[((size_t)w * (size_t)a.trace_sweeps + (size_t)(a.sweep_base + sw)) * (size_t)N + i] = r;
             }
             if (acc) {
                 if (G == 1) {
@@ -465,17 +462,20 @@ __global__ void __launch_bounds__(kMaxSweepBlock) k_sweep_polymer(const PolyArgs
         tunnel_step(b, 0, a.B - 1, tst, ev);
         __syncwarp();
     }
-    __syncthreads();  // the chunk's counts into the histogram
-    for (int i = threadIdx.x; i < a.B; i += blockDim.x) {
-        const unsigned c = hs[i];
-        if (c) {
-            atomicAdd(a.H + i, (unsigned long long)c);
-            hs[i] = 0u;
+    // the block's last warp to finish adds the counters to the histogram (the launch's sweeps
+    // fit the 32-bit counters: launch_g splits longer iterates)
+    __threadfence_block();  // this warp's visits are counted before it reports
+    __syncwarp();
+    const int nwarps = min(wpb, (a.p - blockIdx.x * spb + W - 1) / W);  // warps of the block with walkers
+    unsigned last = 0u;
+    if (lane == 0) last = (atomicAdd(done, 1u) == (unsigned)nwarps - 1u);
+    if (__shfl_sync(0xffffffffu, last, 0)) {
+        __threadfence_block();
+        for (int i = lane; i < a.B; i += 32) {
+            const unsigned c = hs[i];
+            if (c) atomicAdd(a.H + i, (unsigned long long)c);
         }
     }
-    __syncthreads();
-    }
-    if (!wactive) return;  // (no block-wide operation follows)
     const bool lead = li == 0 && active;
     flush_metrics(a.metrics, lead ? nacc : 0ull, lead ? ev : 0u);
     if (lead && a.tun) a.tun[w] = (uint8_t)tst;
@@ -538,7 +538,7 @@ constexpr size_t kPolySmemMax = 227u * 1024u;
 // The block's 32-bit histogram counters (one per bin), after the warps' shared memory.
 static size_t poly_hist_smem(const PolyArgs &a)
 {
-    return ((size_t)a.B * sizeof(unsigned) + 15) / 16 * 16;
+    return ((size_t)(a.B + 1) * sizeof(unsigned) + 15) / 16 * 16;
 }
 
 template <int G>
@@ -554,17 +554,26 @@ static cudaError_t launch_g(const PolyArgs &a, int block, cudaStream_t s)
     const int spb = wpb * (32 / G);
     const size_t smem = (size_t)wpb * per_warp + hist;
     const int nblk = (a.p + spb - 1) / spb;
-    cudaError_t e;
-    if (a.record == 0) {
-        e = cudaFuncSetAttribute(k_sweep_polymer<G, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        k_sweep_polymer<G, 0><<<nblk, block, smem, s>>>(a);
-    } else {
-        e = cudaFuncSetAttribute(k_sweep_polymer<G, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        k_sweep_polymer<G, 1><<<nblk, block, smem, s>>>(a);
+    cudaError_t e = (a.record == 0)
+                        ? cudaFuncSetAttribute(k_sweep_polymer<G, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
+                        : cudaFuncSetAttribute(k_sweep_polymer<G, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    // one launch per chunk of sweeps whose visits fit the block's 32-bit counters (spb N a sweep
+    // at most), or fewer ("flush_every")
+    int64_t fe = (int64_t)(0xFFFFFFFFu / (unsigned)(spb * a.N));
+    if (a.flush_every > 0 && a.flush_every < fe) fe = a.flush_every;
+    for (int64_t s0 = 0; s0 < a.sweeps; s0 += fe) {
+        PolyArgs c = a;
+        c.sweep_base = s0;
+        c.sweeps = (a.sweeps - s0 < fe) ? a.sweeps - s0 : fe;
+        c.trace_sweeps = a.sweeps;
+        if (a.record == 0)
+            k_sweep_polymer<G, 0><<<nblk, block, smem, s>>>(c);
+        else
+            k_sweep_polymer<G, 1><<<nblk, block, smem, s>>>(c);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
-    return cudaGetLastError();
+    return cudaSuccess;
 }
 
 // Lanes per walker: the fixed cost of an attempt (group reductions, the bin and
