@@ -117,7 +117,13 @@ MIX = [(0, L, 2) for L in (16, 24, 32, 48, 64)] + [(1, L, 10) for L in (16, 24, 
 MIX_P = 2048
 
 
-def run_mix(m, torch, sweeps=1000, short_sweeps=10, short_iters=20):
+def mix_mopt(p=MIX_P):
+    """Each mix system's optimal iteration length from the fits of Eq. 4: M_opt = 5.7 L^2.51 / p
+    (Ising) and 24 L^2.67 / p (the 8-Potts fit, used for q = 10)."""
+    return [max(1, round((5.7 * L ** 2.51 if s_ == 0 else 24.0 * L ** 2.67) / p)) for s_, L, _ in MIX]
+
+
+def run_mix(m, torch, sweeps=1000, short_sweeps=10, short_iters=20, mopt_iters=50):
     """Plain (one system per launch, host loop) vs batched (both batch forms) vs graph."""
     sites = sum(L * L for _, L, _ in MIX)
 
@@ -147,6 +153,15 @@ def run_mix(m, torch, sweeps=1000, short_sweeps=10, short_iters=20):
 
     t_plain = timed(lambda: plain_iter(sysA, sweeps))
     t_plain_s = timed(lambda: [plain_iter(sysA, short_sweeps) for _ in range(short_iters)])
+    mopt = mix_mopt()
+
+    def plain_mopt():
+        for c, sw in zip(sysA, mopt):
+            c.iterate(sw)
+            c.merge_and_update()
+
+    t_plain_m = timed(lambda: [plain_mopt() for _ in range(mopt_iters)])
+    att_m = MIX_P * sum(sw * L * L for sw, (_, L, _) in zip(mopt, MIX)) * mopt_iters
     att = MIX_P * sweeps * sites
     att_s = MIX_P * short_sweeps * sites * short_iters
     # batched forms: 0 = one persistent launch over all systems' tiles (one warp per 32 walkers),
@@ -163,10 +178,14 @@ def run_mix(m, torch, sweeps=1000, short_sweeps=10, short_iters=20):
         batch.run(short_iters, short_sweeps, use_graph=True)  # capture
         t_graph_s = timed(lambda: batch.run(short_iters, short_sweeps, use_graph=True))
         t_batch_s = timed(lambda: batch.run(short_iters, short_sweeps, use_graph=False))
+        batch.set_sweeps(mopt)  # every system at its own M_opt
+        batch.run(mopt_iters, 1, use_graph=True)  # capture
+        t_graph_m = timed(lambda: batch.run(mopt_iters, 1, use_graph=True))
+        t_batch_m = timed(lambda: batch.run(mopt_iters, 1, use_graph=False))
         batch.close()
-        forms[form] = (t_batch, t_graph, t_batch_s, t_graph_s)
+        forms[form] = (t_batch, t_graph, t_batch_s, t_graph_s, t_batch_m, t_graph_m)
     best = min(forms, key=lambda f: forms[f][1])
-    t_batch, t_graph, t_batch_s, t_graph_s = forms[best]
+    t_batch, t_graph, t_batch_s, t_graph_s, t_batch_m, t_graph_m = forms[best]
     out["throughput"] = {"sweeps_per_iteration": sweeps, "attempts_per_iteration": att, "batch_form": best,
                          "plain_attempts_per_s": att / t_plain, "batched_attempts_per_s": att / t_batch,
                          "graph_attempts_per_s": att / t_graph, "batched_over_plain": t_plain / t_batch,
@@ -179,6 +198,14 @@ def run_mix(m, torch, sweeps=1000, short_sweeps=10, short_iters=20):
                                "graph_attempts_per_s": att_s / t_graph_s, "graph_over_plain": t_plain_s / t_graph_s,
                                "by_form": {str(f): {"batched_attempts_per_s": att_s / v[2],
                                                     "graph_attempts_per_s": att_s / v[3]} for f, v in forms.items()}}
+    # each system at its own M_opt (Eq. 4) for p = 2048: uneven iteration lengths
+    out["mopt_iterations"] = {"sweeps_per_iteration": dict(zip(["ising%d" % L if s_ == 0 else "potts%d" % L
+                                                                for s_, L, _ in MIX], mopt)),
+                              "iterations": mopt_iters, "batch_form": best,
+                              "plain_attempts_per_s": att_m / t_plain_m, "batched_attempts_per_s": att_m / t_batch_m,
+                              "graph_attempts_per_s": att_m / t_graph_m, "graph_over_plain": t_plain_m / t_graph_m,
+                              "by_form": {str(f): {"batched_attempts_per_s": att_m / v[4],
+                                                   "graph_attempts_per_s": att_m / v[5]} for f, v in forms.items()}}
     for c in sysA + made:
         c.close()
     return out

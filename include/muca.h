@@ -320,8 +320,10 @@ int muca_batch_create(muca_ctx *const *systems, int n, muca_batch **out);
 int muca_batch_run(muca_batch *batch, int n_iter, int64_t sweeps, int use_graph);
 int muca_batch_free(muca_batch *batch);
 /* How a batch runs its sweeps.  form 1 (default): each context's own sweep
- * kernel in its configured form ("pipeline", "block"), one stream per
- * context, forked from and joined back into the batch's stream, heaviest
+ * kernel in its configured form ("pipeline", "block"; a q-Potts context whose
+ * 32-walker default came from small p runs 64-walker blocks when the batch's
+ * contexts together have more 32-walker blocks than the GPU has SMs), one
+ * stream per context, forked from and joined back into the batch's stream, heaviest
  * system first, so the launches run side by side (in a graph: as parallel
  * branches); the merge, recursion and threshold launches stay batched.
  * form 0: the one persistent launch over a tile list described above (one
@@ -329,6 +331,14 @@ int muca_batch_free(muca_batch *batch);
  * Changing the form drops a captured graph.  Errors: MUCA_ERR_ARG for another
  * value. */
 int muca_batch_set_form(muca_batch *batch, int form);
+/* Sweeps per context and iteration: sweeps[i] >= 1 for context i (e.g. each
+ * system's own optimal iteration length M_opt of Eq. 4, so that short and long
+ * lattices iterate at their own pace), or sweeps = NULL to give every context
+ * the `sweeps` argument of muca_batch_run again (the default).  The systems'
+ * launch order and tile list follow the new work, heaviest first; a captured
+ * graph is re-captured on the next run.  Synchronises the batch's stream.
+ * Errors: MUCA_ERR_ARG for n != the number of contexts or a count < 1. */
+int muca_batch_set_sweeps(muca_batch *batch, const int64_t *sweeps, int n);
 
 /* Diagnostics: evaluate the library's deterministic binary64 exp (fn = 0) or
  * log (fn = 1) -- the functions the weight recursion and the threshold build

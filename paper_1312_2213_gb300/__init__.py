@@ -25,7 +25,7 @@ __all__ = ["Muca", "MucaError", "ISING2D", "POTTS2D", "ISING2D_MUMA", "POLYMER3D
            "muca_get_state", "muca_set_state",
            "muca_get_spins", "muca_get_walker_bins", "muca_get_thresholds", "muca_get_sweep_counter",
            "muca_synchronize", "muca_free", "muca_last_error", "muca_det_math",
-           "muca_iterate_noalloc", "muca_set_lnW", "muca_poly_trace", "POLY_TRACE_DTYPE", "muca_get_coords", "muca_get_drift", "muca_batch_create", "muca_batch_run", "muca_batch_free", "muca_batch_set_form", "Batch"]
+           "muca_iterate_noalloc", "muca_set_lnW", "muca_poly_trace", "POLY_TRACE_DTYPE", "muca_get_coords", "muca_get_drift", "muca_batch_create", "muca_batch_run", "muca_batch_free", "muca_batch_set_form", "muca_batch_set_sweeps", "Batch"]
 
 
 def _p(a: np.ndarray):
@@ -205,6 +205,15 @@ def muca_batch_set_form(b, form: int):
     check(load().muca_batch_set_form(b, int(form)), "muca_batch_set_form")
 
 
+def muca_batch_set_sweeps(b, sweeps):
+    """Per-system sweeps of every batch iteration, or None for the run's argument."""
+    if sweeps is None:
+        check(load().muca_batch_set_sweeps(b, None, 0), "muca_batch_set_sweeps")
+        return
+    arr = np.ascontiguousarray(sweeps, dtype=np.int64)
+    check(load().muca_batch_set_sweeps(b, _p(arr), arr.size), "muca_batch_set_sweeps")
+
+
 def muca_batch_free(b):
     check(load().muca_batch_free(b), "muca_batch_free")
 
@@ -223,6 +232,10 @@ class Batch:
 
     def set_form(self, form: int):
         muca_batch_set_form(self.h, form)
+
+    def set_sweeps(self, sweeps):
+        """Each system's own sweeps an iteration (e.g. its M_opt, Eq. 4), or None."""
+        muca_batch_set_sweeps(self.h, sweeps)
 
     def run(self, n_iter: int, sweeps: int, use_graph: bool = True):
         muca_batch_run(self.h, n_iter, sweeps, use_graph)

@@ -52,6 +52,7 @@ PROTOTYPES = {
     "muca_batch_run": (c_int, [c_vp, c_int, c_i64, c_int]),
     "muca_batch_free": (c_int, [c_vp]),
     "muca_batch_set_form": (c_int, [c_vp, c_int]),
+    "muca_batch_set_sweeps": (c_int, [c_vp, c_vp, c_int]),
     "muca_synchronize": (c_int, [c_vp]),
     "muca_free": (c_int, [c_vp]),
 }

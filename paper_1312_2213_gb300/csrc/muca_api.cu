@@ -68,6 +68,7 @@ struct muca_ctx {
     uint64_t seed = 0;
     double beta = 0.0, flat_ratio = 0.5;
     int record = 0, block = 64, walker_offset = 0;
+    bool block_small_p = false;  // q-Potts: 32 walkers a block because every block has an SM to itself
     int lanes = 0;     // polymer: lanes per walker in the sweep (8, 16, 32; 0 = chosen by N)
     int model = 0;     // polymer: 0 benchmark parameters, 1 the paper's (Eq. 7)
     int moves = 0;     // polymer: 0 single-bead shifts, 1 shifts and spherical rotations
@@ -306,13 +307,14 @@ SpinSweepArgs sweep_args(const muca_ctx *c, int64_t sweeps, int block)
 
 // The context's sweep in its configured form (code form, producer/consumer or one warp), falling
 // back to the next lower form where one does not fit the system, L, bin count or block.
-cudaError_t launch_system_sweep(const muca_ctx *c, const SpinSweepArgs &a, cudaStream_t s)
+cudaError_t launch_system_sweep(const muca_ctx *c, const SpinSweepArgs &a, cudaStream_t s, int block = 0)
 {
-    if (c->pipeline >= 2 && spin_sweep_tn_fits(c->system, c->L, c->B, c->block))
-        return launch_spin_sweep_tn(c->system, c->L, a, c->block, s);
-    if (c->pipeline >= 1 && spin_sweep_pc_fits(c->system, c->L, c->B, c->block))
-        return launch_spin_sweep_pc(c->system, c->L, a, c->block, s);
-    return launch_spin_sweep(c->system, c->L, a, c->block, s);
+    if (block <= 0) block = c->block;
+    if (c->pipeline >= 2 && spin_sweep_tn_fits(c->system, c->L, c->B, block))
+        return launch_spin_sweep_tn(c->system, c->L, a, block, s);
+    if (c->pipeline >= 1 && spin_sweep_pc_fits(c->system, c->L, c->B, block))
+        return launch_spin_sweep_pc(c->system, c->L, a, block, s);
+    return launch_spin_sweep(c->system, c->L, a, block, s);
 }
 
 PolyArgs poly_args(const muca_ctx *c, int64_t sweeps)
@@ -452,8 +454,10 @@ int create(muca_ctx **out, int system, int L, int q, int p, uint64_t seed, void 
     if (system == kPotts && c->block == 64 && spin_sweep_tn_fits(system, L, c->B, 32)) {
         int dev = 0, nsm = 0;
         if (cudaGetDevice(&dev) == cudaSuccess &&
-            cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && (p + 31) / 32 <= nsm)
+            cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && (p + 31) / 32 <= nsm) {
             c->block = 32;
+            c->block_small_p = true;
+        }
     }
     c->seed = seed;
     if (const char *env = std::getenv("MUCA_SPIN_LIMIT")) {  // bound of the hand-over waits
@@ -708,6 +712,7 @@ int muca_set_param(muca_ctx *c, const char *key, double v)
         if ((double)b != v || b < 32 || b > kMaxSweepBlock || (b % 32) != 0)
             return fail(MUCA_ERR_ARG, "block must be a multiple of 32 in [32, %d]", kMaxSweepBlock);
         c->block = b;
+        c->block_small_p = false;
         return MUCA_OK;
     }
     if (k == "debug_check") {
@@ -1291,9 +1296,27 @@ struct muca_batch {
     std::vector<SpinSweepArgs> h_own;  // form 1: per-system launch arguments
     std::vector<int> order;            // systems, heaviest first (tile order; form 1 launch order)
     bool tiles_fit = true;             // every system's table fits the form-0 kernel's shared memory
+    std::vector<int64_t> sw;           // per-system sweeps of an iteration (empty: the run's argument)
+    std::vector<int> blk;              // form 1: each system's walkers per block in this batch
+    std::vector<int64_t> g_sw;         // per-system sweeps the captured graph was made with
 };
 
 namespace {
+
+// Systems heaviest first (sites x sweeps, Potts sites counted 2.5 times), so that their
+// blocks or tiles start in the first wave.
+std::vector<int> batch_order(const muca_batch *b)
+{
+    const int n = (int)b->sys.size();
+    std::vector<int> order(n);
+    for (int i = 0; i < n; ++i) order[i] = i;
+    auto cost = [&](int i) {
+        return (double)b->sys[i]->N * (b->sys[i]->system == kPotts ? 2.5 : 1.0) * (b->sw.empty() ? 1.0 : (double)b->sw[i]);
+    };
+    for (int i = 1; i < n; ++i)
+        for (int j = i; j > 0 && cost(order[j]) > cost(order[j - 1]); --j) std::swap(order[j], order[j - 1]);
+    return order;
+}
 
 int batch_enqueue_iteration(muca_batch *b, int64_t sweeps)
 {
@@ -1303,14 +1326,15 @@ int batch_enqueue_iteration(muca_batch *b, int64_t sweeps)
         // heaviest first, so that their blocks take the SMs before the light systems' blocks
         for (int i : b->order) {
             MUCA_CUDA(cudaStreamWaitEvent(b->sub[i], b->ev_fork, 0));
-            MUCA_CUDA(launch_system_sweep(b->sys[i], b->h_own[i], b->sub[i]));
+            MUCA_CUDA(launch_system_sweep(b->sys[i], b->h_own[i], b->sub[i], b->blk[i]));
             MUCA_CUDA(cudaEventRecord(b->ev_join[i], b->sub[i]));
         }
         for (int i = 0; i < n; ++i) MUCA_CUDA(cudaStreamWaitEvent(b->stream, b->ev_join[i], 0));
     } else {
         MUCA_CUDA(launch_sweep_batch(b->d_sys, b->d_tiles, b->ntiles, b->block, b->smem, b->stream));
     }
-    MUCA_CUDA(launch_advance_batch(b->d_states, n, sweeps, b->stream));
+    (void)sweeps;
+    MUCA_CUDA(launch_advance_batch(b->d_states, b->d_sys, n, b->stream));
     MUCA_CUDA(launch_merge_batch(b->d_upd, n, b->max_bins, b->stream));
     MUCA_CUDA(launch_recursion_batch(b->d_upd, n, b->max_nreach, b->stream));
     MUCA_CUDA(launch_thresholds_batch(b->d_upd, n, b->max_cells, b->stream));
@@ -1349,12 +1373,23 @@ int muca_batch_create(muca_ctx *const *systems, int n, muca_batch **out)
         delete b;
         return fail(MUCA_ERR_CUDA, "muca_batch_create: cannot create stream/events");
     }
-    // Heaviest systems first, so their tiles start in the first wave.
-    std::vector<int> order(n);
-    for (int i = 0; i < n; ++i) order[i] = i;
-    auto cost = [&](int i) { return (double)b->sys[i]->N * (b->sys[i]->system == kPotts ? 2.5 : 1.0); };
-    for (int i = 1; i < n; ++i)
-        for (int j = i; j > 0 && cost(order[j]) > cost(order[j - 1]); --j) std::swap(order[j], order[j - 1]);
+    const std::vector<int> order = batch_order(b);
+    // Form 1 runs each system in its own block size, except that q-Potts systems given 32-walker
+    // blocks because every block would have an SM to itself go back to 64 when the batch's
+    // systems together have more such blocks than the GPU has SMs (they share the SMs then).
+    {
+        int dev = 0, nsm = 0;
+        long long blocks32 = 0;
+        for (int i = 0; i < n; ++i) blocks32 += (b->sys[i]->p + 31) / 32;
+        const bool shared = cudaGetDevice(&dev) == cudaSuccess &&
+                            cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
+                            blocks32 > nsm;
+        b->blk.resize(n);
+        for (int i = 0; i < n; ++i) {
+            const muca_ctx *c = b->sys[i];
+            b->blk[i] = (shared && c->block_small_p && spin_sweep_tn_fits(c->system, c->L, c->B, 64)) ? 64 : c->block;
+        }
+    }
     std::vector<int2> tiles;
     std::vector<UpdateArgs> upd(n);
     std::vector<DevState *> states(n);
@@ -1420,9 +1455,10 @@ int muca_batch_run(muca_batch *b, int n_iter, int64_t sweeps, int use_graph)
     for (int i = 0; i < n; ++i)
         if (b->sys[i]->open)
             return fail(MUCA_ERR_STATE, "system %d has unmerged sweeps; call muca_merge_and_update first", i);
-    for (int i = 0; i < n; ++i) b->h_sys[i] = sweep_args(b->sys[i], sweeps, b->block);
+    auto sweeps_of = [&](int i) { return b->sw.empty() ? sweeps : b->sw[i]; };
+    for (int i = 0; i < n; ++i) b->h_sys[i] = sweep_args(b->sys[i], sweeps_of(i), b->block);
     b->h_own.resize(n);
-    for (int i = 0; i < n; ++i) b->h_own[i] = sweep_args(b->sys[i], sweeps, b->sys[i]->block);
+    for (int i = 0; i < n; ++i) b->h_own[i] = sweep_args(b->sys[i], sweeps_of(i), b->blk[i]);
     // order the batch's own stream after the systems' earlier work
     MUCA_CUDA(cudaEventRecord(b->ev_in, b->ctx_stream));
     MUCA_CUDA(cudaStreamWaitEvent(b->stream, b->ev_in, 0));
@@ -1431,12 +1467,13 @@ int muca_batch_run(muca_batch *b, int n_iter, int64_t sweeps, int use_graph)
     // the flatness ratio may change between runs
     std::vector<UpdateArgs> upd(n);
     for (int i = 0; i < n; ++i) {
-        upd[i] = update_args(b->sys[i]);  // form 1: each system's own block count
-        if (b->form == 0) upd[i].nblocks = (b->sys[i]->p + b->block - 1) / b->block;
+        upd[i] = update_args(b->sys[i]);
+        const int blk = (b->form == 0) ? b->block : b->blk[i];  // form 1: each system's block in the batch
+        upd[i].nblocks = (b->sys[i]->p + blk - 1) / blk;
     }
     MUCA_CUDA(cudaMemcpyAsync(b->d_upd, upd.data(), sizeof(UpdateArgs) * n, cudaMemcpyHostToDevice, b->stream));
     if (use_graph) {
-        if (!b->exec || b->g_iter != n_iter || b->g_sweeps != sweeps) {
+        if (!b->exec || b->g_iter != n_iter || b->g_sweeps != sweeps || b->g_sw != b->sw) {
             if (b->exec) {
                 cudaGraphExecDestroy(b->exec);
                 b->exec = nullptr;
@@ -1461,6 +1498,7 @@ int muca_batch_run(muca_batch *b, int n_iter, int64_t sweeps, int use_graph)
             }
             b->g_iter = n_iter;
             b->g_sweeps = sweeps;
+            b->g_sw = b->sw;
         }
         MUCA_CUDA(cudaGraphLaunch(b->exec, b->stream));
     } else {
@@ -1491,6 +1529,26 @@ int muca_batch_free(muca_batch *b)
     cudaEventDestroy(b->ev_out);
     delete b;
     if (e != cudaSuccess) return fail(MUCA_ERR_CUDA, "muca_batch_free: %s", cudaGetErrorString(e));
+    return MUCA_OK;
+}
+
+int muca_batch_set_sweeps(muca_batch *b, const int64_t *sweeps, int n)
+{
+    if (!b) return fail(MUCA_ERR_ARG, "batch is NULL");
+    std::vector<int64_t> sw;
+    if (sweeps) {
+        if (n != (int)b->sys.size()) return fail(MUCA_ERR_ARG, "need %d sweep counts, got %d", (int)b->sys.size(), n);
+        for (int i = 0; i < n; ++i)
+            if (sweeps[i] < 1) return fail(MUCA_ERR_ARG, "system %d: sweeps must be >= 1", i);
+        sw.assign(sweeps, sweeps + n);
+    }
+    MUCA_CUDA(cudaStreamSynchronize(b->stream));  // the tile list may be in use
+    b->sw = sw;
+    b->order = batch_order(b);
+    std::vector<int2> tiles;
+    for (int i : b->order)
+        for (int w0 = 0; w0 < b->sys[i]->p; w0 += b->block) tiles.push_back(make_int2(i, w0));
+    MUCA_CUDA(cudaMemcpy(b->d_tiles, tiles.data(), sizeof(int2) * tiles.size(), cudaMemcpyHostToDevice));
     return MUCA_OK;
 }
 

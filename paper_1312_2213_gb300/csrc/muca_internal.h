@@ -165,7 +165,7 @@ cudaError_t launch_merge_batch(const UpdateArgs *d_args, int n, int max_bins, cu
 cudaError_t launch_recursion_batch(const UpdateArgs *d_args, int n, int max_nreach, cudaStream_t s);
 cudaError_t prepare_recursion_batch(int max_nreach);
 cudaError_t launch_thresholds_batch(const UpdateArgs *d_args, int n, int max_cells, cudaStream_t s);
-cudaError_t launch_advance_batch(DevState *const *d_states, int n, int64_t sweeps, cudaStream_t s);
+cudaError_t launch_advance_batch(DevState *const *d_states, const SpinSweepArgs *d_sys, int n, cudaStream_t s);
 cudaError_t launch_recursion(const UpdateArgs &a, cudaStream_t s);
 cudaError_t launch_thresholds(const UpdateArgs &a, cudaStream_t s);
 cudaError_t launch_advance(DevState *st, int64_t sweeps, cudaStream_t s);

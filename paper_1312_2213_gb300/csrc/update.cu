@@ -192,10 +192,10 @@ __global__ void k_thresholds_batch(const UpdateArgs *__restrict__ arr)
 
 __global__ void k_advance(DevState *st, long long sweeps) { st->sweep_counter += (unsigned long long)sweeps; }
 
-__global__ void k_advance_batch(DevState *const *states, int n, long long sweeps)
+__global__ void k_advance_batch(DevState *const *states, const SpinSweepArgs *sys, int n)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) states[i]->sweep_counter += (unsigned long long)sweeps;
+    if (i < n) states[i]->sweep_counter += (unsigned long long)sys[i].sweeps;  // each system's own count
 }
 
 __global__ void k_init_weights(const UpdateArgs a)
@@ -460,9 +460,9 @@ cudaError_t launch_thresholds_batch(const UpdateArgs *d_args, int n, int max_cel
     return cudaGetLastError();
 }
 
-cudaError_t launch_advance_batch(DevState *const *d_states, int n, int64_t sweeps, cudaStream_t s)
+cudaError_t launch_advance_batch(DevState *const *d_states, const SpinSweepArgs *d_sys, int n, cudaStream_t s)
 {
-    k_advance_batch<<<(n + 127) / 128, 128, 0, s>>>(d_states, n, (long long)sweeps);
+    k_advance_batch<<<(n + 127) / 128, 128, 0, s>>>(d_states, d_sys, n);
     return cudaGetLastError();
 }
 

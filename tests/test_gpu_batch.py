@@ -53,6 +53,39 @@ def test_batch_equals_individual_runs(use_graph, form):
 
 
 @pytest.mark.parametrize("form", [0, 1])
+@pytest.mark.parametrize("use_graph", [False, True])
+def test_batch_with_per_system_sweeps(use_graph, form):
+    """Each system iterates at its own length (as with each system's M_opt, Eq. 4): the batch
+    equals every context run alone with its own sweep count, iteration by iteration.  New counts
+    re-capture the graph and reorder the launches; None restores the run's argument."""
+    ref, sys_ = _make(), _make()
+    b = m.Batch(sys_, form=form)
+
+    def alone(counts, n_iter):
+        for _ in range(n_iter):
+            for c, sw in zip(ref, counts):
+                c.iterate(sw)
+                c.merge_and_update()
+
+    total = np.zeros(len(MIX), dtype=np.int64)
+    for counts, n_iter, arg in (([3, 17, 8, 25, 11, 40], 2, 5), ([7, 2, 13, 5, 9, 4], 2, 5), (None, 1, 6)):
+        b.set_sweeps(counts)
+        b.run(n_iter, arg, use_graph=use_graph)
+        eff = counts if counts is not None else [arg] * len(MIX)
+        alone(eff, n_iter)
+        total += n_iter * np.asarray(eff)
+    for r, s, t in zip(ref, sys_, total):
+        np.testing.assert_array_equal(r.histogram(), s.histogram())
+        np.testing.assert_array_equal(r.lnW().view(np.uint64), s.lnW().view(np.uint64))
+        np.testing.assert_array_equal(r.spins(), s.spins())
+        assert r.sweep_counter() == s.sweep_counter() == t
+    for bad in ([3] * (len(MIX) - 1), [3, 0, 3, 3, 3, 3]):
+        with pytest.raises(m.MucaError):
+            b.set_sweeps(bad)
+    b.close()
+
+
+@pytest.mark.parametrize("form", [0, 1])
 def test_batch_graph_replay_matches_oracle(form):
     sys_ = _make()
     b = m.Batch(sys_, form=form)
