@@ -39,9 +39,15 @@ namespace muca {
 
 bool polymer_supported(int N) { return N >= 2 && N <= kPolyMaxN; }
 
+// (sigma/r)^2 from the hardware's approximate reciprocal (PTX rcp.approx.ftz.f32, at most one
+// ulp off: the r^-12 term then carries a few ulp, a few 1e-8 of the pair's error scale
+// |v| + |r v'|, which is 48 (sigma/r)^12 and more).  A correctly rounded reciprocal took a
+// quarter of the sweep's time at N = 128.
 __device__ __forceinline__ float lj_energy(float r2, const PolyArgs &a)
 {
-    const float ir2 = __frcp_rn(r2) * a.lj_sigma2;  // (sigma/r)^2; sigma = 1 in model 0
+    float rr;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rr) : "f"(r2));
+    const float ir2 = rr * a.lj_sigma2;  // sigma = 1 in model 0
     const float ir6 = ir2 * ir2 * ir2;
     const float v = 4.0f * (ir6 * ir6 - ir6) - a.lj_shift;
     return r2 < a.lj_rc2 ? v : 0.0f;
