@@ -332,6 +332,15 @@ def test_potts_L64_bit_exact(record, pipeline):
     run_pair(m.POTTS2D, 64, 10, 64, 17, 3, 10, record=record, nthreads=NT, pipeline=pipeline)
 
 
+@pytest.mark.parametrize("q,block", [(10, 64), (5, 32)])
+def test_potts_L64_many_redone_rows(q, block):
+    """The row redo behind the split table at scale: 608 walkers x 3 x 12 sweeps = 9e7 attempts, of
+    which some 700 tie on the 16-bit stand-ins (2^-16 an attempt whose threshold is not 'always'),
+    so rows with a tie on the last site, with two ties, and ties in both blocks' consumers all
+    occur.  Bit-exact against the oracle after every iteration."""
+    run_pair(m.POTTS2D, 64, q, 608, 23, 3, 12, block=block, nthreads=NT)
+
+
 def test_potts_L64_q2_split_table():
     """q = 2 at L = 64 in the code form: the odd bins are unreachable (threshold 0 into them)."""
     run_pair(m.POTTS2D, 64, 2, 40, 5, 2, 8, nthreads=NT)
