@@ -635,8 +635,10 @@ __device__ __forceinline__ bool potts_split_full(const uint32_t *__restrict__ Tg
     return T == kAlways || u < T;
 }
 
-// Row layout of the Potts tables: 10 words a bin (9 thresholds, the counter), or at
-// L = 64 the split row of 5 words: the 9 upper halves of the thresholds and a 16-bit
+// Row layout of the Potts tables: 11 words a bin (9 thresholds, the counter, a pad word that
+// makes the stride odd, so that the bins of a warp's walkers spread over all 32 banks: 1-2 %
+// faster than 10 words), 10 at L = 48 (where the 11th would not fit), or at L = 64 the split
+// row of 5 words: the 9 upper halves of the thresholds and a 16-bit
 // counter, the high half of word 4 (whose low half is column 8).  A visit adds 2^16 to
 // word 4, so column 8 never changes; a producer warp empties the 16-bit counters every
 // few rows (split_scan) before they can wrap.  Codes are scaled to byte offsets into a
@@ -645,7 +647,7 @@ __device__ __forceinline__ bool potts_split_full(const uint32_t *__restrict__ Tg
 template <int L>
 struct PottsRow {
     static constexpr bool split = PottsSplit<L>::on;
-    static constexpr int RSW = split ? 5 : 10;             // words a row
+    static constexpr int RSW = split ? 5 : (L <= 32 ? 11 : 10);  // words a row
     static constexpr int HW = split ? 4 : 9;               // counter word
     static constexpr uint32_t ONE = split ? 0x10000u : 1u;  // one visit
     static constexpr int CSH = split ? 16 : 0;             // counter shift in its word
@@ -895,11 +897,11 @@ __host__ __device__ constexpr size_t tnp_warp_bytes(int L, int RD)
     return (size_t)RD * (size_t)(L / 4) * 32 * ((L > 48 ? 8 : 16) + 8 + 8) + (size_t)(L > 48 ? 2 : 1) * (L / 4) * 32 * 4;
 }
 
-// Bytes of the Potts threshold + counter table: 10 words a bin, or the split rows of
-// 5 words at L = 64.
+// Bytes of the Potts threshold + counter table: PottsRow<L>::RSW words a bin (11, 10 at
+// L = 48, the split rows of 5 at L = 64).
 __host__ __device__ constexpr size_t tnp_table_bytes(int L, int B)
 {
-    return ((size_t)B * (L > 48 ? 20 : 40) + 15) / 16 * 16;
+    return ((size_t)B * (L > 48 ? 20 : (L > 32 ? 40 : 44)) + 15) / 16 * 16;
 }
 
 template <int L, int RD>
