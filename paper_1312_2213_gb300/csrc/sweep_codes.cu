@@ -481,7 +481,7 @@ __host__ __device__ __forceinline__ uint16_t split_hi(uint32_t T)
 // consumer warps) keeps every counter below 2^16.  Words are read eight at a time so the
 // loads overlap; the AND runs only where a count is not zero.
 template <int RS>
-__device__ __forceinline__ void split_scan(const uint32_t *sTH, unsigned long long *Hb, int B, int lane)
+__device__ __forceinline__ void split_scan(uint32_t *sTH, unsigned long long *Hb, int B, int lane)
 {
     const int sbase = (int)__cvta_generic_to_shared(sTH);
     for (int b0 = lane; b0 < B; b0 += 8 * 32) {
@@ -497,7 +497,7 @@ __device__ __forceinline__ void split_scan(const uint32_t *sTH, unsigned long lo
         for (int i = 0; i < 8; ++i) {
             const int b = b0 + 32 * i;
             if (w[i] >> 16) {
-                const uint32_t old = atomicAnd(const_cast<uint32_t *>(&sTH[b * RS + RS - 1]), 0xFFFFu);
+                const uint32_t old = atomicAnd(&sTH[b * RS + RS - 1], 0xFFFFu);
                 atomicAdd(&Hb[b], (unsigned long long)(old >> 16));
             }
         }
@@ -509,11 +509,11 @@ __device__ __forceinline__ void produce_sweep_potts_tn(uint32_t g, uint32_t wid,
                                                        const uint32_t *__restrict__ lat, int ps, uint32_t q,
                                                        void *ring_u, uint2 *ring_c, uint2 *ring_op,
                                                        unsigned long long *full, unsigned long long *empty, int &k,
-                                                       bool &bad, int drop_k, const uint32_t *sTH, unsigned long long *Hb,
+                                                       bool &bad, int drop_k, uint32_t *sTH, unsigned long long *Hb,
                                                        int B, int F, int &since)
 {
     constexpr bool SPLIT = PottsSplit<L>::on;
-    constexpr int RSW = SPLIT ? 5 : 10;
+    constexpr int RSW = 5;  // words a split row (only the split table is scanned)
     static_assert(L % 8 == 0, "whole nibble words a row");
     constexpr int WR = L / 8;
     constexpr size_t S = (size_t)(L / 4) * 32;
