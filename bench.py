@@ -262,7 +262,57 @@ def run_polymer(m, torch, p=4096, budget_attempts=2.0e8):
         res["chains"][str(N)] = {"sweeps": sw, "attempts_per_s": att / t, "pair_evals_per_s": att * 2 * (N - 1) / t,
                                  "energy_drift": g.drift()}
         g.close()
+    res["lengths_batched"] = run_polymer_batch(m, torch, W, p)
     return res
+
+
+def run_polymer_batch(m, torch, W, p=4096, iters=3):
+    """The four lengths side by side in one batch (each 2000 / N sweeps an iteration, so each does
+    about the same attempts) against one after another (plain)."""
+    Ns = (13, 32, 64, 128)
+    sweeps = [max(1, 2000 // N) for N in Ns]
+
+    def make(seed0):
+        out = []
+        for i, N in enumerate(Ns):
+            g = m.Muca(m.POLYMER3D, N, 0, p, seed0 + i, window=(W[str(N)]["e_lo"], W[str(N)]["e_hi"]))
+            g.iterate(max(1, 200 // N))
+            g.merge_and_update()
+            out.append(g)
+        return out
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        fn()
+        b.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / 1e3
+
+    att = iters * p * sum(N * s_ for N, s_ in zip(Ns, sweeps))
+    sysA = make(300)
+
+    def plain():
+        for _ in range(iters):
+            for g, s_ in zip(sysA, sweeps):
+                g.iterate(s_)
+                g.merge_and_update()
+
+    t_plain = timed(plain)
+    sysB = make(400)
+    batch = m.Batch(sysB)
+    batch.set_sweeps(sweeps)
+    batch.run(1, 1, use_graph=False)
+    t_batch = timed(lambda: batch.run(iters, 1, use_graph=False))
+    batch.run(iters, 1, use_graph=True)  # capture
+    t_graph = timed(lambda: batch.run(iters, 1, use_graph=True))
+    batch.close()
+    for g in sysA + sysB:
+        g.close()
+    return {"sweeps_per_iteration": dict(zip([str(N) for N in Ns], sweeps)), "iterations": iters,
+            "plain_attempts_per_s": att / t_plain, "batched_attempts_per_s": att / t_batch,
+            "graph_attempts_per_s": att / t_graph, "graph_over_plain": t_plain / t_graph}
 
 
 def dist_env():

@@ -302,9 +302,10 @@ int muca_get_thresholds(muca_ctx *ctx, uint32_t *host_out, int64_t n);
 int muca_get_sweep_counter(muca_ctx *ctx, int64_t *host_out);
 
 /* Batching.  A batch advances several contexts together -- different systems,
- * lattice sizes and walker counts, e.g. Ising L in {16..64} and q = 10 Potts
- * L in {16..48} with 2048 walkers each -- so that systems too small to fill the
- * GPU alone fill it together.  Each iteration of muca_batch_run is the paper's
+ * lattice sizes, polymer lengths and walker counts, e.g. Ising L in {16..64} and
+ * q = 10 Potts L in {16..48} with 2048 walkers each, or polymers of N = 13..128
+ * beads -- so that systems too small to fill the GPU alone fill it together
+ * (polymers in form 1 only).  Each iteration of muca_batch_run is the paper's
  * Fig. 1 step for every system at once: sweeps of all walkers of all systems
  * (side by side, or in one persistent launch: see muca_batch_set_form), then the merge, the
  * accumulated-statistics recursion and the threshold rebuild for all systems

@@ -1310,8 +1310,10 @@ std::vector<int> batch_order(const muca_batch *b)
     const int n = (int)b->sys.size();
     std::vector<int> order(n);
     for (int i = 0; i < n; ++i) order[i] = i;
-    auto cost = [&](int i) {
-        return (double)b->sys[i]->N * (b->sys[i]->system == kPotts ? 2.5 : 1.0) * (b->sw.empty() ? 1.0 : (double)b->sw[i]);
+    auto cost = [&](int i) {  // a polymer bead attempt counted as ~40 spin attempts (its pair terms)
+        const muca_ctx *c = b->sys[i];
+        const double w = c->system == kPotts ? 2.5 : (c->system == kPolymer ? 40.0 : 1.0);
+        return (double)c->N * w * (b->sw.empty() ? 1.0 : (double)b->sw[i]);
     };
     for (int i = 1; i < n; ++i)
         for (int j = i; j > 0 && cost(order[j]) > cost(order[j - 1]); --j) std::swap(order[j], order[j - 1]);
@@ -1326,7 +1328,14 @@ int batch_enqueue_iteration(muca_batch *b, int64_t sweeps)
         // heaviest first, so that their blocks take the SMs before the light systems' blocks
         for (int i : b->order) {
             MUCA_CUDA(cudaStreamWaitEvent(b->sub[i], b->ev_fork, 0));
-            MUCA_CUDA(launch_system_sweep(b->sys[i], b->h_own[i], b->sub[i], b->blk[i]));
+            muca_ctx *c = b->sys[i];
+            if (c->system == kPolymer) {  // as muca_iterate: the sweeps, then the energies from scratch
+                const PolyArgs pa = poly_args(c, b->h_sys[i].sweeps);
+                MUCA_CUDA(launch_poly_sweep(pa, c->block, b->sub[i]));
+                MUCA_CUDA(launch_poly_energy(pa, 1, b->sub[i]));
+            } else {
+                MUCA_CUDA(launch_system_sweep(c, b->h_own[i], b->sub[i], b->blk[i]));
+            }
             MUCA_CUDA(cudaEventRecord(b->ev_join[i], b->sub[i]));
         }
         for (int i = 0; i < n; ++i) MUCA_CUDA(cudaStreamWaitEvent(b->stream, b->ev_join[i], 0));
@@ -1337,7 +1346,11 @@ int batch_enqueue_iteration(muca_batch *b, int64_t sweeps)
     MUCA_CUDA(launch_advance_batch(b->d_states, b->d_sys, n, b->stream));
     MUCA_CUDA(launch_merge_batch(b->d_upd, n, b->max_bins, b->stream));
     MUCA_CUDA(launch_recursion_batch(b->d_upd, n, b->max_nreach, b->stream));
-    MUCA_CUDA(launch_thresholds_batch(b->d_upd, n, b->max_cells, b->stream));
+    if (b->max_cells > 0)  // (polymers skip it)
+        MUCA_CUDA(launch_thresholds_batch(b->d_upd, n, b->max_cells, b->stream));
+    for (int i = 0; i < n; ++i)
+        if (b->sys[i]->system == kPolymer)
+            MUCA_CUDA(launch_poly_lnwq(b->sys[i]->lnW, b->sys[i]->lnWq, b->sys[i]->B, b->stream));
     return MUCA_OK;
 }
 
@@ -1354,8 +1367,6 @@ int muca_batch_create(muca_ctx *const *systems, int n, muca_batch **out)
         if (!systems[i]) return fail(MUCA_ERR_ARG, "system %d is NULL", i);
         if (systems[i]->stream != systems[0]->stream)
             return fail(MUCA_ERR_ARG, "all systems of a batch must use the same stream");
-        if (systems[i]->system == kPolymer)
-            return fail(MUCA_ERR_ARG, "system %d: the polymer is not part of spin batches", i);
         if (systems[i]->observables)
             return fail(MUCA_ERR_ARG, "system %d records observables, which batches do not support", i);
         for (int j = 0; j < i; ++j)
@@ -1395,18 +1406,23 @@ int muca_batch_create(muca_ctx *const *systems, int n, muca_batch **out)
     std::vector<DevState *> states(n);
     for (int i = 0; i < n; ++i) {
         muca_ctx *c = b->sys[i];
-        const size_t sm = spin_sweep_smem_bytes(c->system, c->B);
-        if (sm <= kMaxSmem) b->smem = std::max(b->smem, sm);
-        else b->tiles_fit = false;  // e.g. q-Potts at L = 64: only form 1 runs it
+        if (c->system == kPolymer) {
+            b->tiles_fit = false;  // the tile launch is for lattices: polymers run in form 1
+        } else {
+            const size_t sm = spin_sweep_smem_bytes(c->system, c->B);
+            if (sm <= kMaxSmem) b->smem = std::max(b->smem, sm);
+            else b->tiles_fit = false;  // e.g. q-Potts at L = 64: only form 1 runs it
+            b->max_cells = std::max(b->max_cells, c->B * c->C);
+        }
         b->max_bins = std::max(b->max_bins, c->B);
         b->max_nreach = std::max(b->max_nreach, c->nreach);
-        b->max_cells = std::max(b->max_cells, c->B * c->C);
         upd[i] = update_args(c);
         upd[i].nblocks = (c->p + b->block - 1) / b->block;
         states[i] = c->state;
     }
     for (int i : order)
-        for (int w0 = 0; w0 < b->sys[i]->p; w0 += b->block) tiles.push_back(make_int2(i, w0));
+        if (b->sys[i]->system != kPolymer)
+            for (int w0 = 0; w0 < b->sys[i]->p; w0 += b->block) tiles.push_back(make_int2(i, w0));
     b->order = order;
     b->ntiles = (int)tiles.size();
     b->h_sys.resize(n);
@@ -1456,9 +1472,21 @@ int muca_batch_run(muca_batch *b, int n_iter, int64_t sweeps, int use_graph)
         if (b->sys[i]->open)
             return fail(MUCA_ERR_STATE, "system %d has unmerged sweeps; call muca_merge_and_update first", i);
     auto sweeps_of = [&](int i) { return b->sw.empty() ? sweeps : b->sw[i]; };
-    for (int i = 0; i < n; ++i) b->h_sys[i] = sweep_args(b->sys[i], sweeps_of(i), b->block);
+    for (int i = 0; i < n; ++i)
+        if (b->sys[i]->system == kPolymer && sweeps_of(i) > 0x7fffffffLL / b->sys[i]->N)
+            return fail(MUCA_ERR_RANGE, "system %d: too many sweeps in one iteration", i);
     b->h_own.resize(n);
-    for (int i = 0; i < n; ++i) b->h_own[i] = sweep_args(b->sys[i], sweeps_of(i), b->blk[i]);
+    for (int i = 0; i < n; ++i) {
+        if (b->sys[i]->system == kPolymer) {  // only the sweep count and the state (counter advance)
+            SpinSweepArgs z{};
+            z.sweeps = sweeps_of(i);
+            z.state = b->sys[i]->state;
+            b->h_sys[i] = b->h_own[i] = z;
+        } else {
+            b->h_sys[i] = sweep_args(b->sys[i], sweeps_of(i), b->block);
+            b->h_own[i] = sweep_args(b->sys[i], sweeps_of(i), b->blk[i]);
+        }
+    }
     // order the batch's own stream after the systems' earlier work
     MUCA_CUDA(cudaEventRecord(b->ev_in, b->ctx_stream));
     MUCA_CUDA(cudaStreamWaitEvent(b->stream, b->ev_in, 0));
@@ -1468,8 +1496,10 @@ int muca_batch_run(muca_batch *b, int n_iter, int64_t sweeps, int use_graph)
     std::vector<UpdateArgs> upd(n);
     for (int i = 0; i < n; ++i) {
         upd[i] = update_args(b->sys[i]);
-        const int blk = (b->form == 0) ? b->block : b->blk[i];  // form 1: each system's block in the batch
-        upd[i].nblocks = (b->sys[i]->p + blk - 1) / blk;
+        if (b->sys[i]->system != kPolymer) {  // (a polymer's open histogram is one slot)
+            const int blk = (b->form == 0) ? b->block : b->blk[i];  // form 1: each system's block in the batch
+            upd[i].nblocks = (b->sys[i]->p + blk - 1) / blk;
+        }
     }
     MUCA_CUDA(cudaMemcpyAsync(b->d_upd, upd.data(), sizeof(UpdateArgs) * n, cudaMemcpyHostToDevice, b->stream));
     if (use_graph) {
@@ -1547,8 +1577,10 @@ int muca_batch_set_sweeps(muca_batch *b, const int64_t *sweeps, int n)
     b->order = batch_order(b);
     std::vector<int2> tiles;
     for (int i : b->order)
-        for (int w0 = 0; w0 < b->sys[i]->p; w0 += b->block) tiles.push_back(make_int2(i, w0));
-    MUCA_CUDA(cudaMemcpy(b->d_tiles, tiles.data(), sizeof(int2) * tiles.size(), cudaMemcpyHostToDevice));
+        if (b->sys[i]->system != kPolymer)
+            for (int w0 = 0; w0 < b->sys[i]->p; w0 += b->block) tiles.push_back(make_int2(i, w0));
+    if (!tiles.empty())
+        MUCA_CUDA(cudaMemcpy(b->d_tiles, tiles.data(), sizeof(int2) * tiles.size(), cudaMemcpyHostToDevice));
     return MUCA_OK;
 }
 

@@ -155,6 +155,7 @@ __global__ void __launch_bounds__(1024) k_recursion_batch(const UpdateArgs *__re
 
 __device__ __forceinline__ void thresholds_body(const UpdateArgs &a, int i)
 {
+    if (a.system == kPolymer) return;  // its weights go to the fixed-point table instead (k_poly_lnwq)
     const int C = num_cols(a.system);
     if (i >= a.B * C) return;
     const int b = i / C, c = i - (i / C) * C;

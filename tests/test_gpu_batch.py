@@ -207,3 +207,43 @@ def test_batch_runs_after_restoring_a_merged_checkpoint():
         b.run(1, 5, use_graph=False)
     assert e.value.code == -5
     b.close()
+
+
+POLY_MIX = [(13, 64, (33.3, 87.3), 21), (32, 40, (53.0, 176.7), 22), (64, 33, (106.6, 405.7), 23)]
+
+
+def _make_poly_mix():
+    out = [m.Muca(m.POLYMER3D, N, 0, p, seed, window=win) for N, p, win, seed in POLY_MIX]
+    out.append(m.Muca(m.ISING2D, 16, 2, 64, 24))
+    return out
+
+
+@pytest.mark.parametrize("use_graph", [False, True])
+def test_polymer_lengths_in_one_batch(use_graph):
+    """Polymers of several lengths (and a lattice system) side by side in one batch, with their
+    own sweep counts: every context ends bit-identical to running alone (coordinates, energies
+    refreshed from scratch, histogram, ln W), and the tile form is refused."""
+    sweeps = [6, 3, 2, 20]
+    ref, sys_ = _make_poly_mix(), _make_poly_mix()
+    for _ in range(3):
+        for c, sw in zip(ref, sweeps):
+            c.iterate(sw)
+            c.merge_and_update()
+    b = m.Batch(sys_)
+    with pytest.raises(m.MucaError):
+        b.set_form(0)
+    b.set_sweeps(sweeps)
+    b.run(3, 1, use_graph=use_graph)
+    for c in sys_:
+        c.synchronize()
+    for r, s in zip(ref, sys_):
+        np.testing.assert_array_equal(r.histogram(), s.histogram())
+        np.testing.assert_array_equal(r.lnW().view(np.uint64), s.lnW().view(np.uint64))
+        assert r.sweep_counter() == s.sweep_counter()
+        if r.system == m.POLYMER3D:
+            np.testing.assert_array_equal(r.coords(), s.coords())
+            np.testing.assert_array_equal(r.energies(), s.energies())
+            np.testing.assert_array_equal(r.bins(), s.bins())
+        else:
+            np.testing.assert_array_equal(r.spins(), s.spins())
+    b.close()
