@@ -282,6 +282,7 @@ class Muca:
         self.C = {ISING2D: 5, POTTS2D: 9, ISING2D_MUMA: 10}.get(system, 0)
         if stream is not None:
             muca_set_stream(self.h, int(getattr(stream, "cuda_stream", stream)))
+        self.beta = beta
         if beta is not None:
             muca_set_param(self.h, "beta", beta)
         if record:

@@ -132,6 +132,114 @@ def tune(system: int, L: int, q: int, p: int, beta: float = 0.4407, window=None,
     return res
 
 
+BATCH_BLOCKS = (32, 64)  # walkers per block of the code form
+
+
+def _weight(spec) -> float:
+    system, L = spec[0], spec[1]
+    return L if system == POLYMER3D else L * L * (2.5 if system == 1 else 1.0)
+
+
+MIN_GAIN = 0.03  # a batch shape must shorten the iteration by this much to replace another
+
+
+def _time_batch(specs, blocks, sweeps, iters=3):
+    """Milliseconds of one graph-captured batch iteration (the best of `iters`) on scratch
+    contexts with the given walkers per block (None: the context's default)."""
+    import torch
+
+    from . import Batch
+
+    ctxs = []
+    try:
+        for k, (system, L, q, p, extra) in enumerate(specs):
+            kw = {"block": blocks[k]} if blocks[k] is not None else {}
+            if system == POLYMER3D:
+                kw["window"] = extra
+            elif system == ISING2D_MUMA:
+                kw["beta"] = extra
+            ctxs.append(Muca(system, L, q, p, 777 + k, **kw))
+        b = Batch(ctxs)
+        try:
+            b.set_sweeps(sweeps)
+            b.run(1, 1, use_graph=True)  # capture and warm up
+            best = None
+            for _ in range(iters):
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                b.run(1, 1, use_graph=True)
+                e1.record()
+                torch.cuda.synchronize()
+                t = e0.elapsed_time(e1)
+                best = t if best is None else min(best, t)
+            return best
+        finally:
+            b.close()
+    finally:
+        for c in ctxs:
+            c.close()
+
+
+def tune_batch(specs, sweeps, timer=None, use_cache: bool = True) -> dict:
+    """Walkers per block for every lattice system of a side-by-side batch, chosen on the batch's
+    own iteration time: the systems share the SMs, so the best shape of a system alone need not be
+    the best inside the batch.  `specs` lists (system, L, q, p, extra) with extra = beta for the
+    multimagnetic system, the window for a polymer, else None; `sweeps` the sweeps of each system
+    an iteration (as for Batch.set_sweeps).  Coordinate descent from the library's defaults: for
+    every lattice system, heaviest first, each other block size of the code form is timed with the
+    rest fixed and kept if the iteration gets shorter by at least MIN_GAIN (the spread of one
+    batch timing is a few per cent: where the blocks of nine systems land varies).  Polymers keep their block.  Returns
+    {"blocks": [...] (None = the default), "ms": ..., "trials": n}; `timer(blocks)` replaces the
+    timing (tests)."""
+    specs = [tuple(s_) for s_ in specs]
+    sweeps = [int(x) for x in sweeps]
+    path = cache_path()
+    device = _device_name() if timer is None else "test"
+    key = "batch/%s/%s/%s" % (json.dumps(specs), json.dumps(sweeps), device)
+    data = _load(path) if use_cache else {}
+    if use_cache and key in data:
+        return data[key]
+    t_of = timer or (lambda blocks: _time_batch(specs, blocks, sweeps))
+    blocks = [None] * len(specs)
+    best = t_of(blocks)
+    trials = 1
+    order = sorted(range(len(specs)), key=lambda k: -_weight(specs[k]) * sweeps[k])
+    for k in order:
+        if specs[k][0] == POLYMER3D:
+            continue
+        for cand in BATCH_BLOCKS:
+            trial = list(blocks)
+            trial[k] = cand
+            try:
+                t = t_of(trial)
+            except Exception:
+                t = None  # a block size this system's code form cannot take
+            trials += 1
+            if t is not None and t < best * (1.0 - MIN_GAIN):
+                best, blocks = t, trial
+    res = {"blocks": blocks, "ms": best, "trials": trials}
+    if use_cache:
+        data = _load(path)
+        data[key] = res
+        _store(path, data)
+    return res
+
+
+def apply_batch(contexts, sweeps, **kw) -> dict:
+    """Tune the walkers per block of the contexts for a batch with these per-system sweeps and set
+    them; call before the contexts' first iterate and before creating the Batch."""
+    specs = []
+    for g in contexts:
+        extra = g.window if g.system == POLYMER3D else (g.beta if g.system == ISING2D_MUMA else None)
+        specs.append((g.system, g.L, g.q, g.p, extra))
+    res = tune_batch(specs, sweeps, **kw)
+    for g, bl in zip(contexts, res["blocks"]):
+        if bl is not None:
+            g.set_param("block", bl)
+    return res
+
+
 def apply(g: Muca, **kw) -> dict:
     """Tune (or look up) the context's configuration and set the result on it; call before its
     first iterate."""

@@ -37,3 +37,29 @@ def test_polymer_tunes_block_only(tmp_path, monkeypatch):
     monkeypatch.setenv("MUCA_TUNE_CACHE", str(tmp_path / "tune.json"))
     r = autotune.tune(m.POLYMER3D, 32, 0, 4096, timer=lambda b: {128: 2.0, 256: 1.0, 512: 1.5}[b])
     assert r["block"] == 256 and "pipeline" not in r
+
+
+def test_batch_tuner_descends_per_system(tmp_path, monkeypatch):
+    """The batch tuner starts from the defaults and keeps a block size only where the whole
+    batch's iteration gets shorter; polymers are left alone; the result is cached."""
+    monkeypatch.setenv("MUCA_TUNE_CACHE", str(tmp_path / "tune.json"))
+    specs = [(m.ISING2D, 64, 2, 2048, None), (m.POTTS2D, 32, 10, 2048, None),
+             (m.POLYMER3D, 13, 0, 1024, (33.3, 87.3)), (m.ISING2D_MUMA, 16, 2, 512, 0.4407)]
+    seen = []
+
+    def timer(blocks):  # the Potts system prefers 64 inside this batch, Ising L = 64 its default
+        seen.append(tuple(blocks))
+        t = 10.0
+        if blocks[1] == 64:
+            t -= 2.0
+        if blocks[0] == 32:
+            t += 5.0
+        if blocks[3] == 32:
+            raise RuntimeError("does not fit")
+        return t
+
+    r = autotune.tune_batch(specs, [95, 122, 150, 3], timer=timer)
+    assert r["blocks"] == [None, 64, None, None] and r["ms"] == 8.0
+    assert all(b[2] is None for b in seen)  # the polymer's block is never tried
+    n = len(seen)
+    assert autotune.tune_batch(specs, [95, 122, 150, 3], timer=timer) == r and len(seen) == n

@@ -38,3 +38,28 @@ def test_polymer_block_tuning(tmp_path, monkeypatch):
     monkeypatch.setenv("MUCA_TUNE_CACHE", str(tmp_path / "tune.json"))
     r = autotune.tune(m.POLYMER3D, 13, 0, 512, window=(33.3, 87.3), sweeps=4)
     assert r["block"] in autotune.POLY_CANDIDATES
+
+
+def test_batch_tuning_keeps_results(tmp_path, monkeypatch):
+    """The batch tuner times real batch iterations, returns a code-form block (or the default) for
+    every lattice system, and contexts set to its choice give the same results as default ones."""
+    import numpy as np
+
+    monkeypatch.setenv("MUCA_TUNE_CACHE", str(tmp_path / "tune.json"))
+    spec = [(m.ISING2D, 32, 2, 300, None), (m.POTTS2D, 16, 10, 200, None), (m.ISING2D_MUMA, 16, 2, 100, 0.4407)]
+    sweeps = [6, 9, 4]
+    r = autotune.tune_batch(spec, sweeps)
+    assert len(r["blocks"]) == 3 and all(b in (None, 32, 64) for b in r["blocks"]) and r["trials"] == 7
+    runs = []
+    for tuned in (False, True):
+        ctx = [m.Muca(s_, L, q, p, 90 + k, beta=x) for k, (s_, L, q, p, x) in enumerate(spec)]
+        if tuned:
+            autotune.apply_batch(ctx, sweeps)  # from the cache written above
+        b = m.Batch(ctx)
+        b.set_sweeps(sweeps)
+        b.run(3, 1)
+        runs.append([(c.histogram(), c.spins(), c.lnW().view(np.uint64)) for c in ctx])
+        b.close()
+    for x, y in zip(*runs):
+        for a_, b_ in zip(x, y):
+            np.testing.assert_array_equal(a_, b_)
