@@ -475,27 +475,28 @@ __host__ __device__ __forceinline__ uint16_t split_hi(uint32_t T)
 
 // The split table's 16-bit counters, emptied into the block's 64-bit slot: every bin's
 // count is taken and cleared with one atomic AND while the consumers keep counting.
-// Producer part 1 of every consumer warp scans all bins after every F-th row it hands
-// over.  Having produced row k it knows its consumer has finished row k - RD, so the
-// consumer counts at most F + RD rows between two scans, and F + RD <= 2^16 / (32 L x
-// consumer warps) keeps every counter below 2^16.  Words are read eight at a time so the
+// Producer part 1 of every consumer warp scans one F-th of the bins (b = slice mod F) after
+// every row it hands over, so every bin is scanned once every F rows and no row carries the
+// whole table.  Having produced row k it knows its consumer has finished row k - RD, so the
+// consumer counts at most F + RD rows between two scans of a bin, and F + RD <= 2^16 / (32 L
+// x consumer warps) keeps every counter below 2^16.  Words are read eight at a time so the
 // loads overlap; the AND runs only where a count is not zero.
 template <int RS>
-__device__ __forceinline__ void split_scan(uint32_t *sTH, unsigned long long *Hb, int B, int lane)
+__device__ __forceinline__ void split_scan(uint32_t *sTH, unsigned long long *Hb, int B, int lane, int slice, int F)
 {
     const int sbase = (int)__cvta_generic_to_shared(sTH);
-    for (int b0 = lane; b0 < B; b0 += 8 * 32) {
+    for (int b0 = slice + F * lane; b0 < B; b0 += F * 8 * 32) {
         uint32_t w[8];
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
-            const int b = b0 + 32 * i;
+            const int b = b0 + F * 32 * i;
             w[i] = 0u;
             if (b < B)
                 asm volatile("ld.shared.u32 %0, [%1];" : "=r"(w[i]) : "r"(checked_addr(sbase + 4 * (b * RS + RS - 1), sbase)));
         }
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
-            const int b = b0 + 32 * i;
+            const int b = b0 + F * 32 * i;
             if (w[i] >> 16) {
                 const uint32_t old = atomicAnd(&sTH[b * RS + RS - 1], 0xFFFFu);
                 atomicAdd(&Hb[b], (unsigned long long)(old >> 16));
@@ -610,9 +611,9 @@ __device__ __forceinline__ void produce_sweep_potts_tn(uint32_t g, uint32_t wid,
         }
         if (k != drop_k) mbar_arrive(&full[slot]);
         ++k;
-        if (SPLIT && PART == 1 && ++since == F) {  // empty the 16-bit counters (split_scan)
-            since = 0;
-            split_scan<RSW>(sTH, Hb, B, (int)(threadIdx.x & 31));
+        if (SPLIT && PART == 1) {  // empty one F-th of the 16-bit counters (split_scan)
+            split_scan<RSW>(sTH, Hb, B, (int)(threadIdx.x & 31), since, F);
+            if (++since == F) since = 0;
         }
 #pragma unroll
         for (int j = 0; j < WR; ++j) {
