@@ -113,6 +113,8 @@ def _bind_polymer(L):
     L.orc_poly_set_beta.argtypes = [c.c_void_p, c.c_double]
     L.orc_poly_set_model.argtypes = [c.c_void_p, c.c_int]
     L.orc_poly_set_moves.argtypes = [c.c_void_p, c.c_int]
+    L.orc_poly_set_grid.argtypes = [c.c_void_p, c.c_int, c.c_double]
+    L.orc_poly_set_grid.restype = c.c_int
     L.orc_poly_reweight.argtypes = [c.c_void_p, c.c_double, c.c_void_p, c.c_void_p]
     L.orc_poly_get_walker_events.argtypes = [c.c_void_p, c.c_void_p]
     L.orc_poly_refresh_energy.argtypes = [c.c_void_p]
@@ -335,12 +337,15 @@ class PolyRun:
     """Oracle multicanonical run of a bead-spring polymer of N beads (p walkers)."""
 
     def __init__(self, N: int, p: int, seed: int, e_lo: float, e_hi: float, K: float = 40.0, R: float = 1.5,
-                 record: int = 0, beta: float = 0.0, model: int = 0, moves: int = 0):
+                 record: int = 0, beta: float = 0.0, model: int = 0, moves: int = 0, bin_k: int = 10,
+                 step_q: int = 1229):
         self._lib = lib()
         self.h = self._lib.orc_poly_create(N, p, seed, e_lo, e_hi, K, R, record)
         if not self.h:
             raise ValueError("oracle: bad polymer configuration")
         self.N, self.p = N, p
+        if (bin_k, step_q) != (10, 1229) and self._lib.orc_poly_set_grid(self.h, bin_k, float(step_q)) < 0:
+            raise ValueError("oracle: bad bin width or step")
         self.B = self._lib.orc_poly_num_bins(self.h)
         if beta > 0:
             self._lib.orc_poly_set_beta(self.h, beta)

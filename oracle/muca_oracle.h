@@ -104,6 +104,7 @@ int orc_poly_num_bins(void *h);
 void orc_poly_set_beta(void *h, double beta);
 void orc_poly_set_model(void *h, int model); /* 1: the paper's parameters (Eq. 7); before init */
 void orc_poly_set_moves(void *h, int moves); /* 1: shifts and spherical rotations */
+int orc_poly_set_grid(void *h, int bin_k, double step_q); /* bin width 1/bin_k, cube side step_q/4096; before init */
 void orc_poly_init(void *h);
 void orc_poly_iterate(void *h, int64_t sweeps, int nthreads);
 void orc_poly_iterate_range(void *h, int64_t sweeps, int w0, int w1, int nthreads);

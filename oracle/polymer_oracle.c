@@ -10,13 +10,15 @@
  *   V_FENE(r) = -(K/2) R^2 ln(1 - (r/R)^2),  r < R, else +infinity (move rejected)
  *               (K = 40, R = 1.5, bond rest length 0)
  * Move: beads i = 0..N-1 in order; bead i is displaced by
- *   delta_a = (u_a - 2^31) * 1229 * 2^-44,  a = x, y, z,
- * i.e. uniform in a cube of side 1229/4096 = 0.30005 on a dyadic grid of
- * spacing 1229 * 2^-44, so every coordinate stays an exact binary64 value and
+ *   delta_a = (u_a - 2^31) * Q * 2^-44,  a = x, y, z,  Q = 1229 by default,
+ * i.e. uniform in a cube of side Q/4096 (0.30005) on a dyadic grid of
+ * spacing Q * 2^-44, so every coordinate stays an exact binary64 value and
  * any implementation that adds the same integers lands on the same bits.
+ * orc_poly_set_grid takes another cube side (as Q = round(side * 4096)).
  * Random words: Philox4x32-10, counter (bead, global sweep, walker, tag 1),
  * words 0..2 the displacement, word 3 the acceptance.
- * Energy bins: b = floor((E - e_lo) * 10) (width 0.1); the window is
+ * Energy bins: b = floor((E - e_lo) * k), width 1/k (k = 10 by default, any
+ * integer k >= 1 through orc_poly_set_grid); the window is
  * 0 <= b < B.  Inside the window a move to E' is accepted iff b' is inside and
  * (d >= 0 or u_3 < floor(2^32 exp(d))), d = ln W(b') - ln W(b); outside the
  * window (walk-in after the start) a move is accepted iff it does not increase
@@ -86,7 +88,8 @@
 #define POLY_TAG_INIT 2u
 #define POLY_TAG_MOVE 3u
 #define POLY_TAG_SPHERE 4u
-#define POLY_STEP_Q 1229.0
+#define POLY_STEP_Q 1229.0 /* default cube side 1229/4096 */
+#define POLY_BIN_K 10      /* default bins per unit energy (width 0.1) */
 #define POLY_GRID 0x1p-44
 #define POLY_RC 2.5
 #define POLY_PAPER_R0 0.7
@@ -96,6 +99,8 @@ typedef struct {
     int N, p, B, record;
     uint64_t seed;
     double e_lo, e_hi, K, R, beta;
+    int bin_k;        /* bins per unit energy (width 1/bin_k) */
+    double step_q;    /* displacement grid units per unit of (u - 2^31) */
     int model;        /* 0: benchmark parameters, 1: the paper's (Eq. 7) */
     int moves;        /* 0: single-bead shifts, 1: shifts and spherical rotations */
     double r0, sigma2; /* model 1: FENE rest length, LJ sigma^2 */
@@ -232,11 +237,11 @@ static double poly_scale_all(const orc_poly *P, const double *X)
     return S;
 }
 
-/* Is E within m of a bin edge of the window (e_lo + k / 10, k = 0 .. B)? */
+/* Is E within m of a bin edge of the window (e_lo + k / bin_k, k = 0 .. B)? */
 static int poly_near_edge(const orc_poly *P, double E, double m)
 {
-    const double t = (E - P->e_lo) * 10.0, k = nearbyint(t);
-    return k >= 0.0 && k <= (double)P->B && fabs(t - k) < 10.0 * m;
+    const double t = (E - P->e_lo) * (double)P->bin_k, k = nearbyint(t);
+    return k >= 0.0 && k <= (double)P->B && fabs(t - k) < (double)P->bin_k * m;
 }
 
 /* A bond of squared length r2 within 1e-5 (relative) of breaking. */
@@ -282,7 +287,7 @@ static double poly_energy_perturbed(const orc_poly *P, const double *X, uint32_t
  * outside it (overlapping beads) cannot overflow the conversion. */
 static int poly_bin(const orc_poly *P, double E)
 {
-    double t = floor((E - P->e_lo) * 10.0);
+    double t = floor((E - P->e_lo) * (double)P->bin_k);
     if (!(t >= -1.0)) return -1;
     if (t > (double)P->B) return P->B;
     return (int)t;
@@ -300,7 +305,9 @@ void *orc_poly_create(int N, int p, uint64_t seed, double e_lo, double e_hi, dou
     P->K = K;
     P->R = R;
     P->record = record;
-    P->B = (int)floor((e_hi - e_lo) * 10.0 + 0.5);
+    P->bin_k = POLY_BIN_K;
+    P->step_q = POLY_STEP_Q;
+    P->B = (int)floor((e_hi - e_lo) * (double)P->bin_k + 0.5);
     if (P->B < 2) { free(P); return NULL; }
     P->X = (double *)calloc((size_t)p * N * 3, sizeof(double));
     P->E = (double *)calloc((size_t)p, sizeof(double));
@@ -339,6 +346,32 @@ int orc_poly_num_bins(void *h) { return ((orc_poly *)h)->B; }
 void orc_poly_set_beta(void *h, double beta) { ((orc_poly *)h)->beta = beta; }
 
 void orc_poly_set_moves(void *h, int moves) { ((orc_poly *)h)->moves = moves; }
+
+/* Bins of width 1/bin_k and a cube of side step_q/4096 for the moves (before init).  The
+ * window keeps its edges; the bin count and every per-bin array follow.  Returns the new bin
+ * count, or -1 for bin_k < 1, step_q < 1 or a window of fewer than 2 bins. */
+int orc_poly_set_grid(void *h, int bin_k, double step_q)
+{
+    orc_poly *P = (orc_poly *)h;
+    if (bin_k < 1 || !(step_q >= 1.0) || step_q != floor(step_q)) return -1;
+    const int B = (int)floor((P->e_hi - P->e_lo) * (double)bin_k + 0.5);
+    if (B < 2) return -1;
+    P->bin_k = bin_k;
+    P->step_q = step_q;
+    if (B != P->B) {
+        P->B = B;
+        double **d[4] = {&P->lnW, &P->lnW_sampled, &P->G, &P->lnR};
+        for (int i = 0; i < 4; ++i) {
+            free(*d[i]);
+            *d[i] = (double *)calloc((size_t)B, sizeof(double));
+        }
+        free(P->H_open);
+        free(P->H_last);
+        P->H_open = (uint64_t *)calloc((size_t)B, sizeof(uint64_t));
+        P->H_last = (uint64_t *)calloc((size_t)B, sizeof(uint64_t));
+    }
+    return B;
+}
 
 /* Spherical rotation of bead i of walker w (move set 1): the new position on
  * the grid in xn, or 0 if Marsaglia's method found no point in 64 pairs. */
@@ -471,7 +504,7 @@ static void poly_walker_sweeps(orc_poly *P, int w, int64_t g0, int64_t sweeps, u
             }
             if (!rotation)
                 for (int a = 0; a < 3; ++a)
-                    xn[a] = X[3 * i + a] + (double)((int64_t)u[a] - 2147483648LL) * POLY_STEP_Q * POLY_GRID;
+                    xn[a] = X[3 * i + a] + (double)((int64_t)u[a] - 2147483648LL) * P->step_q * POLY_GRID;
             /* energy change and its error scale S (old and new pair terms) */
             double dE = 0.0, S = 0.0;
             for (int j = 0; j < N; ++j) {
@@ -747,7 +780,7 @@ void orc_poly_reweight(void *h, double beta, double out[4], double *lnP)
         x[b] = lo[b] = -INFINITY;
         if (P->H_last[b] == 0) continue;
         lo[b] = log((double)P->H_last[b]) - P->lnW_sampled[b];
-        x[b] = lo[b] - beta * (P->e_lo + 0.1 * (b + 0.5));
+        x[b] = lo[b] - beta * (P->e_lo + (b + 0.5) / (double)P->bin_k);
         if (x[b] > m) m = x[b];
         if (lo[b] > m2) m2 = lo[b];
     }
@@ -762,7 +795,7 @@ void orc_poly_reweight(void *h, double beta, double out[4], double *lnP)
         double lp = (x[b] > -INFINITY) ? x[b] - lse : -INFINITY;
         if (lnP) lnP[b] = lp;
         if (x[b] == -INFINITY) continue;
-        double E = P->e_lo + 0.1 * (b + 0.5), pr = exp(lp);
+        double E = P->e_lo + (b + 0.5) / (double)P->bin_k, pr = exp(lp);
         a1 += pr * E;
         a2 += pr * E * E;
     }

@@ -67,6 +67,30 @@ def test_moves_are_exact_and_energy_tracks(orc):
 
 
 
+def test_bin_width_and_cube_side_are_parameters(orc):
+    """Bins of width 1/k and moves in a cube of side Q/4096: every walker's bin is
+    floor((E - e_lo) k), and over one sweep every bead moves relative to bead 0 by whole grid steps
+    Q 2^-44, at most the side Q 2^-12 per axis (bead and bead 0 each move at most half of it); a
+    planted default step would move some bead by more than Q 2^-12."""
+    lo, hi, Q = 33.3, 87.3, 300
+    P = orc.PolyRun(13, 8, 5, lo, hi, bin_k=5, step_q=Q)
+    assert P.B == round((hi - lo) * 5)
+    P.init()
+    P.iterate(300, 4)   # walk in
+    P.update()
+    X0 = P.coords().copy()
+    P.iterate(1, 4)
+    P.update()
+    d = (P.coords() - X0) * 2.0 ** 44
+    assert np.all(d % Q == 0) and np.abs(d).max() <= Q * 2.0 ** 32
+    E, b = P.energy(), P.bins()
+    inside = (E >= lo) & (E < hi)
+    assert inside.any()
+    np.testing.assert_array_equal(b[inside], np.floor((E[inside] - lo) * 5).astype(int))
+    with pytest.raises(ValueError):
+        orc.PolyRun(13, 8, 5, lo, hi, bin_k=0)
+
+
 def test_walk_in_never_moves_away_and_records_inside_only(orc):
     """Thermalisation reading: random-walk chains start far above the N = 13 pilot window; outside
     it a move is accepted only if it does not increase the distance to the window, and only attempts
@@ -96,17 +120,20 @@ def test_walk_in_never_moves_away_and_records_inside_only(orc):
             break
     assert np.all(d == 0.0)
 
-def test_fene_dimer_density_of_states(orc):
+@pytest.mark.parametrize("bin_k,step_q", [(10, 1229), (4, 819)])
+def test_fene_dimer_density_of_states(orc, bin_k, step_q):
     """N = 2: the energy is the FENE energy of the bond vector, uniform in the ball r < R, so the
-    binned density of states is (4 pi/3)(r(E_b)^3 - r(E_a)^3) with r(E) = R sqrt(1 - exp(-2E/(K R^2)))."""
+    binned density of states is (4 pi/3)(r(E_b)^3 - r(E_a)^3) with r(E) = R sqrt(1 - exp(-2E/(K R^2))).
+    Also with bins of width 0.25 and moves in a cube of side 819/4096 = 0.2."""
     e_lo, e_hi = 0.0, 12.0
-    P = orc.PolyRun(2, 64, 11, e_lo, e_hi)
+    P = orc.PolyRun(2, 64, 11, e_lo, e_hi, bin_k=bin_k, step_q=step_q)
     P.init()
     for _ in range(14):
         P.iterate(3000, 8)
         P.update()
     B = P.B
-    edges = [e_lo + 0.1 * b for b in range(B + 1)]
+    assert B == round(12.0 * bin_k)
+    edges = [e_lo + b / bin_k for b in range(B + 1)]
     omega = np.array(ex.fene_dimer_omega(edges, 40.0, 1.5))
     H = P.histogram().astype(float)
     seen = H > 0
@@ -117,7 +144,7 @@ def test_fene_dimer_density_of_states(orc):
     assert np.max(np.abs(lo + off - le)) < 0.15
     # Eq. 2 at bin centres: the oracle's reweighting equals the formula written out on its own
     # estimate ln H - ln W, and, from the exact binned Omega, <E> within the estimate's spread
-    centres = np.array(edges[:-1]) + 0.05
+    centres = np.array(edges[:-1]) + 0.5 / bin_k
     for beta in (0.5, 1.0):
         out, _ = P.reweight(beta)
         la = lo - beta * centres[seen]
