@@ -168,10 +168,12 @@ int muca_init_ex(muca_ctx **out, int system, int L_or_N, int q, int p, uint64_t 
  *                 runs with different values agree within the FP32 tolerance,
  *                 not bit for bit.  Any time.
  *   Polymer only (before the first iterate): "e_lo", "e_hi" (the energy
- *   window, bins of width 0.1, at most 12288 bins; default [2N, 6N)),
- *   "fene_K", "fene_R" (default 40, 1.5).  Fixed: LJ eps = sigma = 1 cut at
- *   2.5 and shifted, acting on beads |i-j| >= 2; FENE on bonds; single-bead
- *   moves uniform in a cube of side 1229/4096 on a 2^-44 grid.
+ *   window, at most 12288 bins; default [2N, 6N)), "bin_width" (1/k for a
+ *   whole k in 1..1000; default 0.1), "step" (the side of the move cube,
+ *   rounded to a multiple of 1/4096 in [1/4096, 2]; default 1229/4096 =
+ *   0.30005), "fene_K", "fene_R" (default 40, 1.5).  Fixed: LJ eps = sigma = 1
+ *   cut at 2.5 and shifted, acting on beads |i-j| >= 2; FENE on bonds;
+ *   single-bead moves uniform in the cube on a 2^-44 grid.
  * Unknown key or bad value: MUCA_ERR_ARG; too late: MUCA_ERR_STATE. */
 int muca_set_param(muca_ctx *ctx, const char *key, double value);
 

@@ -316,6 +316,11 @@ class Muca:
 
     def set_param(self, key: str, value: float):
         muca_set_param(self.h, key, value)
+        if key in ("e_lo", "e_hi", "bin_width"):  # the polymer's bin count follows the window
+            self.B = muca_num_bins(self.h)
+            if key != "bin_width":
+                lo, hi = self.window if self.window is not None else (None, None)
+                self.window = (value, hi) if key == "e_lo" else (lo, value)
 
     def set_stream(self, stream):
         muca_set_stream(self.h, int(getattr(stream, "cuda_stream", stream)))

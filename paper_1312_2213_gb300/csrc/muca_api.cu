@@ -102,6 +102,8 @@ struct muca_ctx {
     // polymer: energies and ln W in fixed point, window and FENE parameters
     long long *Eq = nullptr, *lnWq = nullptr;
     double e_lo = 0.0, e_hi = 0.0, fene_K = 40.0, fene_R = 1.5;
+    int bin_k = 10;            // polymer: bins per unit energy (width 1 / bin_k)
+    long long step_q = kPolyStepQ;  // polymer: move grid units per unit of (u - 2^31) (cube side step_q / 4096)
     std::vector<uint8_t> h_reach;
     std::vector<int32_t> h_rlist;
 };
@@ -124,8 +126,8 @@ bool valid_config(int system, int L, int q, int p, std::string &why)
     return true;
 }
 
-// Polymer bins of width 0.1 over [e_lo, e_hi).
-int polymer_bins(double e_lo, double e_hi) { return (int)((e_hi - e_lo) * 10.0 + 0.5); }
+// Polymer bins of width 1 / k over [e_lo, e_hi).
+int polymer_bins(double e_lo, double e_hi, int k) { return (int)((e_hi - e_lo) * (double)k + 0.5); }
 
 void fill_shape(muca_ctx *c, int system, int L, int q, int p)
 {
@@ -137,7 +139,7 @@ void fill_shape(muca_ctx *c, int system, int L, int q, int p)
         c->p = p;
         c->e_lo = 2.0 * L;  // default window; set "e_lo"/"e_hi" for the run's own
         c->e_hi = 6.0 * L;
-        c->B = polymer_bins(c->e_lo, c->e_hi);
+        c->B = polymer_bins(c->e_lo, c->e_hi, c->bin_k);
         c->C = 0;
         c->pstride = p;
         c->wpw = 0;
@@ -256,6 +258,7 @@ UpdateArgs update_args(const muca_ctx *c)
     a.beta = c->beta;
     a.flat_ratio = c->flat_ratio;
     a.e_lo = c->e_lo;
+    a.bin_w = 1.0 / (double)c->bin_k;
     a.recursion = c->recursion;
     a.metrics = c->metrics;
     if (c->system == kPolymer) a.nblocks = 1;  // the open histogram is one global slot
@@ -333,8 +336,10 @@ PolyArgs poly_args(const muca_ctx *c, int64_t sweeps)
     a.walker_offset = c->walker_offset;
     a.lanes = c->lanes;
     a.flush_every = c->flush_cap;
-    a.elo_q = llrint(c->e_lo * 4294967296.0);                      // e_lo * 2^32
-    a.ehi_q = a.elo_q + ((long long)c->B * 4294967296LL + 9) / 10;  // first energy with bin >= B
+    a.bin_k = c->bin_k;
+    a.step_q = (int)c->step_q;
+    a.elo_q = llrint(c->e_lo * 4294967296.0);                                          // e_lo * 2^32
+    a.ehi_q = a.elo_q + ((long long)c->B * 4294967296LL + c->bin_k - 1) / c->bin_k;  // first energy with bin >= B
     a.model = c->model;
     a.moves = c->moves;
     if (c->model == 1) {  // the paper's parameters of Eq. 7: K = 40, r0 = 0.7, r_max = 1, no LJ cutoff
@@ -520,8 +525,9 @@ int d2h(muca_ctx *c, void *host, const void *dev, size_t bytes)
 // Checkpoint blob: fixed header, then the device sections in this order.
 struct StateHeader {
     char magic[8];
-    int32_t version, system, L, q, p, B, C, wpw, pstride, record, walker_offset, model;
+    int32_t version, system, L, q, p, B, C, wpw, pstride, record, walker_offset, model, bin_k, pad;
     uint64_t seed;
+    int64_t step_q;
     double beta, e_lo, e_hi, fene_K, fene_R;
     DevState dev;
 };
@@ -680,25 +686,41 @@ int muca_set_param(muca_ctx *c, const char *key, double v)
         MUCA_CUDA(launch_thresholds(a, c->stream));
         return MUCA_OK;
     }
-    if (k == "e_lo" || k == "e_hi" || k == "fene_K" || k == "fene_R") {
+    if (k == "e_lo" || k == "e_hi" || k == "fene_K" || k == "fene_R" || k == "bin_width") {
         if (c->system != kPolymer) return fail(MUCA_ERR_ARG, "'%s' applies to the polymer only", key);
         if (locked) return fail(MUCA_ERR_STATE, "%s must be set before the first iterate", key);
         if (!(v == v) || v > 1e6 || v < -1e6) return fail(MUCA_ERR_ARG, "bad value for %s", key);
         double lo = c->e_lo, hi = c->e_hi, K = c->fene_K, R = c->fene_R;
+        int bk = c->bin_k;
         if (k == "e_lo") lo = v;
         if (k == "e_hi") hi = v;
         if (k == "fene_K") K = v;
         if (k == "fene_R") R = v;
+        if (k == "bin_width") {  // 1 / k for a whole k, so that a bin is an exact fixed-point product
+            const double kk = (v > 0.0) ? std::nearbyint(1.0 / v) : 0.0;
+            if (!(kk >= 1.0 && kk <= 1000.0) || std::fabs(1.0 / kk - v) > 1e-12 * v)
+                return fail(MUCA_ERR_ARG, "bin_width must be 1/k for a whole k in 1..1000");
+            bk = (int)kk;
+        }
         if (!(K > 0.0) || !(R > 0.0)) return fail(MUCA_ERR_ARG, "fene_K and fene_R must be > 0");
-        const int B = (hi > lo) ? polymer_bins(lo, hi) : 0;
+        const int B = (hi > lo) ? polymer_bins(lo, hi, bk) : 0;
         if (B < 2 || B > kPolyMaxBins)
-            return fail(MUCA_ERR_RANGE, "window [%g, %g) gives %d bins of 0.1; need 2..%d", lo, hi, B, kPolyMaxBins);
+            return fail(MUCA_ERR_RANGE, "window [%g, %g) gives %d bins of 1/%d; need 2..%d", lo, hi, B, bk, kPolyMaxBins);
         c->e_lo = lo;
         c->e_hi = hi;
         c->fene_K = K;
         c->fene_R = R;
+        c->bin_k = bk;
         c->B = B;
         return reset_weights(c);
+    }
+    if (k == "step") {  // the side of the move cube, on the grid: step_q = round(side * 4096)
+        if (c->system != kPolymer) return fail(MUCA_ERR_ARG, "'step' applies to the polymer only");
+        if (locked) return fail(MUCA_ERR_STATE, "step must be set before the first iterate");
+        const double q = std::nearbyint(v * 4096.0);
+        if (!(q >= 1.0 && q <= 8192.0)) return fail(MUCA_ERR_ARG, "step must be in [1/4096, 2]");
+        c->step_q = (long long)q;
+        return MUCA_OK;
     }
     if (k == "record") {
         if (locked) return fail(MUCA_ERR_STATE, "record must be set before the first iterate");
@@ -1103,8 +1125,8 @@ int muca_get_state(muca_ctx *c, void *host_buf, size_t *bytes)
     if (*bytes < need) return fail(MUCA_ERR_ARG, "state buffer too small: need %zu bytes", need);
     char *p = (char *)host_buf;
     StateHeader h{};
-    memcpy(h.magic, "MUCAST4", 8);
-    h.version = 4;
+    memcpy(h.magic, "MUCAST5", 8);
+    h.version = 5;
     h.system = c->system;
     h.L = c->L;
     h.q = c->q;
@@ -1122,6 +1144,8 @@ int muca_get_state(muca_ctx *c, void *host_buf, size_t *bytes)
     h.e_hi = c->e_hi;
     h.fene_K = c->fene_K;
     h.fene_R = c->fene_R;
+    h.bin_k = c->bin_k;
+    h.step_q = c->step_q;
     if (int rc = d2h(c, &h.dev, c->state, sizeof h.dev)) return rc;
     memcpy(p, &h, sizeof h);
     p += sizeof h;
@@ -1155,12 +1179,13 @@ int muca_set_state(muca_ctx *c, const void *host_buf, size_t bytes)
     if (bytes < sizeof(StateHeader)) return fail(MUCA_ERR_ARG, "not a muca state buffer");
     StateHeader h;
     memcpy(&h, host_buf, sizeof h);
-    if (memcmp(h.magic, "MUCAST4", 8) != 0 || h.version != 4) return fail(MUCA_ERR_ARG, "not a muca state buffer");
+    if (memcmp(h.magic, "MUCAST5", 8) != 0 || h.version != 5) return fail(MUCA_ERR_ARG, "not a muca state buffer");
     if (h.system != c->system || h.L != c->L || h.q != c->q || h.p != c->p || h.C != c->C || h.wpw != c->wpw ||
         h.pstride != c->pstride || h.seed != c->seed)
         return fail(MUCA_ERR_ARG, "state buffer was written by a different configuration");
     if (c->system == kPolymer) {
-        if (h.B < 2 || h.B > kPolyMaxBins || h.B != polymer_bins(h.e_lo, h.e_hi))
+        if (h.bin_k < 1 || h.bin_k > 1000 || h.step_q < 1 || h.step_q > 8192 || h.B < 2 || h.B > kPolyMaxBins ||
+            h.B != polymer_bins(h.e_lo, h.e_hi, h.bin_k))
             return fail(MUCA_ERR_ARG, "state buffer: bad polymer window");
     } else if (h.B != c->B) {
         return fail(MUCA_ERR_ARG, "state buffer was written by a different configuration");
@@ -1202,6 +1227,10 @@ int muca_set_state(muca_ctx *c, const void *host_buf, size_t bytes)
     c->e_hi = h.e_hi;
     c->fene_K = h.fene_K;
     c->fene_R = h.fene_R;
+    if (c->system == kPolymer) {
+        c->bin_k = h.bin_k;
+        c->step_q = h.step_q;
+    }
     c->model = h.model;
     if (c->system == kPolymer) {
         reachable_bins(c);

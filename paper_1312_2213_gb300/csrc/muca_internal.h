@@ -132,6 +132,8 @@ struct PolyArgs {
     uint8_t *tun = nullptr;                 // [p] tunnelling state per walker
     PolyTraceRec *trace = nullptr;          // [p][sweeps][N] attempt records, or null
     int flush_every = 0;  // most sweeps between flushes of the block's counters (0: their own bound)
+    int bin_k = 10;               // bins per unit energy (width 1 / bin_k)
+    int step_q = 1229;            // move grid units per unit of (u - 2^31): cube side step_q / 4096
     int64_t sweep_base = 0;    // this launch's first sweep within the iterate (launch_poly_sweep chunks)
     int64_t trace_sweeps = 0;  // sweeps of the traced iterate
 };
@@ -147,6 +149,7 @@ struct UpdateArgs {
     int system, B, nreach, nblocks, N, q, p, pstride, L;
     double beta, flat_ratio;
     double e_lo;  // polymer: energy of the window's lower edge
+    double bin_w = 0.1;  // polymer: bin width
     int recursion;  // 0: accumulated statistics, 1: plain W/H
     const uint8_t *reach;
     const int32_t *rlist;

@@ -106,7 +106,7 @@ __device__ __forceinline__ float q32_to_float(long long v)
 
 __device__ __forceinline__ int poly_bin(long long E, const PolyArgs &a)
 {
-    const long long b = ((E - a.elo_q) * 10) >> 32;
+    const long long b = ((E - a.elo_q) * a.bin_k) >> 32;
     return b < -1 ? -1 : (b > (long long)a.B ? a.B : (int)b);
 }
 
@@ -305,7 +305,7 @@ __global__ void __launch_bounds__(kMaxSweepBlock) k_sweep_polymer(const PolyArgs
     unsigned long long nacc = 0;
     unsigned ev = 0;
     int tst = (active && a.tun) ? a.tun[w] : 0;
-    constexpr float kStep = (float)kPolyStepQ * 0x1p-44f;
+    const float kStep = (float)a.step_q * 0x1p-44f;
     for (int64_t sw = 0; sw < a.sweeps; ++sw) {
         const uint32_t g = g0 + (uint32_t)sw;
         const long long A0 = Xg[0], A1 = Xg[N], A2 = Xg[2 * N];
@@ -341,8 +341,9 @@ __global__ void __launch_bounds__(kMaxSweepBlock) k_sweep_polymer(const PolyArgs
             const float dx = (float)sx * kStep, dy = (float)sy * kStep, dz = (float)sz * kStep;
             float xn = xo + dx, yn = yo + dy, zn = zo + dz;
             float lxn = lxo + ((xo - xn) + dx), lyn = lyo + ((yo - yn) + dy), lzn = lzo + ((zo - zn) + dz);
-            long long n0 = X0 + (long long)sx * kPolyStepQ, n1 = X1 + (long long)sy * kPolyStepQ,
-                      n2 = X2 + (long long)sz * kPolyStepQ;
+            // (32 x 32-bit products: the grid step fits an int)
+            long long n0 = X0 + (long long)sx * (long long)a.step_q, n1 = X1 + (long long)sy * (long long)a.step_q,
+                      n2 = X2 + (long long)sz * (long long)a.step_q;
             float s = 0.0f, c = 0.0f;
             bool broken = false;
             if (a.moves) {

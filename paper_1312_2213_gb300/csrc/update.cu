@@ -296,7 +296,7 @@ __global__ void __launch_bounds__(1024) k_reweight(const UpdateArgs a, double be
             if (a.system == kMuma) {
                 x = lnOmega;
             } else if (a.system == kPolymer) {
-                x = lnOmega - beta * (a.e_lo + 0.1 * (b + 0.5));
+                x = lnOmega - beta * (a.e_lo + a.bin_w * (b + 0.5));
             } else {
                 const double E = (a.system == kIsing) ? (double)(4 * b - 2 * N) : (double)(b - 2 * N);
                 x = lnOmega - beta * E;
@@ -333,7 +333,7 @@ __global__ void __launch_bounds__(1024) k_reweight(const UpdateArgs a, double be
             const double P = exp(lp);
             double v;
             if (a.system == kMuma) v = fabs((double)(2 * b - N));
-            else if (a.system == kPolymer) v = a.e_lo + 0.1 * (b + 0.5);
+            else if (a.system == kPolymer) v = a.e_lo + a.bin_w * (b + 0.5);
             else v = (a.system == kIsing) ? (double)(4 * b - 2 * N) : (double)(b - 2 * N);
             a1 += P * v;
             a2 += P * v * v;
@@ -358,7 +358,7 @@ __global__ void __launch_bounds__(1024) k_reweight(const UpdateArgs a, double be
         __syncthreads();
         double m2 = NEG_INF;
         for (int b = tid; b < B; b += bs)
-            if (sx[b] > NEG_INF) m2 = fmax(m2, sx[b] + beta * (a.e_lo + 0.1 * (b + 0.5)));
+            if (sx[b] > NEG_INF) m2 = fmax(m2, sx[b] + beta * (a.e_lo + a.bin_w * (b + 0.5)));
         red2[tid] = m2;
         __syncthreads();
         for (int st = bs / 2; st > 0; st >>= 1) {
@@ -369,7 +369,7 @@ __global__ void __launch_bounds__(1024) k_reweight(const UpdateArgs a, double be
         __syncthreads();
         double z2 = 0.0;
         for (int b = tid; b < B; b += bs)
-            if (sx[b] > NEG_INF) z2 += exp(sx[b] + beta * (a.e_lo + 0.1 * (b + 0.5)) - m2);
+            if (sx[b] > NEG_INF) z2 += exp(sx[b] + beta * (a.e_lo + a.bin_w * (b + 0.5)) - m2);
         red2[tid] = z2;
         __syncthreads();
         for (int st = bs / 2; st > 0; st >>= 1) {

@@ -49,27 +49,30 @@ def _gpu():
         pytest.skip("no CUDA device")
 
 
-def _pair(N, p, seed, model, moves, lanes=0, block=None, window=None):
+def _pair(N, p, seed, model, moves, lanes=0, block=None, window=None, grid=(10, 1229)):
     lo, hi = window if window else (WINDOWS[model][str(N)]["e_lo"], WINDOWS[model][str(N)]["e_hi"])
     g = m.Muca(m.POLYMER3D, N, 0, p, seed, window=(lo, hi), block=block)
+    if grid != (10, 1229):  # bins of width 1/k, moves in a cube of side step_q / 4096
+        g.set_param("bin_width", 1.0 / grid[0])
+        g.set_param("step", grid[1] / 4096.0)
     if model:
         g.set_param("model", model)
     if moves:
         g.set_param("moves", moves)
     if lanes:
         g.set_param("lanes", lanes)
-    o = oracle.PolyRun(N, p, seed, lo, hi, model=model, moves=moves)
+    o = oracle.PolyRun(N, p, seed, lo, hi, model=model, moves=moves, bin_k=grid[0], step_q=grid[1])
     o.init()
     return g, o, lo
 
 
-def compare_call(tg, to, g, o, lo, alive, stats, what):
+def compare_call(tg, to, g, o, lo, alive, stats, what, k=10):
     """Compare one call's traces walker by walker (see the module docstring); updates `alive`."""
     compare_arrays(tg, to, g.coords(), o.coords(), g.bins(), o.bins(), o.energy(), o.delta(), lo, alive, stats,
-                   what)
+                   what, k)
 
 
-def compare_arrays(tg, to, Xg, Xo, bins_g, bins_o, E_end, d_end, lo, alive, stats, what):
+def compare_arrays(tg, to, Xg, Xo, bins_g, bins_o, E_end, d_end, lo, alive, stats, what, k=10):
     """compare_call on arrays: traces (walkers, sweeps, N), end coordinates and bins of both sides,
     the oracle's refreshed energies and bounds, all for the same walkers in the same order."""
     p = tg.shape[0]
@@ -100,8 +103,8 @@ def compare_arrays(tg, to, Xg, Xo, bins_g, bins_o, E_end, d_end, lo, alive, stat
         else:
             np.testing.assert_array_equal(Xg[w], Xo[w], err_msg="%s: walker %d coordinates" % (what, w))
             if bins_g[w] != bins_o[w]:   # only the closing refresh may move the bin, within its bound
-                t = (E_end[w] - lo) * 10.0
-                assert abs(t - round(t)) < 10.0 * d_end[w], "%s: walker %d bin after the refresh" % (what, w)
+                t = (E_end[w] - lo) * k
+                assert abs(t - round(t)) < k * d_end[w], "%s: walker %d bin after the refresh" % (what, w)
                 stats["diverged"] += 1
                 alive[w] = False
     stats["attempts"] += int(alive.size * dis.shape[1])
@@ -152,6 +155,42 @@ def test_trajectories_agree_until_the_first_event(N, lanes, p, block, model, mov
     # most of the run is compared, not excused
     assert stats["compared"] > 0.5 * stats["attempts"]
     assert r.max() <= TAU
+
+
+@pytest.mark.parametrize("N,grid,calls", [(13, (5, 614), [150, 30, 30]), (32, (20, 2048), [150, 20, 20])])
+def test_trajectories_with_other_bins_and_steps(N, grid, calls):
+    """Bins of width 0.2 and moves in a cube of side 0.15 (N = 13); bins of 0.05 and a cube of
+    side 0.5 (N = 32): the same trajectory rule as above."""
+    p = 48
+    g, o, lo = _pair(N, p, 17, 0, 0, grid=grid)
+    assert g.B == o.B == round((WINDOWS[0][str(N)]["e_hi"] - lo) * grid[0])
+    alive = np.ones(p, dtype=bool)
+    stats = {"ratio": [], "energy": [], "compared": 0, "attempts": 0, "diverged": 0}
+    for k, S in enumerate(calls):
+        tg = g.iterate_traced(S)
+        to = o.iterate_traced(S, NT)
+        compare_call(tg, to, g, o, lo, alive, stats, "call %d" % k, grid[0])
+        g.merge_and_update()
+        o.update()
+        g.set_lnW(o.lnW())
+    r = np.concatenate(stats["ratio"])
+    assert stats["compared"] > 0.5 * stats["attempts"]
+    assert r.max() <= TAU
+
+
+def test_bin_width_and_step_arguments():
+    g = m.Muca(m.POLYMER3D, 13, 0, 8, 1, window=(33.3, 87.3))
+    for key, bad in (("bin_width", 0.3), ("bin_width", 0.0), ("step", 0.0), ("step", 3.0)):
+        with pytest.raises(m.MucaError):
+            g.set_param(key, bad)
+    g.set_param("bin_width", 0.25)
+    assert g.B == 216
+    s = m.Muca(m.ISING2D, 8, 2, 32, 1)
+    with pytest.raises(m.MucaError):
+        s.set_param("bin_width", 0.5)
+    g.iterate(2)
+    with pytest.raises(m.MucaError):
+        g.set_param("step", 0.2)   # too late
 
 
 def test_set_lnW_round_trip_and_errors():
