@@ -291,7 +291,8 @@ class Muca:
             muca_set_param(self.h, "block", block)
         if walker_offset:
             muca_set_param(self.h, "walker_offset", walker_offset)
-        self.window = window
+        # the polymer's energy window (the library's default is [2N, 6N))
+        self.window = window if window is not None or system != POLYMER3D else (2.0 * L, 6.0 * L)
         if window is not None:
             muca_set_param(self.h, "e_lo", window[0])
             muca_set_param(self.h, "e_hi", window[1])
@@ -318,9 +319,9 @@ class Muca:
         muca_set_param(self.h, key, value)
         if key in ("e_lo", "e_hi", "bin_width"):  # the polymer's bin count follows the window
             self.B = muca_num_bins(self.h)
-            if key != "bin_width":
-                lo, hi = self.window if self.window is not None else (None, None)
-                self.window = (value, hi) if key == "e_lo" else (lo, value)
+            if key != "bin_width" and self.window is not None:
+                lo, hi = self.window
+                self.window = (float(value), hi) if key == "e_lo" else (lo, float(value))
 
     def set_stream(self, stream):
         muca_set_stream(self.h, int(getattr(stream, "cuda_stream", stream)))
