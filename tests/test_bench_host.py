@@ -56,3 +56,14 @@ def test_clock_record_flags_thermal_slowdown():
 def test_no_samples_gives_no_record():
     assert _sampler_with(["not csv"]).stop() is None
     assert _bench().ClockSampler(0).stop() is None   # nvidia-smi never started
+
+
+def test_mix_iteration_lengths_follow_eq4():
+    """The mix's third regime runs every system at its own M_opt from the fits of Eq. 4 at
+    p = 2048: 5.7 L^2.51 / p for Ising, 24 L^2.67 / p (the 8-Potts fit) for q = 10 Potts."""
+    bench = _bench()
+    got = dict(zip(bench.MIX, bench.mix_mopt()))
+    for (system, L, q), m_opt in got.items():
+        exact = (5.7 * L ** 2.51 if system == 0 else 24.0 * L ** 2.67) / 2048
+        assert m_opt == max(1, round(exact)) and abs(m_opt - exact) <= 0.5
+    assert got[(0, 64, 2)] == 95 and got[(1, 48, 10)] == 361
